@@ -1,0 +1,335 @@
+#!/usr/bin/env python
+"""Benchmark of the docking hot path on GB300.
+
+One step = one complete docking of the paper-scale workload through adg_dock:
+64^3 FP32 maps (9) of a 3,000-atom pseudo-receptor, one ligand of 40 heavy
+atoms + 4 polar H with 8 torsions, 100 LGA runs x population 150 x 2.5M
+evaluations per run, ADADELTA local search (300 iterations) on analytic
+gradients.  Metric: energy(+gradient) evaluations per second (and docked
+ligands per second) on 1 GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank docks its own
+ligand (replicas; no data-path collective), value = all ranks' evaluations /
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "energy+gradient evals/s and docked ligands/s on 1 GB300 vs plain form, at tol"
+UNIT = "evals/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ_FALLBACK = 2070.0
+
+
+# ---------------------------------------------------------------- algorithmic work per evaluation
+def flops_per_eval(natoms: int, npairs: int, sum_moving: int, grad: bool) -> float:
+    """Per-unit algorithmic FP32 work of one evaluation (FMA = 2 flops; MUFU
+    ops not counted): pose 18 (N + sum|S_k|), intermolecular 130 N,
+    intramolecular 55 P, gradient reductions 9 (N + sum|S_k|) (energy+gradient only)."""
+    f = 18.0 * (natoms + sum_moving) + 130.0 * natoms + 55.0 * npairs
+    if grad:
+        f += 9.0 * (natoms + sum_moving)
+    return f
+
+
+def fp32_peak_tflops() -> tuple[float, str]:
+    mhz = SM_MAX_MHZ_FALLBACK
+    src = "recipe max SM clock"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+            src = "MEASURED_PEAKS.json sm_max_mhz"
+    except Exception:
+        pass
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12, src
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        try:
+            rows = [l.split(",") for l in open(self.path) if l.strip()]
+        except Exception:
+            return out
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if sm:
+            sm.sort()
+            out.update(sm_mhz=sm[len(sm) // 2], sm_max_mhz=max(mx), reasons=sorted(reasons), samples=len(sm))
+        return out
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
+def _oracle_worker(args):
+    maps_path, nev, run = args
+    import numpy as np
+    import oracle as O
+    from paper_2007_03678_gb300 import synth as S
+    grid, rec, lig = S.workload_inputs(S.PAPER)
+    maps = np.load(maps_path)
+    p = O.SearchParams(nrun=1, pop_size=S.PAPER["pop"], nev=nev, ls_method=2)
+    t0 = time.perf_counter()
+    best, _, evals, gens, _ = O.lga_run(S.forcefield(), grid, maps, O.Ligand(lig), p, run=run)
+    return evals, time.perf_counter() - t0
+
+
+def oracle_sample(nev: int, cores: int, maps_path: str, run0: int = 0) -> dict:
+    """Run `cores` single-threaded oracle LGA runs of the paper-scale ligand in
+    parallel (spawned processes), each until `nev` evaluations; return the
+    aggregate evaluation rate."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(cores) as pool:
+        t0 = time.perf_counter()
+        out = pool.map(_oracle_worker, [(maps_path, nev, run0 + i) for i in range(cores)])
+        wall = time.perf_counter() - t0
+    evals = sum(e for e, _ in out)
+    return dict(evals=evals, wall=wall, rate=evals / wall)
+
+
+def oracle_maps_file() -> str:
+    import numpy as np
+    import oracle as O
+    from paper_2007_03678_gb300 import synth as S
+    grid, rec, lig = S.workload_inputs(S.PAPER)
+    maps = O.maps_build(S.forcefield(), grid, rec).astype(np.float32).astype(np.float64)
+    fd, path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    np.save(path, maps)
+    return path
+
+
+ORACLE_SAMPLE_NEV = 150 + 45150  # initial population + one ADADELTA generation
+
+
+def cpu_cores() -> int:
+    return max(1, min(os.cpu_count() or 1, 16))
+
+
+def run_reference(args, rank: int) -> None:
+    if rank != 0:
+        return
+    cores = cpu_cores()
+    maps_path = oracle_maps_file()
+    try:
+        for w in range(args.warmup):
+            oracle_sample(150 + 1500, cores, maps_path)
+        rates, walls, evals = [], [], 0
+        for s in range(args.steps):
+            r = oracle_sample(ORACLE_SAMPLE_NEV, cores, maps_path, run0=s * cores)
+            walls.append(r["wall"])
+            evals += r["evals"]
+        value = evals / sum(walls)
+    finally:
+        os.unlink(maps_path)
+    sample = (f"{cores} parallel single-thread oracle LGA runs of the paper-scale ligand per step, "
+              f"each stopped after {ORACLE_SAMPLE_NEV} evaluations (initial population + 1 ADADELTA generation)")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(walls) / len(walls), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- our arm
+def workload_config() -> dict:
+    from paper_2007_03678_gb300 import synth as S
+    w = S.PAPER
+    return {"workload": "paper-scale docking: 64^3 x 9 FP32 maps (0.375 A) of a 3000-atom pseudo-receptor, "
+                        "one ligand of 40 heavy atoms + 4 polar H with 8 torsions, 100 LGA runs x pop 150 x "
+                        "2.5M evals, ADADELTA local search",
+            "grid": w["grid_n"], "receptor_atoms": w["rec_atoms"], "ligand_atoms": w["n_heavy"] + w["n_hd"],
+            "torsions": w["n_tors"], "nrun": w["nrun"], "pop": w["pop"], "nev": w["nev"], "local_search": "adadelta",
+            "l2": "flushed between steps (256 MB write); maps (29 MB packed) are meant to stay L2-resident within a step",
+            "parallelism": "replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+    from paper_2007_03678_gb300 import adg, build, synth as S
+
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    ff = S.forcefield()
+    w = S.PAPER
+    grid, rec, lig_desc = S.workload_inputs(w, lig_index=rank)
+    stream = torch.cuda.Stream()
+    ctx = adg.Context(local, stream=stream)
+    maps = adg.maps_build(ctx, ff, grid, rec)
+    R = adg.Receptor(ctx, grid, maps)
+    ctx.sync()
+    del maps
+    L = adg.Ligand(ctx, ff, lig_desc)
+    p = adg.search_params(nrun=w["nrun"], pop_size=w["pop"], nev=w["nev"], ls_method=adg.LS_ADADELTA,
+                          seed=S.SEARCH_SEED, lig_id=rank)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+
+    for _ in range(args.warmup):
+        adg.dock(ctx, R, L, p)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ctx.stats(reset=True)
+    ctx.set_timing(True)
+    step_ms, evals, results = [], 0, None
+    barrier()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            results = adg.dock(ctx, R, L, p)[0]
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            evals += int(results["evals"].sum())
+    barrier()
+    ctx.set_timing(False)
+    st = ctx.stats(reset=True)
+    total_ms = sum(step_ms)
+    if dist is not None:
+        t = torch.tensor([total_ms], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        ev = torch.tensor([evals], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(ev)
+        evals = int(ev.item())
+    value = evals / (total_ms / 1e3)
+    ligands_per_s = world * args.steps / (total_ms / 1e3)
+
+    # roofline of the dominant kernel (the GA-generation kernel: selection + ADADELTA)
+    gens = int(results["generations"][0])
+    iters = p.ls_max_iters
+    f_eg = flops_per_eval(L.natoms, L.npairs, L.sum_moving, True)
+    f_e = flops_per_eval(L.natoms, L.npairs, L.sum_moving, False)
+    gen_flops_per_step = p.nrun * gens * ((p.pop_size - 1) * f_e + p.pop_size * iters * f_eg)
+    gen_ms_per_launch = st["gen_kernel_ms"] / max(1, st["gen_timed"])
+    flops_per_launch = gen_flops_per_step / gens
+    achieved = flops_per_launch / (gen_ms_per_launch / 1e3) / 1e12
+    peak, peak_src = fp32_peak_tflops()
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "k_dock_generation<2,ADADELTA>",
+                "launch_ms": gen_ms_per_launch, "flops_per_launch": flops_per_launch,
+                "gen_share_of_step": st["gen_kernel_ms"] / total_ms if world == 1 else None,
+                "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peak_src}"}
+
+    # end to end through the public API with host buffers: ligand upload + dock + results read back
+    ctx.stats(reset=True)
+    e2e_t, e2e_evals = 0.0, 0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Lh = adg.Ligand(ctx, ff, lig_desc)
+        r = adg.dock(ctx, R, Lh, p)[0]
+        Lh.close()
+        e2e_t += time.perf_counter() - t0
+        e2e_evals += int(r["evals"].sum())
+    st2 = ctx.stats(reset=True)
+    e2e = {"value": e2e_evals / e2e_t * (world if dist is not None else 1), "unit": UNIT,
+           "h2d_bytes_per_step": st2["h2d_bytes"] // args.steps, "d2h_bytes_per_step": st2["d2h_bytes"] // args.steps,
+           "ligands_per_s": args.steps / e2e_t * world}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cores = cpu_cores()
+        path = oracle_maps_file()
+        try:
+            r = oracle_sample(ORACLE_SAMPLE_NEV, cores, path)
+        finally:
+            os.unlink(path)
+        cpu = {"value": r["rate"], "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": f"{cores} parallel single-thread oracle LGA runs of the paper-scale ligand, each stopped "
+                         f"after {ORACLE_SAMPLE_NEV} evaluations ({r['evals']} evals in {r['wall']:.1f} s)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(), "ligands_per_s": ligands_per_s,
+                "best_energy_median": float(np.median(results["best_energy"])),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "gpu_launches": st["kernel_launches"]}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

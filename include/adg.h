@@ -1,0 +1,268 @@
+/*
+ * adg.h -- C ABI of libadg.so, a GB300 (sm_103a) implementation of the hot
+ * path of AutoDock-GPU-style protein-ligand docking (arXiv 2007.03678).
+ *
+ * The paper's statement of the problem (Sec. 1, 1.1, 2.2): one receptor given
+ * as interaction grid maps (atom-type affinity, electrostatic and
+ * desolvation maps, Sec. 2.2.1 and 2.3), many ligands given as atom
+ * coordinates, types, charges and rotatable bonds, and the run parameters
+ * nrun / nev (Sec. 1.1); out come the best pose and energy of each of the
+ * nrun independent Lamarckian-GA runs (Sec. 1, 1.1).  The receptor maps are
+ * uploaded once and stay resident, and the context keeps its device memory
+ * for reuse between ligands (Sec. 2.2.3).
+ *
+ * Conventions for every call:
+ *  - Return value: ADG_OK (0) or a negative ADG_E* code; adg_strerror() gives
+ *    its text.  On error nothing is written to the caller's outputs except
+ *    where stated, and no exception crosses the ABI.
+ *  - Ownership: the caller owns every pointer it passes; the library copies
+ *    what it needs.  Handles are freed only by their *_destroy call.
+ *  - "device" pointers are CUDA global-memory addresses on the context's
+ *    device (for example a torch tensor's data_ptr()); "host" pointers are
+ *    ordinary CPU memory.  Device work is ordered on the context's stream.
+ *  - Threading: one context per host thread.
+ *  - Units: Angstrom, radian, kcal/mol.  Floating point is IEEE binary32.
+ */
+#ifndef ADG_H
+#define ADG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADG_NTYPES 7          /* ligand atom types C, A, N, NA, OA, HD, S (map index 0..6) */
+#define ADG_NMAPS 9           /* 7 type maps, 7 = electrostatic, 8 = desolvation           */
+#define ADG_MAP_ELEC 7
+#define ADG_MAP_DESOLV 8
+#define ADG_MAX_ATOMS 128
+#define ADG_MAX_TORS 16
+#define ADG_MAX_GENES (7 + ADG_MAX_TORS)
+
+enum {
+    ADG_OK = 0,
+    ADG_EINVAL = -1,   /* null pointer, negative or inconsistent size            */
+    ADG_ETYPE = -2,    /* atom type outside 0..ADG_NTYPES-1                      */
+    ADG_ETOOBIG = -3,  /* more than ADG_MAX_ATOMS atoms or ADG_MAX_TORS torsions */
+    ADG_EGRID = -4,    /* fewer than 2 points on an axis or spacing <= 0         */
+    ADG_ECUDA = -5,    /* a CUDA runtime call failed                             */
+    ADG_ETIMEOUT = -6, /* a bounded device-side wait expired                     */
+    ADG_ENOMEM = -7,   /* device or host allocation failed                       */
+    ADG_ETOPO = -8     /* bonds do not form one tree, or a torsion is not a bond */
+};
+
+typedef struct adg_ctx adg_ctx;
+typedef struct adg_receptor adg_receptor;
+typedef struct adg_ligand adg_ligand;
+
+/* Force-field table (AutoDock4 free-energy model, paper Sec. 1: vdW,
+ * H-bond, electrostatics with a distance-dependent dielectric, desolvation,
+ * torsional entropy).  Per-type arrays are indexed by map index 0..6.
+ *   pair vdW/H-bond: generalised n-m potential with minimum -eps at r0;
+ *     12-6 with r0 = (Rii_i+Rii_j)/2, eps = sqrt(epsii_i epsii_j), weight w_vdw;
+ *     12-10 between a donor and an acceptor with the acceptor's hb_R/hb_eps,
+ *     weight w_hb; value capped at e_cap.
+ *   elec: w_elec * coulomb * q_i q_j / (eps(r) r), Mehler-Solmajer
+ *     eps(r) = ms_A + B / (1 + ms_k exp(-ms_lambda B r)), B = ms_eps0 - ms_A.
+ *   desolvation: w_desolv [(solpar_i + qasp|q_i|) vol_j + (solpar_j + qasp|q_j|) vol_i]
+ *     * exp(-r^2 / (2 sigma^2)).
+ *   r is floored at r_min.  Maps use a smooth cutoff switching from 1 at
+ *   map_r_on to 0 at map_r_off.  Outside the grid box an atom pays k_out d^2. */
+typedef struct {
+    float Rii[ADG_NTYPES], epsii[ADG_NTYPES], vol[ADG_NTYPES], solpar[ADG_NTYPES];
+    int32_t hb_donor[ADG_NTYPES], hb_acceptor[ADG_NTYPES];
+    float hb_R[ADG_NTYPES], hb_eps[ADG_NTYPES];
+    float w_vdw, w_hb, w_elec, w_desolv, w_tors;
+    float qasp, sigma, coulomb;
+    float ms_A, ms_eps0, ms_lambda, ms_k;
+    float r_min, e_cap, map_r_on, map_r_off, k_out;
+} adg_forcefield;
+
+/* Grid: n[0..2] points along x, y, z; node (i,j,k) at origin + (i,j,k)*spacing.
+ * Map storage is [map][z][y][x] (x fastest), ADG_NMAPS maps. */
+typedef struct {
+    int32_t n[3];
+    float origin[3];
+    float spacing;
+} adg_grid_desc;
+
+/* Ligand description (host memory).  xyz[3*natoms] is the reference
+ * conformation; type[natoms] map indices; charge[natoms]; bonds[2*nbonds]
+ * must form one tree (the library builds the torsion tree from it);
+ * tors[2*ntors] lists rotatable bonds (either orientation: the side not
+ * holding `root` is the one that moves). */
+typedef struct {
+    int32_t natoms;
+    const float* xyz;
+    const int32_t* type;
+    const float* charge;
+    int32_t nbonds;
+    const int32_t* bonds;
+    int32_t ntors;
+    const int32_t* tors;
+    int32_t root;
+} adg_ligand_desc;
+
+enum { ADG_LS_NONE = 0, ADG_LS_SOLIS_WETS = 1, ADG_LS_ADADELTA = 2 };
+
+/* Search parameters.  nrun and nev follow the paper (Sec. 1.1): nrun
+ * independent LGA runs per ligand, each stopping once it has spent nev
+ * energy evaluations (checked between generations, so the last generation
+ * may overshoot).  One energy call or one energy+gradient call is one
+ * evaluation.  The remaining defaults are readings of "other parameters
+ * default" (Sec. 2.3); adg_search_params_default() fills them in. */
+typedef struct {
+    int32_t nrun, pop_size, nev, max_gen, ls_method, ls_max_iters, elitism;
+    float ls_rate, crossover_rate, mutation_rate, tournament_rate;
+    float sw_rho0, sw_rho_min, sw_expand, sw_contract;
+    int32_t sw_succ, sw_fail;
+    float sw_scale_t, sw_scale_rot, sw_scale_tors;
+    float ad_rho, ad_eps;
+    float mut_t, mut_rot, mut_tors;
+    uint64_t seed;      /* Philox key                                          */
+    uint32_t lig_id;    /* Philox counter word 0 of the first ligand in a call */
+    int32_t pad0;
+} adg_search_params;
+
+/* Result of one run (host memory).  genes: [t(3), q(4) (w,x,y,z), theta(T)];
+ * xyz: posed coordinates of the best genotype, 3*natoms floats. */
+typedef struct {
+    float best_energy;
+    int32_t generations;
+    int64_t evals;
+    float genes[ADG_MAX_GENES];
+    float xyz[3 * ADG_MAX_ATOMS];
+} adg_result;
+
+/* Optional record of the first `ngen` generations of a one-ligand dock, for
+ * replaying the GA decisions.  All arrays are host memory, caller-allocated:
+ *   decisions [nrun][ngen][pop][8] int32: parent1, parent2, crossover lo,
+ *             crossover hi (-1 when no crossover), mutation block mask,
+ *             local search applied, 0, 0
+ *   genes     [nrun][ngen][pop][7+T] population after each generation
+ *   energies  [nrun][ngen][pop]
+ *   init_genes[nrun][pop][7+T] and init_energies[nrun][pop]: generation 0.
+ * Any pointer may be NULL to skip that array. */
+typedef struct {
+    int32_t ngen;
+    int32_t* decisions;
+    float* genes;
+    float* energies;
+    float* init_genes;
+    float* init_energies;
+} adg_dock_trace;
+
+/* Error code -> static text.  Never fails. */
+const char* adg_strerror(int code);
+
+/* Defaults: pop 150, nev 2,500,000, max_gen 27,000, Solis-Wets, 300
+ * iterations, elitism 1, ls_rate 1, crossover 0.8, mutation 0.02,
+ * tournament 0.6, rho0 1, rho_min 0.01, x2 after 4 successes, x0.5 after 4
+ * failures, step scales 1 A / 0.5 rad / 0.5 rad, ADADELTA rho 0.8 eps 0.01,
+ * mutation half-widths 2 A / pi/2 / pi/2, seed 42, nrun 10. */
+void adg_search_params_default(adg_search_params* p);
+
+/* Context: selects `device`, creates or adopts a CUDA stream (`stream` may be
+ * NULL for a library-owned stream, else a cudaStream_t the caller keeps
+ * alive), and owns a reusable device arena (context and memory reuse,
+ * paper Sec. 2.2.3).  *out receives the handle. */
+int adg_ctx_create(adg_ctx** out, int device, void* stream);
+int adg_ctx_destroy(adg_ctx* ctx);
+/* Block until the context's stream has drained; reports a deferred CUDA error. */
+int adg_sync(adg_ctx* ctx);
+/* Detail text of the last ADG_ECUDA on this context ("" if none). */
+const char* adg_ctx_last_error(const adg_ctx* ctx);
+
+/* Receptor grid maps from receptor atoms (the role AutoGrid4 plays in the
+ * paper, Sec. 2.3): for every node p
+ *   M_t(p) = min(e_cap, sum_j S(r)[vdW/HB(t, type_j)(r) + w_desolv (solpar_t vol_j
+ *            + (solpar_j + qasp|q_j|) vol_t) G(r)]),        t = 0..6
+ *   M_e(p) = sum_j S(r) w_elec coulomb q_j / (eps(r) r)
+ *   M_d(p) = sum_j S(r) w_desolv qasp vol_j G(r)
+ * with S the smooth cutoff and G(r) = exp(-r^2/(2 sigma^2)).
+ * rec_xyz[3*nrec], rec_type[nrec], rec_q[nrec]: host.  maps_out: device,
+ * ADG_NMAPS*nz*ny*nx floats, [map][z][y][x].  Asynchronous on the stream. */
+int adg_maps_build(adg_ctx* ctx, const adg_forcefield* ff, const adg_grid_desc* grid, int nrec,
+                   const float* rec_xyz, const int32_t* rec_type, const float* rec_q, float* maps_out);
+
+/* Resident receptor (paper Sec. 2.2.3: grids sent once and left on device).
+ * maps: ADG_NMAPS*nz*ny*nx floats [map][z][y][x], host memory when
+ * maps_on_device == 0, else device memory.  The library keeps its own
+ * packed copy; the caller may free `maps` once this returns. */
+int adg_receptor_create(adg_ctx* ctx, const adg_grid_desc* grid, const float* maps, int maps_on_device,
+                        adg_receptor** out);
+int adg_receptor_destroy(adg_receptor* rec);
+
+/* Ligand: copies the description, builds the torsion tree (rigid fragments,
+ * moving set of each rotatable bond, deepest-first application order) and
+ * the intramolecular pair list (pairs in different rigid fragments and more
+ * than 3 bonds apart), with per-pair coefficients from `ff`, and uploads it. */
+int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_desc* desc, adg_ligand** out);
+int adg_ligand_destroy(adg_ligand* lig);
+/* Sizes of a built ligand: atoms, torsions, intramolecular pairs, the sum
+ * over torsions of the moving-set sizes, and the bytes uploaded for it. */
+typedef struct {
+    int32_t natoms, ntors, npairs, sum_moving;
+    int64_t device_bytes;
+} adg_ligand_stats;
+int adg_ligand_info(const adg_ligand* lig, adg_ligand_stats* out);
+
+enum { ADG_GRAD_NONE = 0, ADG_GRAD_GENES = 1, ADG_GRAD_TANGENT = 2 };
+
+/* Energy (and gradient) of npose genotypes of one ligand (Sec. 1: the
+ * AD4 energy evaluated on LGA genotypes).  Genotype = [t(3), q(4) (w,x,y,z)
+ * used as q/|q|, theta(T) as deltas from the input conformation].  The pose
+ * applies the torsions deepest first about their reference axes, then
+ * x' = R(q/|q|)(x - centroid) + t.  Energy = intermolecular (trilinear map
+ * interpolation + out-of-box restraint) + intramolecular pair terms.
+ *   genes:  device [npose][7+T]
+ *   energy: device [npose]
+ *   grad:   device; NULL when grad_kind == ADG_GRAD_NONE;
+ *           ADG_GRAD_GENES   -> [npose][7+T]: dE/dt, dE/dq, dE/dtheta
+ *           ADG_GRAD_TANGENT -> [npose][6+T]: dE/dt, torque, dE/dtheta
+ * Asynchronous on the context's stream. */
+int adg_score(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* lig, const float* genes, int npose,
+              float* energy, float* grad, int grad_kind);
+
+/* Posed coordinates of npose genotypes: xyz device [npose][natoms][3]. */
+int adg_pose(adg_ctx* ctx, const adg_ligand* lig, const float* genes, int npose, float* xyz);
+
+/* Dock nlig ligands against one receptor: p->nrun independent Lamarckian GA
+ * runs each (Sec. 1, 1.1), every run a population of p->pop_size genotypes
+ * refined by Solis-Wets or ADADELTA local search, until p->nev evaluations
+ * or p->max_gen generations.  out: host, caller-allocated [nlig][p->nrun].
+ * trace: NULL, or (nlig == 1 only) the record described at adg_dock_trace.
+ * Returns when the results are in `out`. */
+int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig,
+             const adg_search_params* p, adg_result* out, adg_dock_trace* trace);
+
+/* Launch accounting of a context, for measurement.  Counts every kernel the
+ * library launched on the context since the last reset; when timing is on
+ * (adg_ctx_set_timing), each GA-generation launch of adg_dock is bracketed
+ * by CUDA events on the context's stream and gen_kernel_ms is their sum. */
+typedef struct {
+    int64_t kernel_launches;  /* all kernels launched by the library       */
+    int64_t gen_launches;     /* generation kernels (selection + LS) only  */
+    double gen_kernel_ms;     /* summed event time of generation launches  */
+    int64_t gen_timed;        /* generation launches included in that sum  */
+    int64_t h2d_bytes;        /* host -> device bytes copied by the library */
+    int64_t d2h_bytes;        /* device -> host bytes copied by the library */
+} adg_stats;
+
+int adg_ctx_set_timing(adg_ctx* ctx, int enable);
+/* Copy the counters to *out; zero them when reset != 0.  Waits for the
+ * stream when timing is on (to read the events). */
+int adg_ctx_stats(adg_ctx* ctx, adg_stats* out, int reset);
+
+/* Philox4x32-10 (Salmon et al., SC'11) on the device: out[4i..4i+3] =
+ * Philox(counter ctr[4i..4i+3], key = (key & 0xffffffff, key >> 32)).
+ * ctr and out: device, 4*n uint32, each 16-byte aligned (ADG_EINVAL otherwise). */
+int adg_philox(adg_ctx* ctx, const uint32_t* ctr, int n, uint64_t key, uint32_t* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADG_H */

@@ -1,0 +1,386 @@
+"""Thin Python binding of libadg.so (include/adg.h), same names as the C ABI.
+
+Only argument marshalling lives here: every step of the docking hot path
+runs in the CUDA library.  PyTorch provides device memory and streams.
+There is no CPU fallback: if libadg.so is missing or no GPU is present the
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import synth
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libadg.so")
+
+NTYPES = 7
+NMAPS = 9
+MAX_ATOMS = 128
+MAX_TORS = 16
+MAX_GENES = 7 + MAX_TORS
+
+ADG_OK = 0
+GRAD_NONE, GRAD_GENES, GRAD_TANGENT = 0, 1, 2
+LS_NONE, LS_SOLIS_WETS, LS_ADADELTA = 0, 1, 2
+
+
+class AdgError(RuntimeError):
+    def __init__(self, code: int, what: str, detail: str = ""):
+        self.code = code
+        msg = f"{what}: {strerror(code)} ({code})"
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+# ---------------------------------------------------------------- structs
+class adg_forcefield(C.Structure):
+    _fields_ = [("Rii", C.c_float * NTYPES), ("epsii", C.c_float * NTYPES), ("vol", C.c_float * NTYPES),
+                ("solpar", C.c_float * NTYPES), ("hb_donor", C.c_int32 * NTYPES),
+                ("hb_acceptor", C.c_int32 * NTYPES), ("hb_R", C.c_float * NTYPES), ("hb_eps", C.c_float * NTYPES)] + \
+               [(n, C.c_float) for n in ("w_vdw", "w_hb", "w_elec", "w_desolv", "w_tors", "qasp", "sigma", "coulomb",
+                                         "ms_A", "ms_eps0", "ms_lambda", "ms_k", "r_min", "e_cap", "map_r_on",
+                                         "map_r_off", "k_out")]
+
+
+class adg_grid_desc(C.Structure):
+    _fields_ = [("n", C.c_int32 * 3), ("origin", C.c_float * 3), ("spacing", C.c_float)]
+
+
+class adg_ligand_desc(C.Structure):
+    _fields_ = [("natoms", C.c_int32), ("xyz", C.POINTER(C.c_float)), ("type", C.POINTER(C.c_int32)),
+                ("charge", C.POINTER(C.c_float)), ("nbonds", C.c_int32), ("bonds", C.POINTER(C.c_int32)),
+                ("ntors", C.c_int32), ("tors", C.POINTER(C.c_int32)), ("root", C.c_int32)]
+
+
+class adg_search_params(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("nrun", "pop_size", "nev", "max_gen", "ls_method", "ls_max_iters",
+                                         "elitism")] + \
+               [(n, C.c_float) for n in ("ls_rate", "crossover_rate", "mutation_rate", "tournament_rate", "sw_rho0",
+                                         "sw_rho_min", "sw_expand", "sw_contract")] + \
+               [("sw_succ", C.c_int32), ("sw_fail", C.c_int32)] + \
+               [(n, C.c_float) for n in ("sw_scale_t", "sw_scale_rot", "sw_scale_tors", "ad_rho", "ad_eps", "mut_t",
+                                         "mut_rot", "mut_tors")] + \
+               [("seed", C.c_uint64), ("lig_id", C.c_uint32), ("pad0", C.c_int32)]
+
+
+class adg_result(C.Structure):
+    _fields_ = [("best_energy", C.c_float), ("generations", C.c_int32), ("evals", C.c_int64),
+                ("genes", C.c_float * MAX_GENES), ("xyz", C.c_float * (3 * MAX_ATOMS))]
+
+
+class adg_dock_trace(C.Structure):
+    _fields_ = [("ngen", C.c_int32), ("decisions", C.POINTER(C.c_int32)), ("genes", C.POINTER(C.c_float)),
+                ("energies", C.POINTER(C.c_float)), ("init_genes", C.POINTER(C.c_float)),
+                ("init_energies", C.POINTER(C.c_float))]
+
+
+class adg_stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_int64), ("gen_launches", C.c_int64), ("gen_kernel_ms", C.c_double),
+                ("gen_timed", C.c_int64), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+
+
+class adg_ligand_stats(C.Structure):
+    _fields_ = [("natoms", C.c_int32), ("ntors", C.c_int32), ("npairs", C.c_int32), ("sum_moving", C.c_int32),
+                ("device_bytes", C.c_int64)]
+
+
+# The full exported symbol list of include/adg.h.
+EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_ctx_destroy", "adg_sync",
+           "adg_ctx_last_error", "adg_maps_build", "adg_receptor_create", "adg_receptor_destroy", "adg_ligand_create",
+           "adg_ligand_destroy", "adg_ligand_info", "adg_score", "adg_pose", "adg_dock", "adg_philox",
+           "adg_ctx_set_timing", "adg_ctx_stats")
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libadg.so.  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with `python -m paper_2007_03678_gb300.build`")
+        L = C.CDLL(path)
+        _vp, _i, _f = C.c_void_p, C.c_int, C.c_float
+        L.adg_strerror.restype = C.c_char_p
+        L.adg_strerror.argtypes = [_i]
+        L.adg_search_params_default.argtypes = [C.POINTER(adg_search_params)]
+        L.adg_search_params_default.restype = None
+        L.adg_ctx_create.argtypes = [C.POINTER(_vp), _i, _vp]
+        L.adg_ctx_destroy.argtypes = [_vp]
+        L.adg_sync.argtypes = [_vp]
+        L.adg_ctx_last_error.argtypes = [_vp]
+        L.adg_ctx_last_error.restype = C.c_char_p
+        L.adg_maps_build.argtypes = [_vp, C.POINTER(adg_forcefield), C.POINTER(adg_grid_desc), _i, _vp, _vp, _vp,
+                                     _vp]
+        L.adg_receptor_create.argtypes = [_vp, C.POINTER(adg_grid_desc), _vp, _i, C.POINTER(_vp)]
+        L.adg_receptor_destroy.argtypes = [_vp]
+        L.adg_ligand_create.argtypes = [_vp, C.POINTER(adg_forcefield), C.POINTER(adg_ligand_desc), C.POINTER(_vp)]
+        L.adg_ligand_destroy.argtypes = [_vp]
+        L.adg_ligand_info.argtypes = [_vp, C.POINTER(adg_ligand_stats)]
+        L.adg_score.argtypes = [_vp, _vp, _vp, _vp, _i, _vp, _vp, _i]
+        L.adg_pose.argtypes = [_vp, _vp, _vp, _i, _vp]
+        L.adg_dock.argtypes = [_vp, _vp, C.POINTER(_vp), _i, C.POINTER(adg_search_params), C.POINTER(adg_result),
+                               C.POINTER(adg_dock_trace)]
+        L.adg_philox.argtypes = [_vp, _vp, _i, C.c_uint64, _vp]
+        L.adg_ctx_set_timing.argtypes = [_vp, _i]
+        L.adg_ctx_stats.argtypes = [_vp, C.POINTER(adg_stats), _i]
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().adg_strerror(code).decode()
+    except Exception:  # library missing: still format the error
+        return "error"
+
+
+def _check(rc: int, what: str, ctx=None):
+    if rc != ADG_OK:
+        detail = ""
+        if ctx is not None and ctx.handle:
+            detail = load().adg_ctx_last_error(ctx.handle).decode()
+        raise AdgError(rc, what, detail)
+
+
+def _ptr(t) -> int:
+    """Device pointer of a CUDA tensor (checked contiguous, on a GPU)."""
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------- helpers
+def forcefield_struct(ff: dict) -> adg_forcefield:
+    s = adg_forcefield()
+    for name in ("Rii", "epsii", "vol", "solpar", "hb_R", "hb_eps"):
+        arr = getattr(s, name)
+        for t in range(NTYPES):
+            arr[t] = float(ff[name][t])
+    for name in ("hb_donor", "hb_acceptor"):
+        arr = getattr(s, name)
+        for t in range(NTYPES):
+            arr[t] = int(ff[name][t])
+    for name, _ in adg_forcefield._fields_[8:]:
+        setattr(s, name, float(ff[name]))
+    return s
+
+
+def grid_struct(grid) -> adg_grid_desc:
+    g = adg_grid_desc()
+    for a in range(3):
+        g.n[a] = int(grid.n[a])
+        g.origin[a] = float(grid.origin[a])
+    g.spacing = float(grid.spacing)
+    return g
+
+
+def search_params(**kw) -> adg_search_params:
+    p = adg_search_params()
+    load().adg_search_params_default(C.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise KeyError(k)
+        setattr(p, k, v)
+    return p
+
+
+# ---------------------------------------------------------------- objects
+class Context:
+    """adg_ctx_create / adg_ctx_destroy.  `stream`: a torch.cuda.Stream (or
+    None for a library-owned stream)."""
+
+    def __init__(self, device: int = 0, stream=None):
+        L = load()
+        h = C.c_void_p()
+        sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+        _check(L.adg_ctx_create(C.byref(h), device, sp), "adg_ctx_create")
+        self.handle = h
+        self.device = device
+        self.stream = stream
+
+    def sync(self):
+        _check(load().adg_sync(self.handle), "adg_sync", self)
+
+    def set_timing(self, enable: bool):
+        _check(load().adg_ctx_set_timing(self.handle, int(enable)), "adg_ctx_set_timing", self)
+
+    def stats(self, reset: bool = False) -> dict:
+        st = adg_stats()
+        _check(load().adg_ctx_stats(self.handle, C.byref(st), int(reset)), "adg_ctx_stats", self)
+        return {name: getattr(st, name) for name, _ in adg_stats._fields_}
+
+    def close(self):
+        if self.handle:
+            load().adg_ctx_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def maps_build(ctx: Context, ff: dict, grid, rec: "synth.Receptor"):
+    """adg_maps_build -> torch float32 tensor [9, nz, ny, nx] on the device."""
+    import torch
+    nx, ny, nz = grid.n
+    out = torch.empty((NMAPS, nz, ny, nx), dtype=torch.float32, device=f"cuda:{ctx.device}")
+    xyz = np.ascontiguousarray(rec.xyz, np.float32)
+    typ = np.ascontiguousarray(rec.type, np.int32)
+    q = np.ascontiguousarray(rec.charge, np.float32)
+    ffs, gs = forcefield_struct(ff), grid_struct(grid)
+    _check(load().adg_maps_build(ctx.handle, C.byref(ffs), C.byref(gs), len(typ), xyz.ctypes.data, typ.ctypes.data,
+                                 q.ctypes.data, _ptr(out)), "adg_maps_build", ctx)
+    return out
+
+
+class Receptor:
+    """adg_receptor_create: maps [9][nz][ny][nx] float32 (numpy host array or CUDA tensor)."""
+
+    def __init__(self, ctx: Context, grid, maps):
+        self.ctx = ctx
+        self.grid = grid
+        gs = grid_struct(grid)
+        h = C.c_void_p()
+        if isinstance(maps, np.ndarray):
+            m = np.ascontiguousarray(maps, np.float32)
+            rc = load().adg_receptor_create(ctx.handle, C.byref(gs), m.ctypes.data, 0, C.byref(h))
+        else:
+            rc = load().adg_receptor_create(ctx.handle, C.byref(gs), _ptr(maps), 1, C.byref(h))
+        _check(rc, "adg_receptor_create", ctx)
+        self.handle = h
+
+    def close(self):
+        if self.handle:
+            load().adg_receptor_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Ligand:
+    """adg_ligand_create from a synth.Ligand-like object (xyz, type, charge, bonds, tors, root)."""
+
+    def __init__(self, ctx: Context, ff: dict, lig):
+        self.ctx = ctx
+        xyz = np.ascontiguousarray(lig.xyz, np.float32).reshape(-1)
+        typ = np.ascontiguousarray(lig.type, np.int32)
+        q = np.ascontiguousarray(lig.charge, np.float32)
+        bonds = np.ascontiguousarray(lig.bonds, np.int32).reshape(-1)
+        tors = np.ascontiguousarray(lig.tors, np.int32).reshape(-1)
+        d = adg_ligand_desc()
+        d.natoms = len(typ)
+        d.xyz = xyz.ctypes.data_as(C.POINTER(C.c_float))
+        d.type = typ.ctypes.data_as(C.POINTER(C.c_int32))
+        d.charge = q.ctypes.data_as(C.POINTER(C.c_float))
+        d.nbonds = len(bonds) // 2
+        d.bonds = bonds.ctypes.data_as(C.POINTER(C.c_int32))
+        d.ntors = len(tors) // 2
+        d.tors = tors.ctypes.data_as(C.POINTER(C.c_int32))
+        d.root = int(lig.root)
+        ffs = forcefield_struct(ff)
+        h = C.c_void_p()
+        _check(load().adg_ligand_create(ctx.handle, C.byref(ffs), C.byref(d), C.byref(h)), "adg_ligand_create", ctx)
+        self.handle = h
+        st = adg_ligand_stats()
+        _check(load().adg_ligand_info(h, C.byref(st)), "adg_ligand_info", ctx)
+        self.natoms, self.ntors, self.npairs = st.natoms, st.ntors, st.npairs
+        self.sum_moving, self.device_bytes = st.sum_moving, st.device_bytes
+
+    def close(self):
+        if self.handle:
+            load().adg_ligand_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def score(ctx: Context, rec: Receptor, lig: Ligand, genes, grad_kind: int = GRAD_NONE, energy=None, grad=None):
+    """adg_score on CUDA tensors.  genes: float32 [npose, 7+T] on the device.
+    Returns (energy [npose], grad or None); outputs may be passed in."""
+    import torch
+    n = genes.shape[0]
+    if energy is None:
+        energy = torch.empty(n, dtype=torch.float32, device=genes.device)
+    if grad_kind != GRAD_NONE and grad is None:
+        width = 7 + lig.ntors if grad_kind == GRAD_GENES else 6 + lig.ntors
+        grad = torch.empty((n, width), dtype=torch.float32, device=genes.device)
+    _check(load().adg_score(ctx.handle, rec.handle, lig.handle, _ptr(genes), n, _ptr(energy),
+                            _ptr(grad) if grad is not None else None, grad_kind), "adg_score", ctx)
+    return energy, grad
+
+
+def pose(ctx: Context, lig: Ligand, genes):
+    import torch
+    n = genes.shape[0]
+    xyz = torch.empty((n, lig.natoms, 3), dtype=torch.float32, device=genes.device)
+    _check(load().adg_pose(ctx.handle, lig.handle, _ptr(genes), n, _ptr(xyz)), "adg_pose", ctx)
+    return xyz
+
+
+def philox(ctx: Context, ctr, key: int):
+    """ctr: uint32-compatible int32 CUDA tensor [n, 4] -> same shape output."""
+    import torch
+    out = torch.empty_like(ctr)
+    _check(load().adg_philox(ctx.handle, _ptr(ctr), ctr.shape[0], key, _ptr(out)), "adg_philox", ctx)
+    return out
+
+
+def dock(ctx: Context, rec: Receptor, ligs, params: adg_search_params, trace_ngen: int = 0):
+    """adg_dock.  Returns a list (per ligand) of dicts with arrays over runs:
+    best_energy [nrun], genes [nrun, 7+T], xyz [nrun, natoms, 3], evals, generations;
+    plus a trace dict when trace_ngen > 0 (one ligand only)."""
+    if isinstance(ligs, Ligand):
+        ligs = [ligs]
+    n = len(ligs)
+    nrun, pop = params.nrun, params.pop_size
+    res = (adg_result * (n * nrun))()
+    hs = (C.c_void_p * n)(*[l.handle.value for l in ligs])
+    tr = None
+    trace = None
+    if trace_ngen > 0:
+        G = 7 + ligs[0].ntors
+        dec = np.zeros((nrun, trace_ngen, pop, 8), np.int32)
+        tg = np.zeros((nrun, trace_ngen, pop, G), np.float32)
+        te = np.zeros((nrun, trace_ngen, pop), np.float32)
+        ig = np.zeros((nrun, pop, G), np.float32)
+        ie = np.zeros((nrun, pop), np.float32)
+        tr = adg_dock_trace()
+        tr.ngen = trace_ngen
+        tr.decisions = dec.ctypes.data_as(C.POINTER(C.c_int32))
+        tr.genes = tg.ctypes.data_as(C.POINTER(C.c_float))
+        tr.energies = te.ctypes.data_as(C.POINTER(C.c_float))
+        tr.init_genes = ig.ctypes.data_as(C.POINTER(C.c_float))
+        tr.init_energies = ie.ctypes.data_as(C.POINTER(C.c_float))
+        trace = dict(decisions=dec, genes=tg, energies=te, init_genes=ig, init_energies=ie)
+    _check(load().adg_dock(ctx.handle, rec.handle, hs, n, C.byref(params), res,
+                           C.byref(tr) if tr is not None else None), "adg_dock", ctx)
+    raw = np.frombuffer(res, dtype=np.uint8).reshape(n * nrun, C.sizeof(adg_result))
+    out = []
+    for li, lig in enumerate(ligs):
+        G, N = 7 + lig.ntors, lig.natoms
+        rr = [res[li * nrun + r] for r in range(nrun)]
+        out.append(dict(best_energy=np.array([r.best_energy for r in rr], np.float32),
+                        genes=np.array([r.genes[:G] for r in rr], np.float32),
+                        xyz=np.array([r.xyz[:3 * N] for r in rr], np.float32).reshape(nrun, N, 3),
+                        evals=np.array([r.evals for r in rr], np.int64),
+                        generations=np.array([r.generations for r in rr], np.int32)))
+    del raw
+    return (out, trace) if trace_ngen > 0 else out

@@ -1,0 +1,802 @@
+// adg_api.cu -- host half of libadg.so: the C ABI declared in include/adg.h.
+//
+// Holds the context (device, stream, a grow-only device arena reused across
+// dock calls: the paper's context and memory reuse, Sec. 2.2.3), the
+// resident receptor (maps uploaded once, Sec. 2.2.3), the ligand
+// preprocessing (torsion tree, intramolecular pair list and its lane
+// schedule) and the generation loop of adg_dock.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "adg_internal.h"
+
+using namespace adg;
+
+namespace adg {
+void pair_coefs(const adg_forcefield& ff, int ti, int tj, float* c12, float* c6, float* c10);
+}
+
+struct adg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string last_error;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    int* host_active = nullptr;  // pinned
+    // measurement
+    bool timing = false;
+    adg_stats stats{};
+    std::vector<cudaEvent_t> ev_free;                       // reusable events
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
+};
+
+struct adg_receptor {
+    adg_ctx* ctx = nullptr;
+    adg_grid_desc grid{};
+    float4* packed = nullptr;
+    MapsDev maps{};
+};
+
+struct adg_ligand {
+    adg_ctx* ctx = nullptr;
+    void* blob = nullptr;  // LigandDev followed by the pair arrays
+    LigandRef ref{};
+    int natoms = 0, ntors = 0, npairs = 0, apl = 1, sum_moving = 0;
+    size_t bytes = 0;
+};
+
+namespace {
+
+int cuda_fail(adg_ctx* ctx, cudaError_t e, const char* what)
+{
+    if (ctx) ctx->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return ADG_ECUDA;
+}
+
+#define CK(ctx, call)                                        \
+    do {                                                     \
+        cudaError_t _e = (call);                             \
+        if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
+    } while (0)
+
+int apl_for(int natoms) { return natoms <= 32 ? 1 : (natoms <= 64 ? 2 : 4); }
+
+uint32_t prob_threshold(float p)
+{
+    if (p <= 0.f) return 0u;
+    if (p >= 1.f) return 16777216u;
+    return (uint32_t)floor((double)p * 16777216.0);
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+int check_grid(const adg_grid_desc* g)
+{
+    if (!g) return ADG_EINVAL;
+    for (int a = 0; a < 3; ++a)
+        if (g->n[a] < 2) return ADG_EGRID;
+    if (!(g->spacing > 0.f)) return ADG_EGRID;
+    return ADG_OK;
+}
+
+cudaError_t take_event(adg_ctx* ctx, cudaEvent_t* ev)
+{
+    if (!ctx->ev_free.empty()) {
+        *ev = ctx->ev_free.back();
+        ctx->ev_free.pop_back();
+        return cudaSuccess;
+    }
+    return cudaEventCreate(ev);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* adg_strerror(int code)
+{
+    switch (code) {
+    case ADG_OK: return "ok";
+    case ADG_EINVAL: return "invalid argument (null pointer or bad size)";
+    case ADG_ETYPE: return "atom type outside 0..6";
+    case ADG_ETOOBIG: return "ligand exceeds ADG_MAX_ATOMS atoms or ADG_MAX_TORS torsions";
+    case ADG_EGRID: return "grid needs at least 2 points per axis and a positive spacing";
+    case ADG_ECUDA: return "CUDA runtime error";
+    case ADG_ETIMEOUT: return "bounded device wait expired";
+    case ADG_ENOMEM: return "out of memory";
+    case ADG_ETOPO: return "bonds are not one tree or a torsion is not a bond";
+    default: return "unknown error";
+    }
+}
+
+void adg_search_params_default(adg_search_params* p)
+{
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->nrun = 10;
+    p->pop_size = 150;
+    p->nev = 2500000;
+    p->max_gen = 27000;
+    p->ls_method = ADG_LS_SOLIS_WETS;
+    p->ls_max_iters = 300;
+    p->elitism = 1;
+    p->ls_rate = 1.f;
+    p->crossover_rate = 0.8f;
+    p->mutation_rate = 0.02f;
+    p->tournament_rate = 0.6f;
+    p->sw_rho0 = 1.f;
+    p->sw_rho_min = 0.01f;
+    p->sw_expand = 2.f;
+    p->sw_contract = 0.5f;
+    p->sw_succ = 4;
+    p->sw_fail = 4;
+    p->sw_scale_t = 1.f;
+    p->sw_scale_rot = 0.5f;
+    p->sw_scale_tors = 0.5f;
+    p->ad_rho = 0.8f;
+    p->ad_eps = 0.01f;
+    p->mut_t = 2.f;
+    p->mut_rot = 1.57079632679490f;
+    p->mut_tors = 1.57079632679490f;
+    p->seed = 42;
+    p->lig_id = 0;
+}
+
+int adg_ctx_create(adg_ctx** out, int device, void* stream)
+{
+    if (!out) return ADG_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return ADG_EINVAL;
+    adg_ctx* c = new (std::nothrow) adg_ctx();
+    if (!c) return ADG_ENOMEM;
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) {
+        if (stream) {
+            c->stream = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+            c->own_stream = true;
+        }
+    }
+    if (e == cudaSuccess) e = cudaMallocHost(&c->host_active, sizeof(int) * 4);
+    if (e != cudaSuccess) {
+        if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+        delete c;
+        return ADG_ECUDA;
+    }
+    *out = c;
+    return ADG_OK;
+}
+
+int adg_ctx_destroy(adg_ctx* ctx)
+{
+    if (!ctx) return ADG_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto& pr : ctx->ev_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    for (auto ev : ctx->ev_free) cudaEventDestroy(ev);
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->host_active) cudaFreeHost(ctx->host_active);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return ADG_OK;
+}
+
+int adg_sync(adg_ctx* ctx)
+{
+    if (!ctx) return ADG_EINVAL;
+    CK(ctx, cudaSetDevice(ctx->device));
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return ADG_OK;
+}
+
+const char* adg_ctx_last_error(const adg_ctx* ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+int adg_ctx_set_timing(adg_ctx* ctx, int enable)
+{
+    if (!ctx) return ADG_EINVAL;
+    ctx->timing = enable != 0;
+    return ADG_OK;
+}
+
+int adg_ctx_stats(adg_ctx* ctx, adg_stats* out, int reset)
+{
+    if (!ctx || !out) return ADG_EINVAL;
+    CK(ctx, cudaSetDevice(ctx->device));
+    if (!ctx->ev_pending.empty()) {
+        CK(ctx, cudaStreamSynchronize(ctx->stream));
+        for (auto& pr : ctx->ev_pending) {
+            float ms = 0.f;
+            CK(ctx, cudaEventElapsedTime(&ms, pr.first, pr.second));
+            ctx->stats.gen_kernel_ms += ms;
+            ctx->stats.gen_timed += 1;
+            ctx->ev_free.push_back(pr.first);
+            ctx->ev_free.push_back(pr.second);
+        }
+        ctx->ev_pending.clear();
+    }
+    *out = ctx->stats;
+    if (reset) ctx->stats = adg_stats{};
+    return ADG_OK;
+}
+
+int adg_maps_build(adg_ctx* ctx, const adg_forcefield* ff, const adg_grid_desc* grid, int nrec, const float* rec_xyz,
+                   const int32_t* rec_type, const float* rec_q, float* maps_out)
+{
+    if (!ctx || !ff || !rec_xyz || !rec_type || !rec_q || !maps_out || nrec <= 0) return ADG_EINVAL;
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    std::vector<float4> xq(nrec);
+    for (int i = 0; i < nrec; ++i) {
+        if (rec_type[i] < 0 || rec_type[i] >= ADG_NTYPES) return ADG_ETYPE;
+        xq[i] = make_float4(rec_xyz[3 * i], rec_xyz[3 * i + 1], rec_xyz[3 * i + 2], rec_q[i]);
+    }
+    CK(ctx, cudaSetDevice(ctx->device));
+    float4* d_xq = nullptr;
+    int* d_t = nullptr;
+    CK(ctx, cudaMallocAsync(&d_xq, sizeof(float4) * nrec, ctx->stream));
+    CK(ctx, cudaMallocAsync(&d_t, sizeof(int) * nrec, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(d_xq, xq.data(), sizeof(float4) * nrec, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, cudaMemcpyAsync(d_t, rec_type, sizeof(int) * nrec, cudaMemcpyHostToDevice, ctx->stream));
+    CK(ctx, launch_maps_build(ctx->stream, *ff, *grid, nrec, d_xq, d_t, maps_out));
+    ctx->stats.kernel_launches += 1;
+    CK(ctx, cudaFreeAsync(d_xq, ctx->stream));
+    CK(ctx, cudaFreeAsync(d_t, ctx->stream));
+    // the host vectors are read by the copies above: wait before they go out of scope
+    CK(ctx, cudaStreamSynchronize(ctx->stream));
+    return ADG_OK;
+}
+
+int adg_receptor_create(adg_ctx* ctx, const adg_grid_desc* grid, const float* maps, int maps_on_device,
+                        adg_receptor** out)
+{
+    if (!ctx || !maps || !out) return ADG_EINVAL;
+    *out = nullptr;
+    int rc = check_grid(grid);
+    if (rc) return rc;
+    CK(ctx, cudaSetDevice(ctx->device));
+    const long npt = (long)grid->n[0] * grid->n[1] * grid->n[2];
+    adg_receptor* r = new (std::nothrow) adg_receptor();
+    if (!r) return ADG_ENOMEM;
+    r->ctx = ctx;
+    r->grid = *grid;
+    cudaError_t e = cudaMalloc(&r->packed, sizeof(float4) * ADG_NTYPES * npt);
+    if (e != cudaSuccess) {
+        delete r;
+        return cuda_fail(ctx, e, "cudaMalloc(packed maps)");
+    }
+    const float* src = maps;
+    float* tmp = nullptr;
+    if (!maps_on_device) {
+        e = cudaMallocAsync(&tmp, sizeof(float) * ADG_NMAPS * npt, ctx->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(tmp, maps, sizeof(float) * ADG_NMAPS * npt, cudaMemcpyHostToDevice, ctx->stream);
+        src = tmp;
+    }
+    if (e == cudaSuccess) e = launch_pack_maps(ctx->stream, src, *grid, r->packed);
+    ctx->stats.kernel_launches += 1;
+    if (tmp) cudaFreeAsync(tmp, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        cudaFree(r->packed);
+        delete r;
+        return cuda_fail(ctx, e, "receptor upload");
+    }
+    MapsDev& m = r->maps;
+    m.packed = r->packed;
+    m.nx = grid->n[0];
+    m.ny = grid->n[1];
+    m.nz = grid->n[2];
+    m.ox = grid->origin[0];
+    m.oy = grid->origin[1];
+    m.oz = grid->origin[2];
+    m.h = grid->spacing;
+    m.inv_h = 1.f / grid->spacing;
+    m.hx = grid->origin[0] + (grid->n[0] - 1) * grid->spacing;
+    m.hy = grid->origin[1] + (grid->n[1] - 1) * grid->spacing;
+    m.hz = grid->origin[2] + (grid->n[2] - 1) * grid->spacing;
+    *out = r;
+    return ADG_OK;
+}
+
+int adg_receptor_destroy(adg_receptor* rec)
+{
+    if (!rec) return ADG_EINVAL;
+    cudaSetDevice(rec->ctx->device);
+    cudaStreamSynchronize(rec->ctx->stream);
+    cudaFree(rec->packed);
+    delete rec;
+    return ADG_OK;
+}
+
+int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_desc* d, adg_ligand** out)
+{
+    if (!ctx || !ff || !d || !out || !d->xyz || !d->type || !d->charge) return ADG_EINVAL;
+    *out = nullptr;
+    const int N = d->natoms, T = d->ntors;
+    if (N < 1 || T < 0 || d->nbonds < 0) return ADG_EINVAL;
+    if (N > ADG_MAX_ATOMS || T > ADG_MAX_TORS) return ADG_ETOOBIG;
+    if ((d->nbonds > 0 && !d->bonds) || (T > 0 && !d->tors)) return ADG_EINVAL;
+    if (d->root < 0 || d->root >= N) return ADG_EINVAL;
+    for (int i = 0; i < N; ++i)
+        if (d->type[i] < 0 || d->type[i] >= ADG_NTYPES) return ADG_ETYPE;
+    for (int i = 0; i < 3 * N; ++i)
+        if (!isfinite(d->xyz[i])) return ADG_EINVAL;
+    // --- tree: adjacency, BFS from the root (parent, depth)
+    if (d->nbonds != N - 1) return ADG_ETOPO;
+    std::vector<std::vector<int>> adj(N);
+    for (int b = 0; b < d->nbonds; ++b) {
+        const int i = d->bonds[2 * b], j = d->bonds[2 * b + 1];
+        if (i < 0 || j < 0 || i >= N || j >= N || i == j) return ADG_ETOPO;
+        adj[i].push_back(j);
+        adj[j].push_back(i);
+    }
+    std::vector<int> parent(N, -2), depth(N, 0), bfs;
+    bfs.reserve(N);
+    parent[d->root] = -1;
+    bfs.push_back(d->root);
+    for (size_t h = 0; h < bfs.size(); ++h)
+        for (int v : adj[bfs[h]])
+            if (parent[v] == -2) {
+                parent[v] = bfs[h];
+                depth[v] = depth[bfs[h]] + 1;
+                bfs.push_back(v);
+            }
+    if ((int)bfs.size() != N) return ADG_ETOPO;
+    // --- torsions: orient a -> b away from the root; moving set = subtree of b
+    std::vector<int> ta(T), tb(T);
+    std::vector<std::vector<char>> moving(T, std::vector<char>(N, 0));
+    for (int k = 0; k < T; ++k) {
+        int a = d->tors[2 * k], b = d->tors[2 * k + 1];
+        if (a < 0 || b < 0 || a >= N || b >= N) return ADG_ETOPO;
+        if (parent[b] == a) {
+        } else if (parent[a] == b) {
+            std::swap(a, b);
+        } else {
+            return ADG_ETOPO;
+        }
+        ta[k] = a;
+        tb[k] = b;
+        // atoms whose root path passes through b: walk up from each atom
+        for (int i = 0; i < N; ++i) {
+            for (int u = i; u >= 0; u = parent[u])
+                if (u == b) {
+                    moving[k][i] = 1;
+                    break;
+                }
+        }
+    }
+    // --- application order: deepest torsion first (depth = ancestor torsions)
+    std::vector<int> tdepth(T, 0), order(T);
+    for (int k = 0; k < T; ++k)
+        for (int j = 0; j < T; ++j)
+            if (j != k && moving[j][tb[k]]) ++tdepth[k];
+    for (int k = 0; k < T; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return tdepth[x] > tdepth[y]; });
+    // --- rigid fragments (bonds that are not rotatable) and graph distances <= 3
+    std::vector<int> frag(N, -1);
+    auto is_rot = [&](int u, int v) {
+        for (int k = 0; k < T; ++k)
+            if ((ta[k] == u && tb[k] == v) || (ta[k] == v && tb[k] == u)) return true;
+        return false;
+    };
+    int nf = 0;
+    for (int s = 0; s < N; ++s) {
+        if (frag[s] >= 0) continue;
+        std::vector<int> st{s};
+        frag[s] = nf;
+        while (!st.empty()) {
+            const int u = st.back();
+            st.pop_back();
+            for (int v : adj[u])
+                if (frag[v] < 0 && !is_rot(u, v)) {
+                    frag[v] = nf;
+                    st.push_back(v);
+                }
+        }
+        ++nf;
+    }
+    std::vector<std::vector<char>> near(N, std::vector<char>(N, 0));
+    for (int s = 0; s < N; ++s) {
+        std::vector<int> dist(N, -1), q{s};
+        dist[s] = 0;
+        for (size_t h = 0; h < q.size(); ++h) {
+            const int u = q[h];
+            if (dist[u] == 3) continue;
+            for (int v : adj[u])
+                if (dist[v] < 0) {
+                    dist[v] = dist[u] + 1;
+                    q.push_back(v);
+                }
+        }
+        for (int v : q) near[s][v] = 1;
+    }
+    std::vector<std::pair<int, int>> pairs;
+    for (int i = 0; i < N; ++i)
+        for (int j = i + 1; j < N; ++j)
+            if (frag[i] != frag[j] && !near[i][j]) pairs.emplace_back(i, j);
+    const int P = (int)pairs.size();
+    // --- lane schedule: 32 pairs per step, greedily without a repeated atom
+    std::vector<int> slots;
+    {
+        std::vector<char> taken(P, 0);
+        int left = P;
+        std::vector<int> used(N, -1);
+        int step = 0;
+        while (left > 0) {
+            std::vector<int> cur;
+            for (int p = 0; p < P && (int)cur.size() < 32; ++p) {
+                if (taken[p]) continue;
+                if (used[pairs[p].first] == step || used[pairs[p].second] == step) continue;
+                cur.push_back(p);
+                used[pairs[p].first] = used[pairs[p].second] = step;
+                taken[p] = 1;
+            }
+            for (int p = 0; p < P && (int)cur.size() < 32; ++p)
+                if (!taken[p]) {
+                    cur.push_back(p);
+                    taken[p] = 1;
+                }
+            left -= (int)cur.size();
+            while ((int)cur.size() < 32) cur.push_back(-1);
+            slots.insert(slots.end(), cur.begin(), cur.end());
+            ++step;
+        }
+    }
+    const int nsteps = (int)slots.size() / 32;
+    // --- device header
+    LigandDev h;
+    memset(&h, 0, sizeof(h));
+    h.natoms = N;
+    h.ntors = T;
+    h.npairs = P;
+    h.nsteps = nsteps;
+    double c[3] = {0, 0, 0};
+    for (int i = 0; i < N; ++i)
+        for (int a = 0; a < 3; ++a) c[a] += d->xyz[3 * i + a];
+    h.cx = (float)(c[0] / N);
+    h.cy = (float)(c[1] / N);
+    h.cz = (float)(c[2] / N);
+    const double B = (double)ff->ms_eps0 - ff->ms_A;
+    h.e_cap = ff->e_cap;
+    h.rmin2 = ff->r_min * ff->r_min;
+    h.ms_A = ff->ms_A;
+    h.ms_B = (float)B;
+    h.ms_k = ff->ms_k;
+    h.ms_lb = (float)((double)ff->ms_lambda * B);
+    h.inv_2s2 = (float)(1.0 / (2.0 * (double)ff->sigma * ff->sigma));
+    h.inv_s2 = (float)(1.0 / ((double)ff->sigma * ff->sigma));
+    h.k_out = ff->k_out;
+    for (int i = 0; i < N; ++i) {
+        h.ref[i] = make_float4(d->xyz[3 * i], d->xyz[3 * i + 1], d->xyz[3 * i + 2], d->charge[i]);
+        h.type[i] = d->type[i];
+        uint32_t m = 0;
+        for (int s = 0; s < T; ++s)
+            if (moving[order[s]][i]) m |= 1u << s;
+        h.tmask[i] = m;
+    }
+    for (int s = 0; s < T; ++s) {
+        const int k = order[s];
+        h.gene_of[s] = k;
+        h.ta[s] = ta[k];
+        h.tb[s] = tb[k];
+        const float* pa = d->xyz + 3 * ta[k];
+        const float* pb = d->xyz + 3 * tb[k];
+        double u[3] = {(double)pb[0] - pa[0], (double)pb[1] - pa[1], (double)pb[2] - pa[2]};
+        const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+        if (!(un > 0)) return ADG_ETOPO;
+        h.tpt[s] = make_float4(pa[0], pa[1], pa[2], 0.f);
+        h.tax[s] = make_float4((float)(u[0] / un), (float)(u[1] / un), (float)(u[2] / un), 0.f);
+    }
+    // --- pair arrays in slot order
+    const int ns = nsteps * 32;
+    std::vector<int> ij(ns, -1);
+    std::vector<float4> coef(ns, make_float4(0, 0, 0, 0));
+    std::vector<float> cd(ns, 0.f);
+    const double wq = (double)ff->w_elec * ff->coulomb;
+    for (int s = 0; s < ns; ++s) {
+        const int p = slots[s];
+        if (p < 0) continue;
+        const int i = pairs[p].first, j = pairs[p].second;
+        const int ti = d->type[i], tj = d->type[j];
+        const double qi = d->charge[i], qj = d->charge[j];
+        float c12, c6, c10;
+        pair_coefs(*ff, ti, tj, &c12, &c6, &c10);
+        ij[s] = i | (j << 16);
+        coef[s] = make_float4(c12, c6, c10, (float)(wq * qi * qj));
+        cd[s] = (float)((double)ff->w_desolv * (((double)ff->solpar[ti] + (double)ff->qasp * fabs(qi)) * ff->vol[tj] +
+                                                ((double)ff->solpar[tj] + (double)ff->qasp * fabs(qj)) * ff->vol[ti]));
+    }
+    const size_t off_ij = align_up(sizeof(LigandDev), 256);
+    const size_t off_coef = align_up(off_ij + sizeof(int) * ns, 256);
+    const size_t off_cd = align_up(off_coef + sizeof(float4) * ns, 256);
+    const size_t bytes = align_up(off_cd + sizeof(float) * ns, 256);
+    CK(ctx, cudaSetDevice(ctx->device));
+    adg_ligand* L = new (std::nothrow) adg_ligand();
+    if (!L) return ADG_ENOMEM;
+    std::vector<char> host(bytes, 0);
+    memcpy(host.data(), &h, sizeof(h));
+    memcpy(host.data() + off_ij, ij.data(), sizeof(int) * ns);
+    memcpy(host.data() + off_coef, coef.data(), sizeof(float4) * ns);
+    memcpy(host.data() + off_cd, cd.data(), sizeof(float) * ns);
+    cudaError_t e = cudaMalloc(&L->blob, bytes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(L->blob, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+        if (L->blob) cudaFree(L->blob);
+        delete L;
+        return cuda_fail(ctx, e, "ligand upload");
+    }
+    char* base = (char*)L->blob;
+    L->ctx = ctx;
+    L->ref.hdr = (const LigandDev*)base;
+    L->ref.pairs.ij = (const int*)(base + off_ij);
+    L->ref.pairs.coef = (const float4*)(base + off_coef);
+    L->ref.pairs.cd = (const float*)(base + off_cd);
+    L->natoms = N;
+    L->ntors = T;
+    L->npairs = P;
+    L->apl = apl_for(N);
+    L->bytes = bytes;
+    for (int k = 0; k < T; ++k)
+        for (int i = 0; i < N; ++i) L->sum_moving += moving[k][i];
+    ctx->stats.h2d_bytes += (int64_t)bytes;
+    *out = L;
+    return ADG_OK;
+}
+
+int adg_ligand_destroy(adg_ligand* lig)
+{
+    if (!lig) return ADG_EINVAL;
+    cudaSetDevice(lig->ctx->device);
+    cudaStreamSynchronize(lig->ctx->stream);
+    cudaFree(lig->blob);
+    delete lig;
+    return ADG_OK;
+}
+
+int adg_ligand_info(const adg_ligand* lig, adg_ligand_stats* out)
+{
+    if (!lig || !out) return ADG_EINVAL;
+    out->natoms = lig->natoms;
+    out->ntors = lig->ntors;
+    out->npairs = lig->npairs;
+    out->sum_moving = lig->sum_moving;
+    out->device_bytes = (int64_t)lig->bytes;
+    return ADG_OK;
+}
+
+int adg_score(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* lig, const float* genes, int npose,
+              float* energy, float* grad, int grad_kind)
+{
+    if (!ctx || !rec || !lig || npose < 0 || (npose > 0 && (!genes || !energy))) return ADG_EINVAL;
+    if (grad_kind != ADG_GRAD_NONE && grad_kind != ADG_GRAD_GENES && grad_kind != ADG_GRAD_TANGENT) return ADG_EINVAL;
+    if (grad_kind != ADG_GRAD_NONE && npose > 0 && !grad) return ADG_EINVAL;
+    if (npose == 0) return ADG_OK;
+    CK(ctx, cudaSetDevice(ctx->device));
+    CK(ctx, launch_score(ctx->stream, rec->maps, lig->ref, lig->apl, genes, npose, energy, grad, grad_kind));
+    ctx->stats.kernel_launches += 1;
+    return ADG_OK;
+}
+
+int adg_pose(adg_ctx* ctx, const adg_ligand* lig, const float* genes, int npose, float* xyz)
+{
+    if (!ctx || !lig || npose < 0 || (npose > 0 && (!genes || !xyz))) return ADG_EINVAL;
+    if (npose == 0) return ADG_OK;
+    CK(ctx, cudaSetDevice(ctx->device));
+    CK(ctx, launch_pose(ctx->stream, lig->ref, genes, npose, xyz));
+    ctx->stats.kernel_launches += 1;
+    return ADG_OK;
+}
+
+int adg_philox(adg_ctx* ctx, const uint32_t* ctr, int n, uint64_t key, uint32_t* out)
+{
+    if (!ctx || n < 0 || (n > 0 && (!ctr || !out))) return ADG_EINVAL;
+    if (((uintptr_t)ctr | (uintptr_t)out) & 15u) return ADG_EINVAL;  // read and written as uint4
+    if (n == 0) return ADG_OK;
+    CK(ctx, cudaSetDevice(ctx->device));
+    CK(ctx, launch_philox(ctx->stream, ctr, n, (uint32_t)(key & 0xffffffffu), (uint32_t)(key >> 32), out));
+    ctx->stats.kernel_launches += 1;
+    return ADG_OK;
+}
+
+int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig,
+             const adg_search_params* p, adg_result* out, adg_dock_trace* trace)
+{
+    if (!ctx || !rec || !ligs || nlig <= 0 || !p || !out) return ADG_EINVAL;
+    if (p->nrun <= 0 || p->nrun > 65535 || p->pop_size < 2 || p->pop_size > 65535 || p->nev < 0 || p->max_gen < 0 ||
+        p->ls_max_iters < 0 || p->elitism < 0 || p->elitism > 1 || p->ls_method < 0 || p->ls_method > 2)
+        return ADG_EINVAL;
+    if (trace && (nlig != 1 || trace->ngen < 0)) return ADG_EINVAL;
+    int apl = 1;
+    for (int i = 0; i < nlig; ++i) {
+        if (!ligs[i] || ligs[i]->ctx != ctx) return ADG_EINVAL;
+        apl = std::max(apl, ligs[i]->apl);
+    }
+    CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const long nruns = (long)nlig * p->nrun;
+    const long nind = nruns * p->pop_size;
+    const int tr_ngen = trace ? trace->ngen : 0;
+    const long tr_slots = trace ? (long)p->nrun * tr_ngen * p->pop_size : 0;
+    // arena layout
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    const size_t o_g0 = take(sizeof(float) * nind * kGeneStride), o_g1 = take(sizeof(float) * nind * kGeneStride);
+    const size_t o_e0 = take(sizeof(float) * nind), o_e1 = take(sizeof(float) * nind);
+    const size_t o_ev = take(sizeof(unsigned long long) * 2 * nruns);
+    const size_t o_gd = take(sizeof(int) * nruns);
+    const size_t o_act = take(sizeof(int) * 2);
+    const size_t o_lr = take(sizeof(LigandRef) * nlig);
+    const size_t o_id = take(sizeof(uint32_t) * nlig);
+    const size_t o_res = take(sizeof(ResultDev) * nruns);
+    const size_t o_td = take(sizeof(int) * 8 * tr_slots);
+    const size_t o_tg = take(sizeof(float) * kGeneStride * tr_slots);
+    const size_t o_te = take(sizeof(float) * tr_slots);
+    if (off > ctx->arena_bytes) {
+        CK(ctx, cudaStreamSynchronize(st));
+        if (ctx->arena) cudaFree(ctx->arena);
+        ctx->arena = nullptr;
+        ctx->arena_bytes = 0;
+        cudaError_t e = cudaMalloc(&ctx->arena, off);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ADG_ENOMEM : cuda_fail(ctx, e, "arena");
+        ctx->arena_bytes = off;
+    }
+    char* A = (char*)ctx->arena;
+    std::vector<LigandRef> lr(nlig);
+    std::vector<uint32_t> ids(nlig);
+    for (int i = 0; i < nlig; ++i) {
+        lr[i] = ligs[i]->ref;
+        ids[i] = p->lig_id + (uint32_t)i;
+    }
+    SearchDev S;
+    S.nrun = p->nrun;
+    S.pop = p->pop_size;
+    S.nev = p->nev;
+    S.max_gen = p->max_gen;
+    S.ls_method = p->ls_method;
+    S.ls_max_iters = p->ls_max_iters;
+    S.elitism = p->elitism;
+    S.thr_ls = prob_threshold(p->ls_rate);
+    S.thr_cross = prob_threshold(p->crossover_rate);
+    S.thr_mut = prob_threshold(p->mutation_rate);
+    S.thr_tour = prob_threshold(p->tournament_rate);
+    S.sw_rho0 = p->sw_rho0;
+    S.sw_rho_min = p->sw_rho_min;
+    S.sw_expand = p->sw_expand;
+    S.sw_contract = p->sw_contract;
+    S.sw_succ = p->sw_succ;
+    S.sw_fail = p->sw_fail;
+    S.sw_scale_t = p->sw_scale_t;
+    S.sw_scale_rot = p->sw_scale_rot;
+    S.sw_scale_tors = p->sw_scale_tors;
+    S.ad_rho = p->ad_rho;
+    S.ad_eps = p->ad_eps;
+    S.mut_t = p->mut_t;
+    S.mut_rot = p->mut_rot;
+    S.mut_tors = p->mut_tors;
+    S.key0 = (uint32_t)(p->seed & 0xffffffffu);
+    S.key1 = (uint32_t)(p->seed >> 32);
+    DockDev D;
+    D.ligs = (const LigandRef*)(A + o_lr);
+    D.lig_id = (const uint32_t*)(A + o_id);
+    D.nlig = nlig;
+    D.pop_genes[0] = (float*)(A + o_g0);
+    D.pop_genes[1] = (float*)(A + o_g1);
+    D.pop_e[0] = (float*)(A + o_e0);
+    D.pop_e[1] = (float*)(A + o_e1);
+    D.evals = (unsigned long long*)(A + o_ev);
+    D.gen_done = (int*)(A + o_gd);
+    D.trace_ngen = tr_ngen;
+    D.tr_dec = (int*)(A + o_td);
+    D.tr_genes = (float*)(A + o_tg);
+    D.tr_e = (float*)(A + o_te);
+    int* d_active = (int*)(A + o_act);
+    ResultDev* d_res = (ResultDev*)(A + o_res);
+    const MapsDev& M = rec->maps;
+    CK(ctx, cudaMemcpyAsync(A + o_lr, lr.data(), sizeof(LigandRef) * nlig, cudaMemcpyHostToDevice, st));
+    CK(ctx, cudaMemcpyAsync(A + o_id, ids.data(), sizeof(uint32_t) * nlig, cudaMemcpyHostToDevice, st));
+    ctx->stats.h2d_bytes += (int64_t)((sizeof(LigandRef) + sizeof(uint32_t)) * nlig);
+    CK(ctx, cudaMemsetAsync(D.evals, 0, sizeof(unsigned long long) * 2 * nruns, st));
+    CK(ctx, cudaMemsetAsync(D.gen_done, 0, sizeof(int) * nruns, st));
+    CK(ctx, launch_dock_init(st, M, S, D, apl));
+    ctx->stats.kernel_launches += 1;
+    std::vector<float> init_g, init_e;
+    if (trace && (trace->init_genes || trace->init_energies)) {
+        init_g.resize((size_t)nind * kGeneStride);
+        init_e.resize(nind);
+        CK(ctx, cudaMemcpyAsync(init_g.data(), D.pop_genes[0], sizeof(float) * nind * kGeneStride,
+                                cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaMemcpyAsync(init_e.data(), D.pop_e[0], sizeof(float) * nind, cudaMemcpyDeviceToHost, st));
+    }
+    // generation loop: launch a chunk, then read how many runs are still active
+    const int chunk = 4;
+    int gen = 0;
+    // the initial population spent pop_size evaluations; with nev <= pop_size no generation runs
+    const bool need_more = p->max_gen > 0 && p->pop_size < p->nev;
+    while (need_more) {
+        int last = gen;
+        for (int c = 0; c < chunk && gen < p->max_gen; ++c) {
+            ++gen;
+            CK(ctx, cudaMemsetAsync(d_active, 0, sizeof(int), st));
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (ctx->timing) {
+                CK(ctx, take_event(ctx, &e0));
+                CK(ctx, take_event(ctx, &e1));
+                CK(ctx, cudaEventRecord(e0, st));
+            }
+            CK(ctx, launch_dock_generation(st, M, S, D, apl, gen));
+            if (ctx->timing) {
+                CK(ctx, cudaEventRecord(e1, st));
+                ctx->ev_pending.emplace_back(e0, e1);
+            }
+            CK(ctx, launch_dock_count_active(st, S, D, gen, d_active));
+            ctx->stats.kernel_launches += 2;
+            ctx->stats.gen_launches += 1;
+            last = gen;
+        }
+        CK(ctx, cudaMemcpyAsync(ctx->host_active, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        ctx->stats.d2h_bytes += (int64_t)sizeof(int);
+        CK(ctx, cudaStreamSynchronize(st));
+        if (*ctx->host_active == 0 || last >= p->max_gen) break;
+    }
+    CK(ctx, launch_dock_finalize(st, M, S, D, d_res));
+    ctx->stats.kernel_launches += 1;
+    std::vector<ResultDev> res(nruns);
+    CK(ctx, cudaMemcpyAsync(res.data(), d_res, sizeof(ResultDev) * nruns, cudaMemcpyDeviceToHost, st));
+    ctx->stats.d2h_bytes += (int64_t)(sizeof(ResultDev) * nruns);
+    std::vector<int> tdec;
+    std::vector<float> tg, te;
+    if (trace && tr_slots > 0) {
+        tdec.resize((size_t)tr_slots * 8);
+        tg.resize((size_t)tr_slots * kGeneStride);
+        te.resize(tr_slots);
+        CK(ctx, cudaMemcpyAsync(tdec.data(), D.tr_dec, sizeof(int) * 8 * tr_slots, cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaMemcpyAsync(tg.data(), D.tr_genes, sizeof(float) * kGeneStride * tr_slots, cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaMemcpyAsync(te.data(), D.tr_e, sizeof(float) * tr_slots, cudaMemcpyDeviceToHost, st));
+    }
+    CK(ctx, cudaStreamSynchronize(st));
+    for (long r = 0; r < nruns; ++r) {
+        adg_result& o = out[r];
+        const ResultDev& s = res[r];
+        const int lig = (int)(r / p->nrun);
+        const int G = 7 + ligs[lig]->ntors, N = ligs[lig]->natoms;
+        memset(&o, 0, sizeof(o));
+        o.best_energy = s.best_energy;
+        o.generations = s.generations;
+        o.evals = s.evals;
+        for (int k = 0; k < G; ++k) o.genes[k] = s.genes[k];
+        for (int k = 0; k < 3 * N; ++k) o.xyz[k] = s.xyz[k];
+    }
+    if (trace) {
+        const int G = 7 + ligs[0]->ntors;
+        if (trace->decisions && tr_slots) memcpy(trace->decisions, tdec.data(), sizeof(int) * 8 * tr_slots);
+        if (trace->energies && tr_slots) memcpy(trace->energies, te.data(), sizeof(float) * tr_slots);
+        if (trace->genes)
+            for (long s = 0; s < tr_slots; ++s)
+                for (int k = 0; k < G; ++k) trace->genes[s * G + k] = tg[s * kGeneStride + k];
+        if (trace->init_genes)
+            for (long s = 0; s < nind; ++s)
+                for (int k = 0; k < G; ++k) trace->init_genes[s * G + k] = init_g[s * kGeneStride + k];
+        if (trace->init_energies) memcpy(trace->init_energies, init_e.data(), sizeof(float) * nind);
+    }
+    return ADG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// adg_internal.h -- layouts shared by the host half (adg_api.cu) and the
+// device half (adg_kernels.cu) of libadg.so.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "adg.h"
+
+namespace adg {
+
+constexpr int kMaxAtoms = ADG_MAX_ATOMS;
+constexpr int kMaxTors = ADG_MAX_TORS;
+constexpr int kGeneStride = 24;  // population rows are padded to 24 floats (>= 7 + 16)
+constexpr int kWarpsPerBlock = 8;
+
+// Ligand as the kernels read it: one POD blob in device memory.
+// Torsions are stored in application order s (deepest first); gene_of[s] is
+// the genotype index k of torsion s (theta_k = genes[7 + k]).
+struct LigandDev {
+    int natoms, ntors, npairs, nsteps;   // nsteps = ceil(npairs / 32) pair slots per lane
+    float cx, cy, cz;                    // reference centroid
+    // scoring constants (from the force field)
+    float e_cap, rmin2, ms_A, ms_B, ms_k, ms_lb, inv_2s2, inv_s2, k_out;
+    float4 ref[kMaxAtoms];               // reference x, y, z and charge q
+    int type[kMaxAtoms];                 // map index 0..6
+    uint32_t tmask[kMaxAtoms];           // bit s set when the atom is moved by torsion s
+    int gene_of[kMaxTors];
+    int ta[kMaxTors], tb[kMaxTors];      // bond atoms of torsion s (a on the root side)
+    float4 tpt[kMaxTors];                // reference position of atom a
+    float4 tax[kMaxTors];                // reference unit axis a -> b
+};
+
+// Intramolecular pairs, lane-interleaved: slot (step, lane) = step * 32 + lane.
+// ij = i | j << 16, or -1 for an empty slot.  coef = (c12, c6, c10, cq):
+// E_pair = min(c12 r^-12 - c6 r^-6 - c10 r^-10, e_cap) + cq / (eps(r) r) + cd exp(-r^2/(2 s^2)).
+struct PairsDev {
+    const int* ij;
+    const float4* coef;
+    const float* cd;
+};
+
+struct LigandRef {
+    const LigandDev* hdr;
+    PairsDev pairs;
+};
+
+// Receptor maps, packed per ligand atom type t: node = (M_t, M_elec, M_desolv, 0).
+struct MapsDev {
+    const float4* packed;  // [7][nz][ny][nx]
+    int nx, ny, nz;
+    float ox, oy, oz;      // origin
+    float h, inv_h;
+    float hx, hy, hz;      // upper corner of the box
+};
+
+struct SearchDev {
+    int nrun, pop, nev, max_gen, ls_method, ls_max_iters, elitism;
+    uint32_t thr_ls, thr_cross, thr_mut, thr_tour;  // probability thresholds floor(p * 2^24)
+    float sw_rho0, sw_rho_min, sw_expand, sw_contract;
+    int sw_succ, sw_fail;
+    float sw_scale_t, sw_scale_rot, sw_scale_tors;
+    float ad_rho, ad_eps;
+    float mut_t, mut_rot, mut_tors;
+    uint32_t key0, key1;
+};
+
+struct DockDev {
+    const LigandRef* ligs;     // [nlig]
+    const uint32_t* lig_id;    // Philox counter word 0 per ligand
+    int nlig;
+    float* pop_genes[2];       // [nlig*nrun][pop][kGeneStride], double-buffered by generation parity
+    float* pop_e[2];           // [nlig*nrun][pop]
+    unsigned long long* evals; // [nlig*nrun]
+    int* gen_done;             // [nlig*nrun]
+    // optional trace (one ligand): decisions [nrun][ngen][pop][8], genes [nrun][ngen][pop][kGeneStride], e
+    int trace_ngen;
+    int* tr_dec;
+    float* tr_genes;
+    float* tr_e;
+};
+
+struct ResultDev {
+    float best_energy;
+    int generations;
+    long long evals;
+    float genes[kGeneStride];
+    float xyz[3 * kMaxAtoms];
+};
+
+// Launchers (adg_kernels.cu).  All asynchronous on `st`; return cudaGetLastError().
+cudaError_t launch_maps_build(cudaStream_t st, const adg_forcefield& ff, const adg_grid_desc& g, int nrec,
+                              const float4* rec_xyzq, const int* rec_type, float* maps_out);
+cudaError_t launch_pack_maps(cudaStream_t st, const float* maps, const adg_grid_desc& g, float4* packed);
+cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, int apl, const float* genes,
+                         int npose, float* energy, float* grad, int grad_kind);
+cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const float* genes, int npose, float* xyz);
+cudaError_t launch_philox(cudaStream_t st, const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out);
+cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, int apl);
+cudaError_t launch_dock_generation(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d,
+                                   int apl, int gen);
+cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const DockDev& d, int next_gen,
+                                     int* active);
+cudaError_t launch_dock_finalize(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d,
+                                 ResultDev* out);
+
+}  // namespace adg

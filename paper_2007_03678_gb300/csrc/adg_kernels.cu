@@ -1,0 +1,953 @@
+// adg_kernels.cu -- sm_103a kernels of the docking hot path (arXiv 2007.03678).
+//
+// One warp owns one individual (one genotype): lanes own atoms for the pose
+// and the grid gather, lanes own intramolecular pairs for the pair terms,
+// and warp shuffles reduce the energy and the genotype gradient.  A whole
+// GA generation of an individual -- selection, crossover, mutation, the
+// offspring evaluation and its local search (Solis-Wets or ADADELTA) -- runs
+// inside that one warp, so a generation of every run of every ligand is one
+// launch.  The receptor maps are packed per atom type as float4 nodes
+// (M_t, M_elec, M_desolv, 0) so that a trilinear gather is 8 16-byte loads
+// served from L2 (a 64^3 receptor is 29 MB packed, well inside the 126 MB L2).
+#include <math.h>
+#include <stdint.h>
+
+#include "adg_internal.h"
+
+namespace adg {
+
+#define FULL_MASK 0xffffffffu
+
+// ------------------------------------------------------------------ Philox
+// Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32 multiplies
+// whose high halves are xored into the other words with the round key; the
+// key is bumped by the Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox(uint4 c, uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    }
+    return c;
+}
+
+// Stream layout: counter = (ligand id, run << 16 | individual, generation,
+// purpose << 20 | block), key = 64-bit seed.
+enum { P_INIT = 1, P_SELECT = 2, P_MUTATE = 3, P_LSPICK = 4, P_LS = 5 };
+
+struct Rng {
+    uint32_t k0, k1, lig, run, ind, gen;
+    __device__ __forceinline__ uint4 block(int purpose, int blk) const
+    {
+        return philox(make_uint4(lig, (run << 16) | ind, gen, ((uint32_t)purpose << 20) | (uint32_t)blk), k0, k1);
+    }
+};
+
+__device__ __forceinline__ float u01(uint32_t x) { return (float)(x >> 8) * (1.0f / 16777216.0f); }
+__device__ __forceinline__ float u01_open0(uint32_t x) { return (float)((x >> 8) + 1u) * (1.0f / 16777216.0f); }
+__device__ __forceinline__ int uindex(uint32_t x, int n) { return (int)(((unsigned long long)x * (unsigned)n) >> 32); }
+__device__ __forceinline__ bool ptest(uint32_t x, uint32_t thr) { return (x >> 8) < thr; }
+__device__ __forceinline__ uint32_t word(uint4 w, int i) { return i == 0 ? w.x : i == 1 ? w.y : i == 2 ? w.z : w.w; }
+
+__global__ void k_philox(const uint32_t* __restrict__ ctr, int n, uint32_t k0, uint32_t k1, uint32_t* __restrict__ out)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint4 c = reinterpret_cast<const uint4*>(ctr)[i];
+    reinterpret_cast<uint4*>(out)[i] = philox(c, k0, k1);
+}
+
+cudaError_t launch_philox(cudaStream_t st, const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out)
+{
+    if (n > 0) k_philox<<<(n + 255) / 256, 256, 0, st>>>(ctr, n, k0, k1, out);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ maps (a0)
+struct MapConst {
+    float c12[ADG_NTYPES][ADG_NTYPES], c6[ADG_NTYPES][ADG_NTYPES], c10[ADG_NTYPES][ADG_NTYPES];
+    float solpar[ADG_NTYPES], vol[ADG_NTYPES];
+    float w_desolv, qasp, inv_2s2, w_elec_coul;
+    float ms_A, ms_B, ms_k, ms_lb;
+    float r_min, rmin2, e_cap, r_on, r_off;
+    float ox, oy, oz, h;
+    int nx, ny, nz;
+};
+
+// One thread per grid node; receptor atoms stream through shared memory.
+__global__ void __launch_bounds__(256) k_maps_build(MapConst C, int nrec, const float4* __restrict__ rxyzq,
+                                                    const int* __restrict__ rtype, float* __restrict__ maps)
+{
+    __shared__ float4 sa[256];
+    __shared__ int st[256];
+    const long npt = (long)C.nx * C.ny * C.nz;
+    const long node = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int ix = (int)(node % C.nx), iy = (int)((node / C.nx) % C.ny), iz = (int)(node / ((long)C.nx * C.ny));
+    const float px = C.ox + ix * C.h, py = C.oy + iy * C.h, pz = C.oz + iz * C.h;
+    float acc[ADG_NMAPS];
+#pragma unroll
+    for (int m = 0; m < ADG_NMAPS; ++m) acc[m] = 0.f;
+    const float roff2 = C.r_off * C.r_off;
+    for (int base = 0; base < nrec; base += 256) {
+        __syncthreads();
+        if (base + threadIdx.x < nrec) {
+            sa[threadIdx.x] = rxyzq[base + threadIdx.x];
+            st[threadIdx.x] = rtype[base + threadIdx.x];
+        }
+        __syncthreads();
+        const int cnt = min(256, nrec - base);
+        if (node >= npt) continue;
+        for (int j = 0; j < cnt; ++j) {
+            const float4 a = sa[j];
+            const float dx = px - a.x, dy = py - a.y, dz = pz - a.z;
+            const float r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 >= roff2) continue;
+            const float r = sqrtf(r2);
+            float sw = 1.f;
+            if (r > C.r_on) {
+                const float u = (r - C.r_on) / (C.r_off - C.r_on);
+                sw = 1.f - 3.f * u * u + 2.f * u * u * u;
+            }
+            const float rr2 = r2 < C.rmin2 ? C.rmin2 : r2;
+            const float rr = r < C.r_min ? C.r_min : r;
+            const float G = expf(-rr2 * C.inv_2s2);
+            const float ri2 = 1.f / rr2;
+            const float ri6 = ri2 * ri2 * ri2, ri12 = ri6 * ri6, ri10 = ri6 * ri2 * ri2;
+            const int tj = st[j];
+            const float qj = a.w, aqj = fabsf(a.w);
+#pragma unroll
+            for (int t = 0; t < ADG_NTYPES; ++t) {
+                float e = C.c12[t][tj] * ri12 - C.c6[t][tj] * ri6 - C.c10[t][tj] * ri10;
+                e = fminf(e, C.e_cap);
+                e += C.w_desolv * (C.solpar[t] * C.vol[tj] + (C.solpar[tj] + C.qasp * aqj) * C.vol[t]) * G;
+                acc[t] += sw * e;
+            }
+            const float eps = C.ms_A + C.ms_B / (1.f + C.ms_k * expf(-C.ms_lb * rr));
+            acc[ADG_MAP_ELEC] += sw * C.w_elec_coul * qj / (eps * rr);
+            acc[ADG_MAP_DESOLV] += sw * C.w_desolv * C.qasp * C.vol[tj] * G;
+        }
+    }
+    if (node >= npt) return;
+#pragma unroll
+    for (int t = 0; t < ADG_NTYPES; ++t) acc[t] = fminf(acc[t], C.e_cap);
+#pragma unroll
+    for (int m = 0; m < ADG_NMAPS; ++m) maps[m * npt + node] = acc[m];
+}
+
+static void lj_coefs(const adg_forcefield& ff, int ti, int tj, double* c12, double* c6, double* c10)
+{
+    // generalised n-m well with minimum -eps at r0: C_n = m/(n-m) eps r0^n, C_m = n/(n-m) eps r0^m
+    const bool hb = (ff.hb_donor[ti] && ff.hb_acceptor[tj]) || (ff.hb_donor[tj] && ff.hb_acceptor[ti]);
+    double r0, eps, w;
+    int m;
+    if (hb) {
+        const int acc = ff.hb_acceptor[tj] ? tj : ti;
+        r0 = ff.hb_R[acc];
+        eps = ff.hb_eps[acc];
+        w = ff.w_hb;
+        m = 10;
+    } else {
+        r0 = 0.5 * ((double)ff.Rii[ti] + ff.Rii[tj]);
+        eps = sqrt((double)ff.epsii[ti] * ff.epsii[tj]);
+        w = ff.w_vdw;
+        m = 6;
+    }
+    double rn = 1.0, rm = 1.0;
+    for (int k = 0; k < 12; ++k) rn *= r0;
+    for (int k = 0; k < m; ++k) rm *= r0;
+    *c12 = w * (double)m / (12 - m) * eps * rn;
+    const double cm = w * 12.0 / (12 - m) * eps * rm;
+    *c6 = m == 6 ? cm : 0.0;
+    *c10 = m == 10 ? cm : 0.0;
+}
+
+void pair_coefs(const adg_forcefield& ff, int ti, int tj, float* c12, float* c6, float* c10)
+{
+    double a, b, c;
+    lj_coefs(ff, ti, tj, &a, &b, &c);
+    *c12 = (float)a;
+    *c6 = (float)b;
+    *c10 = (float)c;
+}
+
+cudaError_t launch_maps_build(cudaStream_t st, const adg_forcefield& ff, const adg_grid_desc& g, int nrec,
+                              const float4* rec_xyzq, const int* rec_type, float* maps_out)
+{
+    MapConst C;
+    for (int t = 0; t < ADG_NTYPES; ++t)
+        for (int u = 0; u < ADG_NTYPES; ++u) pair_coefs(ff, t, u, &C.c12[t][u], &C.c6[t][u], &C.c10[t][u]);
+    for (int t = 0; t < ADG_NTYPES; ++t) {
+        C.solpar[t] = ff.solpar[t];
+        C.vol[t] = ff.vol[t];
+    }
+    C.w_desolv = ff.w_desolv;
+    C.qasp = ff.qasp;
+    C.inv_2s2 = (float)(1.0 / (2.0 * (double)ff.sigma * ff.sigma));
+    C.w_elec_coul = (float)((double)ff.w_elec * ff.coulomb);
+    C.ms_A = ff.ms_A;
+    C.ms_B = (float)((double)ff.ms_eps0 - ff.ms_A);
+    C.ms_k = ff.ms_k;
+    C.ms_lb = (float)((double)ff.ms_lambda * ((double)ff.ms_eps0 - ff.ms_A));
+    C.r_min = ff.r_min;
+    C.rmin2 = ff.r_min * ff.r_min;
+    C.e_cap = ff.e_cap;
+    C.r_on = ff.map_r_on;
+    C.r_off = ff.map_r_off;
+    C.ox = g.origin[0];
+    C.oy = g.origin[1];
+    C.oz = g.origin[2];
+    C.h = g.spacing;
+    C.nx = g.n[0];
+    C.ny = g.n[1];
+    C.nz = g.n[2];
+    const long npt = (long)g.n[0] * g.n[1] * g.n[2];
+    k_maps_build<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(C, nrec, rec_xyzq, rec_type, maps_out);
+    return cudaGetLastError();
+}
+
+__global__ void k_pack_maps(const float* __restrict__ maps, long npt, float4* __restrict__ packed)
+{
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npt) return;
+    const float e = maps[ADG_MAP_ELEC * npt + i], d = maps[ADG_MAP_DESOLV * npt + i];
+#pragma unroll
+    for (int t = 0; t < ADG_NTYPES; ++t) packed[t * npt + i] = make_float4(maps[t * npt + i], e, d, 0.f);
+}
+
+cudaError_t launch_pack_maps(cudaStream_t st, const float* maps, const adg_grid_desc& g, float4* packed)
+{
+    const long npt = (long)g.n[0] * g.n[1] * g.n[2];
+    k_pack_maps<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(maps, npt, packed);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ warp scoring
+struct WarpSmem {
+    float4 xyz[kMaxAtoms];                         // posed coordinates
+    float fx[kMaxAtoms], fy[kMaxAtoms], fz[kMaxAtoms];  // intramolecular forces
+    float genes[32];                               // current genotype
+    float cand[32];                                // trial genotype
+    float best[32];                                // best genotype of a local search
+    float cs[kMaxTors], sn[kMaxTors];              // cos / sin of the torsion genes
+};
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+    return v;
+}
+
+// Genotype g (shared memory, 7+T floats) -> posed coordinates in ws.xyz.
+// Torsions deepest first about their reference axes (Rodrigues), then
+// x' = R(q/|q|) (x - c) + t.
+template <int APL>
+__device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, WarpSmem& ws, int lane)
+{
+    const int N = L->natoms, T = L->ntors;
+    if (lane < T) {
+        float s, c;
+        sincosf(g[7 + L->gene_of[lane]], &s, &c);
+        ws.sn[lane] = s;
+        ws.cs[lane] = c;
+    }
+    float qw = g[3], qx = g[4], qy = g[5], qz = g[6];
+    const float qi = 1.f / sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    qw *= qi; qx *= qi; qy *= qi; qz *= qi;
+    const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
+    const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
+    const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
+    const float tx = g[0], ty = g[1], tz = g[2];
+    const float cx = L->cx, cy = L->cy, cz = L->cz;
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < APL; ++j) {
+        const int a = lane + 32 * j;
+        if (a < N) {
+            const float4 r = L->ref[a];
+            float px = r.x, py = r.y, pz = r.z;
+            const uint32_t m = L->tmask[a];
+            for (int s = 0; s < T; ++s) {
+                if ((m >> s) & 1u) {
+                    const float4 o = L->tpt[s], u = L->tax[s];
+                    const float c = ws.cs[s], sn = ws.sn[s];
+                    const float vx = px - o.x, vy = py - o.y, vz = pz - o.z;
+                    const float kx = u.y * vz - u.z * vy, ky = u.z * vx - u.x * vz, kz = u.x * vy - u.y * vx;
+                    const float d = (u.x * vx + u.y * vy + u.z * vz) * (1.f - c);
+                    px = o.x + vx * c + kx * sn + u.x * d;
+                    py = o.y + vy * c + ky * sn + u.y * d;
+                    pz = o.z + vz * c + kz * sn + u.z * d;
+                }
+            }
+            const float dx = px - cx, dy = py - cy, dz = pz - cz;
+            ws.xyz[a] = make_float4(R00 * dx + R01 * dy + R02 * dz + tx, R10 * dx + R11 * dy + R12 * dz + ty,
+                                    R20 * dx + R21 * dy + R22 * dz + tz, 0.f);
+        }
+    }
+    __syncwarp();
+}
+
+// Intermolecular energy of one atom: trilinear interpolation of
+// M_t + q M_e + |q| M_d at the point clamped into the box, plus k_out d^2
+// outside it; gradient accumulated into (gx, gy, gz).
+template <bool GRAD>
+__device__ __forceinline__ float atom_inter(const MapsDev& M, float k_out, int t, float q, float x, float y, float z,
+                                            float& gx, float& gy, float& gz)
+{
+    float pen = 0.f, pgx = 0.f, pgy = 0.f, pgz = 0.f;
+    bool clx = false, cly = false, clz = false;
+    float xc = x, yc = y, zc = z;
+    if (x < M.ox) { pen += (M.ox - x) * (M.ox - x); pgx = 2.f * k_out * (x - M.ox); xc = M.ox; clx = true; }
+    if (x > M.hx) { pen += (x - M.hx) * (x - M.hx); pgx = 2.f * k_out * (x - M.hx); xc = M.hx; clx = true; }
+    if (y < M.oy) { pen += (M.oy - y) * (M.oy - y); pgy = 2.f * k_out * (y - M.oy); yc = M.oy; cly = true; }
+    if (y > M.hy) { pen += (y - M.hy) * (y - M.hy); pgy = 2.f * k_out * (y - M.hy); yc = M.hy; cly = true; }
+    if (z < M.oz) { pen += (M.oz - z) * (M.oz - z); pgz = 2.f * k_out * (z - M.oz); zc = M.oz; clz = true; }
+    if (z > M.hz) { pen += (z - M.hz) * (z - M.hz); pgz = 2.f * k_out * (z - M.hz); zc = M.hz; clz = true; }
+    const float ux = (xc - M.ox) * M.inv_h, uy = (yc - M.oy) * M.inv_h, uz = (zc - M.oz) * M.inv_h;
+    int ix = min(max((int)floorf(ux), 0), M.nx - 2);
+    int iy = min(max((int)floorf(uy), 0), M.ny - 2);
+    int iz = min(max((int)floorf(uz), 0), M.nz - 2);
+    const float fx = ux - ix, fy = uy - iy, fz = uz - iz;
+    const long nxy = (long)M.nx * M.ny;
+    const float4* p = M.packed + (long)t * nxy * M.nz + (iz * nxy + (long)iy * M.nx + ix);
+    const float aq = fabsf(q);
+    const float4 c000 = __ldg(p), c100 = __ldg(p + 1), c010 = __ldg(p + M.nx), c110 = __ldg(p + M.nx + 1);
+    const float4 c001 = __ldg(p + nxy), c101 = __ldg(p + nxy + 1), c011 = __ldg(p + nxy + M.nx),
+                 c111 = __ldg(p + nxy + M.nx + 1);
+    const float v000 = c000.x + q * c000.y + aq * c000.z, v100 = c100.x + q * c100.y + aq * c100.z;
+    const float v010 = c010.x + q * c010.y + aq * c010.z, v110 = c110.x + q * c110.y + aq * c110.z;
+    const float v001 = c001.x + q * c001.y + aq * c001.z, v101 = c101.x + q * c101.y + aq * c101.z;
+    const float v011 = c011.x + q * c011.y + aq * c011.z, v111 = c111.x + q * c111.y + aq * c111.z;
+    const float a00 = v000 + fx * (v100 - v000), a10 = v010 + fx * (v110 - v010);
+    const float a01 = v001 + fx * (v101 - v001), a11 = v011 + fx * (v111 - v011);
+    const float b0 = a00 + fy * (a10 - a00), b1 = a01 + fy * (a11 - a01);
+    const float val = b0 + fz * (b1 - b0);
+    if (GRAD) {
+        const float dx0 = (v100 - v000) + fy * ((v110 - v010) - (v100 - v000));
+        const float dx1 = (v101 - v001) + fy * ((v111 - v011) - (v101 - v001));
+        const float dvx = dx0 + fz * (dx1 - dx0);
+        const float dvy = (a10 - a00) + fz * ((a11 - a01) - (a10 - a00));
+        const float dvz = b1 - b0;
+        gx += (clx ? 0.f : dvx * M.inv_h) + pgx;
+        gy += (cly ? 0.f : dvy * M.inv_h) + pgy;
+        gz += (clz ? 0.f : dvz * M.inv_h) + pgz;
+    }
+    return val + k_out * pen;
+}
+
+struct ScoreOut {
+    float e;         // total energy (all lanes)
+    float gtan;      // lane d < 6+T: tangent gradient component d
+    float tx, ty, tz;  // torque (all lanes)
+};
+
+// Energy (and gradient) of the genotype in shared memory `g`.
+template <int APL, bool GRAD>
+__device__ ScoreOut warp_score(const LigandDev* __restrict__ L, const PairsDev& P, const MapsDev& M, const float* g,
+                               WarpSmem& ws, int lane)
+{
+    warp_pose<APL>(L, g, ws, lane);
+    const int N = L->natoms, T = L->ntors;
+    const float k_out = L->k_out;
+    float e = 0.f;
+    float fxr[APL], fyr[APL], fzr[APL];
+#pragma unroll
+    for (int j = 0; j < APL; ++j) {
+        fxr[j] = fyr[j] = fzr[j] = 0.f;
+        const int a = lane + 32 * j;
+        if (a < N) {
+            const float4 x = ws.xyz[a];
+            e += atom_inter<GRAD>(M, k_out, L->type[a], L->ref[a].w, x.x, x.y, x.z, fxr[j], fyr[j], fzr[j]);
+            if (GRAD) ws.fx[a] = ws.fy[a] = ws.fz[a] = 0.f;
+        }
+    }
+    if (GRAD) __syncwarp();
+    // intramolecular pairs
+    const float cap = L->e_cap, rmin2 = L->rmin2, msA = L->ms_A, msB = L->ms_B, msk = L->ms_k, mslb = L->ms_lb;
+    const float inv_2s2 = L->inv_2s2, inv_s2 = L->inv_s2;
+    for (int stp = 0; stp < L->nsteps; ++stp) {
+        const int idx = stp * 32 + lane;
+        const int ij = __ldg(P.ij + idx);
+        if (ij < 0) continue;
+        const int i = ij & 0xffff, j = ij >> 16;
+        const float4 xi = ws.xyz[i], xj = ws.xyz[j];
+        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+        const float r2 = dx * dx + dy * dy + dz * dz;
+        const float4 c = __ldg(P.coef + idx);
+        const float cd = __ldg(P.cd + idx);
+        const bool fl = r2 < rmin2;
+        const float rr2 = fl ? rmin2 : r2;
+        const float ri = rsqrtf(rr2);
+        const float r = rr2 * ri;
+        const float ri2 = ri * ri;
+        const float ri6 = ri2 * ri2 * ri2, ri12 = ri6 * ri6, ri10 = ri6 * ri2 * ri2;
+        float elj = c.x * ri12 - c.y * ri6 - c.z * ri10;
+        const float ex = __expf(-mslb * r);
+        const float den = 1.f + msk * ex;
+        const float D = msA * den + msB;   // eps(r) = D / den
+        const float rD = __fdividef(1.f, D);
+        const float eel = c.w * den * ri * rD;
+        const float gs = __expf(-rr2 * inv_2s2);
+        const float eds = cd * gs;
+        if (GRAD) {
+            float dlj = (-12.f * c.x * ri12 + 6.f * c.y * ri6 + 10.f * c.z * ri10) * ri2;  // (dE/dr) / r
+            if (elj > cap) dlj = 0.f;
+            const float dden = -mslb * msk * ex;
+            const float deel = c.w * (dden * rD * ri - den * rD * rD * ri * ri * (msA * dden * r + D)) * ri;
+            const float dds = -eds * inv_s2;
+            const float fs = fl ? 0.f : (dlj + deel + dds);
+            atomicAdd(&ws.fx[i], fs * dx);
+            atomicAdd(&ws.fy[i], fs * dy);
+            atomicAdd(&ws.fz[i], fs * dz);
+            atomicAdd(&ws.fx[j], -fs * dx);
+            atomicAdd(&ws.fy[j], -fs * dy);
+            atomicAdd(&ws.fz[j], -fs * dz);
+        }
+        e += fminf(elj, cap) + eel + eds;
+    }
+    ScoreOut out;
+    out.e = warp_sum(e);
+    out.gtan = 0.f;
+    out.tx = out.ty = out.tz = 0.f;
+    if (!GRAD) return out;
+    __syncwarp();
+    const float tx = g[0], ty = g[1], tz = g[2];
+    float sgx = 0.f, sgy = 0.f, sgz = 0.f, stx = 0.f, sty = 0.f, stz = 0.f;
+#pragma unroll
+    for (int j = 0; j < APL; ++j) {
+        const int a = lane + 32 * j;
+        if (a < N) {
+            fxr[j] += ws.fx[a];
+            fyr[j] += ws.fy[a];
+            fzr[j] += ws.fz[a];
+            const float4 x = ws.xyz[a];
+            const float rx = x.x - tx, ry = x.y - ty, rz = x.z - tz;
+            sgx += fxr[j]; sgy += fyr[j]; sgz += fzr[j];
+            stx += ry * fzr[j] - rz * fyr[j];
+            sty += rz * fxr[j] - rx * fzr[j];
+            stz += rx * fyr[j] - ry * fxr[j];
+        }
+    }
+    sgx = warp_sum(sgx); sgy = warp_sum(sgy); sgz = warp_sum(sgz);
+    stx = warp_sum(stx); sty = warp_sum(sty); stz = warp_sum(stz);
+    float mine = lane == 0 ? sgx : lane == 1 ? sgy : lane == 2 ? sgz : lane == 3 ? stx : lane == 4 ? sty : stz;
+    for (int s = 0; s < T; ++s) {
+        const float4 xa = ws.xyz[L->ta[s]], xb = ws.xyz[L->tb[s]];
+        float ux = xb.x - xa.x, uy = xb.y - xa.y, uz = xb.z - xa.z;
+        const float un = rsqrtf(ux * ux + uy * uy + uz * uz);
+        ux *= un; uy *= un; uz *= un;
+        float cs = 0.f;
+#pragma unroll
+        for (int j = 0; j < APL; ++j) {
+            const int a = lane + 32 * j;
+            if (a < N && ((L->tmask[a] >> s) & 1u)) {
+                const float4 x = ws.xyz[a];
+                const float vx = x.x - xa.x, vy = x.y - xa.y, vz = x.z - xa.z;
+                cs += (uy * vz - uz * vy) * fxr[j] + (uz * vx - ux * vz) * fyr[j] + (ux * vy - uy * vx) * fzr[j];
+            }
+        }
+        cs = warp_sum(cs);
+        if (lane == 6 + L->gene_of[s]) mine = cs;
+    }
+    out.gtan = lane < 6 + T ? mine : 0.f;
+    out.tx = stx;
+    out.ty = sty;
+    out.tz = stz;
+    return out;
+}
+
+// ------------------------------------------------------------------ score / pose API kernels
+template <int APL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_score(MapsDev M, LigandRef LR, const float* __restrict__ genes,
+                                                               int npose, float* __restrict__ energy,
+                                                               float* __restrict__ grad, int grad_kind)
+{
+    __shared__ WarpSmem smem[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long pose = (long)blockIdx.x * kWarpsPerBlock + w;
+    if (pose >= npose) return;
+    WarpSmem& ws = smem[w];
+    const LigandDev* L = LR.hdr;
+    const int T = L->ntors, G = 7 + T, D = 6 + T;
+    if (lane < G) ws.genes[lane] = genes[pose * G + lane];
+    __syncwarp();
+    if (grad_kind == ADG_GRAD_NONE) {
+        ScoreOut o = warp_score<APL, false>(L, LR.pairs, M, ws.genes, ws, lane);
+        if (lane == 0) energy[pose] = o.e;
+        return;
+    }
+    ScoreOut o = warp_score<APL, true>(L, LR.pairs, M, ws.genes, ws, lane);
+    if (lane == 0) energy[pose] = o.e;
+    if (grad_kind == ADG_GRAD_TANGENT) {
+        if (lane < D) grad[pose * D + lane] = o.gtan;
+        return;
+    }
+    // gene gradient: t and theta from the tangent gradient, q by the chain rule
+    // dE/dq = 2 (-tau.v, w tau + tau x v) / |q| with q/|q| = (w, v).
+    const float prev = __shfl_sync(FULL_MASK, o.gtan, lane > 0 ? lane - 1 : 0);
+    float val = 0.f;
+    if (lane < 3) val = o.gtan;
+    else if (lane < 7) {
+        float qw = ws.genes[3], qx = ws.genes[4], qy = ws.genes[5], qz = ws.genes[6];
+        const float qn = sqrtf(qw * qw + qx * qx + qy * qy + qz * qz), iq = 1.f / qn;
+        qw *= iq; qx *= iq; qy *= iq; qz *= iq;
+        const float tx = o.tx, ty = o.ty, tz = o.tz;
+        if (lane == 3) val = -2.f * (tx * qx + ty * qy + tz * qz) * iq;
+        else if (lane == 4) val = 2.f * (qw * tx + (ty * qz - tz * qy)) * iq;
+        else if (lane == 5) val = 2.f * (qw * ty + (tz * qx - tx * qz)) * iq;
+        else val = 2.f * (qw * tz + (tx * qy - ty * qx)) * iq;
+    } else if (lane < G) val = prev;
+    if (lane < G) grad[pose * G + lane] = val;
+}
+
+cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, int apl, const float* genes, int npose,
+                         float* energy, float* grad, int grad_kind)
+{
+    if (npose <= 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((npose + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (apl <= 1) k_score<1><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, l, genes, npose, energy, grad, grad_kind);
+    else if (apl == 2) k_score<2><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, l, genes, npose, energy, grad, grad_kind);
+    else k_score<4><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, l, genes, npose, energy, grad, grad_kind);
+    return cudaGetLastError();
+}
+
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_pose(LigandRef LR, const float* __restrict__ genes, int npose,
+                                                              float* __restrict__ xyz)
+{
+    __shared__ WarpSmem smem[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long pose = (long)blockIdx.x * kWarpsPerBlock + w;
+    if (pose >= npose) return;
+    WarpSmem& ws = smem[w];
+    const LigandDev* L = LR.hdr;
+    const int G = 7 + L->ntors, N = L->natoms;
+    if (lane < G) ws.genes[lane] = genes[pose * G + lane];
+    __syncwarp();
+    warp_pose<4>(L, ws.genes, ws, lane);
+    for (int a = lane; a < N; a += 32) {
+        const float4 x = ws.xyz[a];
+        xyz[(pose * N + a) * 3 + 0] = x.x;
+        xyz[(pose * N + a) * 3 + 1] = x.y;
+        xyz[(pose * N + a) * 3 + 2] = x.z;
+    }
+}
+
+cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const float* genes, int npose, float* xyz)
+{
+    if (npose <= 0) return cudaSuccess;
+    k_pose<<<(unsigned)((npose + kWarpsPerBlock - 1) / kWarpsPerBlock), kWarpsPerBlock * 32, 0, st>>>(l, genes, npose,
+                                                                                                      xyz);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ moves
+// Unit quaternion of the rotation vector w (angle |w| about w/|w|).
+__device__ __forceinline__ float4 quat_from_rotvec(float wx, float wy, float wz)
+{
+    const float ang = sqrtf(wx * wx + wy * wy + wz * wz);
+    if (ang < 1e-12f) return make_float4(1.f, 0.5f * wx, 0.5f * wy, 0.5f * wz);
+    float s, c;
+    sincosf(0.5f * ang, &s, &c);
+    s /= ang;
+    return make_float4(c, s * wx, s * wy, s * wz);  // (w, x, y, z)
+}
+
+// a (x) b for quaternions stored (w, x, y, z).
+__device__ __forceinline__ float4 quat_mul(float4 a, float4 b)
+{
+    return make_float4(a.x * b.x - a.y * b.y - a.z * b.z - a.w * b.w, a.x * b.y + b.x * a.y + a.z * b.w - a.w * b.z,
+                       a.x * b.z + b.x * a.z + a.w * b.y - a.y * b.w, a.x * b.w + b.x * a.w + a.y * b.z - a.z * b.y);
+}
+
+__device__ __forceinline__ float4 quat_normalise(float4 q)
+{
+    const float in = 1.f / sqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    return make_float4(q.x * in, q.y * in, q.z * in, q.w * in);
+}
+
+// out = x (+) sign*xi, xi distributed over lanes (lane d holds tangent component d):
+// t += xi_t; q <- exp(xi_w) (x) q, normalised; theta += xi_theta.
+__device__ __forceinline__ void warp_step(const float* x, float* out, float xi, float sign, int T, int lane)
+{
+    const float w0 = __shfl_sync(FULL_MASK, xi, 3), w1 = __shfl_sync(FULL_MASK, xi, 4),
+                w2 = __shfl_sync(FULL_MASK, xi, 5);
+    const float prev = __shfl_sync(FULL_MASK, xi, lane > 0 ? lane - 1 : 0);
+    if (lane < 3) {
+        out[lane] = x[lane] + sign * xi;
+    } else if (lane < 7) {
+        const float4 dq = quat_from_rotvec(sign * w0, sign * w1, sign * w2);
+        const float4 nq = quat_normalise(quat_mul(dq, make_float4(x[3], x[4], x[5], x[6])));
+        out[lane] = lane == 3 ? nq.x : lane == 4 ? nq.y : lane == 5 ? nq.z : nq.w;
+    } else if (lane < 7 + T) {
+        out[lane] = x[lane] + sign * prev;
+    }
+    __syncwarp();
+}
+
+// Box-Muller Gaussian of tangent dimension d, Solis-Wets iteration `it`.
+__device__ __forceinline__ float ls_gauss(const Rng& r, int it, int d)
+{
+    const uint4 w = r.block(P_LS, it * 8 + d / 4);
+    const int p = (d / 2) % 2;
+    const uint32_t a = p ? w.z : w.x, b = p ? w.w : w.y;
+    const float u1 = u01_open0(a), u2 = u01(b);
+    const float rad = sqrtf(-2.f * logf(u1));
+    float s, c;
+    sincospif(2.f * u2, &s, &c);
+    return (d & 1) ? rad * s : rad * c;
+}
+
+// Solis & Wets (1981) adaptive random search on the genotype in ws.genes.
+template <int APL>
+__device__ int warp_solis_wets(const LigandDev* L, const PairsDev& P, const MapsDev& M, const SearchDev& S,
+                               const Rng& rng, WarpSmem& ws, float& e, int lane)
+{
+    const int T = L->ntors, D = 6 + T;
+    const float scale = lane < 3 ? S.sw_scale_t : (lane < 6 ? S.sw_scale_rot : S.sw_scale_tors);
+    float bias = 0.f, rho = S.sw_rho0;
+    int succ = 0, fail = 0, nev = 0;
+    for (int it = 0; it < S.ls_max_iters && rho >= S.sw_rho_min; ++it) {
+        const float xi = lane < D ? bias + rho * scale * ls_gauss(rng, it, lane) : 0.f;
+        warp_step(ws.genes, ws.cand, xi, 1.f, T, lane);
+        const float e1 = warp_score<APL, false>(L, P, M, ws.cand, ws, lane).e;
+        ++nev;
+        if (e1 < e) {
+            if (lane < 7 + T) ws.genes[lane] = ws.cand[lane];
+            e = e1;
+            bias = 0.4f * xi + 0.2f * bias;
+            ++succ;
+            fail = 0;
+        } else {
+            warp_step(ws.genes, ws.cand, xi, -1.f, T, lane);
+            const float e2 = warp_score<APL, false>(L, P, M, ws.cand, ws, lane).e;
+            ++nev;
+            if (e2 < e) {
+                if (lane < 7 + T) ws.genes[lane] = ws.cand[lane];
+                e = e2;
+                bias = bias - 0.4f * xi;
+                ++succ;
+                fail = 0;
+            } else {
+                bias *= 0.5f;
+                ++fail;
+                succ = 0;
+            }
+        }
+        __syncwarp();
+        if (succ >= S.sw_succ) { rho *= S.sw_expand; succ = 0; }
+        if (fail >= S.sw_fail) { rho *= S.sw_contract; fail = 0; }
+    }
+    return nev;
+}
+
+// ADADELTA (Zeiler 2012) in the tangent space; keeps the best genotype seen.
+template <int APL>
+__device__ int warp_adadelta(const LigandDev* L, const PairsDev& P, const MapsDev& M, const SearchDev& S, WarpSmem& ws,
+                             float& e, int lane)
+{
+    const int T = L->ntors, G = 7 + T;
+    float eg2 = 0.f, edx2 = 0.f, ebest = e;
+    if (lane < G) ws.best[lane] = ws.genes[lane];
+    __syncwarp();
+    for (int it = 0; it < S.ls_max_iters; ++it) {
+        const ScoreOut o = warp_score<APL, true>(L, P, M, ws.genes, ws, lane);
+        if (o.e < ebest) {
+            ebest = o.e;
+            if (lane < G) ws.best[lane] = ws.genes[lane];
+        }
+        const float gd = o.gtan;
+        eg2 = S.ad_rho * eg2 + (1.f - S.ad_rho) * gd * gd;
+        const float dx = -sqrtf(edx2 + S.ad_eps) / sqrtf(eg2 + S.ad_eps) * gd;
+        edx2 = S.ad_rho * edx2 + (1.f - S.ad_rho) * dx * dx;
+        warp_step(ws.genes, ws.cand, dx, 1.f, T, lane);
+        if (lane < G) ws.genes[lane] = ws.cand[lane];
+        __syncwarp();
+    }
+    if (lane < G) ws.genes[lane] = ws.best[lane];
+    __syncwarp();
+    e = ebest;
+    return S.ls_max_iters;
+}
+
+// ------------------------------------------------------------------ LGA kernels
+__device__ __forceinline__ void warp_argmin(float& v, int& i)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        const float ov = __shfl_xor_sync(FULL_MASK, v, o);
+        const int oi = __shfl_xor_sync(FULL_MASK, i, o);
+        if (ov < v || (ov == v && oi < i)) {
+            v = ov;
+            i = oi;
+        }
+    }
+}
+
+__device__ __forceinline__ int tournament(const float* Pe, int pop, uint32_t wa, uint32_t wb, uint32_t wwin, uint32_t thr)
+{
+    const int a = uindex(wa, pop), b = uindex(wb, pop);
+    const float ea = Pe[a], eb = Pe[b];
+    int better, worse;
+    if (ea < eb || (ea == eb && a <= b)) { better = a; worse = b; }
+    else { better = b; worse = a; }
+    return ptest(wwin, thr) ? better : worse;
+}
+
+// Generation 0: random genotypes (t uniform in the box, q uniform on S^3 by
+// Shoemake's three uniforms, theta uniform in [-pi, pi)), evaluated.
+template <int APL>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_init(MapsDev M, SearchDev S, DockDev Dk)
+{
+    __shared__ WarpSmem smem[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long gw = (long)blockIdx.x * kWarpsPerBlock + w;
+    const long nruns = (long)Dk.nlig * S.nrun;
+    if (gw >= nruns * S.pop) return;
+    WarpSmem& ws = smem[w];
+    const int run_g = (int)(gw / S.pop), ind = (int)(gw % S.pop);
+    const int lig = run_g / S.nrun, run = run_g % S.nrun;
+    const LigandRef LR = Dk.ligs[lig];
+    const LigandDev* L = LR.hdr;
+    const int T = L->ntors, G = 7 + T;
+    const Rng rng{S.key0, S.key1, Dk.lig_id[lig], (uint32_t)run, (uint32_t)ind, 0u};
+    float v = 0.f;
+    if (lane < 3) {
+        const uint4 wd = rng.block(P_INIT, 0);
+        const float lo = lane == 0 ? M.ox : lane == 1 ? M.oy : M.oz;
+        const float hi = lane == 0 ? M.hx : lane == 1 ? M.hy : M.hz;
+        v = lo + u01(word(wd, lane)) * (hi - lo);
+    } else if (lane < 7) {
+        const uint4 wd = rng.block(P_INIT, 1);
+        const float u1 = u01(wd.x), u2 = u01(wd.y), u3 = u01(wd.z);
+        const float s1 = sqrtf(1.f - u1), s2 = sqrtf(u1);
+        float sa, ca, sb, cb;
+        sincospif(2.f * u2, &sa, &ca);
+        sincospif(2.f * u3, &sb, &cb);
+        v = lane == 3 ? s2 * cb : lane == 4 ? s1 * sa : lane == 5 ? s1 * ca : s2 * sb;
+    } else if (lane < G) {
+        const int k = lane - 7;
+        const uint4 wd = rng.block(P_INIT, 2 + k / 4);
+        v = -3.14159265358979f + 6.28318530717959f * u01(word(wd, k % 4));
+    }
+    if (lane < G) ws.genes[lane] = v;
+    __syncwarp();
+    const float e = warp_score<APL, false>(L, LR.pairs, M, ws.genes, ws, lane).e;
+    float* pg = Dk.pop_genes[0] + ((long)run_g * S.pop + ind) * kGeneStride;
+    if (lane < G) pg[lane] = v;
+    if (lane == 0) {
+        Dk.pop_e[0][(long)run_g * S.pop + ind] = e;
+        atomicAdd(&Dk.evals[run_g], 1ull);
+    }
+}
+
+// Accumulated per-generation evaluation counts live in evals[nruns + run]
+// until k_dock_bookkeep folds them in, so every warp of a generation sees
+// the same total when it decides whether its run is still active.
+template <int APL, int LS>
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_generation(MapsDev M, SearchDev S, DockDev Dk, int gen)
+{
+    __shared__ WarpSmem smem[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long gw = (long)blockIdx.x * kWarpsPerBlock + w;
+    const long nruns = (long)Dk.nlig * S.nrun;
+    if (gw >= nruns * S.pop) return;
+    const int run_g = (int)(gw / S.pop), ind = (int)(gw % S.pop);
+    if (Dk.evals[run_g] >= (unsigned long long)S.nev || gen > S.max_gen) return;
+    WarpSmem& ws = smem[w];
+    const int lig = run_g / S.nrun, run = run_g % S.nrun;
+    const LigandRef LR = Dk.ligs[lig];
+    const LigandDev* L = LR.hdr;
+    const int T = L->ntors, G = 7 + T, nb = 2 + T, pop = S.pop;
+    const Rng rng{S.key0, S.key1, Dk.lig_id[lig], (uint32_t)run, (uint32_t)ind, (uint32_t)gen};
+    const float* Pg = Dk.pop_genes[(gen - 1) & 1] + (long)run_g * pop * kGeneStride;
+    const float* Pe = Dk.pop_e[(gen - 1) & 1] + (long)run_g * pop;
+
+    // elite = argmin of the previous population (ties to the lower index)
+    float bv = INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < pop; i += 32) {
+        const float v = Pe[i];
+        if (v < bv) { bv = v; bi = i; }
+    }
+    warp_argmin(bv, bi);
+    if (bi >= pop) bi = 0;  // only when every energy is NaN
+
+    float child = 0.f, e;
+    int p1, p2, lo = -1, hi = -1, mmask = 0, nev = 0;
+    if (ind < S.elitism) {
+        p1 = p2 = bi;
+        if (lane < G) child = Pg[(long)bi * kGeneStride + lane];
+        e = bv;
+        if (lane < G) ws.genes[lane] = child;
+        __syncwarp();
+    } else {
+        const uint4 w0 = rng.block(P_SELECT, 0), w1 = rng.block(P_SELECT, 1), w2 = rng.block(P_SELECT, 2);
+        p1 = tournament(Pe, pop, w0.x, w0.y, w0.z, S.thr_tour);
+        p2 = tournament(Pe, pop, w1.x, w1.y, w1.z, S.thr_tour);
+        if (ptest(w2.x, S.thr_cross)) {
+            const int c1 = uindex(w2.y, nb + 1), c2 = uindex(w2.z, nb + 1);
+            lo = min(c1, c2);
+            hi = max(c1, c2);
+        }
+        const int b = lane < 3 ? 0 : (lane < 7 ? 1 : 2 + (lane - 7));
+        const int src = (b >= lo && b < hi) ? p2 : p1;
+        if (lane < G) child = Pg[(long)src * kGeneStride + lane];
+        bool mut = false;
+        if (lane < G) mut = ptest(word(rng.block(P_SELECT, 3 + b / 4), b % 4), S.thr_mut);
+        const bool first = lane == 0 || lane == 3 || (lane >= 7 && lane < G);
+        const unsigned bal = __ballot_sync(FULL_MASK, mut && first);
+        mmask = (int)((bal & 1u) | (((bal >> 3) & 1u) << 1) | ((bal >> 7) << 2));
+        if (mut && lane < 3) child += S.mut_t * (2.f * u01(word(rng.block(P_MUTATE, 0), lane)) - 1.f);
+        if (mut && lane >= 7 && lane < G) child += S.mut_tors * (2.f * u01(rng.block(P_MUTATE, b).x) - 1.f);
+        const float q0 = __shfl_sync(FULL_MASK, child, 3), q1 = __shfl_sync(FULL_MASK, child, 4),
+                    q2 = __shfl_sync(FULL_MASK, child, 5), q3 = __shfl_sync(FULL_MASK, child, 6);
+        if ((mmask & 2) && lane >= 3 && lane < 7) {
+            const uint4 wm = rng.block(P_MUTATE, 1);
+            const float z = 2.f * u01(wm.x) - 1.f;
+            float sp, cp;
+            sincospif(2.f * u01(wm.y), &sp, &cp);
+            const float s = sqrtf(1.f - z * z);
+            const float ang = S.mut_rot * (2.f * u01(wm.z) - 1.f);
+            const float4 dq = quat_from_rotvec(ang * s * cp, ang * s * sp, ang * z);
+            const float4 nq = quat_normalise(quat_mul(dq, make_float4(q0, q1, q2, q3)));
+            child = lane == 3 ? nq.x : lane == 4 ? nq.y : lane == 5 ? nq.z : nq.w;
+        }
+        if (lane < G) ws.genes[lane] = child;
+        __syncwarp();
+        e = warp_score<APL, false>(L, LR.pairs, M, ws.genes, ws, lane).e;
+        nev = 1;
+    }
+    // local search on this individual with probability ls_rate (Lamarckian write-back)
+    int ls_applied = 0;
+    if (LS != ADG_LS_NONE && ptest(rng.block(P_LSPICK, 0).x, S.thr_ls)) {
+        ls_applied = 1;
+        if (LS == ADG_LS_SOLIS_WETS) nev += warp_solis_wets<APL>(L, LR.pairs, M, S, rng, ws, e, lane);
+        else nev += warp_adadelta<APL>(L, LR.pairs, M, S, ws, e, lane);
+    }
+    float* Ng = Dk.pop_genes[gen & 1] + ((long)run_g * pop + ind) * kGeneStride;
+    if (lane < G) Ng[lane] = ws.genes[lane];
+    if (lane == 0) {
+        Dk.pop_e[gen & 1][(long)run_g * pop + ind] = e;
+        atomicAdd(&Dk.evals[nruns + run_g], (unsigned long long)nev);
+    }
+    if (Dk.trace_ngen > 0 && gen <= Dk.trace_ngen && lig == 0) {
+        const long slot = ((long)run * Dk.trace_ngen + (gen - 1)) * pop + ind;
+        if (lane == 0) {
+            int* d = Dk.tr_dec + slot * 8;
+            d[0] = p1; d[1] = p2; d[2] = lo; d[3] = hi; d[4] = mmask; d[5] = ls_applied; d[6] = 0; d[7] = 0;
+            Dk.tr_e[slot] = e;
+        }
+        if (lane < G) Dk.tr_genes[slot * kGeneStride + lane] = ws.genes[lane];
+    }
+}
+
+// One thread per run: fold the generation's evaluations into the total,
+// record the last completed generation, count runs active for gen+1.
+__global__ void k_dock_bookkeep(SearchDev S, DockDev Dk, int gen, int* active)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nruns = Dk.nlig * S.nrun;
+    if (r >= nruns) return;
+    const unsigned long long nev = (unsigned long long)S.nev;
+    if (Dk.evals[r] < nev && gen <= S.max_gen) {
+        Dk.evals[r] += Dk.evals[nruns + r];
+        Dk.evals[nruns + r] = 0ull;
+        Dk.gen_done[r] = gen;
+    }
+    if (Dk.evals[r] < nev && gen + 1 <= S.max_gen) atomicAdd(active, 1);
+}
+
+template <int APL, int LS>
+static void gen_launch(cudaStream_t st, unsigned blocks, const MapsDev& m, const SearchDev& s, const DockDev& d, int gen)
+{
+    k_dock_generation<APL, LS><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, s, d, gen);
+}
+
+cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, int apl)
+{
+    const long nw = (long)d.nlig * s.nrun * s.pop;
+    const unsigned blocks = (unsigned)((nw + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    if (apl <= 1) k_dock_init<1><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, s, d);
+    else if (apl == 2) k_dock_init<2><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, s, d);
+    else k_dock_init<4><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, s, d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dock_generation(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, int apl,
+                                   int gen)
+{
+    const long nw = (long)d.nlig * s.nrun * s.pop;
+    const unsigned blocks = (unsigned)((nw + kWarpsPerBlock - 1) / kWarpsPerBlock);
+#define ADG_GEN(A)                                                                         \
+    if (s.ls_method == ADG_LS_SOLIS_WETS) gen_launch<A, ADG_LS_SOLIS_WETS>(st, blocks, m, s, d, gen); \
+    else if (s.ls_method == ADG_LS_ADADELTA) gen_launch<A, ADG_LS_ADADELTA>(st, blocks, m, s, d, gen); \
+    else gen_launch<A, ADG_LS_NONE>(st, blocks, m, s, d, gen);
+    if (apl <= 1) { ADG_GEN(1) }
+    else if (apl == 2) { ADG_GEN(2) }
+    else { ADG_GEN(4) }
+#undef ADG_GEN
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const DockDev& d, int gen, int* active)
+{
+    const int nruns = d.nlig * s.nrun;
+    k_dock_bookkeep<<<(nruns + 127) / 128, 128, 0, st>>>(s, d, gen, active);
+    return cudaGetLastError();
+}
+
+// Per run: best genotype of the final population and its posed coordinates.
+__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_finalize(MapsDev M, SearchDev S, DockDev Dk,
+                                                                       ResultDev* __restrict__ out)
+{
+    __shared__ WarpSmem smem[kWarpsPerBlock];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int run_g = blockIdx.x * kWarpsPerBlock + w;
+    const int nruns = Dk.nlig * S.nrun;
+    if (run_g >= nruns) return;
+    WarpSmem& ws = smem[w];
+    const int lig = run_g / S.nrun;
+    const LigandDev* L = Dk.ligs[lig].hdr;
+    const int G = 7 + L->ntors, N = L->natoms, gd = Dk.gen_done[run_g];
+    const float* Pg = Dk.pop_genes[gd & 1] + (long)run_g * S.pop * kGeneStride;
+    const float* Pe = Dk.pop_e[gd & 1] + (long)run_g * S.pop;
+    float bv = INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < S.pop; i += 32) {
+        const float v = Pe[i];
+        if (v < bv) { bv = v; bi = i; }
+    }
+    warp_argmin(bv, bi);
+    if (bi >= S.pop) bi = 0;  // only when every energy is NaN
+    if (lane < G) ws.genes[lane] = Pg[(long)bi * kGeneStride + lane];
+    __syncwarp();
+    warp_pose<4>(L, ws.genes, ws, lane);
+    ResultDev& R = out[run_g];
+    if (lane == 0) {
+        R.best_energy = bv;
+        R.generations = gd;
+        R.evals = (long long)Dk.evals[run_g];
+    }
+    if (lane < kGeneStride) R.genes[lane] = lane < G ? ws.genes[lane] : 0.f;
+    for (int a = lane; a < N; a += 32) {
+        const float4 x = ws.xyz[a];
+        R.xyz[3 * a] = x.x;
+        R.xyz[3 * a + 1] = x.y;
+        R.xyz[3 * a + 2] = x.z;
+    }
+}
+
+cudaError_t launch_dock_finalize(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, ResultDev* out)
+{
+    const int nruns = d.nlig * s.nrun;
+    k_dock_finalize<<<(nruns + kWarpsPerBlock - 1) / kWarpsPerBlock, kWarpsPerBlock * 32, 0, st>>>(m, s, d, out);
+    return cudaGetLastError();
+}
+
+}  // namespace adg
