@@ -40,6 +40,7 @@ extern "C" {
 #define ADG_MAX_ATOMS 128
 #define ADG_MAX_TORS 16
 #define ADG_MAX_GENES (7 + ADG_MAX_TORS)
+#define ADG_TRACE_WIDTH 12    /* int32 words per offspring in adg_dock_trace.decisions */
 
 enum {
     ADG_OK = 0,
@@ -138,9 +139,10 @@ typedef struct {
 
 /* Optional record of the first `ngen` generations of a one-ligand dock, for
  * replaying the GA decisions.  All arrays are host memory, caller-allocated:
- *   decisions [nrun][ngen][pop][8] int32: parent1, parent2, crossover lo,
+ *   decisions [nrun][ngen][pop][12] int32: parent1, parent2, crossover lo,
  *             crossover hi (-1 when no crossover), mutation block mask,
- *             local search applied, 0, 0
+ *             local search applied, tournament candidates a1, b1, a2, b2
+ *             (-1 for the elite slot), 0, 0
  *   genes     [nrun][ngen][pop][7+T] population after each generation
  *   energies  [nrun][ngen][pop]
  *   init_genes[nrun][pop][7+T] and init_energies[nrun][pop]: generation 0.

@@ -72,8 +72,12 @@ class PARAMS(C.Structure):
                [("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("lig_id", C.c_uint32)]
 
 
+TRACE_WIDTH = 12  # parent1, parent2, xlo, xhi, mut_mask, ls_applied, a1, b1, a2, b2, 0, 0
+
+
 class TRACE(C.Structure):
-    _fields_ = [(n, C.c_int32) for n in ("parent1", "parent2", "xlo", "xhi", "mut_mask", "ls_applied", "pad0", "pad1")]
+    _fields_ = [(n, C.c_int32) for n in ("parent1", "parent2", "xlo", "xhi", "mut_mask", "ls_applied",
+                                         "a1", "b1", "a2", "b2", "pad0", "pad1")]
 
 
 class RUNRES(C.Structure):
@@ -114,6 +118,7 @@ def _declare(L):
     L.orc_quat_to_matrix.argtypes = [_d, _d]
     L.orc_pose_batch.argtypes = [_vp, _d, C.c_int, _d]
     L.orc_score_batch.argtypes = [C.POINTER(FF), C.POINTER(GRID), _d, _vp, _d, C.c_int, _d, _d, _d, _d]
+    L.orc_atom_gradients.argtypes = [C.POINTER(FF), C.POINTER(GRID), _d, _vp, _d, C.c_int, _d]
     L.orc_apply_step.argtypes = [C.c_int, _d, _d, C.c_double, _d]
     L.orc_local_search.argtypes = [C.POINTER(FF), C.POINTER(GRID), _d, _vp, C.POINTER(PARAMS), C.c_int,
                                    C.c_int, C.c_int, _d, C.POINTER(C.c_double)]
@@ -311,6 +316,15 @@ def score(ff, grid, maps, L: Ligand, genes: np.ndarray):
     return e, ei, gg, gt
 
 
+def atom_gradients(ff, grid, maps, L: Ligand, genes: np.ndarray) -> np.ndarray:
+    """dE/dx'_i per atom: [npose, natoms, 3]."""
+    genes = np.ascontiguousarray(np.atleast_2d(genes), np.float64)
+    out = np.zeros((genes.shape[0], L.natoms, 3))
+    lib().orc_atom_gradients(C.byref(make_ff(ff)), C.byref(make_grid(grid)),
+                             np.ascontiguousarray(maps, np.float64).reshape(-1), L.ptr, genes, genes.shape[0], out)
+    return out
+
+
 def apply_step(ntors, genes, xi, sign=1.0):
     out = np.zeros(7 + ntors)
     lib().orc_apply_step(ntors, np.ascontiguousarray(genes, np.float64), np.ascontiguousarray(xi, np.float64),
@@ -350,6 +364,6 @@ def lga_run(ff, grid, maps, L, params: SearchParams, run=0, ntrace=0):
         raise ValueError(f"oracle lga_run failed rc={rc}")
     trace = None
     if ntrace:
-        dec = np.frombuffer(tr, dtype=np.int32).reshape(ntrace, pop, 8).copy()
+        dec = np.frombuffer(tr, dtype=np.int32).reshape(ntrace, pop, TRACE_WIDTH).copy()
         trace = (dec, tg[:ntrace], te[:ntrace])
     return res.best_energy, np.array(res.best_genes[:G]), res.evals, res.generations, trace

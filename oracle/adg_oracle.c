@@ -648,6 +648,35 @@ int orc_score(const orc_ff* ff, const orc_grid* g, const double* maps, const orc
     return ORC_OK;
 }
 
+/* Per-atom gradients dE/dx'_i of npose genotypes -> forces[npose][natoms][3]
+ * (used by the tests to bound how FP32 rounding of the coordinates moves
+ * the energy). */
+void orc_atom_gradients(const orc_ff* ff, const orc_grid* g, const double* maps, const orc_ligand* L,
+                        const double* genes, int npose, double* forces)
+{
+    int n = L->natoms, G = 7 + L->ntors;
+    for (int p = 0; p < npose; ++p) {
+        double x[ORC_MAXATOMS * 3];
+        double* f = forces + (size_t)p * n * 3;
+        orc_pose(L, genes + (size_t)p * G, x);
+        for (int i = 0; i < n; ++i) atom_inter(ff, g, maps, L->type[i], L->q[i], x + 3 * i, f + 3 * i);
+        for (int q = 0; q < L->npairs; ++q) {
+            int i = L->pair_i[q], j = L->pair_j[q];
+            double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
+            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+            double d1, d2, d3;
+            orc_pair_lj(ff, L->type[i], L->type[j], r, &d1);
+            orc_pair_elec(ff, L->q[i] * L->q[j], r, &d2);
+            orc_pair_desolv(ff, L->type[i], L->q[i], L->type[j], L->q[j], r, &d3);
+            if (r > 0.0)
+                for (int a = 0; a < 3; ++a) {
+                    f[3 * i + a] += (d1 + d2 + d3) * d[a] / r;
+                    f[3 * j + a] -= (d1 + d2 + d3) * d[a] / r;
+                }
+        }
+    }
+}
+
 /* Batch form for the tests: npose genotypes (stride 7+T) -> energies and
  * gene gradients (stride 7+T) and tangent gradients (stride 6+T). */
 void orc_score_batch(const orc_ff* ff, const orc_grid* g, const double* maps, const orc_ligand* L,
@@ -872,14 +901,18 @@ static void init_individual(const orc_rng* r, const orc_grid* g, int T, int run,
 /* Per-offspring trace of the GA decisions, for the bit-exact replay test. */
 typedef struct {
     int32_t parent1, parent2, xlo, xhi; /* xlo = xhi = -1 when no crossover */
-    int32_t mut_mask, ls_applied, pad0, pad1;
+    int32_t mut_mask, ls_applied;
+    int32_t cand[4];                    /* tournament candidates a1, b1, a2, b2 (-1 for the elite) */
+    int32_t pad0, pad1;
 } orc_trace;
 
 /* Binary tournament: two uniform indices; the better (lower energy, ties to
  * the lower index) wins with probability tournament_rate. */
-static int tournament(const double* E, int pop, uint32_t wa, uint32_t wb, uint32_t wwin, uint32_t thr)
+static int tournament(const double* E, int pop, uint32_t wa, uint32_t wb, uint32_t wwin, uint32_t thr, int32_t* cand)
 {
     int a = uindex(wa, pop), b = uindex(wb, pop);
+    cand[0] = a;
+    cand[1] = b;
     int better, worse;
     if (E[a] < E[b] || (E[a] == E[b] && a <= b)) { better = a; worse = b; }
     else { better = b; worse = a; }
@@ -898,10 +931,11 @@ static void make_offspring(const orc_rng* r, const orc_params* prm, int T, int r
     int G = 7 + T, nb = 2 + T;
     uint32_t w[4];
     uint32_t thr_t = prob_threshold(prm->tournament_rate);
+    int32_t cand[4];
     rng_block(r, run, ind, gen, PURPOSE_SELECT, 0, w);
-    int p1 = tournament(Pe, prm->pop_size, w[0], w[1], w[2], thr_t);
+    int p1 = tournament(Pe, prm->pop_size, w[0], w[1], w[2], thr_t, cand);
     rng_block(r, run, ind, gen, PURPOSE_SELECT, 1, w);
-    int p2 = tournament(Pe, prm->pop_size, w[0], w[1], w[2], thr_t);
+    int p2 = tournament(Pe, prm->pop_size, w[0], w[1], w[2], thr_t, cand + 2);
     rng_block(r, run, ind, gen, PURPOSE_SELECT, 2, w);
     int lo = -1, hi = -1;
     memcpy(child, Pg + (size_t)p1 * G, sizeof(double) * G);
@@ -938,7 +972,10 @@ static void make_offspring(const orc_rng* r, const orc_params* prm, int T, int r
             child[7 + (b - 2)] += prm->mut_tors * (2.0 * u01(m[0]) - 1.0);
         }
     }
-    if (tr) { tr->parent1 = p1; tr->parent2 = p2; tr->xlo = lo; tr->xhi = hi; tr->mut_mask = mask; }
+    if (tr) {
+        tr->parent1 = p1; tr->parent2 = p2; tr->xlo = lo; tr->xhi = hi; tr->mut_mask = mask;
+        for (int k = 0; k < 4; ++k) tr->cand[k] = cand[k];
+    }
 }
 
 typedef struct {
@@ -980,7 +1017,7 @@ int orc_lga_run(const orc_ff* ff, const orc_grid* g, const double* maps, const o
         int elite = 0;
         for (int i = 1; i < pop; ++i) if (Pe[i] < Pe[elite]) elite = i;
         for (int i = 0; i < pop; ++i) {
-            orc_trace tr = {-1, -1, -1, -1, 0, 0, 0, 0};
+            orc_trace tr = {-1, -1, -1, -1, 0, 0, {-1, -1, -1, -1}, 0, 0};
             double* child = Ng + (size_t)i * G;
             if (i < prm->elitism) {
                 memcpy(child, Pg + (size_t)elite * G, sizeof(double) * G);

@@ -22,6 +22,7 @@ NMAPS = 9
 MAX_ATOMS = 128
 MAX_TORS = 16
 MAX_GENES = 7 + MAX_TORS
+TRACE_WIDTH = 12
 
 ADG_OK = 0
 GRAD_NONE, GRAD_GENES, GRAD_TANGENT = 0, 1, 2
@@ -357,7 +358,7 @@ def dock(ctx: Context, rec: Receptor, ligs, params: adg_search_params, trace_nge
     trace = None
     if trace_ngen > 0:
         G = 7 + ligs[0].ntors
-        dec = np.zeros((nrun, trace_ngen, pop, 8), np.int32)
+        dec = np.zeros((nrun, trace_ngen, pop, TRACE_WIDTH), np.int32)
         tg = np.zeros((nrun, trace_ngen, pop, G), np.float32)
         te = np.zeros((nrun, trace_ngen, pop), np.float32)
         ig = np.zeros((nrun, pop, G), np.float32)

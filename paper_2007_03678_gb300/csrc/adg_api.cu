@@ -646,7 +646,7 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
     const size_t o_lr = take(sizeof(LigandRef) * nlig);
     const size_t o_id = take(sizeof(uint32_t) * nlig);
     const size_t o_res = take(sizeof(ResultDev) * nruns);
-    const size_t o_td = take(sizeof(int) * 8 * tr_slots);
+    const size_t o_td = take(sizeof(int) * ADG_TRACE_WIDTH * tr_slots);
     const size_t o_tg = take(sizeof(float) * kGeneStride * tr_slots);
     const size_t o_te = take(sizeof(float) * tr_slots);
     if (off > ctx->arena_bytes) {
@@ -764,10 +764,11 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
     std::vector<int> tdec;
     std::vector<float> tg, te;
     if (trace && tr_slots > 0) {
-        tdec.resize((size_t)tr_slots * 8);
+        tdec.resize((size_t)tr_slots * ADG_TRACE_WIDTH);
         tg.resize((size_t)tr_slots * kGeneStride);
         te.resize(tr_slots);
-        CK(ctx, cudaMemcpyAsync(tdec.data(), D.tr_dec, sizeof(int) * 8 * tr_slots, cudaMemcpyDeviceToHost, st));
+        CK(ctx, cudaMemcpyAsync(tdec.data(), D.tr_dec, sizeof(int) * ADG_TRACE_WIDTH * tr_slots, cudaMemcpyDeviceToHost,
+                                st));
         CK(ctx, cudaMemcpyAsync(tg.data(), D.tr_genes, sizeof(float) * kGeneStride * tr_slots, cudaMemcpyDeviceToHost, st));
         CK(ctx, cudaMemcpyAsync(te.data(), D.tr_e, sizeof(float) * tr_slots, cudaMemcpyDeviceToHost, st));
     }
@@ -786,7 +787,8 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
     }
     if (trace) {
         const int G = 7 + ligs[0]->ntors;
-        if (trace->decisions && tr_slots) memcpy(trace->decisions, tdec.data(), sizeof(int) * 8 * tr_slots);
+        if (trace->decisions && tr_slots)
+            memcpy(trace->decisions, tdec.data(), sizeof(int) * ADG_TRACE_WIDTH * tr_slots);
         if (trace->energies && tr_slots) memcpy(trace->energies, te.data(), sizeof(float) * tr_slots);
         if (trace->genes)
             for (long s = 0; s < tr_slots; ++s)

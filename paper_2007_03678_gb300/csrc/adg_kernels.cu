@@ -90,9 +90,11 @@ __global__ void __launch_bounds__(256) k_maps_build(MapConst C, int nrec, const 
     const long node = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const int ix = (int)(node % C.nx), iy = (int)((node / C.nx) % C.ny), iz = (int)(node / ((long)C.nx * C.ny));
     const float px = C.ox + ix * C.h, py = C.oy + iy * C.h, pz = C.oz + iz * C.h;
-    float acc[ADG_NMAPS];
+    // terms in FP32, sums in FP64: a node near receptor atoms adds capped
+    // terms of 1e5, and FP32 sums of those lose the small ones
+    double acc[ADG_NMAPS];
 #pragma unroll
-    for (int m = 0; m < ADG_NMAPS; ++m) acc[m] = 0.f;
+    for (int m = 0; m < ADG_NMAPS; ++m) acc[m] = 0.0;
     const float roff2 = C.r_off * C.r_off;
     for (int base = 0; base < nrec; base += 256) {
         __syncthreads();
@@ -126,18 +128,18 @@ __global__ void __launch_bounds__(256) k_maps_build(MapConst C, int nrec, const 
                 float e = C.c12[t][tj] * ri12 - C.c6[t][tj] * ri6 - C.c10[t][tj] * ri10;
                 e = fminf(e, C.e_cap);
                 e += C.w_desolv * (C.solpar[t] * C.vol[tj] + (C.solpar[tj] + C.qasp * aqj) * C.vol[t]) * G;
-                acc[t] += sw * e;
+                acc[t] += (double)(sw * e);
             }
             const float eps = C.ms_A + C.ms_B / (1.f + C.ms_k * expf(-C.ms_lb * rr));
-            acc[ADG_MAP_ELEC] += sw * C.w_elec_coul * qj / (eps * rr);
-            acc[ADG_MAP_DESOLV] += sw * C.w_desolv * C.qasp * C.vol[tj] * G;
+            acc[ADG_MAP_ELEC] += (double)(sw * C.w_elec_coul * qj / (eps * rr));
+            acc[ADG_MAP_DESOLV] += (double)(sw * C.w_desolv * C.qasp * C.vol[tj] * G);
         }
     }
     if (node >= npt) return;
 #pragma unroll
-    for (int t = 0; t < ADG_NTYPES; ++t) acc[t] = fminf(acc[t], C.e_cap);
+    for (int t = 0; t < ADG_NTYPES; ++t) acc[t] = fmin(acc[t], (double)C.e_cap);
 #pragma unroll
-    for (int m = 0; m < ADG_NMAPS; ++m) maps[m * npt + node] = acc[m];
+    for (int m = 0; m < ADG_NMAPS; ++m) maps[m * npt + node] = (float)acc[m];
 }
 
 static void lj_coefs(const adg_forcefield& ff, int ti, int tj, double* c12, double* c6, double* c10)
@@ -349,7 +351,7 @@ struct ScoreOut {
 
 // Energy (and gradient) of the genotype in shared memory `g`.
 template <int APL, bool GRAD>
-__device__ ScoreOut warp_score(const LigandDev* __restrict__ L, const PairsDev& P, const MapsDev& M, const float* g,
+__device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, const PairsDev& P, const MapsDev& M, const float* g,
                                WarpSmem& ws, int lane)
 {
     warp_pose<APL>(L, g, ws, lane);
@@ -605,7 +607,7 @@ __device__ __forceinline__ float ls_gauss(const Rng& r, int it, int d)
 
 // Solis & Wets (1981) adaptive random search on the genotype in ws.genes.
 template <int APL>
-__device__ int warp_solis_wets(const LigandDev* L, const PairsDev& P, const MapsDev& M, const SearchDev& S,
+__device__ __forceinline__ int warp_solis_wets(const LigandDev* L, const PairsDev& P, const MapsDev& M, const SearchDev& S,
                                const Rng& rng, WarpSmem& ws, float& e, int lane)
 {
     const int T = L->ntors, D = 6 + T;
@@ -648,7 +650,7 @@ __device__ int warp_solis_wets(const LigandDev* L, const PairsDev& P, const Maps
 
 // ADADELTA (Zeiler 2012) in the tangent space; keeps the best genotype seen.
 template <int APL>
-__device__ int warp_adadelta(const LigandDev* L, const PairsDev& P, const MapsDev& M, const SearchDev& S, WarpSmem& ws,
+__device__ __forceinline__ int warp_adadelta(const LigandDev* L, const PairsDev& P, const MapsDev& M, const SearchDev& S, WarpSmem& ws,
                              float& e, int lane)
 {
     const int T = L->ntors, G = 7 + T;
@@ -689,9 +691,11 @@ __device__ __forceinline__ void warp_argmin(float& v, int& i)
     }
 }
 
-__device__ __forceinline__ int tournament(const float* Pe, int pop, uint32_t wa, uint32_t wb, uint32_t wwin, uint32_t thr)
+__device__ __forceinline__ int tournament(const float* Pe, int pop, uint32_t wa, uint32_t wb, uint32_t wwin, uint32_t thr,
+                                          int& a, int& b)
 {
-    const int a = uindex(wa, pop), b = uindex(wb, pop);
+    a = uindex(wa, pop);
+    b = uindex(wb, pop);
     const float ea = Pe[a], eb = Pe[b];
     int better, worse;
     if (ea < eb || (ea == eb && a <= b)) { better = a; worse = b; }
@@ -780,6 +784,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_generation(MapsDev
 
     float child = 0.f, e;
     int p1, p2, lo = -1, hi = -1, mmask = 0, nev = 0;
+    int a1 = -1, b1 = -1, a2 = -1, b2 = -1;
     if (ind < S.elitism) {
         p1 = p2 = bi;
         if (lane < G) child = Pg[(long)bi * kGeneStride + lane];
@@ -788,8 +793,8 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_generation(MapsDev
         __syncwarp();
     } else {
         const uint4 w0 = rng.block(P_SELECT, 0), w1 = rng.block(P_SELECT, 1), w2 = rng.block(P_SELECT, 2);
-        p1 = tournament(Pe, pop, w0.x, w0.y, w0.z, S.thr_tour);
-        p2 = tournament(Pe, pop, w1.x, w1.y, w1.z, S.thr_tour);
+        p1 = tournament(Pe, pop, w0.x, w0.y, w0.z, S.thr_tour, a1, b1);
+        p2 = tournament(Pe, pop, w1.x, w1.y, w1.z, S.thr_tour, a2, b2);
         if (ptest(w2.x, S.thr_cross)) {
             const int c1 = uindex(w2.y, nb + 1), c2 = uindex(w2.z, nb + 1);
             lo = min(c1, c2);
@@ -839,8 +844,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_generation(MapsDev
     if (Dk.trace_ngen > 0 && gen <= Dk.trace_ngen && lig == 0) {
         const long slot = ((long)run * Dk.trace_ngen + (gen - 1)) * pop + ind;
         if (lane == 0) {
-            int* d = Dk.tr_dec + slot * 8;
-            d[0] = p1; d[1] = p2; d[2] = lo; d[3] = hi; d[4] = mmask; d[5] = ls_applied; d[6] = 0; d[7] = 0;
+            int* d = Dk.tr_dec + slot * ADG_TRACE_WIDTH;
+            d[0] = p1; d[1] = p2; d[2] = lo; d[3] = hi; d[4] = mmask; d[5] = ls_applied;
+            d[6] = a1; d[7] = b1; d[8] = a2; d[9] = b2; d[10] = 0; d[11] = 0;
             Dk.tr_e[slot] = e;
         }
         if (lane < G) Dk.tr_genes[slot * kGeneStride + lane] = ws.genes[lane];

@@ -12,6 +12,12 @@ from paper_2007_03678_gb300 import synth as S
 E_ABS = 1e-3
 E_REL = 1e-5
 G_REL = 1e-3
+# FP32 rounding of a posed coordinate (|x| <= 16 A: one ulp is 9.5e-7 A) moves
+# the energy by up to COORD_EPS * sum_i |dE/dx_i|_1; poses whose per-atom forces
+# stay below F_WELL are held to the plain tolerance above, the rest to that
+# plus this conditioning term.
+COORD_EPS = 1e-6
+F_WELL = 50.0
 
 
 @functools.lru_cache(maxsize=None)
@@ -26,6 +32,14 @@ def problem(name: str):
 
 def energy_ok(e_gpu, e_ref):
     return np.abs(e_gpu - e_ref) <= E_ABS + E_REL * np.abs(e_ref)
+
+
+def energy_tol(e_ref, forces):
+    return E_ABS + E_REL * np.abs(e_ref) + COORD_EPS * np.abs(forces).sum(axis=(1, 2))
+
+
+def well_conditioned(forces):
+    return np.abs(forces).max(axis=(1, 2)) <= F_WELL
 
 
 def grad_ok(g_gpu, g_ref):
@@ -44,3 +58,27 @@ def inside_box(grid, xyz):
     lo = np.asarray(grid.origin)
     hi = lo + np.asarray(grid.extent)
     return ((xyz >= lo) & (xyz <= hi)).all(axis=(1, 2))
+
+
+@functools.lru_cache(maxsize=None)
+def ga_problem():
+    """A well-conditioned variant of the plain problem for replaying GA
+    decisions: the maps saturated smoothly at +-20 kcal/mol (20 tanh(M/20))
+    and the pair cap lowered to 50, so population energies are O(100) and
+    FP32 and FP64 order them alike.  Both sides receive these inputs."""
+    grid, rec, lig, maps64, maps32 = problem("plain")
+    sm32 = (20.0 * np.tanh(maps64 / 20.0)).astype(np.float32)
+    ff = dict(S.forcefield(), e_cap=50.0)
+    return grid, lig, sm32.astype(np.float64), sm32, ff
+
+
+def near_tie(energies, factor=2.0):
+    """True when two different energies of one population lie within
+    `factor` x the energy tolerance of each other."""
+    for pop in energies:
+        s = np.sort(np.asarray(pop, np.float64))
+        d = np.diff(s)
+        tol = E_ABS + E_REL * np.abs(s[1:])
+        if ((d > 0) & (d < factor * tol)).any():
+            return True
+    return False

@@ -627,3 +627,17 @@ def test_init_population_uniform_in_box(plain_inputs):
     # uniform on S^3: E[w^2] = 1/4 per component
     assert np.allclose((g[:, 3:7] ** 2).mean(axis=0), 0.25, atol=0.02)
     assert (np.abs(g[:, 7:]) <= np.pi).all()
+
+
+def test_atom_gradients_sum_to_translation_gradient(ff, plain_inputs, plain_maps):
+    """Per-atom gradients: their sum is dE/dt and their torque sum is the
+    tangent rotation gradient (both pinned by finite differences above)."""
+    grid, rec, lig = plain_inputs
+    L = O.Ligand(lig)
+    g = S.random_genes(lig, 30, grid, 31, spread=0.2)
+    f = O.atom_gradients(ff, grid, plain_maps, L, g)
+    _, _, _, gt = O.score(ff, grid, plain_maps, L, g)
+    x = O.pose(L, g)
+    assert np.allclose(f.sum(axis=1), gt[:, 0:3], rtol=1e-10, atol=1e-8)
+    tau = np.cross(x - g[:, None, 0:3], f).sum(axis=1)
+    assert np.allclose(tau, gt[:, 3:6], rtol=1e-10, atol=1e-8)
