@@ -99,10 +99,12 @@ EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_c
 _lib = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libadg.so.  Raises if it has not been built."""
+def load(path: str | None = None):
+    """Load libadg.so (or the build named by $ADG_LIBRARY).  Raises if it has
+    not been built."""
     global _lib
     if _lib is None:
+        path = path or os.environ.get("ADG_LIBRARY") or LIB_PATH
         if not os.path.exists(path):
             raise RuntimeError(f"{path} is missing: build it with `python -m paper_2007_03678_gb300.build`")
         L = C.CDLL(path)

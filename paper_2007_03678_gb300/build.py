@@ -43,15 +43,19 @@ def _stale() -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False, defines=(), out: str = LIB) -> str:
+    """Compile and link libadg.so.  `defines` (e.g. ["ADG_GEN_MIN_BLOCKS=3"])
+    and `out` build a variant elsewhere, for tuning; the default is the library."""
+    if not force and not defines and out == LIB and not _stale():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    build_dir = BUILD if out == LIB else os.path.join(os.path.dirname(os.path.abspath(out)), "_build_variant")
+    os.makedirs(build_dir, exist_ok=True)
     cc = nvcc()
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(build_dir, src.replace(".cu", ".o"))
         extra = ["-Xptxas", "-v"] if ptxas_v else []
+        extra += [f"-D{d}" for d in defines]
         cmd = [cc, *_flags(extra), "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0 or verbose or ptxas_v:
@@ -62,14 +66,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
 
     with ThreadPoolExecutor(len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = out + f".{os.getpid()}.tmp"
     cmd = [cc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         sys.stderr.write(" ".join(cmd) + "\n" + r.stdout + r.stderr)
         raise RuntimeError("link failed")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, out)
+    return out
 
 
 if __name__ == "__main__":

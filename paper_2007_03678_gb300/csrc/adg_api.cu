@@ -48,7 +48,7 @@ struct adg_ligand {
     adg_ctx* ctx = nullptr;
     void* blob = nullptr;  // LigandDev followed by the pair arrays
     LigandRef ref{};
-    int natoms = 0, ntors = 0, npairs = 0, apl = 1, sum_moving = 0;
+    int natoms = 0, ntors = 0, npairs = 0, apl = 1, sum_moving = 0, nslots = 0;
     size_t bytes = 0;
 };
 
@@ -456,6 +456,32 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         }
     }
     const int nsteps = (int)slots.size() / 32;
+    // --- force-gather program: every atom's (slot, partner) list goes to one
+    // lane; atoms are dealt longest list first to the least loaded lane
+    std::vector<std::vector<uint32_t>> inc(N);
+    for (int sl = 0; sl < (int)slots.size(); ++sl) {
+        const int p = slots[sl];
+        if (p < 0) continue;
+        const int i = pairs[p].first, j = pairs[p].second;
+        inc[i].push_back((uint32_t)i | ((uint32_t)j << 7) | ((uint32_t)sl << 14));
+        inc[j].push_back((uint32_t)j | ((uint32_t)i << 7) | ((uint32_t)sl << 14));
+    }
+    std::vector<int> by_deg(N);
+    for (int i = 0; i < N; ++i) by_deg[i] = i;
+    std::stable_sort(by_deg.begin(), by_deg.end(), [&](int x, int y) { return inc[x].size() > inc[y].size(); });
+    std::vector<std::vector<uint32_t>> lane_list(32);
+    for (int i : by_deg) {
+        if (inc[i].empty()) continue;
+        int best = 0;
+        for (int l = 1; l < 32; ++l)
+            if (lane_list[l].size() < lane_list[best].size()) best = l;
+        lane_list[best].insert(lane_list[best].end(), inc[i].begin(), inc[i].end());
+    }
+    int gsteps = 0;
+    for (auto& v : lane_list) gsteps = std::max(gsteps, (int)v.size());
+    std::vector<uint32_t> gent((size_t)std::max(gsteps, 1) * 32, kGatherPad);
+    for (int l = 0; l < 32; ++l)
+        for (size_t k = 0; k < lane_list[l].size(); ++k) gent[k * 32 + l] = lane_list[l][k];
     // --- device header
     LigandDev h;
     memset(&h, 0, sizeof(h));
@@ -463,6 +489,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     h.ntors = T;
     h.npairs = P;
     h.nsteps = nsteps;
+    h.gsteps = gsteps;
     double c[3] = {0, 0, 0};
     for (int i = 0; i < N; ++i)
         for (int a = 0; a < 3; ++a) c[a] += d->xyz[3 * i + a];
@@ -490,6 +517,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     for (int s = 0; s < T; ++s) {
         const int k = order[s];
         h.gene_of[s] = k;
+        h.s_of_gene[k] = s;
         h.ta[s] = ta[k];
         h.tb[s] = tb[k];
         const float* pa = d->xyz + 3 * ta[k];
@@ -522,7 +550,8 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     const size_t off_ij = align_up(sizeof(LigandDev), 256);
     const size_t off_coef = align_up(off_ij + sizeof(int) * ns, 256);
     const size_t off_cd = align_up(off_coef + sizeof(float4) * ns, 256);
-    const size_t bytes = align_up(off_cd + sizeof(float) * ns, 256);
+    const size_t off_gent = align_up(off_cd + sizeof(float) * ns, 256);
+    const size_t bytes = align_up(off_gent + sizeof(uint32_t) * gent.size(), 256);
     CK(ctx, cudaSetDevice(ctx->device));
     adg_ligand* L = new (std::nothrow) adg_ligand();
     if (!L) return ADG_ENOMEM;
@@ -531,6 +560,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     memcpy(host.data() + off_ij, ij.data(), sizeof(int) * ns);
     memcpy(host.data() + off_coef, coef.data(), sizeof(float4) * ns);
     memcpy(host.data() + off_cd, cd.data(), sizeof(float) * ns);
+    memcpy(host.data() + off_gent, gent.data(), sizeof(uint32_t) * gent.size());
     cudaError_t e = cudaMalloc(&L->blob, bytes);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L->blob, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -545,6 +575,8 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     L->ref.pairs.ij = (const int*)(base + off_ij);
     L->ref.pairs.coef = (const float4*)(base + off_coef);
     L->ref.pairs.cd = (const float*)(base + off_cd);
+    L->ref.pairs.gent = (const uint32_t*)(base + off_gent);
+    L->nslots = ns;
     L->natoms = N;
     L->ntors = T;
     L->npairs = P;
@@ -586,7 +618,8 @@ int adg_score(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* lig, cons
     if (grad_kind != ADG_GRAD_NONE && npose > 0 && !grad) return ADG_EINVAL;
     if (npose == 0) return ADG_OK;
     CK(ctx, cudaSetDevice(ctx->device));
-    CK(ctx, launch_score(ctx->stream, rec->maps, lig->ref, lig->apl, genes, npose, energy, grad, grad_kind));
+    CK(ctx, launch_score(ctx->stream, rec->maps, lig->ref, make_geo(lig->apl, lig->nslots), genes, npose, energy, grad,
+                         grad_kind));
     ctx->stats.kernel_launches += 1;
     return ADG_OK;
 }
@@ -596,7 +629,7 @@ int adg_pose(adg_ctx* ctx, const adg_ligand* lig, const float* genes, int npose,
     if (!ctx || !lig || npose < 0 || (npose > 0 && (!genes || !xyz))) return ADG_EINVAL;
     if (npose == 0) return ADG_OK;
     CK(ctx, cudaSetDevice(ctx->device));
-    CK(ctx, launch_pose(ctx->stream, lig->ref, genes, npose, xyz));
+    CK(ctx, launch_pose(ctx->stream, lig->ref, make_geo(lig->apl, lig->nslots), genes, npose, xyz));
     ctx->stats.kernel_launches += 1;
     return ADG_OK;
 }
@@ -620,11 +653,13 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         p->ls_max_iters < 0 || p->elitism < 0 || p->elitism > 1 || p->ls_method < 0 || p->ls_method > 2)
         return ADG_EINVAL;
     if (trace && (nlig != 1 || trace->ngen < 0)) return ADG_EINVAL;
-    int apl = 1;
+    int apl = 1, nslots = 32;
     for (int i = 0; i < nlig; ++i) {
         if (!ligs[i] || ligs[i]->ctx != ctx) return ADG_EINVAL;
         apl = std::max(apl, ligs[i]->apl);
+        nslots = std::max(nslots, ligs[i]->nslots);
     }
+    const Geo geo = make_geo(apl, nslots);
     CK(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     const long nruns = (long)nlig * p->nrun;
@@ -715,7 +750,7 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
     ctx->stats.h2d_bytes += (int64_t)((sizeof(LigandRef) + sizeof(uint32_t)) * nlig);
     CK(ctx, cudaMemsetAsync(D.evals, 0, sizeof(unsigned long long) * 2 * nruns, st));
     CK(ctx, cudaMemsetAsync(D.gen_done, 0, sizeof(int) * nruns, st));
-    CK(ctx, launch_dock_init(st, M, S, D, apl));
+    CK(ctx, launch_dock_init(st, M, S, D, geo));
     ctx->stats.kernel_launches += 1;
     std::vector<float> init_g, init_e;
     if (trace && (trace->init_genes || trace->init_energies)) {
@@ -741,7 +776,7 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
                 CK(ctx, take_event(ctx, &e1));
                 CK(ctx, cudaEventRecord(e0, st));
             }
-            CK(ctx, launch_dock_generation(st, M, S, D, apl, gen));
+            CK(ctx, launch_dock_generation(st, M, S, D, geo, gen));
             if (ctx->timing) {
                 CK(ctx, cudaEventRecord(e1, st));
                 ctx->ev_pending.emplace_back(e0, e1);
@@ -756,7 +791,7 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         CK(ctx, cudaStreamSynchronize(st));
         if (*ctx->host_active == 0 || last >= p->max_gen) break;
     }
-    CK(ctx, launch_dock_finalize(st, M, S, D, d_res));
+    CK(ctx, launch_dock_finalize(st, M, S, D, geo, d_res));
     ctx->stats.kernel_launches += 1;
     std::vector<ResultDev> res(nruns);
     CK(ctx, cudaMemcpyAsync(res.data(), d_res, sizeof(ResultDev) * nruns, cudaMemcpyDeviceToHost, st));

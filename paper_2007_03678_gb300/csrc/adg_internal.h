@@ -12,13 +12,29 @@ namespace adg {
 constexpr int kMaxAtoms = ADG_MAX_ATOMS;
 constexpr int kMaxTors = ADG_MAX_TORS;
 constexpr int kGeneStride = 24;  // population rows are padded to 24 floats (>= 7 + 16)
-constexpr int kWarpsPerBlock = 8;
+constexpr int kMaxWarpsPerBlock = 8;
+constexpr uint32_t kGatherPad = 0xffffffffu;
+
+// Per-warp shared memory: xyz[na] and f[na] (float4), torsion frames tu[16]
+// and tg[16] (float4), genes/cand/best[32], cs/sn[16], then c[nslots] (the
+// pair scalars (dE/dr)/r).  na = 32 * atoms-per-lane.
+__host__ __device__ inline size_t warp_smem_floats(int na, int nslots) { return (size_t)8 * na + 320 + nslots; }
+
+// Launch geometry of one warp-per-individual kernel launch.
+struct Geo {
+    int apl;      // atoms per lane (1, 2, 4)
+    int na;       // 32 * apl
+    int nslots;   // largest pair-slot count of the launched ligands
+    int wpb;      // warps per block
+    size_t smem;  // dynamic shared memory per block (bytes)
+};
 
 // Ligand as the kernels read it: one POD blob in device memory.
 // Torsions are stored in application order s (deepest first); gene_of[s] is
 // the genotype index k of torsion s (theta_k = genes[7 + k]).
 struct LigandDev {
     int natoms, ntors, npairs, nsteps;   // nsteps = ceil(npairs / 32) pair slots per lane
+    int gsteps;                          // length of the longest per-lane force-gather list
     float cx, cy, cz;                    // reference centroid
     // scoring constants (from the force field)
     float e_cap, rmin2, ms_A, ms_B, ms_k, ms_lb, inv_2s2, inv_s2, k_out;
@@ -26,6 +42,7 @@ struct LigandDev {
     int type[kMaxAtoms];                 // map index 0..6
     uint32_t tmask[kMaxAtoms];           // bit s set when the atom is moved by torsion s
     int gene_of[kMaxTors];
+    int s_of_gene[kMaxTors];             // inverse of gene_of
     int ta[kMaxTors], tb[kMaxTors];      // bond atoms of torsion s (a on the root side)
     float4 tpt[kMaxTors];                // reference position of atom a
     float4 tax[kMaxTors];                // reference unit axis a -> b
@@ -34,10 +51,16 @@ struct LigandDev {
 // Intramolecular pairs, lane-interleaved: slot (step, lane) = step * 32 + lane.
 // ij = i | j << 16, or -1 for an empty slot.  coef = (c12, c6, c10, cq):
 // E_pair = min(c12 r^-12 - c6 r^-6 - c10 r^-10, e_cap) + cq / (eps(r) r) + cd exp(-r^2/(2 s^2)).
+// Force gather: after the pair pass has stored c_p = (dE/dr)/r of every slot,
+// lane l walks its list gent[k * 32 + l] (k < gsteps), entries
+// atom | other << 7 | slot << 14 grouped by atom, and sums
+// f_atom = sum c_p (x_atom - x_other).  Atoms are dealt to lanes by pair
+// count (longest first to the least loaded lane); padding = kGatherPad.
 struct PairsDev {
     const int* ij;
     const float4* coef;
     const float* cd;
+    const uint32_t* gent;
 };
 
 struct LigandRef {
@@ -92,16 +115,17 @@ struct ResultDev {
 cudaError_t launch_maps_build(cudaStream_t st, const adg_forcefield& ff, const adg_grid_desc& g, int nrec,
                               const float4* rec_xyzq, const int* rec_type, float* maps_out);
 cudaError_t launch_pack_maps(cudaStream_t st, const float* maps, const adg_grid_desc& g, float4* packed);
-cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, int apl, const float* genes,
+Geo make_geo(int apl, int nslots);
+cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, const Geo& g, const float* genes,
                          int npose, float* energy, float* grad, int grad_kind);
-cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const float* genes, int npose, float* xyz);
+cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const Geo& g, const float* genes, int npose, float* xyz);
 cudaError_t launch_philox(cudaStream_t st, const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out);
-cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, int apl);
+cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g);
 cudaError_t launch_dock_generation(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d,
-                                   int apl, int gen);
+                                   const Geo& g, int gen);
 cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const DockDev& d, int next_gen,
                                      int* active);
 cudaError_t launch_dock_finalize(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d,
-                                 ResultDev* out);
+                                 const Geo& g, ResultDev* out);
 
 }  // namespace adg

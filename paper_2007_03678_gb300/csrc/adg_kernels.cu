@@ -18,6 +18,12 @@ namespace adg {
 
 #define FULL_MASK 0xffffffffu
 
+// Minimum resident blocks per SM the generation kernel is compiled for
+// (bounds its registers: 2 -> 128, 3 -> 85 per thread at 256 threads).
+#ifndef ADG_GEN_MIN_BLOCKS
+#define ADG_GEN_MIN_BLOCKS 2
+#endif
+
 // ------------------------------------------------------------------ Philox
 // Philox4x32-10 (Salmon et al., SC'11): 10 rounds of two 32x32 multiplies
 // whose high halves are xored into the other words with the round key; the
@@ -230,14 +236,37 @@ cudaError_t launch_pack_maps(cudaStream_t st, const float* maps, const adg_grid_
 }
 
 // ------------------------------------------------------------------ warp scoring
-struct WarpSmem {
-    float4 xyz[kMaxAtoms];                         // posed coordinates
-    float fx[kMaxAtoms], fy[kMaxAtoms], fz[kMaxAtoms];  // intramolecular forces
-    float genes[32];                               // current genotype
-    float cand[32];                                // trial genotype
-    float best[32];                                // best genotype of a local search
-    float cs[kMaxTors], sn[kMaxTors];              // cos / sin of the torsion genes
+// Per-warp views into the dynamic shared memory of the block.
+struct WarpView {
+    float4* xyz;   // posed coordinates [na]
+    float4* f;     // intramolecular force per atom [na] (gather output)
+    float4* tu;    // posed unit axis of torsion s [16]
+    float4* tg;    // u_s x x_a(s) [16]
+    float* genes;  // current genotype [32]
+    float* cand;   // trial genotype [32]
+    float* best;   // best genotype of a local search [32]
+    float* cs;     // cos of torsion s [16]
+    float* sn;     // sin of torsion s [16]
+    float* c;      // (dE/dr)/r per pair slot [nslots]
 };
+
+__device__ __forceinline__ WarpView warp_view(int na, int nslots)
+{
+    extern __shared__ float4 dyn_smem4[];
+    float* base = reinterpret_cast<float*>(dyn_smem4) + (size_t)(threadIdx.x >> 5) * warp_smem_floats(na, nslots);
+    WarpView v;
+    v.xyz = reinterpret_cast<float4*>(base);
+    v.f = reinterpret_cast<float4*>(base + 4 * na);
+    v.tu = reinterpret_cast<float4*>(base + 8 * na);
+    v.tg = reinterpret_cast<float4*>(base + 8 * na + 64);
+    v.genes = base + 8 * na + 128;
+    v.cand = v.genes + 32;
+    v.best = v.cand + 32;
+    v.cs = v.best + 32;
+    v.sn = v.cs + 16;
+    v.c = v.sn + 16;
+    return v;
+}
 
 __device__ __forceinline__ float warp_sum(float v)
 {
@@ -246,11 +275,29 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
+// Sum 32 per-lane values across the warp at once: lane l ends with the
+// total of v[l].  Each halving step keeps half of the values and trades the
+// other half with the partner lane (31 shuffles for 32 sums).
+__device__ __forceinline__ float warp_reduce32(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int w = 16; w >= 1; w >>= 1) {
+        const bool upper = (lane & w) != 0;
+#pragma unroll
+        for (int k = 0; k < w; ++k) {
+            const float send = upper ? v[k] : v[k + w];
+            const float keep = upper ? v[k + w] : v[k];
+            v[k] = keep + __shfl_xor_sync(FULL_MASK, send, w);
+        }
+    }
+    return v[0];
+}
+
 // Genotype g (shared memory, 7+T floats) -> posed coordinates in ws.xyz.
 // Torsions deepest first about their reference axes (Rodrigues), then
 // x' = R(q/|q|) (x - c) + t.
 template <int APL>
-__device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, WarpSmem& ws, int lane)
+__device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, const WarpView& ws, int lane)
 {
     const int N = L->natoms, T = L->ntors;
     if (lane < T) {
@@ -344,15 +391,20 @@ __device__ __forceinline__ float atom_inter(const MapsDev& M, float k_out, int t
 }
 
 struct ScoreOut {
-    float e;         // total energy (all lanes)
-    float gtan;      // lane d < 6+T: tangent gradient component d
+    float e;           // total energy (all lanes)
+    float gtan;        // lane d < 6+T: tangent gradient component d
     float tx, ty, tz;  // torque (all lanes)
 };
 
 // Energy (and gradient) of the genotype in shared memory `g`.
+//  1. pose (lanes own atoms), 2. intermolecular gather (lanes own atoms),
+//  3. pair terms (lanes own pair slots; the gradient pass stores
+//     c_p = (dE/dr)/r per slot), 4. force gather per atom from c_p (no
+//     atomics: each atom belongs to one lane's gather list), 5. one
+//     transposed warp reduction of dE/dt, the torque and every dE/dtheta.
 template <int APL, bool GRAD>
-__device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, const PairsDev& P, const MapsDev& M, const float* g,
-                               WarpSmem& ws, int lane)
+__device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, const PairsDev& P, const MapsDev& M,
+                                               const float* g, const WarpView& ws, int lane)
 {
     warp_pose<APL>(L, g, ws, lane);
     const int N = L->natoms, T = L->ntors;
@@ -366,17 +418,20 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         if (a < N) {
             const float4 x = ws.xyz[a];
             e += atom_inter<GRAD>(M, k_out, L->type[a], L->ref[a].w, x.x, x.y, x.z, fxr[j], fyr[j], fzr[j]);
-            if (GRAD) ws.fx[a] = ws.fy[a] = ws.fz[a] = 0.f;
+            if (GRAD) ws.f[a] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    if (GRAD) __syncwarp();
     // intramolecular pairs
     const float cap = L->e_cap, rmin2 = L->rmin2, msA = L->ms_A, msB = L->ms_B, msk = L->ms_k, mslb = L->ms_lb;
     const float inv_2s2 = L->inv_2s2, inv_s2 = L->inv_s2;
-    for (int stp = 0; stp < L->nsteps; ++stp) {
+    const int nsteps = L->nsteps;
+    for (int stp = 0; stp < nsteps; ++stp) {
         const int idx = stp * 32 + lane;
         const int ij = __ldg(P.ij + idx);
-        if (ij < 0) continue;
+        if (ij < 0) {
+            if (GRAD) ws.c[idx] = 0.f;
+            continue;
+        }
         const int i = ij & 0xffff, j = ij >> 16;
         const float4 xi = ws.xyz[i], xj = ws.xyz[j];
         const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
@@ -389,10 +444,10 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const float r = rr2 * ri;
         const float ri2 = ri * ri;
         const float ri6 = ri2 * ri2 * ri2, ri12 = ri6 * ri6, ri10 = ri6 * ri2 * ri2;
-        float elj = c.x * ri12 - c.y * ri6 - c.z * ri10;
+        const float elj = c.x * ri12 - c.y * ri6 - c.z * ri10;
         const float ex = __expf(-mslb * r);
         const float den = 1.f + msk * ex;
-        const float D = msA * den + msB;   // eps(r) = D / den
+        const float D = msA * den + msB;  // eps(r) = D / den
         const float rD = __fdividef(1.f, D);
         const float eel = c.w * den * ri * rD;
         const float gs = __expf(-rr2 * inv_2s2);
@@ -403,13 +458,7 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
             const float dden = -mslb * msk * ex;
             const float deel = c.w * (dden * rD * ri - den * rD * rD * ri * ri * (msA * dden * r + D)) * ri;
             const float dds = -eds * inv_s2;
-            const float fs = fl ? 0.f : (dlj + deel + dds);
-            atomicAdd(&ws.fx[i], fs * dx);
-            atomicAdd(&ws.fy[i], fs * dy);
-            atomicAdd(&ws.fz[i], fs * dz);
-            atomicAdd(&ws.fx[j], -fs * dx);
-            atomicAdd(&ws.fy[j], -fs * dy);
-            atomicAdd(&ws.fz[j], -fs * dz);
+            ws.c[idx] = fl ? 0.f : (dlj + deel + dds);
         }
         e += fminf(elj, cap) + eel + eds;
     }
@@ -419,62 +468,115 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     out.tx = out.ty = out.tz = 0.f;
     if (!GRAD) return out;
     __syncwarp();
+    // force gather: f_atom = sum over its pairs of c_p (x_atom - x_other)
+    {
+        int cur = -1;
+        float4 xa = make_float4(0.f, 0.f, 0.f, 0.f);
+        float ax = 0.f, ay = 0.f, az = 0.f;
+        const int gsteps = L->gsteps;
+        for (int k = 0; k < gsteps; ++k) {
+            const uint32_t ent = __ldg(P.gent + k * 32 + lane);
+            if (ent == kGatherPad) break;  // a lane's list is padded at its end only
+            const int atom = ent & 127, other = (ent >> 7) & 127, slot = ent >> 14;
+            if (atom != cur) {
+                if (cur >= 0) ws.f[cur] = make_float4(ax, ay, az, 0.f);
+                cur = atom;
+                xa = ws.xyz[atom];
+                ax = ay = az = 0.f;
+            }
+            const float cc = ws.c[slot];
+            const float4 xo = ws.xyz[other];
+            ax += cc * (xa.x - xo.x);
+            ay += cc * (xa.y - xo.y);
+            az += cc * (xa.z - xo.z);
+        }
+        if (cur >= 0) ws.f[cur] = make_float4(ax, ay, az, 0.f);
+    }
+    // posed torsion frames: u_s and u_s x x_a(s), one lane per torsion
+    if (lane < T) {
+        const float4 xa = ws.xyz[L->ta[lane]], xb = ws.xyz[L->tb[lane]];
+        float ux = xb.x - xa.x, uy = xb.y - xa.y, uz = xb.z - xa.z;
+        const float un = rsqrtf(ux * ux + uy * uy + uz * uz);
+        ux *= un; uy *= un; uz *= un;
+        ws.tu[lane] = make_float4(ux, uy, uz, 0.f);
+        ws.tg[lane] = make_float4(uy * xa.z - uz * xa.y, uz * xa.x - ux * xa.z, ux * xa.y - uy * xa.x, 0.f);
+    }
+    __syncwarp();
     const float tx = g[0], ty = g[1], tz = g[2];
-    float sgx = 0.f, sgy = 0.f, sgz = 0.f, stx = 0.f, sty = 0.f, stz = 0.f;
+    float v[32];
+#pragma unroll
+    for (int k = 0; k < 32; ++k) v[k] = 0.f;
 #pragma unroll
     for (int j = 0; j < APL; ++j) {
         const int a = lane + 32 * j;
         if (a < N) {
-            fxr[j] += ws.fx[a];
-            fyr[j] += ws.fy[a];
-            fzr[j] += ws.fz[a];
+            const float4 fi = ws.f[a];
+            const float fx = fxr[j] + fi.x, fy = fyr[j] + fi.y, fz = fzr[j] + fi.z;
             const float4 x = ws.xyz[a];
             const float rx = x.x - tx, ry = x.y - ty, rz = x.z - tz;
-            sgx += fxr[j]; sgy += fyr[j]; sgz += fzr[j];
-            stx += ry * fzr[j] - rz * fyr[j];
-            sty += rz * fxr[j] - rx * fzr[j];
-            stz += rx * fyr[j] - ry * fxr[j];
-        }
-    }
-    sgx = warp_sum(sgx); sgy = warp_sum(sgy); sgz = warp_sum(sgz);
-    stx = warp_sum(stx); sty = warp_sum(sty); stz = warp_sum(stz);
-    float mine = lane == 0 ? sgx : lane == 1 ? sgy : lane == 2 ? sgz : lane == 3 ? stx : lane == 4 ? sty : stz;
-    for (int s = 0; s < T; ++s) {
-        const float4 xa = ws.xyz[L->ta[s]], xb = ws.xyz[L->tb[s]];
-        float ux = xb.x - xa.x, uy = xb.y - xa.y, uz = xb.z - xa.z;
-        const float un = rsqrtf(ux * ux + uy * uy + uz * uz);
-        ux *= un; uy *= un; uz *= un;
-        float cs = 0.f;
+            v[0] += fx;
+            v[1] += fy;
+            v[2] += fz;
+            v[3] += ry * fz - rz * fy;
+            v[4] += rz * fx - rx * fz;
+            v[5] += rx * fy - ry * fx;
+            // dE/dtheta_s += u_s . ((x - x_a) x f) = u_s . (x x f) - (u_s x x_a) . f
+            const float mx = x.y * fz - x.z * fy, my = x.z * fx - x.x * fz, mz = x.x * fy - x.y * fx;
+            const uint32_t m = L->tmask[a];
 #pragma unroll
-        for (int j = 0; j < APL; ++j) {
-            const int a = lane + 32 * j;
-            if (a < N && ((L->tmask[a] >> s) & 1u)) {
-                const float4 x = ws.xyz[a];
-                const float vx = x.x - xa.x, vy = x.y - xa.y, vz = x.z - xa.z;
-                cs += (uy * vz - uz * vy) * fxr[j] + (uz * vx - ux * vz) * fyr[j] + (ux * vy - uy * vx) * fzr[j];
+            for (int s = 0; s < kMaxTors; ++s) {
+                if (s < T && ((m >> s) & 1u)) {
+                    const float4 u = ws.tu[s], q = ws.tg[s];
+                    v[6 + s] += u.x * mx + u.y * my + u.z * mz - (q.x * fx + q.y * fy + q.z * fz);
+                }
             }
         }
-        cs = warp_sum(cs);
-        if (lane == 6 + L->gene_of[s]) mine = cs;
     }
-    out.gtan = lane < 6 + T ? mine : 0.f;
-    out.tx = stx;
-    out.ty = sty;
-    out.tz = stz;
+    const float mine = warp_reduce32(v, lane);
+    // lane 6 + k takes torsion gene k from lane 6 + s_of_gene[k] (application order)
+    const int src = (lane >= 6 && lane < 6 + T) ? 6 + L->s_of_gene[lane - 6] : lane;
+    const float val = __shfl_sync(FULL_MASK, mine, src);
+    out.gtan = lane < 6 + T ? val : 0.f;
+    out.tx = __shfl_sync(FULL_MASK, mine, 3);
+    out.ty = __shfl_sync(FULL_MASK, mine, 4);
+    out.tz = __shfl_sync(FULL_MASK, mine, 5);
     return out;
 }
 
+// ------------------------------------------------------------------ launch geometry
+Geo make_geo(int apl, int nslots)
+{
+    Geo g;
+    g.apl = apl <= 1 ? 1 : (apl <= 2 ? 2 : 4);
+    g.na = 32 * g.apl;
+    g.nslots = nslots < 32 ? 32 : (nslots + 31) / 32 * 32;
+    const size_t per_warp = warp_smem_floats(g.na, g.nslots) * sizeof(float);
+    g.wpb = kMaxWarpsPerBlock;
+    while (g.wpb > 1 && (size_t)g.wpb * per_warp > 160u * 1024u) --g.wpb;
+    g.smem = (size_t)g.wpb * per_warp;
+    return g;
+}
+
+template <typename K>
+static cudaError_t allow_smem(K kernel, size_t bytes)
+{
+    if (bytes <= 48u * 1024u) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+static unsigned blocks_for(long nwarps, const Geo& g) { return (unsigned)((nwarps + g.wpb - 1) / g.wpb); }
+
 // ------------------------------------------------------------------ score / pose API kernels
 template <int APL>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_score(MapsDev M, LigandRef LR, const float* __restrict__ genes,
-                                                               int npose, float* __restrict__ energy,
-                                                               float* __restrict__ grad, int grad_kind)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_score(MapsDev M, LigandRef LR, int na, int nslots,
+                                                                  const float* __restrict__ genes, int npose,
+                                                                  float* __restrict__ energy, float* __restrict__ grad,
+                                                                  int grad_kind)
 {
-    __shared__ WarpSmem smem[kWarpsPerBlock];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long pose = (long)blockIdx.x * kWarpsPerBlock + w;
+    const int lane = threadIdx.x & 31;
+    const long pose = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (pose >= npose) return;
-    WarpSmem& ws = smem[w];
+    const WarpView ws = warp_view(na, nslots);
     const LigandDev* L = LR.hdr;
     const int T = L->ntors, G = 7 + T, D = 6 + T;
     if (lane < G) ws.genes[lane] = genes[pose * G + lane];
@@ -508,25 +610,32 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_score(MapsDev M, Ligand
     if (lane < G) grad[pose * G + lane] = val;
 }
 
-cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, int apl, const float* genes, int npose,
-                         float* energy, float* grad, int grad_kind)
+cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, const Geo& g, const float* genes,
+                         int npose, float* energy, float* grad, int grad_kind)
 {
     if (npose <= 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((npose + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    if (apl <= 1) k_score<1><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, l, genes, npose, energy, grad, grad_kind);
-    else if (apl == 2) k_score<2><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, l, genes, npose, energy, grad, grad_kind);
-    else k_score<4><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, l, genes, npose, energy, grad, grad_kind);
+    const unsigned blocks = blocks_for(npose, g);
+    const unsigned threads = g.wpb * 32;
+    cudaError_t e;
+#define ADG_SCORE(A)                                                                                            \
+    e = allow_smem(k_score<A>, g.smem);                                                                         \
+    if (e != cudaSuccess) return e;                                                                             \
+    k_score<A><<<blocks, threads, g.smem, st>>>(m, l, g.na, g.nslots, genes, npose, energy, grad, grad_kind);
+    if (g.apl == 1) { ADG_SCORE(1) }
+    else if (g.apl == 2) { ADG_SCORE(2) }
+    else { ADG_SCORE(4) }
+#undef ADG_SCORE
     return cudaGetLastError();
 }
 
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_pose(LigandRef LR, const float* __restrict__ genes, int npose,
-                                                              float* __restrict__ xyz)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_pose(LigandRef LR, int na, int nslots,
+                                                                 const float* __restrict__ genes, int npose,
+                                                                 float* __restrict__ xyz)
 {
-    __shared__ WarpSmem smem[kWarpsPerBlock];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long pose = (long)blockIdx.x * kWarpsPerBlock + w;
+    const int lane = threadIdx.x & 31;
+    const long pose = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (pose >= npose) return;
-    WarpSmem& ws = smem[w];
+    const WarpView ws = warp_view(na, nslots);
     const LigandDev* L = LR.hdr;
     const int G = 7 + L->ntors, N = L->natoms;
     if (lane < G) ws.genes[lane] = genes[pose * G + lane];
@@ -540,11 +649,13 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_pose(LigandRef LR, cons
     }
 }
 
-cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const float* genes, int npose, float* xyz)
+cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const Geo& g0, const float* genes, int npose, float* xyz)
 {
     if (npose <= 0) return cudaSuccess;
-    k_pose<<<(unsigned)((npose + kWarpsPerBlock - 1) / kWarpsPerBlock), kWarpsPerBlock * 32, 0, st>>>(l, genes, npose,
-                                                                                                      xyz);
+    const Geo g = make_geo(4, g0.nslots);  // k_pose indexes up to 4 atoms per lane
+    cudaError_t e = allow_smem(k_pose, g.smem);
+    if (e != cudaSuccess) return e;
+    k_pose<<<blocks_for(npose, g), g.wpb * 32, g.smem, st>>>(l, g.na, g.nslots, genes, npose, xyz);
     return cudaGetLastError();
 }
 
@@ -607,8 +718,9 @@ __device__ __forceinline__ float ls_gauss(const Rng& r, int it, int d)
 
 // Solis & Wets (1981) adaptive random search on the genotype in ws.genes.
 template <int APL>
-__device__ __forceinline__ int warp_solis_wets(const LigandDev* L, const PairsDev& P, const MapsDev& M, const SearchDev& S,
-                               const Rng& rng, WarpSmem& ws, float& e, int lane)
+__device__ __forceinline__ int warp_solis_wets(const LigandDev* L, const PairsDev& P, const MapsDev& M,
+                                               const SearchDev& S, const Rng& rng, const WarpView& ws, float& e,
+                                               int lane)
 {
     const int T = L->ntors, D = 6 + T;
     const float scale = lane < 3 ? S.sw_scale_t : (lane < 6 ? S.sw_scale_rot : S.sw_scale_tors);
@@ -650,8 +762,8 @@ __device__ __forceinline__ int warp_solis_wets(const LigandDev* L, const PairsDe
 
 // ADADELTA (Zeiler 2012) in the tangent space; keeps the best genotype seen.
 template <int APL>
-__device__ __forceinline__ int warp_adadelta(const LigandDev* L, const PairsDev& P, const MapsDev& M, const SearchDev& S, WarpSmem& ws,
-                             float& e, int lane)
+__device__ __forceinline__ int warp_adadelta(const LigandDev* L, const PairsDev& P, const MapsDev& M,
+                                             const SearchDev& S, const WarpView& ws, float& e, int lane)
 {
     const int T = L->ntors, G = 7 + T;
     float eg2 = 0.f, edx2 = 0.f, ebest = e;
@@ -706,14 +818,14 @@ __device__ __forceinline__ int tournament(const float* Pe, int pop, uint32_t wa,
 // Generation 0: random genotypes (t uniform in the box, q uniform on S^3 by
 // Shoemake's three uniforms, theta uniform in [-pi, pi)), evaluated.
 template <int APL>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_init(MapsDev M, SearchDev S, DockDev Dk)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_init(MapsDev M, SearchDev S, DockDev Dk, int na,
+                                                                      int nslots)
 {
-    __shared__ WarpSmem smem[kWarpsPerBlock];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long gw = (long)blockIdx.x * kWarpsPerBlock + w;
+    const int lane = threadIdx.x & 31;
+    const long gw = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long nruns = (long)Dk.nlig * S.nrun;
     if (gw >= nruns * S.pop) return;
-    WarpSmem& ws = smem[w];
+    const WarpView ws = warp_view(na, nslots);
     const int run_g = (int)(gw / S.pop), ind = (int)(gw % S.pop);
     const int lig = run_g / S.nrun, run = run_g % S.nrun;
     const LigandRef LR = Dk.ligs[lig];
@@ -750,20 +862,22 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_init(MapsDev M, Se
     }
 }
 
-// Accumulated per-generation evaluation counts live in evals[nruns + run]
-// until k_dock_bookkeep folds them in, so every warp of a generation sees
-// the same total when it decides whether its run is still active.
+// One GA generation of one individual per warp: selection, crossover,
+// mutation, offspring evaluation, local search.  Per-generation evaluation
+// counts accumulate in evals[nruns + run] until k_dock_bookkeep folds them
+// in, so every warp of a generation sees the same total when it decides
+// whether its run is still active.
 template <int APL, int LS>
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_generation(MapsDev M, SearchDev S, DockDev Dk, int gen)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_GEN_MIN_BLOCKS) k_dock_generation(MapsDev M, SearchDev S, DockDev Dk,
+                                                                            int na, int nslots, int gen)
 {
-    __shared__ WarpSmem smem[kWarpsPerBlock];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const long gw = (long)blockIdx.x * kWarpsPerBlock + w;
+    const int lane = threadIdx.x & 31;
+    const long gw = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long nruns = (long)Dk.nlig * S.nrun;
     if (gw >= nruns * S.pop) return;
     const int run_g = (int)(gw / S.pop), ind = (int)(gw % S.pop);
     if (Dk.evals[run_g] >= (unsigned long long)S.nev || gen > S.max_gen) return;
-    WarpSmem& ws = smem[w];
+    const WarpView ws = warp_view(na, nslots);
     const int lig = run_g / S.nrun, run = run_g % S.nrun;
     const LigandRef LR = Dk.ligs[lig];
     const LigandDev* L = LR.hdr;
@@ -869,36 +983,44 @@ __global__ void k_dock_bookkeep(SearchDev S, DockDev Dk, int gen, int* active)
     if (Dk.evals[r] < nev && gen + 1 <= S.max_gen) atomicAdd(active, 1);
 }
 
-template <int APL, int LS>
-static void gen_launch(cudaStream_t st, unsigned blocks, const MapsDev& m, const SearchDev& s, const DockDev& d, int gen)
-{
-    k_dock_generation<APL, LS><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, s, d, gen);
-}
-
-cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, int apl)
+cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g)
 {
     const long nw = (long)d.nlig * s.nrun * s.pop;
-    const unsigned blocks = (unsigned)((nw + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    if (apl <= 1) k_dock_init<1><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, s, d);
-    else if (apl == 2) k_dock_init<2><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, s, d);
-    else k_dock_init<4><<<blocks, kWarpsPerBlock * 32, 0, st>>>(m, s, d);
+    const unsigned blocks = blocks_for(nw, g), threads = g.wpb * 32;
+    cudaError_t e;
+#define ADG_INIT(A)                                                                      \
+    e = allow_smem(k_dock_init<A>, g.smem);                                              \
+    if (e != cudaSuccess) return e;                                                      \
+    k_dock_init<A><<<blocks, threads, g.smem, st>>>(m, s, d, g.na, g.nslots);
+    if (g.apl == 1) { ADG_INIT(1) }
+    else if (g.apl == 2) { ADG_INIT(2) }
+    else { ADG_INIT(4) }
+#undef ADG_INIT
     return cudaGetLastError();
 }
 
-cudaError_t launch_dock_generation(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, int apl,
+template <int APL, int LS>
+static cudaError_t gen_launch(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g,
+                              int gen)
+{
+    const long nw = (long)d.nlig * s.nrun * s.pop;
+    cudaError_t e = allow_smem(k_dock_generation<APL, LS>, g.smem);
+    if (e != cudaSuccess) return e;
+    k_dock_generation<APL, LS><<<blocks_for(nw, g), g.wpb * 32, g.smem, st>>>(m, s, d, g.na, g.nslots, gen);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dock_generation(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g,
                                    int gen)
 {
-    const long nw = (long)d.nlig * s.nrun * s.pop;
-    const unsigned blocks = (unsigned)((nw + kWarpsPerBlock - 1) / kWarpsPerBlock);
-#define ADG_GEN(A)                                                                         \
-    if (s.ls_method == ADG_LS_SOLIS_WETS) gen_launch<A, ADG_LS_SOLIS_WETS>(st, blocks, m, s, d, gen); \
-    else if (s.ls_method == ADG_LS_ADADELTA) gen_launch<A, ADG_LS_ADADELTA>(st, blocks, m, s, d, gen); \
-    else gen_launch<A, ADG_LS_NONE>(st, blocks, m, s, d, gen);
-    if (apl <= 1) { ADG_GEN(1) }
-    else if (apl == 2) { ADG_GEN(2) }
-    else { ADG_GEN(4) }
+#define ADG_GEN(A)                                                                                        \
+    if (s.ls_method == ADG_LS_SOLIS_WETS) return gen_launch<A, ADG_LS_SOLIS_WETS>(st, m, s, d, g, gen);   \
+    if (s.ls_method == ADG_LS_ADADELTA) return gen_launch<A, ADG_LS_ADADELTA>(st, m, s, d, g, gen);       \
+    return gen_launch<A, ADG_LS_NONE>(st, m, s, d, g, gen);
+    if (g.apl == 1) { ADG_GEN(1) }
+    if (g.apl == 2) { ADG_GEN(2) }
+    ADG_GEN(4)
 #undef ADG_GEN
-    return cudaGetLastError();
 }
 
 cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const DockDev& d, int gen, int* active)
@@ -909,15 +1031,14 @@ cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const 
 }
 
 // Per run: best genotype of the final population and its posed coordinates.
-__global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_finalize(MapsDev M, SearchDev S, DockDev Dk,
-                                                                       ResultDev* __restrict__ out)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_finalize(MapsDev M, SearchDev S, DockDev Dk, int na,
+                                                                          int nslots, ResultDev* __restrict__ out)
 {
-    __shared__ WarpSmem smem[kWarpsPerBlock];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int run_g = blockIdx.x * kWarpsPerBlock + w;
+    const int lane = threadIdx.x & 31;
+    const int run_g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int nruns = Dk.nlig * S.nrun;
     if (run_g >= nruns) return;
-    WarpSmem& ws = smem[w];
+    const WarpView ws = warp_view(na, nslots);
     const int lig = run_g / S.nrun;
     const LigandDev* L = Dk.ligs[lig].hdr;
     const int G = 7 + L->ntors, N = L->natoms, gd = Dk.gen_done[run_g];
@@ -949,10 +1070,14 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32) k_dock_finalize(MapsDev M
     }
 }
 
-cudaError_t launch_dock_finalize(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, ResultDev* out)
+cudaError_t launch_dock_finalize(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g0,
+                                 ResultDev* out)
 {
     const int nruns = d.nlig * s.nrun;
-    k_dock_finalize<<<(nruns + kWarpsPerBlock - 1) / kWarpsPerBlock, kWarpsPerBlock * 32, 0, st>>>(m, s, d, out);
+    const Geo g = make_geo(4, g0.nslots);  // the final pose indexes up to 4 atoms per lane
+    cudaError_t e = allow_smem(k_dock_finalize, g.smem);
+    if (e != cudaSuccess) return e;
+    k_dock_finalize<<<blocks_for(nruns, g), g.wpb * 32, g.smem, st>>>(m, s, d, g.na, g.nslots, out);
     return cudaGetLastError();
 }
 
