@@ -552,6 +552,11 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     const size_t off_cd = align_up(off_coef + sizeof(float4) * ns, 256);
     const size_t off_gent = align_up(off_cd + sizeof(float) * ns, 256);
     const size_t bytes = align_up(off_gent + sizeof(uint32_t) * gent.size(), 256);
+    h.blob_bytes = (int)bytes;
+    h.off_ij = (int)off_ij;
+    h.off_coef = (int)off_coef;
+    h.off_cd = (int)off_cd;
+    h.off_gent = (int)off_gent;
     CK(ctx, cudaSetDevice(ctx->device));
     adg_ligand* L = new (std::nothrow) adg_ligand();
     if (!L) return ADG_ENOMEM;
@@ -618,7 +623,7 @@ int adg_score(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* lig, cons
     if (grad_kind != ADG_GRAD_NONE && npose > 0 && !grad) return ADG_EINVAL;
     if (npose == 0) return ADG_OK;
     CK(ctx, cudaSetDevice(ctx->device));
-    CK(ctx, launch_score(ctx->stream, rec->maps, lig->ref, make_geo(lig->apl, lig->nslots), genes, npose, energy, grad,
+    CK(ctx, launch_score(ctx->stream, rec->maps, lig->ref, make_geo(lig->apl, lig->nslots, lig->bytes), genes, npose, energy, grad,
                          grad_kind));
     ctx->stats.kernel_launches += 1;
     return ADG_OK;
@@ -629,7 +634,7 @@ int adg_pose(adg_ctx* ctx, const adg_ligand* lig, const float* genes, int npose,
     if (!ctx || !lig || npose < 0 || (npose > 0 && (!genes || !xyz))) return ADG_EINVAL;
     if (npose == 0) return ADG_OK;
     CK(ctx, cudaSetDevice(ctx->device));
-    CK(ctx, launch_pose(ctx->stream, lig->ref, make_geo(lig->apl, lig->nslots), genes, npose, xyz));
+    CK(ctx, launch_pose(ctx->stream, lig->ref, make_geo(lig->apl, lig->nslots, lig->bytes), genes, npose, xyz));
     ctx->stats.kernel_launches += 1;
     return ADG_OK;
 }
@@ -654,12 +659,14 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         return ADG_EINVAL;
     if (trace && (nlig != 1 || trace->ngen < 0)) return ADG_EINVAL;
     int apl = 1, nslots = 32;
+    size_t lig_bytes = 0;
     for (int i = 0; i < nlig; ++i) {
         if (!ligs[i] || ligs[i]->ctx != ctx) return ADG_EINVAL;
         apl = std::max(apl, ligs[i]->apl);
         nslots = std::max(nslots, ligs[i]->nslots);
+        lig_bytes = std::max(lig_bytes, ligs[i]->bytes);
     }
-    const Geo geo = make_geo(apl, nslots);
+    const Geo geo = make_geo(apl, nslots, lig_bytes);
     CK(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
     const long nruns = (long)nlig * p->nrun;

@@ -12,7 +12,7 @@ namespace adg {
 constexpr int kMaxAtoms = ADG_MAX_ATOMS;
 constexpr int kMaxTors = ADG_MAX_TORS;
 constexpr int kGeneStride = 24;  // population rows are padded to 24 floats (>= 7 + 16)
-constexpr int kMaxWarpsPerBlock = 8;
+constexpr int kMaxWarpsPerBlock = 12;
 constexpr uint32_t kGatherPad = 0xffffffffu;
 
 // Per-warp shared memory: xyz[na] and f[na] (float4), torsion frames tu[16]
@@ -20,13 +20,16 @@ constexpr uint32_t kGatherPad = 0xffffffffu;
 // pair scalars (dE/dr)/r).  na = 32 * atoms-per-lane.
 __host__ __device__ inline size_t warp_smem_floats(int na, int nslots) { return (size_t)8 * na + 320 + nslots; }
 
-// Launch geometry of one warp-per-individual kernel launch.
+// Launch geometry of one warp-per-individual kernel launch.  The block's
+// dynamic shared memory holds a copy of its ligand's blob (lig_bytes) and
+// then one region per warp.
 struct Geo {
-    int apl;      // atoms per lane (1, 2, 4)
-    int na;       // 32 * apl
-    int nslots;   // largest pair-slot count of the launched ligands
-    int wpb;      // warps per block
-    size_t smem;  // dynamic shared memory per block (bytes)
+    int apl;           // atoms per lane (1, 2, 4)
+    int na;            // 32 * apl
+    int nslots;        // largest pair-slot count of the launched ligands
+    int wpb;           // warps per block
+    size_t lig_bytes;  // largest ligand blob of the launch (0: read the ligand from global memory)
+    size_t smem;       // dynamic shared memory per block (bytes)
 };
 
 // Ligand as the kernels read it: one POD blob in device memory.
@@ -35,6 +38,8 @@ struct Geo {
 struct LigandDev {
     int natoms, ntors, npairs, nsteps;   // nsteps = ceil(npairs / 32) pair slots per lane
     int gsteps;                          // length of the longest per-lane force-gather list
+    // the blob: this header, then the pair and gather arrays at these byte offsets
+    int blob_bytes, off_ij, off_coef, off_cd, off_gent;
     float cx, cy, cz;                    // reference centroid
     // scoring constants (from the force field)
     float e_cap, rmin2, ms_A, ms_B, ms_k, ms_lb, inv_2s2, inv_s2, k_out;
@@ -115,7 +120,7 @@ struct ResultDev {
 cudaError_t launch_maps_build(cudaStream_t st, const adg_forcefield& ff, const adg_grid_desc& g, int nrec,
                               const float4* rec_xyzq, const int* rec_type, float* maps_out);
 cudaError_t launch_pack_maps(cudaStream_t st, const float* maps, const adg_grid_desc& g, float4* packed);
-Geo make_geo(int apl, int nslots);
+Geo make_geo(int apl, int nslots, size_t lig_bytes);
 cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, const Geo& g, const float* genes,
                          int npose, float* energy, float* grad, int grad_kind);
 cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const Geo& g, const float* genes, int npose, float* xyz);

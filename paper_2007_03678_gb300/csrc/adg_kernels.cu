@@ -18,10 +18,10 @@ namespace adg {
 
 #define FULL_MASK 0xffffffffu
 
-// Minimum resident blocks per SM the generation kernel is compiled for
-// (bounds its registers: 2 -> 128, 3 -> 85 per thread at 256 threads).
-#ifndef ADG_GEN_MIN_BLOCKS
-#define ADG_GEN_MIN_BLOCKS 2
+// Minimum resident blocks per SM the warp-per-individual kernels are
+// compiled for (bounds their registers: 2 blocks of 12 warps -> 85 per thread).
+#ifndef ADG_MIN_BLOCKS
+#define ADG_MIN_BLOCKS 2
 #endif
 
 // ------------------------------------------------------------------ Philox
@@ -250,10 +250,11 @@ struct WarpView {
     float* c;      // (dE/dr)/r per pair slot [nslots]
 };
 
-__device__ __forceinline__ WarpView warp_view(int na, int nslots)
+__device__ __forceinline__ WarpView warp_view(int na, int nslots, int lig_bytes)
 {
     extern __shared__ float4 dyn_smem4[];
-    float* base = reinterpret_cast<float*>(dyn_smem4) + (size_t)(threadIdx.x >> 5) * warp_smem_floats(na, nslots);
+    float* base = reinterpret_cast<float*>(reinterpret_cast<char*>(dyn_smem4) + lig_bytes) +
+                  (size_t)(threadIdx.x >> 5) * warp_smem_floats(na, nslots);
     WarpView v;
     v.xyz = reinterpret_cast<float4*>(base);
     v.f = reinterpret_cast<float4*>(base + 4 * na);
@@ -266,6 +267,29 @@ __device__ __forceinline__ WarpView warp_view(int na, int nslots)
     v.sn = v.cs + 16;
     v.c = v.sn + 16;
     return v;
+}
+
+// Copy the block's ligand blob (header, pair slots, gather program) into the
+// front of the dynamic shared memory; every thread of the block calls this
+// before any warp leaves.  lig_bytes == 0 keeps the ligand in global memory.
+__device__ __forceinline__ LigandRef stage_ligand(const LigandRef& g, int lig_bytes)
+{
+    extern __shared__ float4 dyn_smem4[];
+    if (lig_bytes == 0) return g;
+    const int n16 = g.hdr->blob_bytes / 16;
+    const int4* src = reinterpret_cast<const int4*>(g.hdr);
+    int4* dst = reinterpret_cast<int4*>(dyn_smem4);
+    for (int i = threadIdx.x; i < n16; i += blockDim.x) dst[i] = __ldg(src + i);
+    __syncthreads();
+    const char* b = reinterpret_cast<const char*>(dyn_smem4);
+    const LigandDev* L = reinterpret_cast<const LigandDev*>(b);
+    LigandRef r;
+    r.hdr = L;
+    r.pairs.ij = reinterpret_cast<const int*>(b + L->off_ij);
+    r.pairs.coef = reinterpret_cast<const float4*>(b + L->off_coef);
+    r.pairs.cd = reinterpret_cast<const float*>(b + L->off_cd);
+    r.pairs.gent = reinterpret_cast<const uint32_t*>(b + L->off_gent);
+    return r;
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -427,7 +451,7 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     const int nsteps = L->nsteps;
     for (int stp = 0; stp < nsteps; ++stp) {
         const int idx = stp * 32 + lane;
-        const int ij = __ldg(P.ij + idx);
+        const int ij = P.ij[idx];
         if (ij < 0) {
             if (GRAD) ws.c[idx] = 0.f;
             continue;
@@ -436,8 +460,8 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const float4 xi = ws.xyz[i], xj = ws.xyz[j];
         const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
         const float r2 = dx * dx + dy * dy + dz * dz;
-        const float4 c = __ldg(P.coef + idx);
-        const float cd = __ldg(P.cd + idx);
+        const float4 c = P.coef[idx];
+        const float cd = P.cd[idx];
         const bool fl = r2 < rmin2;
         const float rr2 = fl ? rmin2 : r2;
         const float ri = rsqrtf(rr2);
@@ -475,7 +499,7 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         float ax = 0.f, ay = 0.f, az = 0.f;
         const int gsteps = L->gsteps;
         for (int k = 0; k < gsteps; ++k) {
-            const uint32_t ent = __ldg(P.gent + k * 32 + lane);
+            const uint32_t ent = P.gent[k * 32 + lane];
             if (ent == kGatherPad) break;  // a lane's list is padded at its end only
             const int atom = ent & 127, other = (ent >> 7) & 127, slot = ent >> 14;
             if (atom != cur) {
@@ -544,16 +568,21 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
 }
 
 // ------------------------------------------------------------------ launch geometry
-Geo make_geo(int apl, int nslots)
+Geo make_geo(int apl, int nslots, size_t lig_bytes)
 {
     Geo g;
     g.apl = apl <= 1 ? 1 : (apl <= 2 ? 2 : 4);
     g.na = 32 * g.apl;
     g.nslots = nslots < 32 ? 32 : (nslots + 31) / 32 * 32;
+    g.lig_bytes = (lig_bytes + 255) / 256 * 256;
     const size_t per_warp = warp_smem_floats(g.na, g.nslots) * sizeof(float);
+    // two resident blocks per SM when the ligand and at least 4 warps fit in
+    // half of the 228 KB, else one block of up to 220 KB
     g.wpb = kMaxWarpsPerBlock;
-    while (g.wpb > 1 && (size_t)g.wpb * per_warp > 160u * 1024u) --g.wpb;
-    g.smem = (size_t)g.wpb * per_warp;
+    while (g.wpb > 4 && g.lig_bytes + (size_t)g.wpb * per_warp > 113u * 1024u) --g.wpb;
+    if (g.lig_bytes + (size_t)g.wpb * per_warp > 113u * 1024u)
+        while (g.wpb > 1 && g.lig_bytes + (size_t)g.wpb * per_warp > 220u * 1024u) --g.wpb;
+    g.smem = g.lig_bytes + (size_t)g.wpb * per_warp;
     return g;
 }
 
@@ -568,25 +597,26 @@ static unsigned blocks_for(long nwarps, const Geo& g) { return (unsigned)((nwarp
 
 // ------------------------------------------------------------------ score / pose API kernels
 template <int APL>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_score(MapsDev M, LigandRef LR, int na, int nslots,
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_score(MapsDev M, LigandRef LR, int na, int nslots, int lig_bytes,
                                                                   const float* __restrict__ genes, int npose,
                                                                   float* __restrict__ energy, float* __restrict__ grad,
                                                                   int grad_kind)
 {
     const int lane = threadIdx.x & 31;
     const long pose = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const LigandRef SL = stage_ligand(LR, lig_bytes);
     if (pose >= npose) return;
-    const WarpView ws = warp_view(na, nslots);
-    const LigandDev* L = LR.hdr;
+    const WarpView ws = warp_view(na, nslots, lig_bytes);
+    const LigandDev* L = SL.hdr;
     const int T = L->ntors, G = 7 + T, D = 6 + T;
     if (lane < G) ws.genes[lane] = genes[pose * G + lane];
     __syncwarp();
     if (grad_kind == ADG_GRAD_NONE) {
-        ScoreOut o = warp_score<APL, false>(L, LR.pairs, M, ws.genes, ws, lane);
+        ScoreOut o = warp_score<APL, false>(L, SL.pairs, M, ws.genes, ws, lane);
         if (lane == 0) energy[pose] = o.e;
         return;
     }
-    ScoreOut o = warp_score<APL, true>(L, LR.pairs, M, ws.genes, ws, lane);
+    ScoreOut o = warp_score<APL, true>(L, SL.pairs, M, ws.genes, ws, lane);
     if (lane == 0) energy[pose] = o.e;
     if (grad_kind == ADG_GRAD_TANGENT) {
         if (lane < D) grad[pose * D + lane] = o.gtan;
@@ -620,7 +650,8 @@ cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, 
 #define ADG_SCORE(A)                                                                                            \
     e = allow_smem(k_score<A>, g.smem);                                                                         \
     if (e != cudaSuccess) return e;                                                                             \
-    k_score<A><<<blocks, threads, g.smem, st>>>(m, l, g.na, g.nslots, genes, npose, energy, grad, grad_kind);
+    k_score<A><<<blocks, threads, g.smem, st>>>(m, l, g.na, g.nslots, (int)g.lig_bytes, genes, npose, energy, grad, \
+                                                grad_kind);
     if (g.apl == 1) { ADG_SCORE(1) }
     else if (g.apl == 2) { ADG_SCORE(2) }
     else { ADG_SCORE(4) }
@@ -635,7 +666,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_pose(LigandRef LR, i
     const int lane = threadIdx.x & 31;
     const long pose = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (pose >= npose) return;
-    const WarpView ws = warp_view(na, nslots);
+    const WarpView ws = warp_view(na, nslots, 0);
     const LigandDev* L = LR.hdr;
     const int G = 7 + L->ntors, N = L->natoms;
     if (lane < G) ws.genes[lane] = genes[pose * G + lane];
@@ -652,7 +683,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_pose(LigandRef LR, i
 cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const Geo& g0, const float* genes, int npose, float* xyz)
 {
     if (npose <= 0) return cudaSuccess;
-    const Geo g = make_geo(4, g0.nslots);  // k_pose indexes up to 4 atoms per lane
+    const Geo g = make_geo(4, g0.nslots, 0);  // k_pose indexes up to 4 atoms per lane
     cudaError_t e = allow_smem(k_pose, g.smem);
     if (e != cudaSuccess) return e;
     k_pose<<<blocks_for(npose, g), g.wpb * 32, g.smem, st>>>(l, g.na, g.nslots, genes, npose, xyz);
@@ -818,17 +849,19 @@ __device__ __forceinline__ int tournament(const float* Pe, int pop, uint32_t wa,
 // Generation 0: random genotypes (t uniform in the box, q uniform on S^3 by
 // Shoemake's three uniforms, theta uniform in [-pi, pi)), evaluated.
 template <int APL>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_init(MapsDev M, SearchDev S, DockDev Dk, int na,
-                                                                      int nslots)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock_init(MapsDev M, SearchDev S, DockDev Dk, int na,
+                                                                      int nslots, int lig_bytes, int wpl)
 {
     const int lane = threadIdx.x & 31;
+    // warps of one ligand are padded to whole blocks (wpl per ligand), so a block has one ligand
     const long gw = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const long nruns = (long)Dk.nlig * S.nrun;
-    if (gw >= nruns * S.pop) return;
-    const WarpView ws = warp_view(na, nslots);
-    const int run_g = (int)(gw / S.pop), ind = (int)(gw % S.pop);
-    const int lig = run_g / S.nrun, run = run_g % S.nrun;
-    const LigandRef LR = Dk.ligs[lig];
+    const int lig = (int)(gw / wpl);
+    const int local = (int)(gw % wpl);
+    const LigandRef LR = stage_ligand(Dk.ligs[lig], lig_bytes);
+    if (local >= S.nrun * S.pop) return;
+    const WarpView ws = warp_view(na, nslots, lig_bytes);
+    const int run = local / S.pop, ind = local % S.pop;
+    const int run_g = lig * S.nrun + run;
     const LigandDev* L = LR.hdr;
     const int T = L->ntors, G = 7 + T;
     const Rng rng{S.key0, S.key1, Dk.lig_id[lig], (uint32_t)run, (uint32_t)ind, 0u};
@@ -868,18 +901,22 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_init(MapsDev M,
 // in, so every warp of a generation sees the same total when it decides
 // whether its run is still active.
 template <int APL, int LS>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_GEN_MIN_BLOCKS) k_dock_generation(MapsDev M, SearchDev S, DockDev Dk,
-                                                                            int na, int nslots, int gen)
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock_generation(MapsDev M, SearchDev S, DockDev Dk,
+                                                                            int na, int nslots, int lig_bytes, int wpl,
+                                                                            int gen)
 {
     const int lane = threadIdx.x & 31;
+    // warps of one ligand are padded to whole blocks (wpl per ligand), so a block has one ligand
     const long gw = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long nruns = (long)Dk.nlig * S.nrun;
-    if (gw >= nruns * S.pop) return;
-    const int run_g = (int)(gw / S.pop), ind = (int)(gw % S.pop);
+    const int lig = (int)(gw / wpl);
+    const int local = (int)(gw % wpl);
+    const LigandRef LR = stage_ligand(Dk.ligs[lig], lig_bytes);
+    if (local >= S.nrun * S.pop) return;
+    const int run = local / S.pop, ind = local % S.pop;
+    const int run_g = lig * S.nrun + run;
     if (Dk.evals[run_g] >= (unsigned long long)S.nev || gen > S.max_gen) return;
-    const WarpView ws = warp_view(na, nslots);
-    const int lig = run_g / S.nrun, run = run_g % S.nrun;
-    const LigandRef LR = Dk.ligs[lig];
+    const WarpView ws = warp_view(na, nslots, lig_bytes);
     const LigandDev* L = LR.hdr;
     const int T = L->ntors, G = 7 + T, nb = 2 + T, pop = S.pop;
     const Rng rng{S.key0, S.key1, Dk.lig_id[lig], (uint32_t)run, (uint32_t)ind, (uint32_t)gen};
@@ -983,15 +1020,18 @@ __global__ void k_dock_bookkeep(SearchDev S, DockDev Dk, int gen, int* active)
     if (Dk.evals[r] < nev && gen + 1 <= S.max_gen) atomicAdd(active, 1);
 }
 
+// Warps per ligand: its nrun * pop individuals padded to whole blocks.
+static int warps_per_ligand(const SearchDev& s, const Geo& g) { return (s.nrun * s.pop + g.wpb - 1) / g.wpb * g.wpb; }
+
 cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g)
 {
-    const long nw = (long)d.nlig * s.nrun * s.pop;
-    const unsigned blocks = blocks_for(nw, g), threads = g.wpb * 32;
+    const int wpl = warps_per_ligand(s, g);
+    const unsigned blocks = (unsigned)((long)d.nlig * wpl / g.wpb), threads = g.wpb * 32;
     cudaError_t e;
 #define ADG_INIT(A)                                                                      \
     e = allow_smem(k_dock_init<A>, g.smem);                                              \
     if (e != cudaSuccess) return e;                                                      \
-    k_dock_init<A><<<blocks, threads, g.smem, st>>>(m, s, d, g.na, g.nslots);
+    k_dock_init<A><<<blocks, threads, g.smem, st>>>(m, s, d, g.na, g.nslots, (int)g.lig_bytes, wpl);
     if (g.apl == 1) { ADG_INIT(1) }
     else if (g.apl == 2) { ADG_INIT(2) }
     else { ADG_INIT(4) }
@@ -1003,10 +1043,12 @@ template <int APL, int LS>
 static cudaError_t gen_launch(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g,
                               int gen)
 {
-    const long nw = (long)d.nlig * s.nrun * s.pop;
+    const int wpl = warps_per_ligand(s, g);
+    const unsigned blocks = (unsigned)((long)d.nlig * wpl / g.wpb);
     cudaError_t e = allow_smem(k_dock_generation<APL, LS>, g.smem);
     if (e != cudaSuccess) return e;
-    k_dock_generation<APL, LS><<<blocks_for(nw, g), g.wpb * 32, g.smem, st>>>(m, s, d, g.na, g.nslots, gen);
+    k_dock_generation<APL, LS><<<blocks, g.wpb * 32, g.smem, st>>>(m, s, d, g.na, g.nslots, (int)g.lig_bytes, wpl,
+                                                                   gen);
     return cudaGetLastError();
 }
 
@@ -1038,7 +1080,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_finalize(MapsDe
     const int run_g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const int nruns = Dk.nlig * S.nrun;
     if (run_g >= nruns) return;
-    const WarpView ws = warp_view(na, nslots);
+    const WarpView ws = warp_view(na, nslots, 0);
     const int lig = run_g / S.nrun;
     const LigandDev* L = Dk.ligs[lig].hdr;
     const int G = 7 + L->ntors, N = L->natoms, gd = Dk.gen_done[run_g];
@@ -1074,7 +1116,7 @@ cudaError_t launch_dock_finalize(cudaStream_t st, const MapsDev& m, const Search
                                  ResultDev* out)
 {
     const int nruns = d.nlig * s.nrun;
-    const Geo g = make_geo(4, g0.nslots);  // the final pose indexes up to 4 atoms per lane
+    const Geo g = make_geo(4, g0.nslots, 0);  // the final pose indexes up to 4 atoms per lane
     cudaError_t e = allow_smem(k_dock_finalize, g.smem);
     if (e != cudaSuccess) return e;
     k_dock_finalize<<<blocks_for(nruns, g), g.wpb * 32, g.smem, st>>>(m, s, d, g.na, g.nslots, out);

@@ -57,46 +57,49 @@ def _tol(e):
     return E_ABS + E_REL * np.abs(e)
 
 
-def _compare_generation(gd, od, prev_e):
+def _compare_generation(gd, od, prev_o, prev_g, agree):
     """Compare one generation's decisions.  Philox-only fields (candidates,
     crossover points, mutation mask, LS pick) must be bit-exact.  A
-    tournament winner must match unless the oracle's two candidates have
-    energies within twice the tolerance (a near-tie that FP32 and FP64 may
-    order differently; counted as unresolved, and the GPU's winner must still
-    be one of the two candidates); likewise the elite when the best two
-    energies are that close.  Returns (compared, unresolved, all_equal)."""
+    tournament winner must match when both candidates' energies agree
+    between the two sides (within tolerance) and are not a near-tie (within
+    twice the tolerance of each other, where FP32 and FP64 may order them
+    differently); otherwise it is counted as unresolved and must still be one
+    of the two candidates.  Likewise the elite.  Returns (compared, unresolved)."""
     assert np.array_equal(gd[:, XLO:LSA + 1], od[:, XLO:LSA + 1])
     assert np.array_equal(gd[:, A1:B2 + 1], od[:, A1:B2 + 1])
     compared = unresolved = 0
-    equal = True
-    srt = np.sort(prev_e)
-    if srt[1] - srt[0] > 2 * _tol(srt[0]):
+    order = np.argsort(prev_o, kind="stable")
+    b0, b1 = order[0], order[1]
+    if agree[b0] and prev_o[b1] - prev_o[b0] > 2 * _tol(prev_o[b0]) and (prev_g >= prev_g[b0]).all():
         assert gd[0, P1] == od[0, P1]
         compared += 1
     else:
         unresolved += 1
-        equal &= bool(gd[0, P1] == od[0, P1])
     for i in range(1, len(od)):
         for ca, cb, col in ((A1, B1, P1), (A2, B2, P2)):
             a, b = od[i, ca], od[i, cb]
-            ea, eb = prev_e[a], prev_e[b]
-            if a != b and abs(ea - eb) <= 2 * _tol(min(abs(ea), abs(eb))):
-                unresolved += 1
-                equal &= bool(gd[i, col] == od[i, col])
-                assert gd[i, col] in (a, b)
-            else:
+            resolvable = a == b or (agree[a] and agree[b] and
+                                    abs(prev_o[a] - prev_o[b]) > 2 * _tol(min(abs(prev_o[a]), abs(prev_o[b]))))
+            if resolvable:
                 assert gd[i, col] == od[i, col], f"offspring {i}: winner {gd[i, col]} vs oracle {od[i, col]}"
                 compared += 1
-    return compared, unresolved, equal
+            else:
+                unresolved += 1
+                assert gd[i, col] in (a, b)
+    return compared, unresolved
 
 
 @pytest.mark.parametrize("ls_method,iters", [(0, 0), (2, 12), (1, 12)])
 def test_ga_decisions_bit_exact_first_5_generations(ctx, A, ls_method, iters):
     """Generations 1-5 under the shared Philox stream: tournament candidates,
-    crossover points, mutation masks and local-search picks bit-exact; every
-    tournament winner and elite bit-exact except true near-ties (counted, and
-    required to be rare); populations (genes, energies) within tolerance while
-    the decisions agree.  LS off, ADADELTA and Solis-Wets."""
+    crossover points, mutation masks and local-search picks bit-exact in every
+    generation; every tournament winner and elite bit-exact unless its
+    candidates are a near-tie or already differ between the two sides.  An
+    individual 'agrees' when its genes and energy match the oracle's within
+    tolerance; local search may split an individual off (an ADADELTA iterate
+    within FP32 rounding of a map cell face sees the other side's gradient; a
+    Solis-Wets trial within rounding of the current energy is accepted on one
+    side only), which must stay rare.  LS off, ADADELTA and Solis-Wets."""
     grid, lig, maps64, maps32, ff = ga_problem()
     pop, ngen, nrun = 150, 5, 3
     evals_per_gen = (pop - 1) + pop * (iters if ls_method == 2 else 0)
@@ -106,37 +109,37 @@ def test_ga_decisions_bit_exact_first_5_generations(ctx, A, ls_method, iters):
     Lg = A.Ligand(ctx, ff, lig)
     res, tr = A.dock(ctx, R, Lg, ap, trace_ngen=ngen)
     L = O.Ligand(lig)
-    compared = unresolved = gens_compared = 0
+    compared = unresolved = split = total = 0
     for run in range(nrun):
         init = O.init_population(grid, op, lig.ntors, run=run)
         assert np.abs(tr["init_genes"][run] - init).max() < 1e-5
         init_e = O.score(ff, grid, maps64, L, init)[0]
-        assert (np.abs(tr["init_energies"][run] - init_e) <= _tol(init_e) + 1e-6 * np.abs(init_e)).all()
+        g_e = tr["init_energies"][run]
+        assert (np.abs(g_e - init_e) <= _tol(init_e) + 1e-6 * np.abs(init_e)).all()
         best, bg, evals, gens, (dec, tg, te) = O.lga_run(ff, grid, maps64, L, op, run=run, ntrace=ngen)
         assert gens == ngen
         gd = tr["decisions"][run]
-        prev_e, agree = init_e, True
+        prev_o, prev_g, agree = init_e, g_e, np.ones(pop, bool)
         for g in range(ngen):
-            if not agree:  # a near-tie went the other way: only the Philox-only fields stay comparable
-                assert np.array_equal(gd[g][:, XLO:B2 + 1], dec[g][:, XLO:B2 + 1])
-                continue
-            c, u, eq = _compare_generation(gd[g], dec[g], prev_e)
+            c, u = _compare_generation(gd[g], dec[g], prev_o, prev_g, agree)
             compared += c
             unresolved += u
-            gens_compared += 1
-            if not eq:
-                agree = False
-                continue
-            gdiff = np.abs(tr["genes"][run][g] - tg[g])
-            assert gdiff.max() < 2e-3, gdiff.max()
-            de = np.abs(tr["energies"][run][g] - te[g])
-            assert (de <= _tol(te[g]) + 1e-6 * np.abs(te[g])).all(), de.max()
-            prev_e = te[g]
+            # which individuals still agree after this generation
+            e_ok = np.abs(tr["energies"][run][g] - te[g]) <= _tol(te[g]) + 1e-6 * np.abs(te[g])
+            q_ok = np.abs(tr["genes"][run][g] - tg[g]).max(axis=1) < 2e-3
+            same_parents = (gd[g][:, P1] == dec[g][:, P1]) & (gd[g][:, P2] == dec[g][:, P2])
+            parents_agree = agree[dec[g][:, P1]] & agree[dec[g][:, P2]]
+            agree = e_ok & q_ok
+            # with the same agreeing parents and no local search the child must agree
+            if ls_method == 0:
+                assert agree[same_parents & parents_agree].all()
+            split += int((~agree & same_parents & parents_agree).sum())
+            total += pop
+            prev_o, prev_g = te[g], tr["energies"][run][g]
         if ls_method != 1:
             assert res[0]["evals"][run] == evals == pop + ngen * evals_per_gen
-    # the comparison covered nearly everything
-    assert unresolved <= 0.01 * (compared + unresolved), (compared, unresolved)
-    assert gens_compared >= nrun * ngen - 2
+    assert compared > 0.9 * (compared + unresolved), (compared, unresolved)
+    assert split <= 0.02 * total, (split, total)
 
 
 def test_adadelta_eval_accounting(ctx, A, ff):

@@ -71,7 +71,11 @@ def test_maps_build_matches_oracle_paper_scale_sampled(ctx, A, ff):
     g = g.cpu().numpy().astype(np.float64)
     # full oracle maps are in problem(); also re-check 500 nodes point by point
     err = np.abs(g - maps64)
-    assert (err <= 2e-3 + 1e-5 * np.abs(maps64)).all(), err.max()
+    tol = 2e-3 + 1e-5 * np.abs(maps64)
+    if not (err <= tol).all():
+        worst = np.argsort(-(err / tol).ravel())[:5]
+        rows = [(np.unravel_index(w, err.shape), g.ravel()[w], maps64.ravel()[w]) for w in worst]
+        raise AssertionError(f"{(err > tol).sum()} nodes off; worst (map,z,y,x), gpu, oracle: {rows}")
     rng = np.random.default_rng(1)
     nx, ny, nz = grid.n
     for _ in range(500):
@@ -128,15 +132,15 @@ def test_score_energy_and_gradients_random_poses(ctx, A, ff, name):
     ref_e, ref_ei, ref_gg, ref_gt = ref
     forces = _forces(ff, name, genes)
     clean = inside_box(grid, xyz) & (ref_e < 1e3)
-    well = clean & well_conditioned(forces)
-    assert well.sum() > 50
-    # non-clashing, well-conditioned poses: the plain tolerance
-    assert energy_ok(e, ref_e)[well].all(), _parity_report(e, ref_e, well)
-    # every pose: plus the propagation of FP32 coordinate rounding
+    # every pose: the plain tolerance plus the propagation of FP32 coordinate
+    # rounding through the per-atom forces (random poses sit on steep walls;
+    # the docked-like test below holds well-conditioned poses to the plain one)
     tol = energy_tol(ref_e, forces)
     assert (np.abs(e - ref_e) <= tol).all(), _parity_report(e, ref_e, np.ones(len(e), bool), tol)
+    well = clean & well_conditioned(forces)
+    assert energy_ok(e, ref_e)[well].all(), _parity_report(e, ref_e, well)
     smooth = clean & ~near_face(grid, xyz)
-    assert smooth.sum() > 0.9 * clean.sum()
+    assert smooth.sum() > 0.9 * clean.sum() and smooth.sum() > 50
     ok = grad_ok(gg, ref_gg)[smooth]
     assert ok.all(), f"{(~ok).any(axis=1).sum()} poses with a gradient component off"
     e2, gt, _, _ = _score_both(ctx, A, ff, name, genes, A.GRAD_TANGENT)
@@ -159,6 +163,8 @@ def test_score_docked_like_poses(ctx, A, ff, name):
     genes = np.array(refined, np.float32)
     e, gg, ref, xyz = _score_both(ctx, A, ff, name, genes, A.GRAD_GENES)
     assert (ref[0] < 0).mean() >= 0.4
+    forces = _forces(ff, name, genes)
+    assert well_conditioned(forces).mean() > 0.8
     assert energy_ok(e, ref[0]).all(), _parity_report(e, ref[0], np.ones(len(e), bool))
     smooth = ~near_face(grid, xyz)
     assert grad_ok(gg, ref[2])[smooth].all()
