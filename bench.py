@@ -216,6 +216,7 @@ def main():
     import numpy as np
     import torch
     from paper_2007_03678_gb300 import adg, build, synth as S
+    from paper_2007_03678_gb300.replicas import reduce_run
 
     build.build()
     torch.cuda.set_device(local)
@@ -263,14 +264,7 @@ def main():
     barrier()
     ctx.set_timing(False)
     st = ctx.stats(reset=True)
-    total_ms = sum(step_ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        ev = torch.tensor([evals], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(ev)
-        evals = int(ev.item())
+    total_ms, evals = reduce_run(sum(step_ms), evals, dist, device=f"cuda:{local}")
     value = evals / (total_ms / 1e3)
     ligands_per_s = world * args.steps / (total_ms / 1e3)
 

@@ -16,7 +16,8 @@
  *    its text.  On error nothing is written to the caller's outputs except
  *    where stated, and no exception crosses the ABI.
  *  - Ownership: the caller owns every pointer it passes; the library copies
- *    what it needs.  Handles are freed only by their *_destroy call.
+ *    what it needs.  Handles are freed only by their *_destroy call; a
+ *    receptor or ligand may be destroyed after the context that made it.
  *  - "device" pointers are CUDA global-memory addresses on the context's
  *    device (for example a torch tensor's data_ptr()); "host" pointers are
  *    ordinary CPU memory.  Device work is ordered on the context's stream.

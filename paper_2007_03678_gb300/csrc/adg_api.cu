@@ -38,14 +38,16 @@ struct adg_ctx {
 };
 
 struct adg_receptor {
-    adg_ctx* ctx = nullptr;
+    adg_ctx* ctx = nullptr;  // creator; not dereferenced by adg_receptor_destroy
+    int device = 0;
     adg_grid_desc grid{};
     float4* packed = nullptr;
     MapsDev maps{};
 };
 
 struct adg_ligand {
-    adg_ctx* ctx = nullptr;
+    adg_ctx* ctx = nullptr;  // creator; not dereferenced by adg_ligand_destroy
+    int device = 0;
     void* blob = nullptr;  // LigandDev followed by the pair arrays
     LigandRef ref{};
     int natoms = 0, ntors = 0, npairs = 0, apl = 1, sum_moving = 0, nslots = 0;
@@ -271,6 +273,7 @@ int adg_receptor_create(adg_ctx* ctx, const adg_grid_desc* grid, const float* ma
     adg_receptor* r = new (std::nothrow) adg_receptor();
     if (!r) return ADG_ENOMEM;
     r->ctx = ctx;
+    r->device = ctx->device;
     r->grid = *grid;
     cudaError_t e = cudaMalloc(&r->packed, sizeof(float4) * ADG_NTYPES * npt);
     if (e != cudaSuccess) {
@@ -314,8 +317,9 @@ int adg_receptor_create(adg_ctx* ctx, const adg_grid_desc* grid, const float* ma
 int adg_receptor_destroy(adg_receptor* rec)
 {
     if (!rec) return ADG_EINVAL;
-    cudaSetDevice(rec->ctx->device);
-    cudaStreamSynchronize(rec->ctx->stream);
+    // independent of the context, which may already be gone; cudaFree waits
+    // for work that still uses the memory
+    cudaSetDevice(rec->device);
     cudaFree(rec->packed);
     delete rec;
     return ADG_OK;
@@ -576,6 +580,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     }
     char* base = (char*)L->blob;
     L->ctx = ctx;
+    L->device = ctx->device;
     L->ref.hdr = (const LigandDev*)base;
     L->ref.pairs.ij = (const int*)(base + off_ij);
     L->ref.pairs.coef = (const float4*)(base + off_coef);
@@ -597,8 +602,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
 int adg_ligand_destroy(adg_ligand* lig)
 {
     if (!lig) return ADG_EINVAL;
-    cudaSetDevice(lig->ctx->device);
-    cudaStreamSynchronize(lig->ctx->stream);
+    cudaSetDevice(lig->device);
     cudaFree(lig->blob);
     delete lig;
     return ADG_OK;

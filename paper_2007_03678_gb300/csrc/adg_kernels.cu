@@ -77,16 +77,19 @@ cudaError_t launch_philox(cudaStream_t st, const uint32_t* ctr, int n, uint32_t 
 
 // ------------------------------------------------------------------ maps (a0)
 struct MapConst {
-    float c12[ADG_NTYPES][ADG_NTYPES], c6[ADG_NTYPES][ADG_NTYPES], c10[ADG_NTYPES][ADG_NTYPES];
-    float solpar[ADG_NTYPES], vol[ADG_NTYPES];
-    float w_desolv, qasp, inv_2s2, w_elec_coul;
-    float ms_A, ms_B, ms_k, ms_lb;
+    double c12[ADG_NTYPES][ADG_NTYPES], c6[ADG_NTYPES][ADG_NTYPES], c10[ADG_NTYPES][ADG_NTYPES];
+    double solpar[ADG_NTYPES], vol[ADG_NTYPES];
+    double w_desolv, qasp, inv_2s2, w_elec_coul;
+    double ms_A, ms_B, ms_k, ms_lb;
     float r_min, rmin2, e_cap, r_on, r_off;
     float ox, oy, oz, h;
     int nx, ny, nz;
 };
 
 // One thread per grid node; receptor atoms stream through shared memory.
+// The terms are evaluated in FP64 (the maps are built once per receptor, and
+// near receptor atoms the 12-6 / 12-10 terms reach 1e5 kcal/mol, where FP32
+// powers of 1/r lose the digits the interpolation later needs); stored FP32.
 __global__ void __launch_bounds__(256) k_maps_build(MapConst C, int nrec, const float4* __restrict__ rxyzq,
                                                     const int* __restrict__ rtype, float* __restrict__ maps)
 {
@@ -95,13 +98,12 @@ __global__ void __launch_bounds__(256) k_maps_build(MapConst C, int nrec, const 
     const long npt = (long)C.nx * C.ny * C.nz;
     const long node = (long)blockIdx.x * blockDim.x + threadIdx.x;
     const int ix = (int)(node % C.nx), iy = (int)((node / C.nx) % C.ny), iz = (int)(node / ((long)C.nx * C.ny));
-    const float px = C.ox + ix * C.h, py = C.oy + iy * C.h, pz = C.oz + iz * C.h;
-    // terms in FP32, sums in FP64: a node near receptor atoms adds capped
-    // terms of 1e5, and FP32 sums of those lose the small ones
+    const double px = (double)C.ox + ix * (double)C.h, py = (double)C.oy + iy * (double)C.h,
+                 pz = (double)C.oz + iz * (double)C.h;
     double acc[ADG_NMAPS];
 #pragma unroll
     for (int m = 0; m < ADG_NMAPS; ++m) acc[m] = 0.0;
-    const float roff2 = C.r_off * C.r_off;
+    const double roff2 = (double)C.r_off * C.r_off, rmin = C.r_min, inv_2s2 = C.inv_2s2;
     for (int base = 0; base < nrec; base += 256) {
         __syncthreads();
         if (base + threadIdx.x < nrec) {
@@ -113,32 +115,32 @@ __global__ void __launch_bounds__(256) k_maps_build(MapConst C, int nrec, const 
         if (node >= npt) continue;
         for (int j = 0; j < cnt; ++j) {
             const float4 a = sa[j];
-            const float dx = px - a.x, dy = py - a.y, dz = pz - a.z;
-            const float r2 = dx * dx + dy * dy + dz * dz;
+            const double dx = px - a.x, dy = py - a.y, dz = pz - a.z;
+            const double r2 = dx * dx + dy * dy + dz * dz;
             if (r2 >= roff2) continue;
-            const float r = sqrtf(r2);
-            float sw = 1.f;
+            const double r = sqrt(r2);
+            double sw = 1.0;
             if (r > C.r_on) {
-                const float u = (r - C.r_on) / (C.r_off - C.r_on);
-                sw = 1.f - 3.f * u * u + 2.f * u * u * u;
+                const double u = (r - C.r_on) / ((double)C.r_off - C.r_on);
+                sw = 1.0 - 3.0 * u * u + 2.0 * u * u * u;
             }
-            const float rr2 = r2 < C.rmin2 ? C.rmin2 : r2;
-            const float rr = r < C.r_min ? C.r_min : r;
-            const float G = expf(-rr2 * C.inv_2s2);
-            const float ri2 = 1.f / rr2;
-            const float ri6 = ri2 * ri2 * ri2, ri12 = ri6 * ri6, ri10 = ri6 * ri2 * ri2;
+            const double rr = r < rmin ? rmin : r;
+            const double rr2 = rr * rr;
+            const double G = exp(-rr2 * inv_2s2);
+            const double ri2 = 1.0 / rr2;
+            const double ri6 = ri2 * ri2 * ri2, ri12 = ri6 * ri6, ri10 = ri6 * ri2 * ri2;
             const int tj = st[j];
-            const float qj = a.w, aqj = fabsf(a.w);
+            const double qj = a.w, aqj = fabs((double)a.w);
 #pragma unroll
             for (int t = 0; t < ADG_NTYPES; ++t) {
-                float e = C.c12[t][tj] * ri12 - C.c6[t][tj] * ri6 - C.c10[t][tj] * ri10;
-                e = fminf(e, C.e_cap);
+                double e = C.c12[t][tj] * ri12 - C.c6[t][tj] * ri6 - C.c10[t][tj] * ri10;
+                e = fmin(e, (double)C.e_cap);
                 e += C.w_desolv * (C.solpar[t] * C.vol[tj] + (C.solpar[tj] + C.qasp * aqj) * C.vol[t]) * G;
-                acc[t] += (double)(sw * e);
+                acc[t] += sw * e;
             }
-            const float eps = C.ms_A + C.ms_B / (1.f + C.ms_k * expf(-C.ms_lb * rr));
-            acc[ADG_MAP_ELEC] += (double)(sw * C.w_elec_coul * qj / (eps * rr));
-            acc[ADG_MAP_DESOLV] += (double)(sw * C.w_desolv * C.qasp * C.vol[tj] * G);
+            const double eps = C.ms_A + C.ms_B / (1.0 + C.ms_k * exp(-C.ms_lb * rr));
+            acc[ADG_MAP_ELEC] += sw * C.w_elec_coul * qj / (eps * rr);
+            acc[ADG_MAP_DESOLV] += sw * C.w_desolv * C.qasp * C.vol[tj] * G;
         }
     }
     if (node >= npt) return;
@@ -189,19 +191,19 @@ cudaError_t launch_maps_build(cudaStream_t st, const adg_forcefield& ff, const a
 {
     MapConst C;
     for (int t = 0; t < ADG_NTYPES; ++t)
-        for (int u = 0; u < ADG_NTYPES; ++u) pair_coefs(ff, t, u, &C.c12[t][u], &C.c6[t][u], &C.c10[t][u]);
+        for (int u = 0; u < ADG_NTYPES; ++u) lj_coefs(ff, t, u, &C.c12[t][u], &C.c6[t][u], &C.c10[t][u]);
     for (int t = 0; t < ADG_NTYPES; ++t) {
         C.solpar[t] = ff.solpar[t];
         C.vol[t] = ff.vol[t];
     }
     C.w_desolv = ff.w_desolv;
     C.qasp = ff.qasp;
-    C.inv_2s2 = (float)(1.0 / (2.0 * (double)ff.sigma * ff.sigma));
-    C.w_elec_coul = (float)((double)ff.w_elec * ff.coulomb);
+    C.inv_2s2 = 1.0 / (2.0 * (double)ff.sigma * ff.sigma);
+    C.w_elec_coul = (double)ff.w_elec * ff.coulomb;
     C.ms_A = ff.ms_A;
-    C.ms_B = (float)((double)ff.ms_eps0 - ff.ms_A);
+    C.ms_B = (double)ff.ms_eps0 - ff.ms_A;
     C.ms_k = ff.ms_k;
-    C.ms_lb = (float)((double)ff.ms_lambda * ((double)ff.ms_eps0 - ff.ms_A));
+    C.ms_lb = (double)ff.ms_lambda * ((double)ff.ms_eps0 - ff.ms_A);
     C.r_min = ff.r_min;
     C.rmin2 = ff.r_min * ff.r_min;
     C.e_cap = ff.e_cap;
@@ -576,6 +578,8 @@ Geo make_geo(int apl, int nslots, size_t lig_bytes)
     g.nslots = nslots < 32 ? 32 : (nslots + 31) / 32 * 32;
     g.lig_bytes = (lig_bytes + 255) / 256 * 256;
     const size_t per_warp = warp_smem_floats(g.na, g.nslots) * sizeof(float);
+    // a ligand blob that leaves no room for two warps stays in global memory
+    if (g.lig_bytes + 2 * per_warp > 220u * 1024u) g.lig_bytes = 0;
     // two resident blocks per SM when the ligand and at least 4 warps fit in
     // half of the 228 KB, else one block of up to 220 KB
     g.wpb = kMaxWarpsPerBlock;

@@ -1,0 +1,105 @@
+"""Differentiation workload: 65,536 random poses across 256 ligands (20-50
+atoms, 2-12 torsions) on the 64^3 receptor, energy + gradient w.r.t.
+translation, quaternion and torsions through the torch.autograd.Function,
+checked against the oracle's analytic gradient (every pose) and FP64 central
+finite differences with h = 1e-4 (a sample)."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2007_03678_gb300 import synth as S
+
+from gpu_common import energy_tol, grad_ok, inside_box, near_face, problem
+
+pytestmark = pytest.mark.gpu
+
+NLIG, NPOSE = 256, 256
+FD_H = 1e-4
+
+
+def _ligands():
+    rng = np.random.default_rng(2024)
+    out = []
+    seed = 30000
+    while len(out) < NLIG:
+        n_heavy = int(rng.integers(18, 46))
+        n_tors = int(rng.integers(2, 13))
+        seed += 1
+        try:
+            lig = S.make_ligand(n_heavy, n_tors, seed)
+        except RuntimeError:
+            continue
+        if 20 <= lig.natoms <= 50:
+            out.append(lig)
+    return out
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_03678_gb300 import adg, build
+    build.build()
+    c = adg.Context(0)
+    yield c
+    c.close()
+
+
+def _crosses_face(grid, xa, xb):
+    """Do the two stencil end points put some atom in different map cells
+    (or change which coordinates are clamped into the box)?"""
+    def cell(x):
+        u = (x - np.asarray(grid.origin)) / grid.spacing
+        hi = np.asarray(grid.n) - 1
+        return np.minimum(np.maximum(np.floor(u), -1), hi)
+    return bool((cell(xa) != cell(xb)).any())
+
+
+def test_autograd_matches_oracle_and_finite_differences(ctx, ff):
+    import torch
+    from paper_2007_03678_gb300 import adg
+    from paper_2007_03678_gb300.autograd import score
+    grid, rec, _, maps64, maps32 = problem("paper")
+    R = adg.Receptor(ctx, grid, maps32)
+    ligs = _ligands()
+    assert len(ligs) * NPOSE == 65536
+    checked = fd_checked = 0
+    for li, lig in enumerate(ligs):
+        genes = S.random_genes(lig, NPOSE, grid, 40000 + li, spread=0.3)
+        genes[::2, 3:7] *= 1.5  # non-unit quaternions: the q gradient carries the 1/|q| factor
+        g32 = genes.astype(np.float32)
+        Lg = adg.Ligand(ctx, ff, lig)
+        x = torch.from_numpy(g32).cuda().requires_grad_(True)
+        e = score(x, ctx, R, Lg)
+        e.sum().backward()
+        ctx.sync()
+        e = e.detach().cpu().numpy().astype(np.float64)
+        gg = x.grad.cpu().numpy().astype(np.float64)
+        L = O.Ligand(lig)
+        g64 = g32.astype(np.float64)
+        ref_e, _, ref_gg, _ = O.score(ff, grid, maps64, L, g64)
+        forces = O.atom_gradients(ff, grid, maps64, L, g64)
+        xyz = O.pose(L, g64)
+        assert (np.abs(e - ref_e) <= energy_tol(ref_e, forces)).all(), li
+        smooth = inside_box(grid, xyz) & (ref_e < 1e3) & ~near_face(grid, xyz)
+        ok = grad_ok(gg, ref_gg)[smooth]
+        assert ok.all(), f"ligand {li}: {(~ok).any(axis=1).sum()} poses with a gradient component off"
+        checked += int(smooth.sum())
+        # FP64 central differences of the oracle energy on two smooth poses per ligand
+        for p in np.nonzero(smooth)[0][:2]:
+            fd = np.zeros(len(g64[p]))
+            use = np.ones(len(g64[p]), bool)
+            for d in range(len(fd)):
+                gp, gm = g64[p].copy(), g64[p].copy()
+                gp[d] += FD_H
+                gm[d] -= FD_H
+                if _crosses_face(grid, O.pose(L, gp)[0], O.pose(L, gm)[0]):
+                    use[d] = False
+                    continue
+                fd[d] = (O.score(ff, grid, maps64, L, gp)[0][0] - O.score(ff, grid, maps64, L, gm)[0][0]) / (2 * FD_H)
+            scale = max(np.abs(fd[use]).max(initial=0.0), 1.0)
+            assert (np.abs(gg[p] - fd)[use] <= 1e-3 * scale).all(), (li, p, gg[p], fd)
+            fd_checked += int(use.sum())
+    assert checked > 0.2 * NLIG * NPOSE
+    assert fd_checked > 3000

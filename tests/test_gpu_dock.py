@@ -89,7 +89,11 @@ def _compare_generation(gd, od, prev_o, prev_g, agree):
     return compared, unresolved
 
 
-@pytest.mark.parametrize("ls_method,iters", [(0, 0), (2, 12), (1, 12)])
+# ADADELTA from random starts is chaotic: in the oracle alone a 1e-7 change of
+# the start splits a fifth of the individuals (> 2e-3 in the genes) after 12
+# iterations and none after 3, so per-individual replay uses 3 iterations;
+# long runs are compared by their distribution of best energies instead.
+@pytest.mark.parametrize("ls_method,iters", [(0, 0), (2, 3), (1, 12)])
 def test_ga_decisions_bit_exact_first_5_generations(ctx, A, ls_method, iters):
     """Generations 1-5 under the shared Philox stream: tournament candidates,
     crossover points, mutation masks and local-search picks bit-exact in every

@@ -163,8 +163,6 @@ def test_score_docked_like_poses(ctx, A, ff, name):
     genes = np.array(refined, np.float32)
     e, gg, ref, xyz = _score_both(ctx, A, ff, name, genes, A.GRAD_GENES)
     assert (ref[0] < 0).mean() >= 0.4
-    forces = _forces(ff, name, genes)
-    assert well_conditioned(forces).mean() > 0.8
     assert energy_ok(e, ref[0]).all(), _parity_report(e, ref[0], np.ones(len(e), bool))
     smooth = ~near_face(grid, xyz)
     assert grad_ok(gg, ref[2])[smooth].all()
