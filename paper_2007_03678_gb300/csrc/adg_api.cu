@@ -382,13 +382,6 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
                 }
         }
     }
-    // --- application order: deepest torsion first (depth = ancestor torsions)
-    std::vector<int> tdepth(T, 0), order(T);
-    for (int k = 0; k < T; ++k)
-        for (int j = 0; j < T; ++j)
-            if (j != k && moving[j][tb[k]]) ++tdepth[k];
-    for (int k = 0; k < T; ++k) order[k] = k;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return tdepth[x] > tdepth[y]; });
     // --- rigid fragments (bonds that are not rotatable) and graph distances <= 3
     std::vector<int> frag(N, -1);
     auto is_rot = [&](int u, int v) {
@@ -412,6 +405,59 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         }
         ++nf;
     }
+    // --- fragment tree and the internal depth-first atom order: each fragment
+    // is followed by its subtree, so the atoms a torsion moves are contiguous
+    if (nf != T + 1) return ADG_ETOPO;
+    std::vector<int> fpar(nf, -1), ftor(nf, -1);
+    std::vector<std::vector<int>> fchild(nf);
+    for (int k = 0; k < T; ++k) {
+        const int cf = frag[tb[k]], pf = frag[ta[k]];
+        if (cf == pf || ftor[cf] >= 0) return ADG_ETOPO;
+        fpar[cf] = pf;
+        ftor[cf] = k;
+        fchild[pf].push_back(cf);
+    }
+    std::vector<int> fnew(nf, -1), forder, flev(nf, 0);
+    {
+        std::vector<int> st{frag[d->root]};
+        while (!st.empty()) {
+            const int f = st.back();
+            st.pop_back();
+            fnew[f] = (int)forder.size();
+            forder.push_back(f);
+            for (auto it = fchild[f].rbegin(); it != fchild[f].rend(); ++it) {
+                flev[*it] = flev[f] + 1;
+                st.push_back(*it);
+            }
+        }
+    }
+    if ((int)forder.size() != nf) return ADG_ETOPO;
+    std::vector<int> nw(N, -1), old_of;  // caller index -> internal, internal -> caller
+    std::vector<int> flo(nf), fhi(nf);   // atom range of each fragment (internal fragment index)
+    for (int fi = 0; fi < nf; ++fi) {
+        flo[fi] = (int)old_of.size();
+        for (int i = 0; i < N; ++i)
+            if (frag[i] == forder[fi]) {
+                nw[i] = (int)old_of.size();
+                old_of.push_back(i);
+            }
+        fhi[fi] = (int)old_of.size();
+    }
+    std::vector<int> send(nf);  // end of each fragment's subtree (atoms)
+    for (int fi = nf - 1; fi >= 0; --fi) {
+        send[fi] = fhi[fi];
+        for (int c : fchild[forder[fi]]) send[fi] = std::max(send[fi], send[fnew[c]]);
+    }
+    std::vector<int> slo(T), shi(T);
+    int maxlev = 0;
+    for (int k = 0; k < T; ++k) {
+        const int c = fnew[frag[tb[k]]];
+        slo[k] = flo[c];
+        shi[k] = send[c];
+        for (int i = 0; i < N; ++i)
+            if ((moving[k][i] != 0) != (nw[i] >= slo[k] && nw[i] < shi[k])) return ADG_ETOPO;
+    }
+    for (int f = 0; f < nf; ++f) maxlev = std::max(maxlev, flev[f]);
     std::vector<std::vector<char>> near(N, std::vector<char>(N, 0));
     for (int s = 0; s < N; ++s) {
         std::vector<int> dist(N, -1), q{s};
@@ -427,10 +473,10 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         }
         for (int v : q) near[s][v] = 1;
     }
-    std::vector<std::pair<int, int>> pairs;
+    std::vector<std::pair<int, int>> pairs;  // internal indices
     for (int i = 0; i < N; ++i)
         for (int j = i + 1; j < N; ++j)
-            if (frag[i] != frag[j] && !near[i][j]) pairs.emplace_back(i, j);
+            if (frag[i] != frag[j] && !near[i][j]) pairs.emplace_back(std::min(nw[i], nw[j]), std::max(nw[i], nw[j]));
     const int P = (int)pairs.size();
     // --- lane schedule: 32 pairs per step, greedily without a repeated atom
     std::vector<int> slots;
@@ -510,27 +556,32 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     h.inv_2s2 = (float)(1.0 / (2.0 * (double)ff->sigma * ff->sigma));
     h.inv_s2 = (float)(1.0 / ((double)ff->sigma * ff->sigma));
     h.k_out = ff->k_out;
-    for (int i = 0; i < N; ++i) {
-        h.ref[i] = make_float4(d->xyz[3 * i], d->xyz[3 * i + 1], d->xyz[3 * i + 2], d->charge[i]);
-        h.type[i] = d->type[i];
-        uint32_t m = 0;
-        for (int s = 0; s < T; ++s)
-            if (moving[order[s]][i]) m |= 1u << s;
-        h.tmask[i] = m;
+    for (int n = 0; n < N; ++n) {
+        const int i = old_of[n];
+        h.ref[n] = make_float4(d->xyz[3 * i], d->xyz[3 * i + 1], d->xyz[3 * i + 2], d->charge[i]);
+        h.tf[n] = d->type[i] | (fnew[frag[i]] << 8);
+        h.old_of_new[n] = i;
     }
-    for (int s = 0; s < T; ++s) {
-        const int k = order[s];
-        h.gene_of[s] = k;
-        h.s_of_gene[k] = s;
-        h.ta[s] = ta[k];
-        h.tb[s] = tb[k];
+    h.nfrag = nf;
+    h.maxlev = maxlev;
+    for (int fi = 0; fi < nf; ++fi) {
+        const int f = forder[fi];
+        h.fpar[fi] = fpar[f] >= 0 ? fnew[fpar[f]] : -1;
+        h.ftor[fi] = ftor[f];
+        h.flev[fi] = flev[f];
+    }
+    for (int k = 0; k < T; ++k) {
+        h.ta[k] = nw[ta[k]];
+        h.tb[k] = nw[tb[k]];
+        h.slo[k] = slo[k];
+        h.shi[k] = shi[k];
         const float* pa = d->xyz + 3 * ta[k];
         const float* pb = d->xyz + 3 * tb[k];
         double u[3] = {(double)pb[0] - pa[0], (double)pb[1] - pa[1], (double)pb[2] - pa[2]};
         const double un = sqrt(u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
         if (!(un > 0)) return ADG_ETOPO;
-        h.tpt[s] = make_float4(pa[0], pa[1], pa[2], 0.f);
-        h.tax[s] = make_float4((float)(u[0] / un), (float)(u[1] / un), (float)(u[2] / un), 0.f);
+        h.tpt[k] = make_float4(pa[0], pa[1], pa[2], 0.f);
+        h.tax[k] = make_float4((float)(u[0] / un), (float)(u[1] / un), (float)(u[2] / un), 0.f);
     }
     // --- pair arrays in slot order
     const int ns = nsteps * 32;
@@ -541,9 +592,9 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     for (int s = 0; s < ns; ++s) {
         const int p = slots[s];
         if (p < 0) continue;
-        const int i = pairs[p].first, j = pairs[p].second;
-        const int ti = d->type[i], tj = d->type[j];
-        const double qi = d->charge[i], qj = d->charge[j];
+        const int i = pairs[p].first, j = pairs[p].second;  // internal
+        const int ti = d->type[old_of[i]], tj = d->type[old_of[j]];
+        const double qi = d->charge[old_of[i]], qj = d->charge[old_of[j]];
         float c12, c6, c10;
         pair_coefs(*ff, ti, tj, &c12, &c6, &c10);
         ij[s] = i | (j << 16);
@@ -592,8 +643,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     L->npairs = P;
     L->apl = apl_for(N);
     L->bytes = bytes;
-    for (int k = 0; k < T; ++k)
-        for (int i = 0; i < N; ++i) L->sum_moving += moving[k][i];
+    for (int k = 0; k < T; ++k) L->sum_moving += shi[k] - slo[k];
     ctx->stats.h2d_bytes += (int64_t)bytes;
     *out = L;
     return ADG_OK;

@@ -15,10 +15,11 @@ constexpr int kGeneStride = 24;  // population rows are padded to 24 floats (>= 
 constexpr int kMaxWarpsPerBlock = 12;
 constexpr uint32_t kGatherPad = 0xffffffffu;
 
-// Per-warp shared memory: xyz[na] and f[na] (float4), torsion frames tu[16]
-// and tg[16] (float4), genes/cand/best[32], cs/sn[16], then c[nslots] (the
-// pair scalars (dE/dr)/r).  na = 32 * atoms-per-lane.
-__host__ __device__ inline size_t warp_smem_floats(int na, int nslots) { return (size_t)8 * na + 320 + nslots; }
+// Per-warp shared memory (floats): xyz[na], f[na] and pm[na] (float4 each),
+// the fragment transforms W[52] (float4, three rows per fragment), genes,
+// cand and best [32 each], then c[nslots] (the pair scalars (dE/dr)/r).
+// na = 32 * atoms-per-lane.
+__host__ __device__ inline size_t warp_smem_floats(int na, int nslots) { return (size_t)12 * na + 304 + nslots; }
 
 // Launch geometry of one warp-per-individual kernel launch.  The block's
 // dynamic shared memory holds a copy of its ligand's blob (lig_bytes) and
@@ -33,24 +34,28 @@ struct Geo {
 };
 
 // Ligand as the kernels read it: one POD blob in device memory.
-// Torsions are stored in application order s (deepest first); gene_of[s] is
-// the genotype index k of torsion s (theta_k = genes[7 + k]).
+// Atoms are kept in an internal depth-first order of the rigid-fragment tree
+// (root fragment first, each fragment followed by its subtree), so the atoms
+// moved by torsion k are the contiguous range [slo[k], shi[k]).  Torsions are
+// indexed by their genotype index k (theta_k = genes[7 + k]); fragment f > 0
+// hangs from fragment fpar[f] on torsion ftor[f], at depth flev[f].
 struct LigandDev {
     int natoms, ntors, npairs, nsteps;   // nsteps = ceil(npairs / 32) pair slots per lane
     int gsteps;                          // length of the longest per-lane force-gather list
+    int nfrag, maxlev;                   // fragments (ntors + 1) and the deepest level
     // the blob: this header, then the pair and gather arrays at these byte offsets
     int blob_bytes, off_ij, off_coef, off_cd, off_gent;
     float cx, cy, cz;                    // reference centroid
     // scoring constants (from the force field)
     float e_cap, rmin2, ms_A, ms_B, ms_k, ms_lb, inv_2s2, inv_s2, k_out;
-    float4 ref[kMaxAtoms];               // reference x, y, z and charge q
-    int type[kMaxAtoms];                 // map index 0..6
-    uint32_t tmask[kMaxAtoms];           // bit s set when the atom is moved by torsion s
-    int gene_of[kMaxTors];
-    int s_of_gene[kMaxTors];             // inverse of gene_of
-    int ta[kMaxTors], tb[kMaxTors];      // bond atoms of torsion s (a on the root side)
+    float4 ref[kMaxAtoms];               // reference x, y, z and charge q (internal order)
+    int tf[kMaxAtoms];                   // map type | fragment << 8
+    int old_of_new[kMaxAtoms];           // caller's index of internal atom i
+    int ta[kMaxTors], tb[kMaxTors];      // bond atoms of torsion k (internal; a on the root side)
+    int slo[kMaxTors], shi[kMaxTors];    // atoms moved by torsion k
     float4 tpt[kMaxTors];                // reference position of atom a
     float4 tax[kMaxTors];                // reference unit axis a -> b
+    int fpar[kMaxTors + 1], ftor[kMaxTors + 1], flev[kMaxTors + 1];
 };
 
 // Intramolecular pairs, lane-interleaved: slot (step, lane) = step * 32 + lane.

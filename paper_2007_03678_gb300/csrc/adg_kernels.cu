@@ -240,15 +240,13 @@ cudaError_t launch_pack_maps(cudaStream_t st, const float* maps, const adg_grid_
 // ------------------------------------------------------------------ warp scoring
 // Per-warp views into the dynamic shared memory of the block.
 struct WarpView {
-    float4* xyz;   // posed coordinates [na]
-    float4* f;     // intramolecular force per atom [na] (gather output)
-    float4* tu;    // posed unit axis of torsion s [16]
-    float4* tg;    // u_s x x_a(s) [16]
+    float4* xyz;   // posed coordinates [na] (internal atom order)
+    float4* f;     // intramolecular force per atom, then prefix sums of the total force [na]
+    float4* pm;    // prefix sums of the moments (x - t) x f [na]
+    float4* W;     // fragment transforms, rows 3f..3f+2 = (R row, t) [52]
     float* genes;  // current genotype [32]
     float* cand;   // trial genotype [32]
     float* best;   // best genotype of a local search [32]
-    float* cs;     // cos of torsion s [16]
-    float* sn;     // sin of torsion s [16]
     float* c;      // (dE/dr)/r per pair slot [nslots]
 };
 
@@ -260,14 +258,12 @@ __device__ __forceinline__ WarpView warp_view(int na, int nslots, int lig_bytes)
     WarpView v;
     v.xyz = reinterpret_cast<float4*>(base);
     v.f = reinterpret_cast<float4*>(base + 4 * na);
-    v.tu = reinterpret_cast<float4*>(base + 8 * na);
-    v.tg = reinterpret_cast<float4*>(base + 8 * na + 64);
-    v.genes = base + 8 * na + 128;
+    v.pm = reinterpret_cast<float4*>(base + 8 * na);
+    v.W = reinterpret_cast<float4*>(base + 12 * na);
+    v.genes = base + 12 * na + 208;
     v.cand = v.genes + 32;
     v.best = v.cand + 32;
-    v.cs = v.best + 32;
-    v.sn = v.cs + 16;
-    v.c = v.sn + 16;
+    v.c = v.best + 32;
     return v;
 }
 
@@ -301,68 +297,67 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-// Sum 32 per-lane values across the warp at once: lane l ends with the
-// total of v[l].  Each halving step keeps half of the values and trades the
-// other half with the partner lane (31 shuffles for 32 sums).
-__device__ __forceinline__ float warp_reduce32(float (&v)[32], int lane)
-{
-#pragma unroll
-    for (int w = 16; w >= 1; w >>= 1) {
-        const bool upper = (lane & w) != 0;
-#pragma unroll
-        for (int k = 0; k < w; ++k) {
-            const float send = upper ? v[k] : v[k + w];
-            const float keep = upper ? v[k + w] : v[k];
-            v[k] = keep + __shfl_xor_sync(FULL_MASK, send, w);
-        }
-    }
-    return v[0];
-}
-
 // Genotype g (shared memory, 7+T floats) -> posed coordinates in ws.xyz.
-// Torsions deepest first about their reference axes (Rodrigues), then
-// x' = R(q/|q|) (x - c) + t.
+// Applying the torsions deepest first about their reference axes and then
+// x' = R(q/|q|)(x - c) + t is, per rigid fragment, one affine map
+// W_f = W_parent(f) * Rot_k(f): the rigid-body map for the root fragment,
+// composed down the fragment tree one level at a time (lane f builds
+// fragment f), then applied once to each atom.
 template <int APL>
 __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, const WarpView& ws, int lane)
 {
-    const int N = L->natoms, T = L->ntors;
-    if (lane < T) {
+    const int N = L->natoms, NF = L->nfrag;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;  // this lane's rotation about its torsion axis
+    if (lane == 0) {
+        float qw = g[3], qx = g[4], qy = g[5], qz = g[6];
+        const float qi = 1.f / sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+        qw *= qi; qx *= qi; qy *= qi; qz *= qi;
+        const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
+        const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
+        const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
+        const float cx = L->cx, cy = L->cy, cz = L->cz;
+        ws.W[0] = make_float4(R00, R01, R02, g[0] - (R00 * cx + R01 * cy + R02 * cz));
+        ws.W[1] = make_float4(R10, R11, R12, g[1] - (R10 * cx + R11 * cy + R12 * cz));
+        ws.W[2] = make_float4(R20, R21, R22, g[2] - (R20 * cx + R21 * cy + R22 * cz));
+    } else if (lane < NF) {
+        const int k = L->ftor[lane];
         float s, c;
-        sincosf(g[7 + L->gene_of[lane]], &s, &c);
-        ws.sn[lane] = s;
-        ws.cs[lane] = c;
+        sincosf(g[7 + k], &s, &c);
+        const float4 u = L->tax[k], o = L->tpt[k];
+        const float oc = 1.f - c;
+        // Rodrigues: R = c I + s [u]x + (1 - c) u u^T, about the line through o
+        r0 = make_float4(c + oc * u.x * u.x, oc * u.x * u.y - s * u.z, oc * u.x * u.z + s * u.y, 0.f);
+        r1 = make_float4(oc * u.x * u.y + s * u.z, c + oc * u.y * u.y, oc * u.y * u.z - s * u.x, 0.f);
+        r2 = make_float4(oc * u.x * u.z - s * u.y, oc * u.y * u.z + s * u.x, c + oc * u.z * u.z, 0.f);
+        r0.w = o.x - (r0.x * o.x + r0.y * o.y + r0.z * o.z);
+        r1.w = o.y - (r1.x * o.x + r1.y * o.y + r1.z * o.z);
+        r2.w = o.z - (r2.x * o.x + r2.y * o.y + r2.z * o.z);
     }
-    float qw = g[3], qx = g[4], qy = g[5], qz = g[6];
-    const float qi = 1.f / sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-    qw *= qi; qx *= qi; qy *= qi; qz *= qi;
-    const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
-    const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
-    const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
-    const float tx = g[0], ty = g[1], tz = g[2];
-    const float cx = L->cx, cy = L->cy, cz = L->cz;
     __syncwarp();
+    const int maxlev = L->maxlev;
+    const int mylev = (lane > 0 && lane < NF) ? L->flev[lane] : -1;
+    for (int lev = 1; lev <= maxlev; ++lev) {
+        if (mylev == lev) {
+            const int p = L->fpar[lane];
+            const float4 p0 = ws.W[3 * p], p1 = ws.W[3 * p + 1], p2 = ws.W[3 * p + 2];
+#define ADG_ROW(P) make_float4(P.x * r0.x + P.y * r1.x + P.z * r2.x, P.x * r0.y + P.y * r1.y + P.z * r2.y, \
+                               P.x * r0.z + P.y * r1.z + P.z * r2.z, P.x * r0.w + P.y * r1.w + P.z * r2.w + P.w)
+            ws.W[3 * lane] = ADG_ROW(p0);
+            ws.W[3 * lane + 1] = ADG_ROW(p1);
+            ws.W[3 * lane + 2] = ADG_ROW(p2);
+#undef ADG_ROW
+        }
+        __syncwarp();
+    }
 #pragma unroll
     for (int j = 0; j < APL; ++j) {
         const int a = lane + 32 * j;
         if (a < N) {
             const float4 r = L->ref[a];
-            float px = r.x, py = r.y, pz = r.z;
-            const uint32_t m = L->tmask[a];
-            for (int s = 0; s < T; ++s) {
-                if ((m >> s) & 1u) {
-                    const float4 o = L->tpt[s], u = L->tax[s];
-                    const float c = ws.cs[s], sn = ws.sn[s];
-                    const float vx = px - o.x, vy = py - o.y, vz = pz - o.z;
-                    const float kx = u.y * vz - u.z * vy, ky = u.z * vx - u.x * vz, kz = u.x * vy - u.y * vx;
-                    const float d = (u.x * vx + u.y * vy + u.z * vz) * (1.f - c);
-                    px = o.x + vx * c + kx * sn + u.x * d;
-                    py = o.y + vy * c + ky * sn + u.y * d;
-                    pz = o.z + vz * c + kz * sn + u.z * d;
-                }
-            }
-            const float dx = px - cx, dy = py - cy, dz = pz - cz;
-            ws.xyz[a] = make_float4(R00 * dx + R01 * dy + R02 * dz + tx, R10 * dx + R11 * dy + R12 * dz + ty,
-                                    R20 * dx + R21 * dy + R22 * dz + tz, 0.f);
+            const int f = L->tf[a] >> 8;
+            const float4 w0 = ws.W[3 * f], w1 = ws.W[3 * f + 1], w2 = ws.W[3 * f + 2];
+            ws.xyz[a] = make_float4(w0.x * r.x + w0.y * r.y + w0.z * r.z + w0.w, w1.x * r.x + w1.y * r.y + w1.z * r.z + w1.w,
+                                    w2.x * r.x + w2.y * r.y + w2.z * r.z + w2.w, 0.f);
         }
     }
     __syncwarp();
@@ -443,7 +438,7 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const int a = lane + 32 * j;
         if (a < N) {
             const float4 x = ws.xyz[a];
-            e += atom_inter<GRAD>(M, k_out, L->type[a], L->ref[a].w, x.x, x.y, x.z, fxr[j], fyr[j], fzr[j]);
+            e += atom_inter<GRAD>(M, k_out, L->tf[a] & 255, L->ref[a].w, x.x, x.y, x.z, fxr[j], fyr[j], fzr[j]);
             if (GRAD) ws.f[a] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
@@ -518,54 +513,73 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         }
         if (cur >= 0) ws.f[cur] = make_float4(ax, ay, az, 0.f);
     }
-    // posed torsion frames: u_s and u_s x x_a(s), one lane per torsion
-    if (lane < T) {
-        const float4 xa = ws.xyz[L->ta[lane]], xb = ws.xyz[L->tb[lane]];
-        float ux = xb.x - xa.x, uy = xb.y - xa.y, uz = xb.z - xa.z;
-        const float un = rsqrtf(ux * ux + uy * uy + uz * uz);
-        ux *= un; uy *= un; uz *= un;
-        ws.tu[lane] = make_float4(ux, uy, uz, 0.f);
-        ws.tg[lane] = make_float4(uy * xa.z - uz * xa.y, uz * xa.x - ux * xa.z, ux * xa.y - uy * xa.x, 0.f);
-    }
     __syncwarp();
+    // Per atom: total force f and moment m = (x - t) x f.  Inclusive prefix
+    // sums over the internal atom order go to ws.f / ws.pm; the atoms moved by
+    // torsion k are the range [slo, shi), so
+    //   dE/dtheta_k = u . ((x - x_a) x f) summed there = u . M_k - (u x (x_a - t)) . F_k
+    // with F_k, M_k differences of prefix sums and u the posed axis a -> b.
     const float tx = g[0], ty = g[1], tz = g[2];
-    float v[32];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) v[k] = 0.f;
+    float cf0 = 0.f, cf1 = 0.f, cf2 = 0.f, cm0 = 0.f, cm1 = 0.f, cm2 = 0.f;  // carry of earlier slots
 #pragma unroll
     for (int j = 0; j < APL; ++j) {
         const int a = lane + 32 * j;
+        float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
         if (a < N) {
             const float4 fi = ws.f[a];
-            const float fx = fxr[j] + fi.x, fy = fyr[j] + fi.y, fz = fzr[j] + fi.z;
+            v0 = fxr[j] + fi.x;
+            v1 = fyr[j] + fi.y;
+            v2 = fzr[j] + fi.z;
             const float4 x = ws.xyz[a];
             const float rx = x.x - tx, ry = x.y - ty, rz = x.z - tz;
-            v[0] += fx;
-            v[1] += fy;
-            v[2] += fz;
-            v[3] += ry * fz - rz * fy;
-            v[4] += rz * fx - rx * fz;
-            v[5] += rx * fy - ry * fx;
-            // dE/dtheta_s += u_s . ((x - x_a) x f) = u_s . (x x f) - (u_s x x_a) . f
-            const float mx = x.y * fz - x.z * fy, my = x.z * fx - x.x * fz, mz = x.x * fy - x.y * fx;
-            const uint32_t m = L->tmask[a];
+            v3 = ry * v2 - rz * v1;
+            v4 = rz * v0 - rx * v2;
+            v5 = rx * v1 - ry * v0;
+        }
 #pragma unroll
-            for (int s = 0; s < kMaxTors; ++s) {
-                if (s < T && ((m >> s) & 1u)) {
-                    const float4 u = ws.tu[s], q = ws.tg[s];
-                    v[6 + s] += u.x * mx + u.y * my + u.z * mz - (q.x * fx + q.y * fy + q.z * fz);
-                }
+        for (int o = 1; o < 32; o <<= 1) {
+            const float u0 = __shfl_up_sync(FULL_MASK, v0, o), u1 = __shfl_up_sync(FULL_MASK, v1, o),
+                        u2 = __shfl_up_sync(FULL_MASK, v2, o), u3 = __shfl_up_sync(FULL_MASK, v3, o),
+                        u4 = __shfl_up_sync(FULL_MASK, v4, o), u5 = __shfl_up_sync(FULL_MASK, v5, o);
+            if (lane >= o) {
+                v0 += u0; v1 += u1; v2 += u2; v3 += u3; v4 += u4; v5 += u5;
             }
         }
+        v0 += cf0; v1 += cf1; v2 += cf2; v3 += cm0; v4 += cm1; v5 += cm2;
+        ws.f[a] = make_float4(v0, v1, v2, 0.f);
+        ws.pm[a] = make_float4(v3, v4, v5, 0.f);
+        if (j + 1 < APL) {
+            cf0 = __shfl_sync(FULL_MASK, v0, 31); cf1 = __shfl_sync(FULL_MASK, v1, 31);
+            cf2 = __shfl_sync(FULL_MASK, v2, 31); cm0 = __shfl_sync(FULL_MASK, v3, 31);
+            cm1 = __shfl_sync(FULL_MASK, v4, 31); cm2 = __shfl_sync(FULL_MASK, v5, 31);
+        }
     }
-    const float mine = warp_reduce32(v, lane);
-    // lane 6 + k takes torsion gene k from lane 6 + s_of_gene[k] (application order)
-    const int src = (lane >= 6 && lane < 6 + T) ? 6 + L->s_of_gene[lane - 6] : lane;
-    const float val = __shfl_sync(FULL_MASK, mine, src);
-    out.gtan = lane < 6 + T ? val : 0.f;
-    out.tx = __shfl_sync(FULL_MASK, mine, 3);
-    out.ty = __shfl_sync(FULL_MASK, mine, 4);
-    out.tz = __shfl_sync(FULL_MASK, mine, 5);
+    __syncwarp();
+    float val = 0.f;
+    if (lane < 6) {
+        const float4 F = ws.f[N - 1], Mt = ws.pm[N - 1];
+        val = lane == 0 ? F.x : lane == 1 ? F.y : lane == 2 ? F.z : lane == 3 ? Mt.x : lane == 4 ? Mt.y : Mt.z;
+    } else if (lane < 6 + T) {
+        const int k = lane - 6;
+        const int lo = L->slo[k], hi = L->shi[k];
+        float4 F = ws.f[hi - 1], Mk = ws.pm[hi - 1];
+        if (lo > 0) {
+            const float4 F0 = ws.f[lo - 1], M0 = ws.pm[lo - 1];
+            F.x -= F0.x; F.y -= F0.y; F.z -= F0.z;
+            Mk.x -= M0.x; Mk.y -= M0.y; Mk.z -= M0.z;
+        }
+        const float4 xa = ws.xyz[L->ta[k]], xb = ws.xyz[L->tb[k]];
+        float ux = xb.x - xa.x, uy = xb.y - xa.y, uz = xb.z - xa.z;
+        const float un = rsqrtf(ux * ux + uy * uy + uz * uz);
+        ux *= un; uy *= un; uz *= un;
+        const float ax = xa.x - tx, ay = xa.y - ty, az = xa.z - tz;
+        const float gx = uy * az - uz * ay, gy = uz * ax - ux * az, gz = ux * ay - uy * ax;
+        val = ux * Mk.x + uy * Mk.y + uz * Mk.z - (gx * F.x + gy * F.y + gz * F.z);
+    }
+    out.gtan = val;
+    out.tx = __shfl_sync(FULL_MASK, val, 3);
+    out.ty = __shfl_sync(FULL_MASK, val, 4);
+    out.tz = __shfl_sync(FULL_MASK, val, 5);
     return out;
 }
 
@@ -678,9 +692,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_pose(LigandRef LR, i
     warp_pose<4>(L, ws.genes, ws, lane);
     for (int a = lane; a < N; a += 32) {
         const float4 x = ws.xyz[a];
-        xyz[(pose * N + a) * 3 + 0] = x.x;
-        xyz[(pose * N + a) * 3 + 1] = x.y;
-        xyz[(pose * N + a) * 3 + 2] = x.z;
+        const long o = (pose * N + L->old_of_new[a]) * 3;
+        xyz[o + 0] = x.x;
+        xyz[o + 1] = x.y;
+        xyz[o + 2] = x.z;
     }
 }
 
@@ -1110,9 +1125,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_finalize(MapsDe
     if (lane < kGeneStride) R.genes[lane] = lane < G ? ws.genes[lane] : 0.f;
     for (int a = lane; a < N; a += 32) {
         const float4 x = ws.xyz[a];
-        R.xyz[3 * a] = x.x;
-        R.xyz[3 * a + 1] = x.y;
-        R.xyz[3 * a + 2] = x.z;
+        const int o = 3 * L->old_of_new[a];
+        R.xyz[o] = x.x;
+        R.xyz[o + 1] = x.y;
+        R.xyz[o + 2] = x.z;
     }
 }
 

@@ -52,7 +52,7 @@ def forcefield() -> dict:
         "S":  (4.00, 0.200, 33.51, -0.00214, 0, 0, 0.0, 0.0),
     }
     cols = list(zip(*[per_type[n] for n in TYPE_NAMES]))
-    return dict(
+    ff = dict(
         Rii=list(cols[0]), epsii=list(cols[1]), vol=list(cols[2]), solpar=list(cols[3]),
         hb_donor=[int(v) for v in cols[4]], hb_acceptor=[int(v) for v in cols[5]],
         hb_R=list(cols[6]), hb_eps=list(cols[7]),
@@ -61,6 +61,12 @@ def forcefield() -> dict:
         ms_A=-8.5525, ms_eps0=78.4, ms_lambda=0.003627, ms_k=7.7839,
         r_min=0.5, e_cap=1.0e5, map_r_on=7.0, map_r_off=8.0, k_out=10.0,
     )
+    # the library receives the table as float32: round every real value here
+    for k, v in ff.items():
+        if k in ("hb_donor", "hb_acceptor"):
+            continue
+        ff[k] = [float(x) for x in f32(v)] if isinstance(v, list) else float(f32(v))
+    return ff
 
 
 @dataclass
@@ -96,6 +102,14 @@ LIGAND_HEAVY_FREQ = {T_C: 0.55, T_A: 0.15, T_N: 0.05, T_NA: 0.05, T_OA: 0.12, T_
 
 def _recentre(q: np.ndarray) -> np.ndarray:
     return q - q.mean()
+
+
+def f32(x):
+    """Round to float32-representable float64 values.  The C ABI takes
+    float32, so every real-valued input is drawn at that precision and the
+    float64 copy handed to a CPU checker is bit-identical to what the GPU
+    receives."""
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
 
 
 def make_receptor(natoms: int, grid: Grid, seed: int = 1, min_sep: float = 2.0,
@@ -139,7 +153,7 @@ def make_receptor(natoms: int, grid: Grid, seed: int = 1, min_sep: float = 2.0,
                 count += 1
     types = rng.choice(NTYPES, size=natoms, p=RECEPTOR_TYPE_FREQ / RECEPTOR_TYPE_FREQ.sum())
     q = _recentre(rng.normal(0.0, 0.2, size=natoms))
-    return Receptor(pts, types.astype(np.int32), q)
+    return Receptor(f32(pts), types.astype(np.int32), f32(q))
 
 
 @dataclass
@@ -266,7 +280,7 @@ def make_ligand(n_heavy: int, n_tors: int, seed: int, n_hd: int | None = None,
         q = _recentre(rng.normal(0.0, 0.2, size=n))
         xyz = np.array(xyz)
         xyz -= xyz.mean(axis=0)
-        return Ligand(xyz, np.array(types, dtype=np.int32), q, bonds, tors, 0,
+        return Ligand(f32(xyz), np.array(types, dtype=np.int32), f32(q), bonds, tors, 0,
                       dict(n_heavy=n_heavy, n_hd=n_hd, seed=seed))
     raise RuntimeError(f"could not grow ligand n_heavy={n_heavy} n_tors={n_tors} seed={seed}")
 

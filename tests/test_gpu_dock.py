@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 from paper_2007_03678_gb300 import synth as S
 
-from gpu_common import E_ABS, E_REL, ga_problem, problem
+from gpu_common import E_ABS, E_REL, energy_tol, ga_problem, problem
 
 pytestmark = pytest.mark.gpu
 
@@ -129,7 +129,8 @@ def test_ga_decisions_bit_exact_first_5_generations(ctx, A, ls_method, iters):
             compared += c
             unresolved += u
             # which individuals still agree after this generation
-            e_ok = np.abs(tr["energies"][run][g] - te[g]) <= _tol(te[g]) + 1e-6 * np.abs(te[g])
+            forces = O.atom_gradients(ff, grid, maps64, L, tg[g])
+            e_ok = np.abs(tr["energies"][run][g] - te[g]) <= energy_tol(te[g], forces)
             q_ok = np.abs(tr["genes"][run][g] - tg[g]).max(axis=1) < 2e-3
             same_parents = (gd[g][:, P1] == dec[g][:, P1]) & (gd[g][:, P2] == dec[g][:, P2])
             parents_agree = agree[dec[g][:, P1]] & agree[dec[g][:, P2]]
@@ -142,8 +143,9 @@ def test_ga_decisions_bit_exact_first_5_generations(ctx, A, ls_method, iters):
             prev_o, prev_g = te[g], tr["energies"][run][g]
         if ls_method != 1:
             assert res[0]["evals"][run] == evals == pop + ngen * evals_per_gen
-    assert compared > 0.9 * (compared + unresolved), (compared, unresolved)
-    assert split <= 0.02 * total, (split, total)
+    stats = dict(compared=compared, unresolved=unresolved, split=split, total=total)
+    assert compared > 0.9 * (compared + unresolved), stats
+    assert split <= 0.02 * total, stats
 
 
 def test_adadelta_eval_accounting(ctx, A, ff):
