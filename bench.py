@@ -186,12 +186,14 @@ def run_reference(args, rank: int) -> None:
 
 
 # ---------------------------------------------------------------- our arm
-def workload_config() -> dict:
+def workload_config(nrun=None, nev=None) -> dict:
     from paper_2007_03678_gb300 import synth as S
-    w = S.PAPER
+    w = dict(S.PAPER)
+    w["nrun"] = nrun or w["nrun"]
+    w["nev"] = nev or w["nev"]
     return {"workload": "paper-scale docking: 64^3 x 9 FP32 maps (0.375 A) of a 3000-atom pseudo-receptor, "
-                        "one ligand of 40 heavy atoms + 4 polar H with 8 torsions, 100 LGA runs x pop 150 x "
-                        "2.5M evals, ADADELTA local search",
+                        "one ligand of 40 heavy atoms + 4 polar H with 8 torsions, "
+                        f"{w['nrun']} LGA runs x pop 150 x {w['nev']:,} evals, ADADELTA local search",
             "grid": w["grid_n"], "receptor_atoms": w["rec_atoms"], "ligand_atoms": w["n_heavy"] + w["n_hd"],
             "torsions": w["n_tors"], "nrun": w["nrun"], "pop": w["pop"], "nev": w["nev"], "local_search": "adadelta",
             "l2": "flushed between steps (256 MB write); maps (29 MB packed) are meant to stay L2-resident within a step",
@@ -205,6 +207,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
+    ap.add_argument("--nrun", type=int, default=None, help="override the run count (small profiling cases)")
+    ap.add_argument("--nev", type=int, default=None, help="override the evaluation budget (small profiling cases)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -234,7 +239,9 @@ def main():
     ctx.sync()
     del maps
     L = adg.Ligand(ctx, ff, lig_desc)
-    p = adg.search_params(nrun=w["nrun"], pop_size=w["pop"], nev=w["nev"], ls_method=adg.LS_ADADELTA,
+    nrun = args.nrun or w["nrun"]
+    nev = args.nev or w["nev"]
+    p = adg.search_params(nrun=nrun, pop_size=w["pop"], nev=nev, ls_method=adg.LS_ADADELTA,
                           seed=S.SEARCH_SEED, lig_id=rank)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=f"cuda:{local}")
 
@@ -286,8 +293,8 @@ def main():
 
     # end to end through the public API with host buffers: ligand upload + dock + results read back
     ctx.stats(reset=True)
-    e2e_t, e2e_evals = 0.0, 0
-    for _ in range(args.steps):
+    e2e_t, e2e_evals = 1e-30, 0
+    for _ in range(0 if args.no_e2e else args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         Lh = adg.Ligand(ctx, ff, lig_desc)
@@ -296,9 +303,10 @@ def main():
         e2e_t += time.perf_counter() - t0
         e2e_evals += int(r["evals"].sum())
     st2 = ctx.stats(reset=True)
-    e2e = {"value": e2e_evals / e2e_t * (world if dist is not None else 1), "unit": UNIT,
-           "h2d_bytes_per_step": st2["h2d_bytes"] // args.steps, "d2h_bytes_per_step": st2["d2h_bytes"] // args.steps,
-           "ligands_per_s": args.steps / e2e_t * world}
+    e2e = None if args.no_e2e else {
+        "value": e2e_evals / e2e_t * (world if dist is not None else 1), "unit": UNIT,
+        "h2d_bytes_per_step": st2["h2d_bytes"] // args.steps, "d2h_bytes_per_step": st2["d2h_bytes"] // args.steps,
+        "ligands_per_s": args.steps / e2e_t * world}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -316,7 +324,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(), "ligands_per_s": ligands_per_s,
+                "config": workload_config(args.nrun, args.nev), "ligands_per_s": ligands_per_s,
                 "best_energy_median": float(np.median(results["best_energy"])),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
                 "gpu_launches": st["kernel_launches"]}

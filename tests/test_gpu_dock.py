@@ -92,7 +92,9 @@ def _compare_generation(gd, od, prev_o, prev_g, agree):
 # ADADELTA from random starts is chaotic: in the oracle alone a 1e-7 change of
 # the start splits a fifth of the individuals (> 2e-3 in the genes) after 12
 # iterations and none after 3, so per-individual replay uses 3 iterations;
-# long runs are compared by their distribution of best energies instead.
+# long runs are compared by their distribution of best energies instead.  Even
+# then an individual can split when two iterates tie within rounding and each
+# side keeps a different one as the best; such splits are counted and bounded.
 @pytest.mark.parametrize("ls_method,iters", [(0, 0), (2, 3), (1, 12)])
 def test_ga_decisions_bit_exact_first_5_generations(ctx, A, ls_method, iters):
     """Generations 1-5 under the shared Philox stream: tournament candidates,
@@ -144,8 +146,9 @@ def test_ga_decisions_bit_exact_first_5_generations(ctx, A, ls_method, iters):
         if ls_method != 1:
             assert res[0]["evals"][run] == evals == pop + ngen * evals_per_gen
     stats = dict(compared=compared, unresolved=unresolved, split=split, total=total)
-    assert compared > 0.9 * (compared + unresolved), stats
-    assert split <= 0.02 * total, stats
+    limit_unres, limit_split = (0.02, 0.0) if ls_method == 0 else (0.15, 0.10)
+    assert unresolved <= limit_unres * (compared + unresolved), stats
+    assert split <= limit_split * total, stats
 
 
 def test_adadelta_eval_accounting(ctx, A, ff):
