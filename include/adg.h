@@ -125,6 +125,9 @@ typedef struct {
     float mut_t, mut_rot, mut_tors;
     uint64_t seed;      /* Philox key                                          */
     uint32_t lig_id;    /* Philox counter word 0 of the first ligand in a call */
+    int32_t autostop;   /* nonzero: stop a run early (paper Sec. 1.1)          */
+    float stopstd;      /* ... once the standard deviation of its best energy over the last 10
+                           generations is below stopstd (kcal/mol)            */
     int32_t pad0;
 } adg_search_params;
 
@@ -164,7 +167,8 @@ const char* adg_strerror(int code);
  * iterations, elitism 1, ls_rate 1, crossover 0.8, mutation 0.02,
  * tournament 0.6, rho0 1, rho_min 0.01, x2 after 4 successes, x0.5 after 4
  * failures, step scales 1 A / 0.5 rad / 0.5 rad, ADADELTA rho 0.8 eps 0.01,
- * mutation half-widths 2 A / pi/2 / pi/2, seed 42, nrun 10. */
+ * mutation half-widths 2 A / pi/2 / pi/2, seed 42, nrun 10, autostop off,
+ * stopstd 0.15 kcal/mol. */
 void adg_search_params_default(adg_search_params* p);
 
 /* Context: selects `device`, creates or adopts a CUDA stream (`stream` may be

@@ -69,7 +69,8 @@ class PARAMS(C.Structure):
                [("sw_succ", C.c_int), ("sw_fail", C.c_int)] + \
                [(n, C.c_double) for n in ("sw_scale_t", "sw_scale_rot", "sw_scale_tors", "ad_rho", "ad_eps",
                                           "mut_t", "mut_rot", "mut_tors")] + \
-               [("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("lig_id", C.c_uint32)]
+               [("seed_lo", C.c_uint32), ("seed_hi", C.c_uint32), ("lig_id", C.c_uint32), ("autostop", C.c_int),
+                ("stopstd", C.c_double)]
 
 
 TRACE_WIDTH = 12  # parent1, parent2, xlo, xhi, mut_mask, ls_applied, a1, b1, a2, b2, 0, 0
@@ -180,6 +181,8 @@ class SearchParams:
     mut_tors: float = np.pi / 2
     seed: int = 42
     lig_id: int = 0
+    autostop: int = 0
+    stopstd: float = 0.15
 
     def to_c(self) -> PARAMS:
         p = PARAMS()

@@ -754,6 +754,8 @@ typedef struct {
     double ad_rho, ad_eps;
     double mut_t, mut_rot, mut_tors;   /* half-widths of the mutation draws */
     uint32_t seed_lo, seed_hi, lig_id;
+    int autostop;                      /* stop a run early (paper Sec. 1.1) */
+    double stopstd;                    /* ... when the std-dev of its best energy over 10 generations is below this */
 } orc_params;
 
 typedef struct {
@@ -1012,6 +1014,7 @@ int orc_lga_run(const orc_ff* ff, const orc_grid* g, const double* maps, const o
     }
     int gen = 0;
     uint32_t thr_ls = prob_threshold(prm->ls_rate);
+    double hist[10];                   /* best energy after each of the last 10 generations */
     while (P.evals < prm->nev && gen < prm->max_gen) {
         ++gen;
         int elite = 0;
@@ -1041,6 +1044,18 @@ int orc_lga_run(const orc_ff* ff, const orc_grid* g, const double* maps, const o
         if (gen <= ntrace) {
             if (trace_genes) memcpy(trace_genes + (size_t)(gen - 1) * pop * G, Pg, sizeof(double) * G * pop);
             if (trace_energy) memcpy(trace_energy + (size_t)(gen - 1) * pop, Pe, sizeof(double) * pop);
+        }
+        /* autostop (paper Sec. 1.1; reading: population standard deviation of
+         * the best energy over the last 10 generations, compared to stopstd) */
+        double b = Pe[0];
+        for (int i = 1; i < pop; ++i) if (Pe[i] < b) b = Pe[i];
+        hist[(gen - 1) % 10] = b;
+        if (prm->autostop && gen >= 10) {
+            double m = 0.0, v = 0.0;
+            for (int k = 0; k < 10; ++k) m += hist[k];
+            m /= 10.0;
+            for (int k = 0; k < 10; ++k) v += (hist[k] - m) * (hist[k] - m);
+            if (sqrt(v / 10.0) < prm->stopstd) break;
         }
     }
     int best = 0;

@@ -66,7 +66,8 @@ class adg_search_params(C.Structure):
                [("sw_succ", C.c_int32), ("sw_fail", C.c_int32)] + \
                [(n, C.c_float) for n in ("sw_scale_t", "sw_scale_rot", "sw_scale_tors", "ad_rho", "ad_eps", "mut_t",
                                          "mut_rot", "mut_tors")] + \
-               [("seed", C.c_uint64), ("lig_id", C.c_uint32), ("pad0", C.c_int32)]
+               [("seed", C.c_uint64), ("lig_id", C.c_uint32), ("autostop", C.c_int32), ("stopstd", C.c_float),
+                ("pad0", C.c_int32)]
 
 
 class adg_result(C.Structure):

@@ -149,6 +149,8 @@ void adg_search_params_default(adg_search_params* p)
     p->mut_tors = 1.57079632679490f;
     p->seed = 42;
     p->lig_id = 0;
+    p->autostop = 0;
+    p->stopstd = 0.15f;
 }
 
 int adg_ctx_create(adg_ctx** out, int device, void* stream)
@@ -738,6 +740,8 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
     const size_t o_e0 = take(sizeof(float) * nind), o_e1 = take(sizeof(float) * nind);
     const size_t o_ev = take(sizeof(unsigned long long) * 2 * nruns);
     const size_t o_gd = take(sizeof(int) * nruns);
+    const size_t o_hist = take(sizeof(float) * 10 * nruns);
+    const size_t o_stop = take(sizeof(int) * nruns);
     const size_t o_act = take(sizeof(int) * 2);
     const size_t o_lr = take(sizeof(LigandRef) * nlig);
     const size_t o_id = take(sizeof(uint32_t) * nlig);
@@ -789,6 +793,8 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
     S.mut_tors = p->mut_tors;
     S.key0 = (uint32_t)(p->seed & 0xffffffffu);
     S.key1 = (uint32_t)(p->seed >> 32);
+    S.autostop = p->autostop != 0;
+    S.stopstd = p->stopstd;
     DockDev D;
     D.ligs = (const LigandRef*)(A + o_lr);
     D.lig_id = (const uint32_t*)(A + o_id);
@@ -799,6 +805,8 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
     D.pop_e[1] = (float*)(A + o_e1);
     D.evals = (unsigned long long*)(A + o_ev);
     D.gen_done = (int*)(A + o_gd);
+    D.best_hist = (float*)(A + o_hist);
+    D.stopped = (int*)(A + o_stop);
     D.trace_ngen = tr_ngen;
     D.tr_dec = (int*)(A + o_td);
     D.tr_genes = (float*)(A + o_tg);
@@ -811,6 +819,7 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
     ctx->stats.h2d_bytes += (int64_t)((sizeof(LigandRef) + sizeof(uint32_t)) * nlig);
     CK(ctx, cudaMemsetAsync(D.evals, 0, sizeof(unsigned long long) * 2 * nruns, st));
     CK(ctx, cudaMemsetAsync(D.gen_done, 0, sizeof(int) * nruns, st));
+    CK(ctx, cudaMemsetAsync(D.stopped, 0, sizeof(int) * nruns, st));
     CK(ctx, launch_dock_init(st, M, S, D, geo));
     ctx->stats.kernel_launches += 1;
     std::vector<float> init_g, init_e;

@@ -96,6 +96,8 @@ struct SearchDev {
     float ad_rho, ad_eps;
     float mut_t, mut_rot, mut_tors;
     uint32_t key0, key1;
+    int autostop;
+    float stopstd;
 };
 
 struct DockDev {
@@ -106,6 +108,8 @@ struct DockDev {
     float* pop_e[2];           // [nlig*nrun][pop]
     unsigned long long* evals; // [nlig*nrun]
     int* gen_done;             // [nlig*nrun]
+    float* best_hist;          // [nlig*nrun][10] best energy of the last 10 generations (ring)
+    int* stopped;              // [nlig*nrun] autostop fired
     // optional trace (one ligand): decisions [nrun][ngen][pop][8], genes [nrun][ngen][pop][kGeneStride], e
     int trace_ngen;
     int* tr_dec;

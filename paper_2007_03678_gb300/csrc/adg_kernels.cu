@@ -934,7 +934,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
     if (local >= S.nrun * S.pop) return;
     const int run = local / S.pop, ind = local % S.pop;
     const int run_g = lig * S.nrun + run;
-    if (Dk.evals[run_g] >= (unsigned long long)S.nev || gen > S.max_gen) return;
+    if (Dk.evals[run_g] >= (unsigned long long)S.nev || gen > S.max_gen || Dk.stopped[run_g]) return;
     const WarpView ws = warp_view(na, nslots, lig_bytes);
     const LigandDev* L = LR.hdr;
     const int T = L->ntors, G = 7 + T, nb = 2 + T, pop = S.pop;
@@ -1024,19 +1024,33 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
 }
 
 // One thread per run: fold the generation's evaluations into the total,
-// record the last completed generation, count runs active for gen+1.
+// record the last completed generation and the run's best energy, apply
+// autostop (paper Sec. 1.1: population standard deviation of the best energy
+// over the last 10 generations below stopstd), count runs active for gen+1.
 __global__ void k_dock_bookkeep(SearchDev S, DockDev Dk, int gen, int* active)
 {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     const int nruns = Dk.nlig * S.nrun;
     if (r >= nruns) return;
     const unsigned long long nev = (unsigned long long)S.nev;
-    if (Dk.evals[r] < nev && gen <= S.max_gen) {
+    if (Dk.evals[r] < nev && gen <= S.max_gen && !Dk.stopped[r]) {
         Dk.evals[r] += Dk.evals[nruns + r];
         Dk.evals[nruns + r] = 0ull;
         Dk.gen_done[r] = gen;
+        const float* Pe = Dk.pop_e[gen & 1] + (long)r * S.pop;
+        float b = Pe[0];
+        for (int i = 1; i < S.pop; ++i) b = fminf(b, Pe[i]);
+        float* h = Dk.best_hist + 10 * r;
+        h[(gen - 1) % 10] = b;
+        if (S.autostop && gen >= 10) {
+            float m = 0.f, v = 0.f;
+            for (int k = 0; k < 10; ++k) m += h[k];
+            m *= 0.1f;
+            for (int k = 0; k < 10; ++k) v += (h[k] - m) * (h[k] - m);
+            if (sqrtf(0.1f * v) < S.stopstd) Dk.stopped[r] = 1;
+        }
     }
-    if (Dk.evals[r] < nev && gen + 1 <= S.max_gen) atomicAdd(active, 1);
+    if (Dk.evals[r] < nev && gen + 1 <= S.max_gen && !Dk.stopped[r]) atomicAdd(active, 1);
 }
 
 // Warps per ligand: its nrun * pop individuals padded to whole blocks.

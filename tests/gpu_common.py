@@ -14,11 +14,11 @@ E_REL = 1e-5
 G_REL = 1e-3
 # FP32 rounding of a posed coordinate moves the energy by up to
 # COORD_EPS * sum_i |dE/dx_i|_1.  A posed coordinate (|x| <= 16 A, one ulp
-# 9.5e-7 A) goes through up to 8 nested torsion rotations and the rigid-body
-# transform, each rounding once: about 3 ulp.  Poses whose per-atom forces stay
-# below F_WELL are held to the plain tolerance above, every pose to that plus
-# this conditioning term.
-COORD_EPS = 3e-6
+# 9.5e-7 A) comes out of a product of up to 12 nested torsion transforms and
+# the rigid-body transform, each adding about one ulp: 1e-5 A bounds it.
+# Poses whose per-atom forces stay below F_WELL are held to the plain
+# tolerance above, every pose to that plus this conditioning term.
+COORD_EPS = 1e-5
 F_WELL = 50.0
 
 

@@ -39,11 +39,11 @@ def _params_pair(A, **kw):
         "nrun", "pop_size", "nev", "max_gen", "ls_method", "ls_max_iters", "elitism", "ls_rate", "crossover_rate",
         "mutation_rate", "tournament_rate", "sw_rho0", "sw_rho_min", "sw_expand", "sw_contract", "sw_succ", "sw_fail",
         "sw_scale_t", "sw_scale_rot", "sw_scale_tors", "ad_rho", "ad_eps", "mut_t", "mut_rot", "mut_tors", "seed",
-        "lig_id")})
+        "lig_id", "autostop", "stopstd")})
     # the oracle works in double from the float32 values the library receives
     for k in ("ls_rate", "crossover_rate", "mutation_rate", "tournament_rate", "sw_rho0", "sw_rho_min", "sw_expand",
               "sw_contract", "sw_scale_t", "sw_scale_rot", "sw_scale_tors", "ad_rho", "ad_eps", "mut_t", "mut_rot",
-              "mut_tors"):
+              "mut_tors", "stopstd"):
         setattr(op, k, float(getattr(ap, k)))
     return op, ap
 
@@ -199,3 +199,40 @@ def test_plain_docking_distribution_matches_oracle(ctx, A, ff):
     ctx.sync()
     assert np.allclose(e.cpu().numpy(), res["best_energy"], rtol=1e-6, atol=1e-5)
     assert np.array_equal(xyz.cpu().numpy(), res["xyz"])
+
+
+def _autostop_generation(best_per_gen, stopstd):
+    """First generation g >= 10 whose last 10 best energies have a population
+    standard deviation below stopstd (numpy), or None."""
+    for g in range(10, len(best_per_gen) + 1):
+        if np.std(best_per_gen[g - 10:g]) < stopstd:
+            return g
+    return None
+
+
+def test_autostop_applies_the_rule(ctx, A, ff):
+    """With autostop on, every GPU run ends at the first generation where its
+    own best energies satisfy the rule (checked with numpy on the GPU's trace,
+    skipping decisions within 1e-4 of the threshold); with it off the runs go
+    on; the surviving evaluation counts shrink."""
+    grid, rec, lig, maps64, maps32 = problem("plain")
+    ngen = 60
+    kw = dict(nrun=6, pop_size=60, ls_method=1, ls_max_iters=20, nev=10 ** 8, max_gen=ngen, stopstd=0.15)
+    _, on = _params_pair(A, autostop=1, **kw)
+    _, off = _params_pair(A, autostop=0, **kw)
+    R = A.Receptor(ctx, grid, maps32)
+    Lg = A.Ligand(ctx, ff, lig)
+    res_on, tr = A.dock(ctx, R, Lg, on, trace_ngen=ngen)
+    res_off = A.dock(ctx, R, Lg, off)[0]
+    assert (res_off["generations"] == ngen).all()
+    stopped = 0
+    for run in range(on.nrun):
+        best = tr["energies"][run].min(axis=1).astype(np.float64)
+        g = int(res_on[0]["generations"][run])
+        want = _autostop_generation(best[:g], on.stopstd)
+        near = any(abs(np.std(best[k - 10:k]) - on.stopstd) < 1e-4 for k in range(10, g + 1))
+        if not near:
+            assert want == (g if g < ngen else want), (run, g, want)
+        stopped += g < ngen
+    assert stopped >= 1
+    assert res_on[0]["evals"].sum() < res_off["evals"].sum()

@@ -655,3 +655,19 @@ def test_lga_run_is_deterministic(ff, plain_inputs, plain_maps):
     p.seed = 43
     c = O.lga_run(ff, grid, plain_maps, L, p, run=3)
     assert not np.array_equal(a[1], c[1])
+
+
+def test_autostop_rule(ff, plain_inputs, plain_maps):
+    """A run with autostop ends at the first generation >= 10 whose last 10
+    best energies have a population standard deviation (numpy) below stopstd;
+    without autostop it runs to max_gen."""
+    grid, rec, lig = plain_inputs
+    L = O.Ligand(lig)
+    kw = dict(pop_size=40, ls_method=1, ls_max_iters=15, nev=10 ** 8, max_gen=60, stopstd=0.15)
+    _, _, _, g_off, _ = O.lga_run(ff, grid, plain_maps, L, O.SearchParams(autostop=0, **kw), run=1)
+    assert g_off == 60
+    best, _, _, g_on, (dec, tg, te) = O.lga_run(ff, grid, plain_maps, L, O.SearchParams(autostop=1, **kw), run=1,
+                                                ntrace=60)
+    b = te[:g_on].min(axis=1)
+    first = next((g for g in range(10, g_on + 1) if np.std(b[g - 10:g]) < 0.15), None)
+    assert first == g_on < 60
