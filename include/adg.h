@@ -263,6 +263,34 @@ int adg_ctx_set_timing(adg_ctx* ctx, int enable);
  * stream when timing is on (to read the events). */
 int adg_ctx_stats(adg_ctx* ctx, adg_stats* out, int reset);
 
+/* Docking without allocation.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate memory -- a host application whose
+ * own allocator owns all device memory and does not let libraries allocate
+ * behind its back, or a latency-critical loop in which cudaMalloc/cudaFree
+ * (which may synchronize the device) would stall other work.
+ *
+ * adg_dock_noalloc docks one ligand like adg_dock with nlig = 1 and no trace,
+ * and allocates nothing: no cudaMalloc, no cudaFree, no host heap, no
+ * allocating library call.  Its working memory is one device array of
+ * ADG_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  Limits: p->nrun <= ADG_NOALLOC_MAX_RUNS and
+ * p->nrun * p->pop_size <= ADG_NOALLOC_MAX_INDIVIDUALS; larger requests return
+ * ADG_ETOOBIG and touch nothing.
+ *   rec, lig: built beforehand with adg_receptor_create / adg_ligand_create
+ *   out:      host, caller-allocated [p->nrun], filled as by adg_dock
+ *   stream:   cudaStream_t to run on (NULL: the legacy default stream)
+ * The first call on a device looks up the array's device address on that
+ * device (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  Every call reuses the same array and clears what must start at
+ * zero; calls whose GPU work overlaps (on different streams or host threads)
+ * race on it and must be serialized by the caller.  Returns when the results
+ * are in `out`. */
+#define ADG_NOALLOC_SCRATCH_BYTES (4u << 20)
+#define ADG_NOALLOC_MAX_RUNS 128
+#define ADG_NOALLOC_MAX_INDIVIDUALS 16384
+int adg_dock_noalloc(const adg_receptor* rec, const adg_ligand* lig, const adg_search_params* p, adg_result* out,
+                     void* stream);
+
 /* Philox4x32-10 (Salmon et al., SC'11) on the device: out[4i..4i+3] =
  * Philox(counter ctr[4i..4i+3], key = (key & 0xffffffff, key >> 32)).
  * ctr and out: device, 4*n uint32, each 16-byte aligned (ADG_EINVAL otherwise). */

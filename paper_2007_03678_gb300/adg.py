@@ -95,7 +95,7 @@ class adg_ligand_stats(C.Structure):
 EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_ctx_destroy", "adg_sync",
            "adg_ctx_last_error", "adg_maps_build", "adg_receptor_create", "adg_receptor_destroy", "adg_ligand_create",
            "adg_ligand_destroy", "adg_ligand_info", "adg_score", "adg_pose", "adg_dock", "adg_philox",
-           "adg_ctx_set_timing", "adg_ctx_stats")
+           "adg_ctx_set_timing", "adg_ctx_stats", "adg_dock_noalloc")
 
 _lib = None
 
@@ -132,6 +132,7 @@ def load(path: str | None = None):
                                C.POINTER(adg_dock_trace)]
         L.adg_philox.argtypes = [_vp, _vp, _i, C.c_uint64, _vp]
         L.adg_ctx_set_timing.argtypes = [_vp, _i]
+        L.adg_dock_noalloc.argtypes = [_vp, _vp, C.POINTER(adg_search_params), C.POINTER(adg_result), _vp]
         L.adg_ctx_stats.argtypes = [_vp, C.POINTER(adg_stats), _i]
         _lib = L
     return _lib
@@ -388,3 +389,19 @@ def dock(ctx: Context, rec: Receptor, ligs, params: adg_search_params, trace_nge
                         generations=np.array([r.generations for r in rr], np.int32)))
     del raw
     return (out, trace) if trace_ngen > 0 else out
+
+
+def dock_noalloc(rec: Receptor, lig: Ligand, params: adg_search_params, stream=None):
+    """adg_dock_noalloc: dock one ligand without any allocation by the library
+    (for callers whose memory the library may not allocate; see include/adg.h).
+    Returns the same per-run dict as dock() for one ligand."""
+    nrun = params.nrun
+    res = (adg_result * nrun)()
+    sp = None if stream is None else C.c_void_p(stream.cuda_stream)
+    _check(load().adg_dock_noalloc(rec.handle, lig.handle, C.byref(params), res, sp), "adg_dock_noalloc")
+    G, N = 7 + lig.ntors, lig.natoms
+    return dict(best_energy=np.array([r.best_energy for r in res], np.float32),
+                genes=np.array([r.genes[:G] for r in res], np.float32),
+                xyz=np.array([r.xyz[:3 * N] for r in res], np.float32).reshape(nrun, N, 3),
+                evals=np.array([r.evals for r in res], np.int64),
+                generations=np.array([r.generations for r in res], np.int32))

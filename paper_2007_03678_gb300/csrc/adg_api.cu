@@ -37,23 +37,6 @@ struct adg_ctx {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
 };
 
-struct adg_receptor {
-    adg_ctx* ctx = nullptr;  // creator; not dereferenced by adg_receptor_destroy
-    int device = 0;
-    adg_grid_desc grid{};
-    float4* packed = nullptr;
-    MapsDev maps{};
-};
-
-struct adg_ligand {
-    adg_ctx* ctx = nullptr;  // creator; not dereferenced by adg_ligand_destroy
-    int device = 0;
-    void* blob = nullptr;  // LigandDev followed by the pair arrays
-    LigandRef ref{};
-    int natoms = 0, ntors = 0, npairs = 0, apl = 1, sum_moving = 0, nslots = 0;
-    size_t bytes = 0;
-};
-
 namespace {
 
 int cuda_fail(adg_ctx* ctx, cudaError_t e, const char* what)

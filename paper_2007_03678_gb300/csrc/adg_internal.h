@@ -141,5 +141,26 @@ cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const 
                                      int* active);
 cudaError_t launch_dock_finalize(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d,
                                  const Geo& g, ResultDev* out);
+// Same, writing adg_result records (device memory) instead of ResultDev.
+cudaError_t launch_dock_finalize_abi(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d,
+                                     const Geo& g, adg_result* out);
 
 }  // namespace adg
+
+// Handles of the C ABI (opaque to callers).
+struct adg_receptor {
+    adg_ctx* ctx = nullptr;  // creator; not dereferenced by adg_receptor_destroy
+    int device = 0;
+    adg_grid_desc grid{};
+    float4* packed = nullptr;
+    adg::MapsDev maps{};
+};
+
+struct adg_ligand {
+    adg_ctx* ctx = nullptr;  // creator; not dereferenced by adg_ligand_destroy
+    int device = 0;
+    void* blob = nullptr;  // LigandDev followed by the pair arrays
+    adg::LigandRef ref{};
+    int natoms = 0, ntors = 0, npairs = 0, apl = 1, sum_moving = 0, nslots = 0;
+    size_t bytes = 0;
+};

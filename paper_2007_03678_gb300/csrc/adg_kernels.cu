@@ -1157,4 +1157,61 @@ cudaError_t launch_dock_finalize(cudaStream_t st, const MapsDev& m, const Search
     return cudaGetLastError();
 }
 
+// Per run: the best genotype of the final population and its pose, written
+// straight into adg_result records (used where the library stages nothing
+// on the host).
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_finalize_abi(MapsDev M, SearchDev S, DockDev Dk,
+                                                                              int na, int nslots,
+                                                                              adg_result* __restrict__ out)
+{
+    const int lane = threadIdx.x & 31;
+    const int run_g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int nruns = Dk.nlig * S.nrun;
+    if (run_g >= nruns) return;
+    const WarpView ws = warp_view(na, nslots, 0);
+    const int lig = run_g / S.nrun;
+    const LigandDev* L = Dk.ligs[lig].hdr;
+    const int G = 7 + L->ntors, N = L->natoms, gd = Dk.gen_done[run_g];
+    const float* Pg = Dk.pop_genes[gd & 1] + (long)run_g * S.pop * kGeneStride;
+    const float* Pe = Dk.pop_e[gd & 1] + (long)run_g * S.pop;
+    float bv = INFINITY;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < S.pop; i += 32) {
+        const float v = Pe[i];
+        if (v < bv) { bv = v; bi = i; }
+    }
+    warp_argmin(bv, bi);
+    if (bi >= S.pop) bi = 0;  // only when every energy is NaN
+    if (lane < G) ws.genes[lane] = Pg[(long)bi * kGeneStride + lane];
+    __syncwarp();
+    warp_pose<4>(L, ws.genes, ws, lane);
+    adg_result& R = out[run_g];
+    if (lane == 0) {
+        R.best_energy = bv;
+        R.generations = gd;
+        R.evals = (int64_t)Dk.evals[run_g];
+    }
+    if (lane < ADG_MAX_GENES) R.genes[lane] = lane < G ? ws.genes[lane] : 0.f;
+    for (int k = lane; k < 3 * ADG_MAX_ATOMS; k += 32) R.xyz[k] = 0.f;
+    __syncwarp();
+    for (int a = lane; a < N; a += 32) {
+        const float4 x = ws.xyz[a];
+        const int o = 3 * L->old_of_new[a];
+        R.xyz[o] = x.x;
+        R.xyz[o + 1] = x.y;
+        R.xyz[o + 2] = x.z;
+    }
+}
+
+cudaError_t launch_dock_finalize_abi(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d,
+                                     const Geo& g0, adg_result* out)
+{
+    const int nruns = d.nlig * s.nrun;
+    const Geo g = make_geo(4, g0.nslots, 0);
+    cudaError_t e = allow_smem(k_dock_finalize_abi, g.smem);
+    if (e != cudaSuccess) return e;
+    k_dock_finalize_abi<<<blocks_for(nruns, g), g.wpb * 32, g.smem, st>>>(m, s, d, g.na, g.nslots, out);
+    return cudaGetLastError();
+}
+
 }  // namespace adg

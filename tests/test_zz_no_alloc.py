@@ -1,0 +1,56 @@
+"""adg_dock_noalloc, the docking entry point for callers that cannot allocate
+memory (an application allocator that owns all device memory, or a loop in
+which cudaMalloc/cudaFree would stall other work): it must return what
+adg_dock returns for the same inputs, on two calls in a row (the second call
+reuses the first call's working memory), and reject requests larger than its
+fixed working memory.  Collected last so that a failure here comes after
+every other test has run; it passes alone in a fresh process too."""
+import numpy as np
+import pytest
+
+from gpu_common import E_ABS, E_REL, problem
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_03678_gb300 import adg, build
+    build.build()
+    c = adg.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("ls_method", [1, 2])
+def test_noalloc_dock_matches_dock_on_two_calls(ctx, ff, ls_method):
+    from paper_2007_03678_gb300 import adg
+    grid, rec, lig, maps64, maps32 = problem("plain")
+    R = adg.Receptor(ctx, grid, maps32)
+    L = adg.Ligand(ctx, ff, lig)
+    p = adg.search_params(nrun=12, pop_size=150, nev=20000, ls_method=ls_method, ls_max_iters=40, seed=77)
+    ref = adg.dock(ctx, R, L, p)[0]
+    ctx.sync()
+    for call in range(2):
+        got = adg.dock_noalloc(R, L, p)
+        e, e0 = got["best_energy"].astype(np.float64), ref["best_energy"].astype(np.float64)
+        assert (np.abs(e - e0) <= E_ABS + E_REL * np.abs(e0)).all(), (call, e, e0)
+        assert np.abs(got["genes"] - ref["genes"]).max() < 2e-3, call
+        assert np.abs(got["xyz"] - ref["xyz"]).max() < 2e-3, call
+        assert np.array_equal(got["evals"], ref["evals"]), call
+        assert np.array_equal(got["generations"], ref["generations"]), call
+
+
+def test_noalloc_rejects_oversized_requests(ctx, ff):
+    from paper_2007_03678_gb300 import adg
+    grid, rec, lig, maps64, maps32 = problem("plain")
+    R = adg.Receptor(ctx, grid, maps32)
+    L = adg.Ligand(ctx, ff, lig)
+    for kw in (dict(nrun=129, pop_size=50), dict(nrun=100, pop_size=200)):
+        p = adg.search_params(nev=1000, **kw)
+        with pytest.raises(adg.AdgError) as ei:
+            adg.dock_noalloc(R, L, p)
+        assert ei.value.code == -3
