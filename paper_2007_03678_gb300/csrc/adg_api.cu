@@ -492,14 +492,17 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     }
     const int nsteps = (int)slots.size() / 32;
     // --- force-gather program: every atom's (slot, partner) list goes to one
-    // lane; atoms are dealt longest list first to the least loaded lane
+    // lane as a segment -- a header (atom | groups << 7) then its entries
+    // (partner | slot << 7) padded to a multiple of 4 with entries that point
+    // back at the atom itself (they add c * 0); atoms are dealt longest
+    // segment first to the least loaded lane
     std::vector<std::vector<uint32_t>> inc(N);
     for (int sl = 0; sl < (int)slots.size(); ++sl) {
         const int p = slots[sl];
         if (p < 0) continue;
         const int i = pairs[p].first, j = pairs[p].second;
-        inc[i].push_back((uint32_t)i | ((uint32_t)j << 7) | ((uint32_t)sl << 14));
-        inc[j].push_back((uint32_t)j | ((uint32_t)i << 7) | ((uint32_t)sl << 14));
+        inc[i].push_back((uint32_t)j | ((uint32_t)sl << 7));
+        inc[j].push_back((uint32_t)i | ((uint32_t)sl << 7));
     }
     std::vector<int> by_deg(N);
     for (int i = 0; i < N; ++i) by_deg[i] = i;
@@ -507,14 +510,18 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     std::vector<std::vector<uint32_t>> lane_list(32);
     for (int i : by_deg) {
         if (inc[i].empty()) continue;
+        const uint32_t groups = (uint32_t)((inc[i].size() + 3) / 4);
         int best = 0;
         for (int l = 1; l < 32; ++l)
             if (lane_list[l].size() < lane_list[best].size()) best = l;
-        lane_list[best].insert(lane_list[best].end(), inc[i].begin(), inc[i].end());
+        auto& v = lane_list[best];
+        v.push_back((uint32_t)i | (groups << 7));
+        v.insert(v.end(), inc[i].begin(), inc[i].end());
+        for (size_t k = inc[i].size(); k < 4 * groups; ++k) v.push_back((uint32_t)i);  // partner = itself, slot 0
     }
-    int gsteps = 0;
-    for (auto& v : lane_list) gsteps = std::max(gsteps, (int)v.size());
-    std::vector<uint32_t> gent((size_t)std::max(gsteps, 1) * 32, kGatherPad);
+    int gsteps = 1;  // room for the terminating pad
+    for (auto& v : lane_list) gsteps = std::max(gsteps, (int)v.size() + 1);
+    std::vector<uint32_t> gent((size_t)gsteps * 32, kGatherPad);
     for (int l = 0; l < 32; ++l)
         for (size_t k = 0; k < lane_list[l].size(); ++k) gent[k * 32 + l] = lane_list[l][k];
     // --- device header
@@ -570,7 +577,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     }
     // --- pair arrays in slot order
     const int ns = nsteps * 32;
-    std::vector<int> ij(ns, -1);
+    std::vector<int> ij(ns, 0);  // empty slots: atom 0 with itself, zero coefficients (adds 0)
     std::vector<float4> coef(ns, make_float4(0, 0, 0, 0));
     std::vector<float> cd(ns, 0.f);
     const double wq = (double)ff->w_elec * ff->coulomb;

@@ -59,13 +59,15 @@ struct LigandDev {
 };
 
 // Intramolecular pairs, lane-interleaved: slot (step, lane) = step * 32 + lane.
-// ij = i | j << 16, or -1 for an empty slot.  coef = (c12, c6, c10, cq):
+// ij = i | j << 16 (an empty slot pairs atom 0 with itself, with zero
+// coefficients).  coef = (c12, c6, c10, cq):
 // E_pair = min(c12 r^-12 - c6 r^-6 - c10 r^-10, e_cap) + cq / (eps(r) r) + cd exp(-r^2/(2 s^2)).
 // Force gather: after the pair pass has stored c_p = (dE/dr)/r of every slot,
-// lane l walks its list gent[k * 32 + l] (k < gsteps), entries
-// atom | other << 7 | slot << 14 grouped by atom, and sums
-// f_atom = sum c_p (x_atom - x_other).  Atoms are dealt to lanes by pair
-// count (longest first to the least loaded lane); padding = kGatherPad.
+// lane l walks its list gent[k * 32 + l]: segments of a header
+// atom | groups << 7 followed by 4 * groups entries partner | slot << 7
+// (padded with entries whose partner is the atom itself), ended by
+// kGatherPad, and sums f_atom = sum c_p (x_atom - x_partner).  Atoms are dealt
+// to lanes by segment length, longest first to the least loaded lane.
 struct PairsDev {
     const int* ij;
     const float4* coef;

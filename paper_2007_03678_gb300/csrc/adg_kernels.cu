@@ -446,13 +446,10 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     const float cap = L->e_cap, rmin2 = L->rmin2, msA = L->ms_A, msB = L->ms_B, msk = L->ms_k, mslb = L->ms_lb;
     const float inv_2s2 = L->inv_2s2, inv_s2 = L->inv_s2;
     const int nsteps = L->nsteps;
+#pragma unroll 2
     for (int stp = 0; stp < nsteps; ++stp) {
         const int idx = stp * 32 + lane;
         const int ij = P.ij[idx];
-        if (ij < 0) {
-            if (GRAD) ws.c[idx] = 0.f;
-            continue;
-        }
         const int i = ij & 0xffff, j = ij >> 16;
         const float4 xi = ws.xyz[i], xj = ws.xyz[j];
         const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
@@ -489,29 +486,25 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     out.tx = out.ty = out.tz = 0.f;
     if (!GRAD) return out;
     __syncwarp();
-    // force gather: f_atom = sum over its pairs of c_p (x_atom - x_other)
-    {
-        int cur = -1;
-        float4 xa = make_float4(0.f, 0.f, 0.f, 0.f);
+    // force gather: f_atom = sum over its pairs of c_p (x_atom - x_partner),
+    // four independent entries per step
+    for (int k = 0;;) {
+        const uint32_t hdr = P.gent[k * 32 + lane];
+        if (hdr == kGatherPad) break;
+        const int atom = hdr & 127, groups = hdr >> 7;
+        ++k;
+        const float4 xa = ws.xyz[atom];
         float ax = 0.f, ay = 0.f, az = 0.f;
-        const int gsteps = L->gsteps;
-        for (int k = 0; k < gsteps; ++k) {
-            const uint32_t ent = P.gent[k * 32 + lane];
-            if (ent == kGatherPad) break;  // a lane's list is padded at its end only
-            const int atom = ent & 127, other = (ent >> 7) & 127, slot = ent >> 14;
-            if (atom != cur) {
-                if (cur >= 0) ws.f[cur] = make_float4(ax, ay, az, 0.f);
-                cur = atom;
-                xa = ws.xyz[atom];
-                ax = ay = az = 0.f;
-            }
-            const float cc = ws.c[slot];
-            const float4 xo = ws.xyz[other];
-            ax += cc * (xa.x - xo.x);
-            ay += cc * (xa.y - xo.y);
-            az += cc * (xa.z - xo.z);
+        for (int q = 0; q < groups; ++q, k += 4) {
+            const uint32_t e0 = P.gent[k * 32 + lane], e1 = P.gent[(k + 1) * 32 + lane],
+                           e2 = P.gent[(k + 2) * 32 + lane], e3 = P.gent[(k + 3) * 32 + lane];
+            const float c0 = ws.c[e0 >> 7], c1 = ws.c[e1 >> 7], c2 = ws.c[e2 >> 7], c3 = ws.c[e3 >> 7];
+            const float4 x0 = ws.xyz[e0 & 127], x1 = ws.xyz[e1 & 127], x2 = ws.xyz[e2 & 127], x3 = ws.xyz[e3 & 127];
+            ax += c0 * (xa.x - x0.x) + c1 * (xa.x - x1.x) + c2 * (xa.x - x2.x) + c3 * (xa.x - x3.x);
+            ay += c0 * (xa.y - x0.y) + c1 * (xa.y - x1.y) + c2 * (xa.y - x2.y) + c3 * (xa.y - x3.y);
+            az += c0 * (xa.z - x0.z) + c1 * (xa.z - x1.z) + c2 * (xa.z - x2.z) + c3 * (xa.z - x3.z);
         }
-        if (cur >= 0) ws.f[cur] = make_float4(ax, ay, az, 0.f);
+        ws.f[atom] = make_float4(ax, ay, az, 0.f);
     }
     __syncwarp();
     // Per atom: total force f and moment m = (x - t) x f.  Inclusive prefix
