@@ -152,6 +152,7 @@ def oracle_maps_file() -> str:
 
 
 ORACLE_SAMPLE_NEV = 150 + 45150  # initial population + one ADADELTA generation
+BATCH_LIGANDS, BATCH_NRUN, BATCH_NEV = 64, 20, 100_000
 
 
 def cpu_cores() -> int:
@@ -208,6 +209,7 @@ def main():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
+    ap.add_argument("--no-batching", action="store_true", help="skip the batching comparison (profiling runs)")
     ap.add_argument("--nrun", type=int, default=None, help="override the run count (small profiling cases)")
     ap.add_argument("--nev", type=int, default=None, help="override the evaluation budget (small profiling cases)")
     args = ap.parse_args()
@@ -308,6 +310,30 @@ def main():
         "h2d_bytes_per_step": st2["h2d_bytes"] // args.steps, "d2h_bytes_per_step": st2["d2h_bytes"] // args.steps,
         "ligands_per_s": args.steps / e2e_t * world}
 
+    # batching (shape classes on concurrent streams, one graph each) against one call per ligand
+    batching = None
+    if not args.no_batching:
+        bl = S.make_batch(BATCH_LIGANDS, seed=7)
+        BL = [adg.Ligand(ctx, ff, l) for l in bl]
+        bp = adg.search_params(nrun=BATCH_NRUN, pop_size=150, nev=BATCH_NEV, ls_method=adg.LS_ADADELTA,
+                               seed=S.SEARCH_SEED)
+        adg.dock(ctx, R, BL[:4], bp)  # warm-up of every path
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rb = adg.dock(ctx, R, BL, bp)
+        t_batch = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        for i, lg in enumerate(BL):
+            bp.lig_id = i
+            adg.dock(ctx, R, lg, bp)
+        t_one = time.perf_counter() - t0
+        ev = int(sum(r["evals"].sum() for r in rb))
+        batching = {"ligands": BATCH_LIGANDS, "atoms": [min(l.natoms for l in bl), max(l.natoms for l in bl)],
+                    "nrun": BATCH_NRUN, "pop": 150, "nev": BATCH_NEV, "local_search": "adadelta",
+                    "ligands_per_s_batched": BATCH_LIGANDS / t_batch,
+                    "ligands_per_s_one_by_one": BATCH_LIGANDS / t_one, "speedup": t_one / t_batch,
+                    "evals_per_s_batched": ev / t_batch}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = cpu_cores()
@@ -326,7 +352,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args.nrun, args.nev), "ligands_per_s": ligands_per_s,
                 "best_energy_median": float(np.median(results["best_energy"])),
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "batching": batching,
                 "gpu_launches": st["kernel_launches"]}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -35,6 +35,7 @@ struct adg_ctx {
     adg_stats stats{};
     std::vector<cudaEvent_t> ev_free;                       // reusable events
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
+    std::vector<cudaStream_t> class_streams;  // extra streams for concurrent shape classes
 };
 
 namespace {
@@ -174,6 +175,10 @@ int adg_ctx_destroy(adg_ctx* ctx)
         cudaEventDestroy(pr.second);
     }
     for (auto ev : ctx->ev_free) cudaEventDestroy(ev);
+    for (auto s2 : ctx->class_streams) {
+        cudaStreamSynchronize(s2);
+        cudaStreamDestroy(s2);
+    }
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->host_active) cudaFreeHost(ctx->host_active);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -696,66 +701,24 @@ int adg_philox(adg_ctx* ctx, const uint32_t* ctr, int n, uint64_t key, uint32_t*
     return ADG_OK;
 }
 
-int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig,
-             const adg_search_params* p, adg_result* out, adg_dock_trace* trace)
+namespace {
+
+// One shape class of a dock call: the ligands sharing an atoms-per-lane
+// width, docked by one graph on one stream.
+struct ClassRun {
+    std::vector<int> ligs;   // indices into the call's ligand list
+    Geo geo;
+    DockDev D;
+    int* d_active = nullptr;
+    int* d_gen = nullptr;
+    ResultDev* d_res = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;  // around the generation loop (timing mode)
+};
+
+void fill_search(const adg_search_params* p, SearchDev& S)
 {
-    if (!ctx || !rec || !ligs || nlig <= 0 || !p || !out) return ADG_EINVAL;
-    if (p->nrun <= 0 || p->nrun > 65535 || p->pop_size < 2 || p->pop_size > 65535 || p->nev < 0 || p->max_gen < 0 ||
-        p->ls_max_iters < 0 || p->elitism < 0 || p->elitism > 1 || p->ls_method < 0 || p->ls_method > 2)
-        return ADG_EINVAL;
-    if (trace && (nlig != 1 || trace->ngen < 0)) return ADG_EINVAL;
-    int apl = 1, nslots = 32;
-    size_t lig_bytes = 0;
-    for (int i = 0; i < nlig; ++i) {
-        if (!ligs[i] || ligs[i]->ctx != ctx) return ADG_EINVAL;
-        apl = std::max(apl, ligs[i]->apl);
-        nslots = std::max(nslots, ligs[i]->nslots);
-        lig_bytes = std::max(lig_bytes, ligs[i]->bytes);
-    }
-    const Geo geo = make_geo(apl, nslots, lig_bytes);
-    CK(ctx, cudaSetDevice(ctx->device));
-    cudaStream_t st = ctx->stream;
-    const long nruns = (long)nlig * p->nrun;
-    const long nind = nruns * p->pop_size;
-    const int tr_ngen = trace ? trace->ngen : 0;
-    const long tr_slots = trace ? (long)p->nrun * tr_ngen * p->pop_size : 0;
-    // arena layout
-    size_t off = 0;
-    auto take = [&](size_t bytes) {
-        const size_t o = off;
-        off = align_up(off + bytes, 256);
-        return o;
-    };
-    const size_t o_g0 = take(sizeof(float) * nind * kGeneStride), o_g1 = take(sizeof(float) * nind * kGeneStride);
-    const size_t o_e0 = take(sizeof(float) * nind), o_e1 = take(sizeof(float) * nind);
-    const size_t o_ev = take(sizeof(unsigned long long) * 2 * nruns);
-    const size_t o_gd = take(sizeof(int) * nruns);
-    const size_t o_hist = take(sizeof(float) * 10 * nruns);
-    const size_t o_stop = take(sizeof(int) * nruns);
-    const size_t o_act = take(sizeof(int) * 2);
-    const size_t o_lr = take(sizeof(LigandRef) * nlig);
-    const size_t o_id = take(sizeof(uint32_t) * nlig);
-    const size_t o_res = take(sizeof(ResultDev) * nruns);
-    const size_t o_td = take(sizeof(int) * ADG_TRACE_WIDTH * tr_slots);
-    const size_t o_tg = take(sizeof(float) * kGeneStride * tr_slots);
-    const size_t o_te = take(sizeof(float) * tr_slots);
-    if (off > ctx->arena_bytes) {
-        CK(ctx, cudaStreamSynchronize(st));
-        if (ctx->arena) cudaFree(ctx->arena);
-        ctx->arena = nullptr;
-        ctx->arena_bytes = 0;
-        cudaError_t e = cudaMalloc(&ctx->arena, off);
-        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ADG_ENOMEM : cuda_fail(ctx, e, "arena");
-        ctx->arena_bytes = off;
-    }
-    char* A = (char*)ctx->arena;
-    std::vector<LigandRef> lr(nlig);
-    std::vector<uint32_t> ids(nlig);
-    for (int i = 0; i < nlig; ++i) {
-        lr[i] = ligs[i]->ref;
-        ids[i] = p->lig_id + (uint32_t)i;
-    }
-    SearchDev S;
     S.nrun = p->nrun;
     S.pop = p->pop_size;
     S.nev = p->nev;
@@ -785,112 +748,291 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
     S.key1 = (uint32_t)(p->seed >> 32);
     S.autostop = p->autostop != 0;
     S.stopstd = p->stopstd;
-    DockDev D;
-    D.ligs = (const LigandRef*)(A + o_lr);
-    D.lig_id = (const uint32_t*)(A + o_id);
-    D.nlig = nlig;
-    D.pop_genes[0] = (float*)(A + o_g0);
-    D.pop_genes[1] = (float*)(A + o_g1);
-    D.pop_e[0] = (float*)(A + o_e0);
-    D.pop_e[1] = (float*)(A + o_e1);
-    D.evals = (unsigned long long*)(A + o_ev);
-    D.gen_done = (int*)(A + o_gd);
-    D.best_hist = (float*)(A + o_hist);
-    D.stopped = (int*)(A + o_stop);
-    D.trace_ngen = tr_ngen;
-    D.tr_dec = (int*)(A + o_td);
-    D.tr_genes = (float*)(A + o_tg);
-    D.tr_e = (float*)(A + o_te);
-    int* d_active = (int*)(A + o_act);
-    ResultDev* d_res = (ResultDev*)(A + o_res);
-    const MapsDev& M = rec->maps;
-    CK(ctx, cudaMemcpyAsync(A + o_lr, lr.data(), sizeof(LigandRef) * nlig, cudaMemcpyHostToDevice, st));
-    CK(ctx, cudaMemcpyAsync(A + o_id, ids.data(), sizeof(uint32_t) * nlig, cudaMemcpyHostToDevice, st));
-    ctx->stats.h2d_bytes += (int64_t)((sizeof(LigandRef) + sizeof(uint32_t)) * nlig);
-    CK(ctx, cudaMemsetAsync(D.evals, 0, sizeof(unsigned long long) * 2 * nruns, st));
-    CK(ctx, cudaMemsetAsync(D.gen_done, 0, sizeof(int) * nruns, st));
-    CK(ctx, cudaMemsetAsync(D.stopped, 0, sizeof(int) * nruns, st));
-    CK(ctx, launch_dock_init(st, M, S, D, geo));
-    ctx->stats.kernel_launches += 1;
-    std::vector<float> init_g, init_e;
-    if (trace && (trace->init_genes || trace->init_energies)) {
-        init_g.resize((size_t)nind * kGeneStride);
-        init_e.resize(nind);
-        CK(ctx, cudaMemcpyAsync(init_g.data(), D.pop_genes[0], sizeof(float) * nind * kGeneStride,
-                                cudaMemcpyDeviceToHost, st));
-        CK(ctx, cudaMemcpyAsync(init_e.data(), D.pop_e[0], sizeof(float) * nind, cudaMemcpyDeviceToHost, st));
+}
+
+// Build the graph of one class: prologue (clear counters, initial
+// population) -> WHILE (generation, bookkeeping, loop control) -> final
+// poses.  The loop runs on the device until no run of the class is active.
+cudaError_t build_class_graph(adg_ctx* ctx, ClassRun& c, const MapsDev& M, const SearchDev& S, bool need_loop,
+                              bool timing, int nruns)
+{
+    cudaStream_t cs = c.stream;
+    cudaGraph_t pro = nullptr, epi = nullptr, g = nullptr;
+    cudaError_t e;
+    // prologue
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    cudaMemsetAsync(c.D.evals, 0, sizeof(unsigned long long) * 2 * nruns, cs);
+    cudaMemsetAsync(c.D.gen_done, 0, sizeof(int) * nruns, cs);
+    cudaMemsetAsync(c.D.stopped, 0, sizeof(int) * nruns, cs);
+    cudaMemsetAsync(c.d_active, 0, sizeof(int), cs);
+    const int one = 1;
+    cudaMemcpyAsync(c.d_gen, &one, sizeof(int), cudaMemcpyHostToDevice, cs);
+    launch_dock_init(cs, M, S, c.D, c.geo);
+    e = cudaStreamEndCapture(cs, &pro);
+    if (e != cudaSuccess) return e;
+    // epilogue
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    launch_dock_finalize(cs, M, S, c.D, c.geo, c.d_res);
+    if ((e = cudaStreamEndCapture(cs, &epi)) != cudaSuccess) return e;
+    // assemble
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return e;
+    cudaGraphNode_t n_pro, n_epi, n_t0 = nullptr, n_t1 = nullptr, n_loop = nullptr;
+    if ((e = cudaGraphAddChildGraphNode(&n_pro, g, nullptr, 0, pro)) != cudaSuccess) return e;
+    cudaGraphNode_t last = n_pro;
+    if (timing) {
+        if ((e = cudaGraphAddEventRecordNode(&n_t0, g, &last, 1, c.t0)) != cudaSuccess) return e;
+        last = n_t0;
     }
-    // generation loop: launch a chunk, then read how many runs are still active
-    const int chunk = 4;
-    int gen = 0;
-    // the initial population spent pop_size evaluations; with nev <= pop_size no generation runs
-    const bool need_more = p->max_gen > 0 && p->pop_size < p->nev;
-    while (need_more) {
-        int last = gen;
-        for (int c = 0; c < chunk && gen < p->max_gen; ++c) {
-            ++gen;
-            CK(ctx, cudaMemsetAsync(d_active, 0, sizeof(int), st));
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (ctx->timing) {
-                CK(ctx, take_event(ctx, &e0));
-                CK(ctx, take_event(ctx, &e1));
-                CK(ctx, cudaEventRecord(e0, st));
+    if (need_loop) {
+        cudaGraphConditionalHandle h;
+        if ((e = cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess) return e;
+        cudaGraphNodeParams np = {};
+        np.type = cudaGraphNodeTypeConditional;
+        np.conditional.handle = h;
+        np.conditional.type = cudaGraphCondTypeWhile;
+        np.conditional.size = 1;
+        if ((e = cudaGraphAddNode(&n_loop, g, &last, nullptr, 1, &np)) != cudaSuccess) return e;
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        launch_dock_generation(cs, M, S, c.D, c.geo, 0, c.d_gen);
+        launch_dock_count_active(cs, S, c.D, 0, c.d_active, c.d_gen);
+        launch_dock_loop_ctl(cs, h, c.d_gen, c.d_active);
+        if ((e = cudaStreamEndCapture(cs, &body)) != cudaSuccess) return e;
+        last = n_loop;
+    }
+    if (timing) {
+        if ((e = cudaGraphAddEventRecordNode(&n_t1, g, &last, 1, c.t1)) != cudaSuccess) return e;
+        last = n_t1;
+    }
+    if ((e = cudaGraphAddChildGraphNode(&n_epi, g, &last, 1, epi)) != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&c.exec, g, 0);
+    cudaGraphDestroy(pro);
+    cudaGraphDestroy(epi);
+    cudaGraphDestroy(g);
+    return e;
+}
+
+}  // namespace
+
+int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig,
+             const adg_search_params* p, adg_result* out, adg_dock_trace* trace)
+{
+    if (!ctx || !rec || !ligs || nlig <= 0 || !p || !out) return ADG_EINVAL;
+    if (p->nrun <= 0 || p->nrun > 65535 || p->pop_size < 2 || p->pop_size > 65535 || p->nev < 0 || p->max_gen < 0 ||
+        p->ls_max_iters < 0 || p->elitism < 0 || p->elitism > 1 || p->ls_method < 0 || p->ls_method > 2)
+        return ADG_EINVAL;
+    if (trace && (nlig != 1 || trace->ngen < 0)) return ADG_EINVAL;
+    for (int i = 0; i < nlig; ++i)
+        if (!ligs[i] || ligs[i]->ctx != ctx) return ADG_EINVAL;
+    CK(ctx, cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    // --- shape classes: ligands grouped by atoms per lane (1, 2, 4)
+    std::vector<ClassRun> cls;
+    for (int apl : {1, 2, 4}) {
+        ClassRun c;
+        int nslots = 32;
+        size_t lig_bytes = 0;
+        for (int i = 0; i < nlig; ++i)
+            if (ligs[i]->apl == apl) {
+                c.ligs.push_back(i);
+                nslots = std::max(nslots, ligs[i]->nslots);
+                lig_bytes = std::max(lig_bytes, ligs[i]->bytes);
             }
-            CK(ctx, launch_dock_generation(st, M, S, D, geo, gen));
-            if (ctx->timing) {
-                CK(ctx, cudaEventRecord(e1, st));
-                ctx->ev_pending.emplace_back(e0, e1);
-            }
-            CK(ctx, launch_dock_count_active(st, S, D, gen, d_active));
-            ctx->stats.kernel_launches += 2;
-            ctx->stats.gen_launches += 1;
-            last = gen;
-        }
-        CK(ctx, cudaMemcpyAsync(ctx->host_active, d_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        ctx->stats.d2h_bytes += (int64_t)sizeof(int);
+        if (c.ligs.empty()) continue;
+        c.geo = make_geo(apl, nslots, lig_bytes);
+        cls.push_back(c);
+    }
+    const int tr_ngen = trace ? trace->ngen : 0;
+    const long tr_slots = trace ? (long)p->nrun * tr_ngen * p->pop_size : 0;
+    // --- arena layout, class after class
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, 256);
+        return o;
+    };
+    struct Offs {
+        size_t g0, g1, e0, e1, ev, gd, hist, stop, act, gen, lr, id, res;
+    };
+    std::vector<Offs> offs(cls.size());
+    for (size_t k = 0; k < cls.size(); ++k) {
+        const long nruns = (long)cls[k].ligs.size() * p->nrun, nind = nruns * p->pop_size;
+        Offs& o = offs[k];
+        o.g0 = take(sizeof(float) * nind * kGeneStride);
+        o.g1 = take(sizeof(float) * nind * kGeneStride);
+        o.e0 = take(sizeof(float) * nind);
+        o.e1 = take(sizeof(float) * nind);
+        o.ev = take(sizeof(unsigned long long) * 2 * nruns);
+        o.gd = take(sizeof(int) * nruns);
+        o.hist = take(sizeof(float) * 10 * nruns);
+        o.stop = take(sizeof(int) * nruns);
+        o.act = take(sizeof(int) * 2);
+        o.gen = take(sizeof(int) * 2);
+        o.lr = take(sizeof(LigandRef) * cls[k].ligs.size());
+        o.id = take(sizeof(uint32_t) * cls[k].ligs.size());
+        o.res = take(sizeof(ResultDev) * nruns);
+    }
+    const size_t o_td = take(sizeof(int) * ADG_TRACE_WIDTH * tr_slots);
+    const size_t o_tg = take(sizeof(float) * kGeneStride * tr_slots);
+    const size_t o_te = take(sizeof(float) * tr_slots);
+    if (off > ctx->arena_bytes) {
         CK(ctx, cudaStreamSynchronize(st));
-        if (*ctx->host_active == 0 || last >= p->max_gen) break;
+        for (cudaStream_t s2 : ctx->class_streams) CK(ctx, cudaStreamSynchronize(s2));
+        if (ctx->arena) cudaFree(ctx->arena);
+        ctx->arena = nullptr;
+        ctx->arena_bytes = 0;
+        cudaError_t e = cudaMalloc(&ctx->arena, off);
+        if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ADG_ENOMEM : cuda_fail(ctx, e, "arena");
+        ctx->arena_bytes = off;
     }
-    CK(ctx, launch_dock_finalize(st, M, S, D, geo, d_res));
-    ctx->stats.kernel_launches += 1;
-    std::vector<ResultDev> res(nruns);
-    CK(ctx, cudaMemcpyAsync(res.data(), d_res, sizeof(ResultDev) * nruns, cudaMemcpyDeviceToHost, st));
-    ctx->stats.d2h_bytes += (int64_t)(sizeof(ResultDev) * nruns);
+    char* A = (char*)ctx->arena;
+    SearchDev S;
+    fill_search(p, S);
+    const MapsDev& M = rec->maps;
+    const bool need_loop = p->max_gen > 0 && p->pop_size < p->nev;
+    // streams: the first class runs on the context's stream, others on their own, joined by events
+    while (ctx->class_streams.size() < cls.size()) {
+        cudaStream_t s2;
+        CK(ctx, cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+        ctx->class_streams.push_back(s2);
+    }
+    std::vector<std::vector<LigandRef>> lr(cls.size());
+    std::vector<std::vector<uint32_t>> ids(cls.size());
+    cudaEvent_t fork;
+    CK(ctx, take_event(ctx, &fork));
+    CK(ctx, cudaEventRecord(fork, st));
+    for (size_t k = 0; k < cls.size(); ++k) {
+        ClassRun& c = cls[k];
+        const Offs& o = offs[k];
+        c.stream = k == 0 ? st : ctx->class_streams[k];
+        if (k > 0) CK(ctx, cudaStreamWaitEvent(c.stream, fork, 0));
+        DockDev& D = c.D;
+        D.ligs = (const LigandRef*)(A + o.lr);
+        D.lig_id = (const uint32_t*)(A + o.id);
+        D.nlig = (int)c.ligs.size();
+        D.pop_genes[0] = (float*)(A + o.g0);
+        D.pop_genes[1] = (float*)(A + o.g1);
+        D.pop_e[0] = (float*)(A + o.e0);
+        D.pop_e[1] = (float*)(A + o.e1);
+        D.evals = (unsigned long long*)(A + o.ev);
+        D.gen_done = (int*)(A + o.gd);
+        D.best_hist = (float*)(A + o.hist);
+        D.stopped = (int*)(A + o.stop);
+        D.trace_ngen = tr_ngen;
+        D.tr_dec = (int*)(A + o_td);
+        D.tr_genes = (float*)(A + o_tg);
+        D.tr_e = (float*)(A + o_te);
+        c.d_active = (int*)(A + o.act);
+        c.d_gen = (int*)(A + o.gen);
+        c.d_res = (ResultDev*)(A + o.res);
+        for (int i : c.ligs) {
+            lr[k].push_back(ligs[i]->ref);
+            ids[k].push_back(p->lig_id + (uint32_t)i);
+        }
+        CK(ctx, cudaMemcpyAsync(A + o.lr, lr[k].data(), sizeof(LigandRef) * c.ligs.size(), cudaMemcpyHostToDevice,
+                                c.stream));
+        CK(ctx, cudaMemcpyAsync(A + o.id, ids[k].data(), sizeof(uint32_t) * c.ligs.size(), cudaMemcpyHostToDevice,
+                                c.stream));
+        ctx->stats.h2d_bytes += (int64_t)((sizeof(LigandRef) + sizeof(uint32_t)) * c.ligs.size());
+        if (ctx->timing) {
+            CK(ctx, take_event(ctx, &c.t0));
+            CK(ctx, take_event(ctx, &c.t1));
+        }
+        const int nruns = (int)c.ligs.size() * p->nrun;
+        CK(ctx, build_class_graph(ctx, c, M, S, need_loop, ctx->timing, nruns));
+        CK(ctx, cudaGraphLaunch(c.exec, c.stream));
+        ctx->stats.kernel_launches += 2;  // initial population and final poses; the loop adds 3 per generation
+    }
+    std::vector<std::vector<ResultDev>> res(cls.size());
+    std::vector<int> gens_dev(cls.size(), 0);
+    for (size_t k = 0; k < cls.size(); ++k) {
+        ClassRun& c = cls[k];
+        const long nruns = (long)c.ligs.size() * p->nrun;
+        res[k].resize(nruns);
+        CK(ctx, cudaMemcpyAsync(res[k].data(), c.d_res, sizeof(ResultDev) * nruns, cudaMemcpyDeviceToHost, c.stream));
+        CK(ctx, cudaMemcpyAsync(&gens_dev[k], c.d_gen, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+        ctx->stats.d2h_bytes += (int64_t)(sizeof(ResultDev) * nruns + sizeof(int));
+    }
     std::vector<int> tdec;
-    std::vector<float> tg, te;
-    if (trace && tr_slots > 0) {
-        tdec.resize((size_t)tr_slots * ADG_TRACE_WIDTH);
-        tg.resize((size_t)tr_slots * kGeneStride);
-        te.resize(tr_slots);
-        CK(ctx, cudaMemcpyAsync(tdec.data(), D.tr_dec, sizeof(int) * ADG_TRACE_WIDTH * tr_slots, cudaMemcpyDeviceToHost,
-                                st));
-        CK(ctx, cudaMemcpyAsync(tg.data(), D.tr_genes, sizeof(float) * kGeneStride * tr_slots, cudaMemcpyDeviceToHost, st));
-        CK(ctx, cudaMemcpyAsync(te.data(), D.tr_e, sizeof(float) * tr_slots, cudaMemcpyDeviceToHost, st));
+    std::vector<float> tg, te, init_g, init_e;
+    for (size_t k = 0; k < cls.size(); ++k) CK(ctx, cudaStreamSynchronize(cls[k].stream));
+    for (size_t k = 0; k < cls.size(); ++k) {
+        ClassRun& c = cls[k];
+        // generations executed by the device loop (the counter starts at 1 and
+        // is advanced once per pass)
+        const int ran = need_loop ? gens_dev[k] - 1 : 0;
+        ctx->stats.gen_launches += ran;
+        ctx->stats.kernel_launches += 3 * (int64_t)ran;
+        if (ctx->timing && need_loop) {
+            float ms = 0.f;
+            CK(ctx, cudaEventElapsedTime(&ms, c.t0, c.t1));
+            ctx->stats.gen_kernel_ms += ms;
+            ctx->stats.gen_timed += ran;
+        }
+        if (c.t0) ctx->ev_free.push_back(c.t0);
+        if (c.t1) ctx->ev_free.push_back(c.t1);
+        cudaGraphExecDestroy(c.exec);
     }
-    CK(ctx, cudaStreamSynchronize(st));
-    for (long r = 0; r < nruns; ++r) {
-        adg_result& o = out[r];
-        const ResultDev& s = res[r];
-        const int lig = (int)(r / p->nrun);
-        const int G = 7 + ligs[lig]->ntors, N = ligs[lig]->natoms;
-        memset(&o, 0, sizeof(o));
-        o.best_energy = s.best_energy;
-        o.generations = s.generations;
-        o.evals = s.evals;
-        for (int k = 0; k < G; ++k) o.genes[k] = s.genes[k];
-        for (int k = 0; k < 3 * N; ++k) o.xyz[k] = s.xyz[k];
+    ctx->ev_free.push_back(fork);
+    if (trace) {
+        // the single ligand's class ran on the context's stream
+        const ClassRun& c = cls[0];
+        const long nind = (long)p->nrun * p->pop_size;
+        if (tr_slots > 0) {
+            tdec.resize((size_t)tr_slots * ADG_TRACE_WIDTH);
+            tg.resize((size_t)tr_slots * kGeneStride);
+            te.resize(tr_slots);
+            CK(ctx, cudaMemcpyAsync(tdec.data(), c.D.tr_dec, sizeof(int) * ADG_TRACE_WIDTH * tr_slots,
+                                    cudaMemcpyDeviceToHost, st));
+            CK(ctx, cudaMemcpyAsync(tg.data(), c.D.tr_genes, sizeof(float) * kGeneStride * tr_slots,
+                                    cudaMemcpyDeviceToHost, st));
+            CK(ctx, cudaMemcpyAsync(te.data(), c.D.tr_e, sizeof(float) * tr_slots, cudaMemcpyDeviceToHost, st));
+        }
+        if (trace->init_genes || trace->init_energies) {
+            // generation 0 is deterministic: replay it into buffer 1 (free once
+            // the results above are read; its evaluation counts are not needed)
+            DockDev D1 = c.D;
+            D1.pop_genes[0] = c.D.pop_genes[1];
+            D1.pop_e[0] = c.D.pop_e[1];
+            CK(ctx, launch_dock_init(st, M, S, D1, c.geo));
+            init_g.resize((size_t)nind * kGeneStride);
+            init_e.resize(nind);
+            CK(ctx, cudaMemcpyAsync(init_g.data(), D1.pop_genes[0], sizeof(float) * nind * kGeneStride,
+                                    cudaMemcpyDeviceToHost, st));
+            CK(ctx, cudaMemcpyAsync(init_e.data(), D1.pop_e[0], sizeof(float) * nind, cudaMemcpyDeviceToHost, st));
+        }
+        CK(ctx, cudaStreamSynchronize(st));
+    }
+    for (size_t k = 0; k < cls.size(); ++k) {
+        const ClassRun& c = cls[k];
+        for (size_t li = 0; li < c.ligs.size(); ++li) {
+            const int lig = c.ligs[li];
+            const int G = 7 + ligs[lig]->ntors, N = ligs[lig]->natoms;
+            for (int run = 0; run < p->nrun; ++run) {
+                adg_result& o = out[(long)lig * p->nrun + run];
+                const ResultDev& sr = res[k][(long)li * p->nrun + run];
+                memset(&o, 0, sizeof(o));
+                o.best_energy = sr.best_energy;
+                o.generations = sr.generations;
+                o.evals = sr.evals;
+                for (int q = 0; q < G; ++q) o.genes[q] = sr.genes[q];
+                for (int q = 0; q < 3 * N; ++q) o.xyz[q] = sr.xyz[q];
+            }
+        }
     }
     if (trace) {
         const int G = 7 + ligs[0]->ntors;
+        const long nind = (long)p->nrun * p->pop_size;
         if (trace->decisions && tr_slots)
             memcpy(trace->decisions, tdec.data(), sizeof(int) * ADG_TRACE_WIDTH * tr_slots);
         if (trace->energies && tr_slots) memcpy(trace->energies, te.data(), sizeof(float) * tr_slots);
         if (trace->genes)
-            for (long s = 0; s < tr_slots; ++s)
-                for (int k = 0; k < G; ++k) trace->genes[s * G + k] = tg[s * kGeneStride + k];
+            for (long q = 0; q < tr_slots; ++q)
+                for (int k2 = 0; k2 < G; ++k2) trace->genes[q * G + k2] = tg[q * kGeneStride + k2];
         if (trace->init_genes)
-            for (long s = 0; s < nind; ++s)
-                for (int k = 0; k < G; ++k) trace->init_genes[s * G + k] = init_g[s * kGeneStride + k];
+            for (long q = 0; q < nind; ++q)
+                for (int k2 = 0; k2 < G; ++k2) trace->init_genes[q * G + k2] = init_g[q * kGeneStride + k2];
         if (trace->init_energies) memcpy(trace->init_energies, init_e.data(), sizeof(float) * nind);
     }
     return ADG_OK;

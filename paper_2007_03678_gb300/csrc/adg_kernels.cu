@@ -915,9 +915,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
 template <int APL, int LS>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock_generation(MapsDev M, SearchDev S, DockDev Dk,
                                                                             int na, int nslots, int lig_bytes, int wpl,
-                                                                            int gen)
+                                                                            int gen_arg, const int* __restrict__ gen_dev)
 {
     const int lane = threadIdx.x & 31;
+    const int gen = gen_dev ? *gen_dev : gen_arg;  // inside a graph loop the generation lives on the device
     // warps of one ligand are padded to whole blocks (wpl per ligand), so a block has one ligand
     const long gw = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long nruns = (long)Dk.nlig * S.nrun;
@@ -1020,8 +1021,9 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
 // record the last completed generation and the run's best energy, apply
 // autostop (paper Sec. 1.1: population standard deviation of the best energy
 // over the last 10 generations below stopstd), count runs active for gen+1.
-__global__ void k_dock_bookkeep(SearchDev S, DockDev Dk, int gen, int* active)
+__global__ void k_dock_bookkeep(SearchDev S, DockDev Dk, int gen_arg, const int* __restrict__ gen_dev, int* active)
 {
+    const int gen = gen_dev ? *gen_dev : gen_arg;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     const int nruns = Dk.nlig * S.nrun;
     if (r >= nruns) return;
@@ -1067,34 +1069,51 @@ cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev&
 
 template <int APL, int LS>
 static cudaError_t gen_launch(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g,
-                              int gen)
+                              int gen, const int* gen_dev)
 {
     const int wpl = warps_per_ligand(s, g);
     const unsigned blocks = (unsigned)((long)d.nlig * wpl / g.wpb);
     cudaError_t e = allow_smem(k_dock_generation<APL, LS>, g.smem);
     if (e != cudaSuccess) return e;
     k_dock_generation<APL, LS><<<blocks, g.wpb * 32, g.smem, st>>>(m, s, d, g.na, g.nslots, (int)g.lig_bytes, wpl,
-                                                                   gen);
+                                                                   gen, gen_dev);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dock_generation(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g,
-                                   int gen)
+                                   int gen, const int* gen_dev)
 {
-#define ADG_GEN(A)                                                                                        \
-    if (s.ls_method == ADG_LS_SOLIS_WETS) return gen_launch<A, ADG_LS_SOLIS_WETS>(st, m, s, d, g, gen);   \
-    if (s.ls_method == ADG_LS_ADADELTA) return gen_launch<A, ADG_LS_ADADELTA>(st, m, s, d, g, gen);       \
-    return gen_launch<A, ADG_LS_NONE>(st, m, s, d, g, gen);
+#define ADG_GEN(A)                                                                                               \
+    if (s.ls_method == ADG_LS_SOLIS_WETS) return gen_launch<A, ADG_LS_SOLIS_WETS>(st, m, s, d, g, gen, gen_dev); \
+    if (s.ls_method == ADG_LS_ADADELTA) return gen_launch<A, ADG_LS_ADADELTA>(st, m, s, d, g, gen, gen_dev);     \
+    return gen_launch<A, ADG_LS_NONE>(st, m, s, d, g, gen, gen_dev);
     if (g.apl == 1) { ADG_GEN(1) }
     if (g.apl == 2) { ADG_GEN(2) }
     ADG_GEN(4)
 #undef ADG_GEN
 }
 
-cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const DockDev& d, int gen, int* active)
+cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const DockDev& d, int gen, int* active,
+                                     const int* gen_dev)
 {
     const int nruns = d.nlig * s.nrun;
-    k_dock_bookkeep<<<(nruns + 127) / 128, 128, 0, st>>>(s, d, gen, active);
+    k_dock_bookkeep<<<(nruns + 127) / 128, 128, 0, st>>>(s, d, gen, gen_dev, active);
+    return cudaGetLastError();
+}
+
+// Loop control of a graph-resident generation loop: continue while some run
+// is active, advance the device-side generation counter, clear the count.
+__global__ void k_dock_loop_ctl(cudaGraphConditionalHandle h, int* gen_dev, int* active)
+{
+    const int more = *active > 0;
+    *gen_dev += 1;
+    *active = 0;
+    cudaGraphSetConditional(h, more ? 1u : 0u);
+}
+
+cudaError_t launch_dock_loop_ctl(cudaStream_t st, cudaGraphConditionalHandle h, int* gen_dev, int* active)
+{
+    k_dock_loop_ctl<<<1, 1, 0, st>>>(h, gen_dev, active);
     return cudaGetLastError();
 }
 

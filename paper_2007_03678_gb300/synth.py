@@ -324,3 +324,23 @@ def workload_inputs(w: dict, lig_index: int = 0):
     rec = make_receptor(w["rec_atoms"], grid, RECEPTOR_SEED, pocket=w["pocket_frac"] * grid.extent[0])
     lig = make_ligand(w["n_heavy"], w["n_tors"], LIGAND_SEED0 + lig_index, n_hd=w["n_hd"])
     return grid, rec, lig
+
+
+def make_batch(n: int, seed: int, heavy=(10, 60), tors=(0, 15)):
+    """Seeded batch of drug-like ligands with heavy atoms uniform in `heavy`
+    and torsions uniform in `tors` (clipped to the rotatable bonds a grown
+    tree offers)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    k = 0
+    while len(out) < n:
+        nh = int(rng.integers(heavy[0], heavy[1] + 1))
+        nt = int(rng.integers(tors[0], tors[1] + 1))
+        for t in range(nt, -1, -1):
+            try:
+                out.append(make_ligand(nh, t, seed * 100003 + k))
+                break
+            except RuntimeError:
+                continue
+        k += 1
+    return out
