@@ -760,18 +760,17 @@ cudaError_t build_class_graph(adg_ctx* ctx, ClassRun& c, const MapsDev& M, const
     cudaGraph_t pro = nullptr, epi = nullptr, g = nullptr;
     cudaError_t e;
     // prologue
-    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
     cudaMemsetAsync(c.D.evals, 0, sizeof(unsigned long long) * 2 * nruns, cs);
     cudaMemsetAsync(c.D.gen_done, 0, sizeof(int) * nruns, cs);
     cudaMemsetAsync(c.D.stopped, 0, sizeof(int) * nruns, cs);
     cudaMemsetAsync(c.d_active, 0, sizeof(int), cs);
-    const int one = 1;
-    cudaMemcpyAsync(c.d_gen, &one, sizeof(int), cudaMemcpyHostToDevice, cs);
+    cudaMemsetAsync(c.d_gen, 0, sizeof(int), cs);  // generations completed by the loop
     launch_dock_init(cs, M, S, c.D, c.geo);
     e = cudaStreamEndCapture(cs, &pro);
     if (e != cudaSuccess) return e;
     // epilogue
-    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal)) != cudaSuccess) return e;
+    if ((e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed)) != cudaSuccess) return e;
     launch_dock_finalize(cs, M, S, c.D, c.geo, c.d_res);
     if ((e = cudaStreamEndCapture(cs, &epi)) != cudaSuccess) return e;
     // assemble
@@ -793,7 +792,7 @@ cudaError_t build_class_graph(adg_ctx* ctx, ClassRun& c, const MapsDev& M, const
         np.conditional.size = 1;
         if ((e = cudaGraphAddNode(&n_loop, g, &last, nullptr, 1, &np)) != cudaSuccess) return e;
         cudaGraph_t body = np.conditional.phGraph_out[0];
-        e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
         if (e != cudaSuccess) return e;
         launch_dock_generation(cs, M, S, c.D, c.geo, 0, c.d_gen);
         launch_dock_count_active(cs, S, c.D, 0, c.d_active, c.d_gen);
@@ -959,9 +958,8 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
     for (size_t k = 0; k < cls.size(); ++k) CK(ctx, cudaStreamSynchronize(cls[k].stream));
     for (size_t k = 0; k < cls.size(); ++k) {
         ClassRun& c = cls[k];
-        // generations executed by the device loop (the counter starts at 1 and
-        // is advanced once per pass)
-        const int ran = need_loop ? gens_dev[k] - 1 : 0;
+        // generations executed by the device loop (the counter counts passes)
+        const int ran = need_loop ? gens_dev[k] : 0;
         ctx->stats.gen_launches += ran;
         ctx->stats.kernel_launches += 3 * (int64_t)ran;
         if (ctx->timing && need_loop) {

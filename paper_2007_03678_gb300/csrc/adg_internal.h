@@ -137,8 +137,9 @@ cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, 
 cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const Geo& g, const float* genes, int npose, float* xyz);
 cudaError_t launch_philox(cudaStream_t st, const uint32_t* ctr, int n, uint32_t k0, uint32_t k1, uint32_t* out);
 cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g);
-// gen_dev: NULL, or a device int holding the generation (read by the kernels
-// in place of `gen`, for generation loops that run inside a CUDA graph).
+// gen_dev: NULL, or a device int holding the number of generations completed
+// (the kernels then run generation *gen_dev + 1 in place of `gen`; used by
+// generation loops that run inside a CUDA graph).
 cudaError_t launch_dock_generation(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d,
                                    const Geo& g, int gen, const int* gen_dev = nullptr);
 cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const DockDev& d, int gen, int* active,

@@ -918,7 +918,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
                                                                             int gen_arg, const int* __restrict__ gen_dev)
 {
     const int lane = threadIdx.x & 31;
-    const int gen = gen_dev ? *gen_dev : gen_arg;  // inside a graph loop the generation lives on the device
+    // inside a graph loop the device counter holds the generations completed so far
+    const int gen = gen_dev ? *gen_dev + 1 : gen_arg;
     // warps of one ligand are padded to whole blocks (wpl per ligand), so a block has one ligand
     const long gw = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     const long nruns = (long)Dk.nlig * S.nrun;
@@ -1023,7 +1024,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
 // over the last 10 generations below stopstd), count runs active for gen+1.
 __global__ void k_dock_bookkeep(SearchDev S, DockDev Dk, int gen_arg, const int* __restrict__ gen_dev, int* active)
 {
-    const int gen = gen_dev ? *gen_dev : gen_arg;
+    const int gen = gen_dev ? *gen_dev + 1 : gen_arg;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     const int nruns = Dk.nlig * S.nrun;
     if (r >= nruns) return;
@@ -1102,7 +1103,7 @@ cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const 
 }
 
 // Loop control of a graph-resident generation loop: continue while some run
-// is active, advance the device-side generation counter, clear the count.
+// is active, count the completed generation, clear the active count.
 __global__ void k_dock_loop_ctl(cudaGraphConditionalHandle h, int* gen_dev, int* active)
 {
     const int more = *active > 0;
