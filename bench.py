@@ -317,11 +317,26 @@ def main():
         BL = [adg.Ligand(ctx, ff, l) for l in bl]
         bp = adg.search_params(nrun=BATCH_NRUN, pop_size=150, nev=BATCH_NEV, ls_method=adg.LS_ADADELTA,
                                seed=S.SEARCH_SEED)
-        adg.dock(ctx, R, BL[:4], bp)  # warm-up of every path
+        # warm-up of every path; tunes the launch geometry of every shape bucket once
+        wp = adg.search_params(nrun=1, pop_size=150, nev=600, ls_method=adg.LS_ADADELTA, seed=S.SEARCH_SEED)
+        ctx.stats(reset=True)
+        t0 = time.perf_counter()
+        adg.dock(ctx, R, BL, wp)
+        t_tune = time.perf_counter() - t0
+        tune_launches = ctx.stats()["tune_launches"]
         torch.cuda.synchronize()
+        ctx.stats(reset=True)
         t0 = time.perf_counter()
         rb = adg.dock(ctx, R, BL, bp)
         t_batch = time.perf_counter() - t0
+        groups = ctx.stats()["dock_groups"]
+        ctx.set_geometry(adg.GEO_HEURISTIC)  # the same batch under the fixed launch rule
+        adg.dock(ctx, R, BL, wp)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        adg.dock(ctx, R, BL, bp)
+        t_fixed = time.perf_counter() - t0
+        ctx.set_geometry(adg.GEO_TUNED)
         t0 = time.perf_counter()
         for i, lg in enumerate(BL):
             bp.lig_id = i
@@ -332,7 +347,10 @@ def main():
                     "nrun": BATCH_NRUN, "pop": 150, "nev": BATCH_NEV, "local_search": "adadelta",
                     "ligands_per_s_batched": BATCH_LIGANDS / t_batch,
                     "ligands_per_s_one_by_one": BATCH_LIGANDS / t_one, "speedup": t_one / t_batch,
-                    "evals_per_s_batched": ev / t_batch}
+                    "ligands_per_s_batched_fixed_rule": BATCH_LIGANDS / t_fixed,
+                    "evals_per_s_batched": ev / t_batch, "groups": groups,
+                    "tuning": {"buckets": len(ctx.tuned()), "launches": tune_launches,
+                               "first_call_s": round(t_tune, 3)}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

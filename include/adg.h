@@ -256,12 +256,51 @@ typedef struct {
     int64_t gen_timed;        /* generation launches included in that sum  */
     int64_t h2d_bytes;        /* host -> device bytes copied by the library */
     int64_t d2h_bytes;        /* device -> host bytes copied by the library */
+    int64_t dock_groups;      /* ligand groups (one graph each) of adg_dock */
+    int64_t tune_launches;    /* kernels launched to tune launch geometry   */
 } adg_stats;
 
 int adg_ctx_set_timing(adg_ctx* ctx, int enable);
 /* Copy the counters to *out; zero them when reset != 0.  Waits for the
  * stream when timing is on (to read the events). */
 int adg_ctx_stats(adg_ctx* ctx, adg_stats* out, int reset);
+
+/* Launch geometry of adg_dock (no counterpart in the paper, whose kernels
+ * have one fixed block shape per ligand).  The generation kernel runs one
+ * individual per warp; per launch it chooses the warps per block and whether
+ * the ligand's pair tables are copied into shared memory once per block or
+ * read through L1, which sets how many warps stay resident per SM.
+ *   ADG_GEO_HEURISTIC: one fixed rule (stage the ligand when it fits beside
+ *     at least four warps, two blocks per SM), ligands grouped by atoms per
+ *     lane (1..4, i.e. up to 32, 64, 96, 128 atoms).
+ *   ADG_GEO_TUNED (default): the first time a shape bucket (atoms per lane,
+ *     local-search kind, pair slots rounded up to 256, ligand bytes rounded
+ *     up to 8 KiB) is met, the library times the geometries that keep the
+ *     most warps resident -- ligand staged, and ligand read through L1 -- on
+ *     a probe batch of that ligand's poses (each warp evaluating its pose
+ *     eight times, as in a local search) and keeps the faster one for the
+ *     life of the context.  A dock call then groups its ligands by the
+ *     geometry they got; each group is one graph, the groups run on
+ *     concurrent streams.
+ * Docking results do not depend on the geometry (every warp does the same
+ * arithmetic in either form). */
+enum { ADG_GEO_HEURISTIC = 0, ADG_GEO_TUNED = 1 };
+int adg_ctx_set_geometry(adg_ctx* ctx, int mode);
+
+/* One entry of a context's tuning table. */
+typedef struct {
+    int32_t apl;             /* atoms per lane                            */
+    int32_t ls_method;       /* ADG_LS_*                                  */
+    int32_t nslots_max;      /* bucket bound: pair slots                  */
+    int32_t bytes_max;       /* bucket bound: ligand blob bytes           */
+    int32_t staged;          /* chosen: ligand copied to shared memory    */
+    int32_t warps_per_block; /* chosen                                    */
+    int32_t blocks_per_sm;   /* resident blocks of the generation kernel  */
+    int32_t ncand;           /* candidates timed (0 or 1: none timed)     */
+    float us_per_eval[2];    /* probe time per evaluation: staged, L1     */
+} adg_tuned_shape;
+/* Copy up to `cap` entries of the tuning table to out; *n = entries held. */
+int adg_ctx_tuned(adg_ctx* ctx, adg_tuned_shape* out, int cap, int* n);
 
 /* Docking without allocation.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate memory -- a host application whose

@@ -27,6 +27,7 @@ TRACE_WIDTH = 12
 ADG_OK = 0
 GRAD_NONE, GRAD_GENES, GRAD_TANGENT = 0, 1, 2
 LS_NONE, LS_SOLIS_WETS, LS_ADADELTA = 0, 1, 2
+GEO_HEURISTIC, GEO_TUNED = 0, 1
 
 
 class AdgError(RuntimeError):
@@ -83,7 +84,13 @@ class adg_dock_trace(C.Structure):
 
 class adg_stats(C.Structure):
     _fields_ = [("kernel_launches", C.c_int64), ("gen_launches", C.c_int64), ("gen_kernel_ms", C.c_double),
-                ("gen_timed", C.c_int64), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64)]
+                ("gen_timed", C.c_int64), ("h2d_bytes", C.c_int64), ("d2h_bytes", C.c_int64),
+                ("dock_groups", C.c_int64), ("tune_launches", C.c_int64)]
+
+
+class adg_tuned_shape(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("apl", "ls_method", "nslots_max", "bytes_max", "staged", "warps_per_block",
+                                         "blocks_per_sm", "ncand")] + [("us_per_eval", C.c_float * 2)]
 
 
 class adg_ligand_stats(C.Structure):
@@ -95,7 +102,7 @@ class adg_ligand_stats(C.Structure):
 EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_ctx_destroy", "adg_sync",
            "adg_ctx_last_error", "adg_maps_build", "adg_receptor_create", "adg_receptor_destroy", "adg_ligand_create",
            "adg_ligand_destroy", "adg_ligand_info", "adg_score", "adg_pose", "adg_dock", "adg_philox",
-           "adg_ctx_set_timing", "adg_ctx_stats", "adg_dock_noalloc")
+           "adg_ctx_set_timing", "adg_ctx_stats", "adg_dock_noalloc", "adg_ctx_set_geometry", "adg_ctx_tuned")
 
 _lib = None
 
@@ -134,6 +141,8 @@ def load(path: str | None = None):
         L.adg_ctx_set_timing.argtypes = [_vp, _i]
         L.adg_dock_noalloc.argtypes = [_vp, _vp, C.POINTER(adg_search_params), C.POINTER(adg_result), _vp]
         L.adg_ctx_stats.argtypes = [_vp, C.POINTER(adg_stats), _i]
+        L.adg_ctx_set_geometry.argtypes = [_vp, _i]
+        L.adg_ctx_tuned.argtypes = [_vp, C.POINTER(adg_tuned_shape), _i, C.POINTER(C.c_int)]
         _lib = L
     return _lib
 
@@ -216,6 +225,23 @@ class Context:
 
     def set_timing(self, enable: bool):
         _check(load().adg_ctx_set_timing(self.handle, int(enable)), "adg_ctx_set_timing", self)
+
+    def set_geometry(self, mode: int):
+        """GEO_HEURISTIC or GEO_TUNED (default) launch geometry for dock."""
+        _check(load().adg_ctx_set_geometry(self.handle, int(mode)), "adg_ctx_set_geometry", self)
+
+    def tuned(self) -> list:
+        """The context's tuning table: one dict per shape bucket."""
+        n = C.c_int(0)
+        _check(load().adg_ctx_tuned(self.handle, None, 0, C.byref(n)), "adg_ctx_tuned", self)
+        buf = (adg_tuned_shape * max(n.value, 1))()
+        _check(load().adg_ctx_tuned(self.handle, buf, n.value, C.byref(n)), "adg_ctx_tuned", self)
+        out = []
+        for t in buf[:n.value]:
+            d = {name: getattr(t, name) for name, _ in adg_tuned_shape._fields_[:-1]}
+            d["us_per_eval"] = [float(t.us_per_eval[0]), float(t.us_per_eval[1])]
+            out.append(d)
+        return out
 
     def stats(self, reset: bool = False) -> dict:
         st = adg_stats()

@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -35,7 +36,12 @@ struct adg_ctx {
     adg_stats stats{};
     std::vector<cudaEvent_t> ev_free;                       // reusable events
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
-    std::vector<cudaStream_t> class_streams;  // extra streams for concurrent shape classes
+    std::vector<cudaStream_t> class_streams;  // extra streams for concurrent ligand groups
+    // launch geometry of adg_dock
+    int geo_mode = ADG_GEO_TUNED;
+    std::map<uint32_t, adg_tuned_shape> tuned;  // by shape bucket
+    void* tune_buf = nullptr;                    // probe poses and energies
+    size_t tune_bytes = 0;
 };
 
 namespace {
@@ -52,7 +58,7 @@ int cuda_fail(adg_ctx* ctx, cudaError_t e, const char* what)
         if (_e != cudaSuccess) return cuda_fail(ctx, _e, #call); \
     } while (0)
 
-int apl_for(int natoms) { return natoms <= 32 ? 1 : (natoms <= 64 ? 2 : 4); }
+int apl_for(int natoms) { return (natoms + 31) / 32; }  // atoms per lane, 1..4
 
 uint32_t prob_threshold(float p)
 {
@@ -180,6 +186,7 @@ int adg_ctx_destroy(adg_ctx* ctx)
         cudaStreamDestroy(s2);
     }
     if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->tune_buf) cudaFree(ctx->tune_buf);
     if (ctx->host_active) cudaFreeHost(ctx->host_active);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -200,6 +207,25 @@ int adg_ctx_set_timing(adg_ctx* ctx, int enable)
 {
     if (!ctx) return ADG_EINVAL;
     ctx->timing = enable != 0;
+    return ADG_OK;
+}
+
+int adg_ctx_set_geometry(adg_ctx* ctx, int mode)
+{
+    if (!ctx || (mode != ADG_GEO_HEURISTIC && mode != ADG_GEO_TUNED)) return ADG_EINVAL;
+    ctx->geo_mode = mode;
+    return ADG_OK;
+}
+
+int adg_ctx_tuned(adg_ctx* ctx, adg_tuned_shape* out, int cap, int* n)
+{
+    if (!ctx || !n || cap < 0 || (cap > 0 && !out)) return ADG_EINVAL;
+    *n = (int)ctx->tuned.size();
+    int k = 0;
+    for (const auto& kv : ctx->tuned) {
+        if (k >= cap) break;
+        out[k++] = kv.second;
+    }
     return ADG_OK;
 }
 
@@ -750,6 +776,186 @@ void fill_search(const adg_search_params* p, SearchDev& S)
     S.stopstd = p->stopstd;
 }
 
+// ---- launch geometry of adg_dock
+// Shape bucket of a ligand: atoms per lane, local-search kind, pair slots
+// rounded up to 256 and blob bytes rounded up to 8 KiB.
+uint32_t bucket_key(int apl, int ls, int nslots, size_t bytes, int* ns_b, int* by_b)
+{
+    *ns_b = (int)align_up((size_t)std::max(nslots, 1), 256);
+    *by_b = (int)align_up(std::max(bytes, (size_t)1), 8192);
+    return (uint32_t)apl | ((uint32_t)ls << 3) | ((uint32_t)(*ns_b / 256) << 8) | ((uint32_t)(*by_b / 8192) << 18);
+}
+
+// Time the candidate geometries (ligand staged, ligand read through L1; each
+// with the block size that keeps the most warps resident) on probe poses of
+// `lig`, the first member met of its bucket, and record the faster form.
+int tune_shape(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* lig, int ls, int ns_b, int by_b,
+               adg_tuned_shape* out)
+{
+    Geo cand[2];
+    const int n = geo_candidates(lig->apl, lig->nslots, lig->bytes, ls, cand, 2);
+    adg_tuned_shape t{};
+    t.apl = lig->apl;
+    t.ls_method = ls;
+    t.nslots_max = ns_b;
+    t.bytes_max = by_b;
+    t.ncand = n;
+    if (n == 0) {  // no candidate launches: keep the fixed rule
+        const Geo g = make_geo(lig->apl, lig->nslots, lig->bytes);
+        t.staged = g.lig_bytes > 0;
+        t.warps_per_block = g.wpb;
+        t.blocks_per_sm = geo_blocks_per_sm(g, ls);
+        *out = t;
+        return ADG_OK;
+    }
+    int pick = 0;
+    if (n > 1) {
+        int nsm = 0, smem_sm = 0, reserve = 0, optin = 0;
+        CK(ctx, cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device));
+        CK(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+        CK(ctx, cudaDeviceGetAttribute(&reserve, cudaDevAttrReservedSharedMemoryPerBlock, ctx->device));
+        CK(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+        int bps[2], maxres = 0;
+        for (int k = 0; k < n; ++k) {
+            bps[k] = geo_blocks_per_sm(cand[k], ls);
+            maxres = std::max(maxres, bps[k] * cand[k].wpb);
+        }
+        const int reps = 8, G = 7 + lig->ntors;
+        const long npose = (long)nsm * maxres * 2;  // two waves of the most resident candidate
+        const size_t need = align_up(sizeof(float) * npose * G, 256) + sizeof(float) * npose;
+        if (need > ctx->tune_bytes) {
+            CK(ctx, cudaStreamSynchronize(ctx->stream));
+            if (ctx->tune_buf) cudaFree(ctx->tune_buf);
+            ctx->tune_buf = nullptr;
+            ctx->tune_bytes = 0;
+            cudaError_t e = cudaMalloc(&ctx->tune_buf, need);
+            if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? ADG_ENOMEM : cuda_fail(ctx, e, "tune buffer");
+            ctx->tune_bytes = need;
+        }
+        float* genes = (float*)ctx->tune_buf;
+        float* energy = (float*)((char*)ctx->tune_buf + align_up(sizeof(float) * npose * G, 256));
+        cudaStream_t st = ctx->stream;
+        const bool grad = ls == ADG_LS_ADADELTA;
+        CK(ctx, launch_probe_genes(st, rec->maps, lig->ntors, (int)npose, 3.0f, 0x5eedu, genes));
+        cudaEvent_t a, b;
+        CK(ctx, take_event(ctx, &a));
+        CK(ctx, take_event(ctx, &b));
+        float best_ms[2] = {0.f, 0.f};
+        for (int k = 0; k < n; ++k) {
+            Geo g = cand[k];
+            // pad the probe's shared memory so that it keeps the generation
+            // kernel's residency whatever its own register count
+            size_t pad = (size_t)(smem_sm / std::max(bps[k], 1) - reserve);
+            pad = std::min(pad, (size_t)optin);
+            if (pad > g.smem) g.smem = pad;
+            CK(ctx, launch_tune(st, rec->maps, lig->ref, g, genes, (int)npose, reps, grad, energy));
+            float best = 1e30f;
+            for (int r = 0; r < 3; ++r) {
+                CK(ctx, cudaEventRecord(a, st));
+                CK(ctx, launch_tune(st, rec->maps, lig->ref, g, genes, (int)npose, reps, grad, energy));
+                CK(ctx, cudaEventRecord(b, st));
+                CK(ctx, cudaEventSynchronize(b));
+                float ms = 0.f;
+                CK(ctx, cudaEventElapsedTime(&ms, a, b));
+                best = std::min(best, ms);
+            }
+            best_ms[k] = best;
+            t.us_per_eval[cand[k].lig_bytes > 0 ? 0 : 1] = best * 1000.f / (float)(npose * reps);
+        }
+        ctx->ev_free.push_back(a);
+        ctx->ev_free.push_back(b);
+        ctx->stats.tune_launches += 1 + 4 * n;
+        ctx->stats.kernel_launches += 1 + 4 * n;
+        pick = best_ms[1] < best_ms[0] ? 1 : 0;
+    }
+    t.staged = cand[pick].lig_bytes > 0;
+    t.warps_per_block = cand[pick].wpb;
+    t.blocks_per_sm = geo_blocks_per_sm(cand[pick], ls);
+    *out = t;
+    return ADG_OK;
+}
+
+// Group the ligands of a dock call.  Heuristic mode: by atoms per lane with
+// the fixed rule.  Tuned mode: every ligand takes the form (staged or read
+// through L1) its bucket was tuned to; ligands of one width and form, in
+// increasing footprint, share a group while the group's largest footprint
+// keeps at least 3/4 of the warps resident that its smallest member alone
+// would (fewer, larger groups leave fewer partly filled waves).
+int group_ligands(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig, int ls,
+                  std::vector<ClassRun>& cls)
+{
+    cls.clear();
+    if (ctx->geo_mode == ADG_GEO_HEURISTIC) {
+        for (int apl = 1; apl <= 4; ++apl) {
+            ClassRun c;
+            int nslots = 32;
+            size_t lig_bytes = 0;
+            for (int i = 0; i < nlig; ++i)
+                if (ligs[i]->apl == apl) {
+                    c.ligs.push_back(i);
+                    nslots = std::max(nslots, ligs[i]->nslots);
+                    lig_bytes = std::max(lig_bytes, ligs[i]->bytes);
+                }
+            if (c.ligs.empty()) continue;
+            c.geo = make_geo(apl, nslots, lig_bytes);
+            cls.push_back(c);
+        }
+        return ADG_OK;
+    }
+    std::map<int, std::vector<int>> by_form;  // apl * 2 + staged -> ligands
+    for (int i = 0; i < nlig; ++i) {
+        int ns_b, by_b;
+        const uint32_t key = bucket_key(ligs[i]->apl, ls, ligs[i]->nslots, ligs[i]->bytes, &ns_b, &by_b);
+        auto it = ctx->tuned.find(key);
+        if (it == ctx->tuned.end()) {
+            adg_tuned_shape t;
+            const int rc = tune_shape(ctx, rec, ligs[i], ls, ns_b, by_b, &t);
+            if (rc != ADG_OK) return rc;
+            it = ctx->tuned.emplace(key, t).first;
+        }
+        by_form[ligs[i]->apl * 2 + (it->second.staged ? 1 : 0)].push_back(i);
+    }
+    for (auto& kv : by_form) {
+        const int apl = kv.first / 2;
+        const bool staged = (kv.first & 1) != 0;
+        std::vector<int>& members = kv.second;
+        std::sort(members.begin(), members.end(), [&](int a, int b) {
+            const size_t fa = (staged ? ligs[a]->bytes : 0) + 4u * ligs[a]->nslots;
+            const size_t fb = (staged ? ligs[b]->bytes : 0) + 4u * ligs[b]->nslots;
+            return fa < fb;
+        });
+        ClassRun c;
+        int nslots = 0, res_first = 0;
+        size_t lig_bytes = 0;
+        for (int i : members) {
+            const int ns2 = std::max(nslots, ligs[i]->nslots);
+            const size_t lb2 = std::max(lig_bytes, ligs[i]->bytes);
+            Geo g2;
+            const int res2 = geo_best(apl, ns2, staged ? lb2 : 0, staged, ls, &g2);
+            if (!c.ligs.empty() && 4 * res2 < 3 * res_first) {  // close the group, start the next with ligand i
+                cls.push_back(c);
+                c = ClassRun();
+                res_first = geo_best(apl, ligs[i]->nslots, staged ? ligs[i]->bytes : 0, staged, ls, &c.geo);
+                nslots = ligs[i]->nslots;
+                lig_bytes = ligs[i]->bytes;
+            } else {
+                if (c.ligs.empty()) res_first = res2;
+                c.geo = g2;
+                nslots = ns2;
+                lig_bytes = lb2;
+            }
+            if (res_first == 0) c.geo = make_geo(apl, nslots, lig_bytes);  // nothing fits: the fixed rule's fallback
+            c.ligs.push_back(i);
+        }
+        cls.push_back(c);
+    }
+    // the group with the most work goes first (on the context's stream)
+    std::stable_sort(cls.begin(), cls.end(), [](const ClassRun& a, const ClassRun& b) {
+        return a.ligs.size() * a.geo.na > b.ligs.size() * b.geo.na;
+    });
+    return ADG_OK;
+}
+
 // Build the graph of one class: prologue (clear counters, initial
 // population) -> WHILE (generation, bookkeeping, loop control) -> final
 // poses.  The loop runs on the device until no run of the class is active.
@@ -826,22 +1032,11 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         if (!ligs[i] || ligs[i]->ctx != ctx) return ADG_EINVAL;
     CK(ctx, cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
-    // --- shape classes: ligands grouped by atoms per lane (1, 2, 4)
+    // --- ligand groups, one graph each
     std::vector<ClassRun> cls;
-    for (int apl : {1, 2, 4}) {
-        ClassRun c;
-        int nslots = 32;
-        size_t lig_bytes = 0;
-        for (int i = 0; i < nlig; ++i)
-            if (ligs[i]->apl == apl) {
-                c.ligs.push_back(i);
-                nslots = std::max(nslots, ligs[i]->nslots);
-                lig_bytes = std::max(lig_bytes, ligs[i]->bytes);
-            }
-        if (c.ligs.empty()) continue;
-        c.geo = make_geo(apl, nslots, lig_bytes);
-        cls.push_back(c);
-    }
+    int rc = group_ligands(ctx, rec, ligs, nlig, p->ls_method, cls);
+    if (rc != ADG_OK) return rc;
+    ctx->stats.dock_groups += (int64_t)cls.size();
     const int tr_ngen = trace ? trace->ngen : 0;
     const long tr_slots = trace ? (long)p->nrun * tr_ngen * p->pop_size : 0;
     // --- arena layout, class after class

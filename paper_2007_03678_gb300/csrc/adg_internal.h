@@ -25,7 +25,7 @@ __host__ __device__ inline size_t warp_smem_floats(int na, int nslots) { return 
 // dynamic shared memory holds a copy of its ligand's blob (lig_bytes) and
 // then one region per warp.
 struct Geo {
-    int apl;           // atoms per lane (1, 2, 4)
+    int apl;           // atoms per lane (1, 2, 3, 4)
     int na;            // 32 * apl
     int nslots;        // largest pair-slot count of the launched ligands
     int wpb;           // warps per block
@@ -132,6 +132,28 @@ cudaError_t launch_maps_build(cudaStream_t st, const adg_forcefield& ff, const a
                               const float4* rec_xyzq, const int* rec_type, float* maps_out);
 cudaError_t launch_pack_maps(cudaStream_t st, const float* maps, const adg_grid_desc& g, float4* packed);
 Geo make_geo(int apl, int nslots, size_t lig_bytes);
+// The same shape with the ligand staged in shared memory or not and `wpb`
+// warps per block (no fitting rule applied; smem may exceed what a block can have).
+Geo make_geo_explicit(int apl, int nslots, size_t lig_bytes, bool staged, int wpb);
+// Resident blocks per SM of the generation kernel for local search `ls` at
+// geometry g (0: the geometry cannot launch).
+int geo_blocks_per_sm(const Geo& g, int ls);
+// The warps per block that keep the most warps of the generation kernel
+// resident for a shape, staged or not; returns that warp count (0: none launches).
+int geo_best(int apl, int nslots, size_t lig_bytes, bool staged, int ls, Geo* out);
+// Launch geometries worth timing for a shape: for the ligand staged in shared
+// memory and for it read through L1, the warps-per-block counts that keep the
+// most warps resident.  Writes up to `cap` entries, returns how many.
+int geo_candidates(int apl, int nslots, size_t lig_bytes, int ls, Geo* out, int cap);
+// Autotuning probe: npose random poses of a ligand with T torsions about the
+// box centre (translation within +-spread), written as [npose][7+T].
+cudaError_t launch_probe_genes(cudaStream_t st, const MapsDev& m, int T, int npose, float spread, uint32_t seed,
+                               float* genes);
+// Autotuning workload: every warp evaluates its pose `reps` times (with a
+// small torsion change between evaluations), as a local search does, with
+// (grad != 0) or without the gradient; energy[pose] receives the last value.
+cudaError_t launch_tune(cudaStream_t st, const MapsDev& m, const LigandRef& l, const Geo& g, const float* genes,
+                        int npose, int reps, int grad, float* energy);
 cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, const Geo& g, const float* genes,
                          int npose, float* energy, float* grad, int grad_kind);
 cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const Geo& g, const float* genes, int npose, float* xyz);

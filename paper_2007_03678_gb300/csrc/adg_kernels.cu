@@ -580,7 +580,7 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
 Geo make_geo(int apl, int nslots, size_t lig_bytes)
 {
     Geo g;
-    g.apl = apl <= 1 ? 1 : (apl <= 2 ? 2 : 4);
+    g.apl = apl <= 1 ? 1 : (apl >= 4 ? 4 : apl);
     g.na = 32 * g.apl;
     g.nslots = nslots < 32 ? 32 : (nslots + 31) / 32 * 32;
     g.lig_bytes = (lig_bytes + 255) / 256 * 256;
@@ -594,6 +594,16 @@ Geo make_geo(int apl, int nslots, size_t lig_bytes)
     if (g.lig_bytes + (size_t)g.wpb * per_warp > 113u * 1024u)
         while (g.wpb > 1 && g.lig_bytes + (size_t)g.wpb * per_warp > 220u * 1024u) --g.wpb;
     g.smem = g.lig_bytes + (size_t)g.wpb * per_warp;
+    return g;
+}
+
+Geo make_geo_explicit(int apl, int nslots, size_t lig_bytes, bool staged, int wpb)
+{
+    Geo g = make_geo(apl, nslots, lig_bytes);
+    if (!staged) g.lig_bytes = 0;
+    else g.lig_bytes = (lig_bytes + 255) / 256 * 256;
+    g.wpb = wpb < 1 ? 1 : (wpb > kMaxWarpsPerBlock ? kMaxWarpsPerBlock : wpb);
+    g.smem = g.lig_bytes + (size_t)g.wpb * warp_smem_floats(g.na, g.nslots) * sizeof(float);
     return g;
 }
 
@@ -665,6 +675,7 @@ cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, 
                                                 grad_kind);
     if (g.apl == 1) { ADG_SCORE(1) }
     else if (g.apl == 2) { ADG_SCORE(2) }
+    else if (g.apl == 3) { ADG_SCORE(3) }
     else { ADG_SCORE(4) }
 #undef ADG_SCORE
     return cudaGetLastError();
@@ -1063,6 +1074,7 @@ cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev&
     k_dock_init<A><<<blocks, threads, g.smem, st>>>(m, s, d, g.na, g.nslots, (int)g.lig_bytes, wpl);
     if (g.apl == 1) { ADG_INIT(1) }
     else if (g.apl == 2) { ADG_INIT(2) }
+    else if (g.apl == 3) { ADG_INIT(3) }
     else { ADG_INIT(4) }
 #undef ADG_INIT
     return cudaGetLastError();
@@ -1090,8 +1102,151 @@ cudaError_t launch_dock_generation(cudaStream_t st, const MapsDev& m, const Sear
     return gen_launch<A, ADG_LS_NONE>(st, m, s, d, g, gen, gen_dev);
     if (g.apl == 1) { ADG_GEN(1) }
     if (g.apl == 2) { ADG_GEN(2) }
+    if (g.apl == 3) { ADG_GEN(3) }
     ADG_GEN(4)
 #undef ADG_GEN
+}
+
+// ------------------------------------------------------------------ launch-geometry tuning
+template <int APL, int LS>
+static int blocks_per_sm(const Geo& g)
+{
+    int optin = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
+    if (g.smem > (size_t)optin) return 0;
+    if (allow_smem(k_dock_generation<APL, LS>, g.smem) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dock_generation<APL, LS>, g.wpb * 32, g.smem) !=
+        cudaSuccess)
+        return 0;
+    return nb;
+}
+
+int geo_blocks_per_sm(const Geo& g, int ls)
+{
+#define ADG_BPS(A)                                                                              \
+    if (ls == ADG_LS_SOLIS_WETS) return blocks_per_sm<A, ADG_LS_SOLIS_WETS>(g);                \
+    if (ls == ADG_LS_ADADELTA) return blocks_per_sm<A, ADG_LS_ADADELTA>(g);                    \
+    return blocks_per_sm<A, ADG_LS_NONE>(g);
+    if (g.apl == 1) { ADG_BPS(1) }
+    if (g.apl == 2) { ADG_BPS(2) }
+    if (g.apl == 3) { ADG_BPS(3) }
+    ADG_BPS(4)
+#undef ADG_BPS
+}
+
+int geo_best(int apl, int nslots, size_t lig_bytes, bool staged, int ls, Geo* out)
+{
+    int best_res = 0;
+    for (int wpb = kMaxWarpsPerBlock; wpb >= 1; --wpb) {  // ties keep the larger block (fewer ligand copies)
+        const Geo g = make_geo_explicit(apl, nslots, lig_bytes, staged, wpb);
+        const int res = geo_blocks_per_sm(g, ls) * wpb;
+        if (res > best_res) {
+            *out = g;
+            best_res = res;
+        }
+    }
+    return best_res;
+}
+
+int geo_candidates(int apl, int nslots, size_t lig_bytes, int ls, Geo* out, int cap)
+{
+    int n = 0;
+    for (int staged = 1; staged >= 0; --staged) {
+        if (staged && lig_bytes == 0) continue;
+        Geo g;
+        if (geo_best(apl, nslots, lig_bytes, staged != 0, ls, &g) > 0 && n < cap) out[n++] = g;
+    }
+    return n;
+}
+
+// Random poses about the box centre: t = centre + U(-spread, spread) per axis,
+// q uniform on S^3 (three uniforms, Shoemake), theta uniform in [-pi, pi).
+__global__ void k_probe_genes(MapsDev M, int T, int npose, float spread, uint32_t seed, float* __restrict__ genes)
+{
+    const int pose = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pose >= npose) return;
+    const int G = 7 + T;
+    float* g = genes + (long)pose * G;
+    const uint4 a = philox(make_uint4((uint32_t)pose, 0u, 0u, 7u << 20), seed, 0x7475u);
+    const uint4 b = philox(make_uint4((uint32_t)pose, 1u, 0u, 7u << 20), seed, 0x7475u);
+    g[0] = 0.5f * (M.ox + M.hx) + spread * (2.f * u01(a.x) - 1.f);
+    g[1] = 0.5f * (M.oy + M.hy) + spread * (2.f * u01(a.y) - 1.f);
+    g[2] = 0.5f * (M.oz + M.hz) + spread * (2.f * u01(a.z) - 1.f);
+    const float u1 = u01(b.x), s1 = sqrtf(1.f - u1), s2 = sqrtf(u1);
+    float sa, ca, sb, cb;
+    sincospif(2.f * u01(b.y), &sa, &ca);
+    sincospif(2.f * u01(b.z), &sb, &cb);
+    g[3] = s2 * cb;
+    g[4] = s1 * sa;
+    g[5] = s1 * ca;
+    g[6] = s2 * sb;
+    for (int k = 0; k < T; k += 4) {
+        const uint4 w = philox(make_uint4((uint32_t)pose, 2u + (uint32_t)k, 0u, 7u << 20), seed, 0x7475u);
+        for (int i = 0; i < 4 && k + i < T; ++i) g[7 + k + i] = -3.14159265f + 6.28318531f * u01(word(w, i));
+    }
+}
+
+cudaError_t launch_probe_genes(cudaStream_t st, const MapsDev& m, int T, int npose, float spread, uint32_t seed,
+                               float* genes)
+{
+    if (npose <= 0) return cudaSuccess;
+    k_probe_genes<<<(unsigned)((npose + 127) / 128), 128, 0, st>>>(m, T, npose, spread, seed, genes);
+    return cudaGetLastError();
+}
+
+template <int APL, bool GRAD>
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_tune(MapsDev M, LigandRef LR, int na,
+                                                                                int nslots, int lig_bytes,
+                                                                                const float* __restrict__ genes,
+                                                                                int npose, int reps,
+                                                                                float* __restrict__ energy)
+{
+    const int lane = threadIdx.x & 31;
+    const long pose = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const LigandRef SL = stage_ligand(LR, lig_bytes);
+    if (pose >= npose) return;
+    const WarpView ws = warp_view(na, nslots, lig_bytes);
+    const LigandDev* L = SL.hdr;
+    const int G = 7 + L->ntors;
+    const float g0 = lane < G ? genes[pose * G + lane] : 0.f;
+    float acc = 0.f;
+    for (int r = 0; r < reps; ++r) {
+        if (lane < G) ws.genes[lane] = lane >= 7 ? g0 + 1e-3f * (float)r : g0;
+        __syncwarp();
+        const ScoreOut o = warp_score<APL, GRAD>(L, SL.pairs, M, ws.genes, ws, lane);
+        acc = o.e + (GRAD ? 1e-30f * __shfl_sync(FULL_MASK, o.gtan, 6) : 0.f);
+        __syncwarp();
+    }
+    if (lane == 0) energy[pose] = acc;
+}
+
+cudaError_t launch_tune(cudaStream_t st, const MapsDev& m, const LigandRef& l, const Geo& g, const float* genes,
+                        int npose, int reps, int grad, float* energy)
+{
+    if (npose <= 0) return cudaSuccess;
+    const unsigned blocks = blocks_for(npose, g);
+    const unsigned threads = g.wpb * 32;
+    cudaError_t e;
+#define ADG_TUNE(A, GR)                                                                                    \
+    e = allow_smem(k_tune<A, GR>, g.smem);                                                                 \
+    if (e != cudaSuccess) return e;                                                                        \
+    k_tune<A, GR><<<blocks, threads, g.smem, st>>>(m, l, g.na, g.nslots, (int)g.lig_bytes, genes, npose, reps, \
+                                                   energy);
+    if (grad) {
+        if (g.apl == 1) { ADG_TUNE(1, true) }
+        else if (g.apl == 2) { ADG_TUNE(2, true) }
+        else if (g.apl == 3) { ADG_TUNE(3, true) }
+        else { ADG_TUNE(4, true) }
+    } else {
+        if (g.apl == 1) { ADG_TUNE(1, false) }
+        else if (g.apl == 2) { ADG_TUNE(2, false) }
+        else if (g.apl == 3) { ADG_TUNE(3, false) }
+        else { ADG_TUNE(4, false) }
+    }
+#undef ADG_TUNE
+    return cudaGetLastError();
 }
 
 cudaError_t launch_dock_count_active(cudaStream_t st, const SearchDev& s, const DockDev& d, int gen, int* active,

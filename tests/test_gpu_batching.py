@@ -40,3 +40,39 @@ def test_batch_equals_one_by_one(ctx, ff, ls_method):
         alone = adg.dock(ctx, R, lg, q)[0]
         for key in ("best_energy", "genes", "xyz", "evals", "generations"):
             assert np.array_equal(batch[i][key], alone[key]), (i, key)
+
+
+def test_geometry_modes_agree_and_tuning_table(ctx, ff):
+    """The tuned launch geometry (per-bucket timing of staged / L1 forms,
+    ligands grouped by the geometry they get) and the fixed rule give the
+    same results bit for bit; every tuned bucket has a launchable choice."""
+    from paper_2007_03678_gb300 import adg
+    grid, rec, _, maps64, maps32 = problem("paper")
+    R = adg.Receptor(ctx, grid, maps32)
+    ligs = S.make_batch(10, seed=11) + [S.make_ligand(88, 12, 4242), S.make_ligand(110, 15, 4343)]
+    sizes = [l.natoms for l in ligs]
+    assert min(sizes) <= 32 and max(sizes) > 96  # atoms-per-lane widths 1 to 4
+    L = [adg.Ligand(ctx, ff, l) for l in ligs]
+    p = adg.search_params(nrun=3, pop_size=40, nev=3000, ls_method=adg.LS_ADADELTA, ls_max_iters=20, seed=17)
+    ctx.set_geometry(adg.GEO_HEURISTIC)
+    ctx.stats(reset=True)
+    ref = adg.dock(ctx, R, L, p)
+    assert ctx.stats()["dock_groups"] == 4
+    ctx.set_geometry(adg.GEO_TUNED)
+    ctx.stats(reset=True)
+    got = adg.dock(ctx, R, L, p)
+    st = ctx.stats()
+    assert st["dock_groups"] >= 4 and st["tune_launches"] >= 0
+    for i in range(len(L)):
+        for key in ("best_energy", "genes", "xyz", "evals", "generations"):
+            assert np.array_equal(ref[i][key], got[i][key]), (i, key)
+    table = ctx.tuned()
+    assert {t["apl"] for t in table} == {1, 2, 3, 4}
+    for t in table:
+        assert t["blocks_per_sm"] >= 1 and 1 <= t["warps_per_block"] <= 12
+        if t["ncand"] == 2:
+            assert min(t["us_per_eval"]) > 0
+    # a second call reuses the table: nothing more is tuned
+    ctx.stats(reset=True)
+    adg.dock(ctx, R, L, p)
+    assert ctx.stats()["tune_launches"] == 0
