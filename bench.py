@@ -201,6 +201,46 @@ def workload_config(nrun=None, nev=None) -> dict:
             "parallelism": "replicas"}
 
 
+TRIAGE_TRAIN, TRIAGE_STREAM = 1200, 2000
+
+
+def run_triage(ctx, R, ff):
+    """Learned triage against the plain path on a seeded stream: the network
+    is trained on full dockings of a training set, then the stream is docked
+    both ways (plain: full search of every ligand; triaged: early search of
+    every ligand, full search of the survivors).  Host-timed end to end."""
+    import numpy as np
+    from paper_2007_03678_gb300 import adg, synth as S, triage as T
+    cfg = T.TriageConfig()
+    LT = [adg.Ligand(ctx, ff, l) for l in S.make_batch(TRIAGE_TRAIN, seed=101, workers=0)]
+    LS = [adg.Ligand(ctx, ff, l) for l in S.make_batch(TRIAGE_STREAM, seed=202, workers=0)]
+    T.assign_stream_ids(LT, 1_000_000)
+    T.assign_stream_ids(LS, 2_000_000)
+    y_tr, x_tr, ev_tr, t_tr = T.dock_full(ctx, R, LT, cfg)
+    tri = T.Triage(ctx, cfg, seed=3)
+    t0 = time.perf_counter()
+    tri.fit(x_tr, y_tr)
+    t_fit = time.perf_counter() - t0
+    T.dock_early(ctx, R, LS[:8], cfg)  # warm-up of the early geometry
+    y_st, _, ev_plain, t_plain = T.dock_full(ctx, R, LS, cfg)
+    out = T.screen(ctx, R, LS, tri)
+    keep = out["keep"]
+    for l in LT + LS:
+        l.close()
+    return {"train_ligands": TRIAGE_TRAIN, "stream_ligands": TRIAGE_STREAM,
+            "search": {"nrun": cfg.nrun, "pop": cfg.pop, "generations": cfg.max_gen, "early_generations": cfg.early_gen,
+                       "local_search": "adadelta", "ls_max_iters": cfg.ls_max_iters},
+            "network": f"{cfg.nin}-256-256-1 ReLU, BF16 weights / FP32 accumulate, ensemble of {tri.folds}",
+            "ligands_per_s_plain": TRIAGE_STREAM / t_plain, "ligands_per_s_triaged": TRIAGE_STREAM / out["seconds"],
+            "speedup": t_plain / out["seconds"], "recall_top1pct": T.recall(y_st, keep, cfg.top_frac),
+            "survivors": float(keep.mean()), "evals_ratio": out["evals"] / ev_plain,
+            "survivors_match_plain": bool(np.array_equal(out["energy"][keep], y_st[keep])),
+            "seconds": {"train_docking": t_tr, "fit": t_fit, "plain": t_plain, "triaged": out["seconds"],
+                        "early": out["seconds_early"], "full_survivors": out["seconds_full"]},
+            "sample": "seeded stand-in for the 10^6-ligand stream: 1,200 training and 2,000 stream ligands "
+                      "(heavy atoms 10-60, torsions 0-15)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -210,6 +250,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
     ap.add_argument("--no-batching", action="store_true", help="skip the batching comparison (profiling runs)")
+    ap.add_argument("--no-triage", action="store_true", help="skip the learned-triage screen")
     ap.add_argument("--nrun", type=int, default=None, help="override the run count (small profiling cases)")
     ap.add_argument("--nev", type=int, default=None, help="override the evaluation budget (small profiling cases)")
     args = ap.parse_args()
@@ -352,6 +393,10 @@ def main():
                     "tuning": {"buckets": len(ctx.tuned()), "launches": tune_launches,
                                "first_call_s": round(t_tune, 3)}}
 
+    triage = None
+    if not args.no_triage:
+        triage = run_triage(ctx, R, ff)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cores = cpu_cores()
@@ -371,7 +416,7 @@ def main():
                 "config": workload_config(args.nrun, args.nev), "ligands_per_s": ligands_per_s,
                 "best_energy_median": float(np.median(results["best_energy"])),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "batching": batching,
-                "gpu_launches": st["kernel_launches"]}
+                "triage": triage, "gpu_launches": st["kernel_launches"]}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -216,6 +216,22 @@ typedef struct {
 } adg_ligand_stats;
 int adg_ligand_info(const adg_ligand* lig, adg_ligand_stats* out);
 
+/* Fixed-length description of a ligand, the input of the triage network
+ * (adg_mlp_*); no counterpart in the paper.  out: host [ADG_NDESC] floats =
+ * atoms, torsions, intramolecular pairs, atom counts of the 7 types (C, A, N,
+ * NA, OA, HD, S), sum |q|, sum q^2, radius of gyration and largest distance
+ * from the centroid of the input conformation (A), rigid fragments, mean
+ * moving-set size per torsion. */
+#define ADG_NDESC 16
+int adg_ligand_descriptors(const adg_ligand* lig, float* out);
+
+/* Random-stream identity of a ligand.  Every Philox counter of a dock call
+ * carries a ligand word: by default p->lig_id + the ligand's index in the
+ * call; after adg_ligand_set_stream_id(lig, id) with 0 <= id < 2^32, `id`
+ * in every call (so a ligand docked alone, in any batch or in any subset of
+ * a batch gives the same runs); id = -1 restores the default. */
+int adg_ligand_set_stream_id(adg_ligand* lig, int64_t id);
+
 enum { ADG_GRAD_NONE = 0, ADG_GRAD_GENES = 1, ADG_GRAD_TANGENT = 2 };
 
 /* Energy (and gradient) of npose genotypes of one ligand (Sec. 1: the
@@ -244,6 +260,15 @@ int adg_pose(adg_ctx* ctx, const adg_ligand* lig, const float* genes, int npose,
  * Returns when the results are in `out`. */
 int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig,
              const adg_search_params* p, adg_result* out, adg_dock_trace* trace);
+
+/* adg_dock that also reports each run's best-energy trace: best_trace, host,
+ * caller-allocated [nlig][p->nrun][ntrace]; entry k is the lowest energy of
+ * the run's population after generation k+1 (with elitism, the best energy
+ * found so far).  Entries past the run's last generation repeat its final
+ * best energy.  The early part of this trace (the mechanism behind the
+ * paper's autostop, Sec. 1.1) feeds the triage network. */
+int adg_dock_traced(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig,
+                    const adg_search_params* p, adg_result* out, float* best_trace, int ntrace);
 
 /* Launch accounting of a context, for measurement.  Counts every kernel the
  * library launched on the context since the last reset; when timing is on
@@ -301,6 +326,47 @@ typedef struct {
 } adg_tuned_shape;
 /* Copy up to `cap` entries of the tuning table to out; *n = entries held. */
 int adg_ctx_tuned(adg_ctx* ctx, adg_tuned_shape* out, int cap, int* n);
+
+/* Triage network (no counterpart in the paper, which has no learned part).
+ * A three-layer perceptron nin -> 256 -> 256 -> 1 with ReLU: BF16 weights,
+ * FP32 accumulation on the tensor cores, FP32 master weights trained by
+ * Adam (beta 0.9 / 0.999, eps 1e-8) on the mean squared error of the
+ * normalised target.  It predicts a ligand's final best docking energy from
+ * adg_ligand_descriptors and the early part of adg_dock_traced's trace.
+ * Parameters are packed as W1 [256][nin], b1 [256], W2 [256][256], b2 [256],
+ * w3 [256], b3 [1] (adg_mlp_nparams floats).  Inputs are normalised inside
+ * the network: x_hat = (x - mu) / sigma; predictions are returned as
+ * y * sigma_y + mu_y.  Device pointers, asynchronous on the context's stream
+ * unless stated. */
+#define ADG_MLP_HIDDEN 256
+#define ADG_MLP_NIN_MAX 32
+typedef struct adg_mlp adg_mlp;
+/* Number of packed parameters for nin inputs (ADG_EINVAL outside 1..32). */
+int adg_mlp_nparams(int nin);
+/* He-uniform weights from `seed`, zero biases, mu = 0, sigma = 1.  Synchronous. */
+int adg_mlp_create(adg_ctx* ctx, int nin, uint64_t seed, adg_mlp** out);
+int adg_mlp_destroy(adg_mlp* mlp);
+/* FP32 master parameters to / from host memory (synchronous); setting them
+ * also clears the Adam state. */
+int adg_mlp_get_params(adg_ctx* ctx, const adg_mlp* mlp, float* out);
+int adg_mlp_set_params(adg_ctx* ctx, adg_mlp* mlp, const float* in);
+/* Normalisation (host arrays of nin floats; every sigma > 0). */
+int adg_mlp_set_norm(adg_mlp* mlp, const float* mu, const float* sigma, float mu_y, float sigma_y);
+/* y[b] = prediction for x[b] (x: [B][nin], y: [B]). */
+int adg_mlp_forward(adg_ctx* ctx, const adg_mlp* mlp, const float* x, int B, float* y);
+/* Gradient of the batch loss (1/B) sum_b (y_b - (t_b - mu_y)/sigma_y)^2 with
+ * respect to the packed parameters into grad [nparams], and the loss into
+ * *loss (nullable); idx (nullable) selects rows of x and t.  No update. */
+int adg_mlp_grad(adg_ctx* ctx, adg_mlp* mlp, const float* x, const float* t, const int* idx, int B, float* grad,
+                 float* loss);
+/* The same gradient followed by one Adam step with learning rate lr. */
+int adg_mlp_train_step(adg_ctx* ctx, adg_mlp* mlp, const float* x, const float* t, const int* idx, int B, float lr,
+                       float* loss);
+/* `epochs` passes over n rows in minibatches of `batch`, rows shuffled each
+ * epoch (seeded), one Adam step per minibatch.  epoch_loss: host [epochs]
+ * (nullable), the mean loss seen during each epoch.  Synchronous. */
+int adg_mlp_fit(adg_ctx* ctx, adg_mlp* mlp, const float* x, const float* t, int n, int batch, int epochs, float lr,
+                uint64_t seed, float* epoch_loss);
 
 /* Docking without allocation.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate memory -- a host application whose

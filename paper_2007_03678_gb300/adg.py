@@ -28,6 +28,7 @@ ADG_OK = 0
 GRAD_NONE, GRAD_GENES, GRAD_TANGENT = 0, 1, 2
 LS_NONE, LS_SOLIS_WETS, LS_ADADELTA = 0, 1, 2
 GEO_HEURISTIC, GEO_TUNED = 0, 1
+NDESC = 16
 
 
 class AdgError(RuntimeError):
@@ -102,7 +103,10 @@ class adg_ligand_stats(C.Structure):
 EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_ctx_destroy", "adg_sync",
            "adg_ctx_last_error", "adg_maps_build", "adg_receptor_create", "adg_receptor_destroy", "adg_ligand_create",
            "adg_ligand_destroy", "adg_ligand_info", "adg_score", "adg_pose", "adg_dock", "adg_philox",
-           "adg_ctx_set_timing", "adg_ctx_stats", "adg_dock_noalloc", "adg_ctx_set_geometry", "adg_ctx_tuned")
+           "adg_ctx_set_timing", "adg_ctx_stats", "adg_dock_noalloc", "adg_ctx_set_geometry", "adg_ctx_tuned",
+           "adg_dock_traced", "adg_ligand_descriptors", "adg_mlp_nparams", "adg_mlp_create", "adg_mlp_destroy",
+           "adg_mlp_get_params", "adg_mlp_set_params", "adg_mlp_set_norm", "adg_mlp_forward", "adg_mlp_grad",
+           "adg_mlp_train_step", "adg_mlp_fit", "adg_ligand_set_stream_id")
 
 _lib = None
 
@@ -142,6 +146,21 @@ def load(path: str | None = None):
         L.adg_dock_noalloc.argtypes = [_vp, _vp, C.POINTER(adg_search_params), C.POINTER(adg_result), _vp]
         L.adg_ctx_stats.argtypes = [_vp, C.POINTER(adg_stats), _i]
         L.adg_ctx_set_geometry.argtypes = [_vp, _i]
+        L.adg_dock_traced.argtypes = [_vp, _vp, C.POINTER(_vp), _i, C.POINTER(adg_search_params),
+                                      C.POINTER(adg_result), C.POINTER(C.c_float), _i]
+        L.adg_ligand_descriptors.argtypes = [_vp, C.POINTER(C.c_float)]
+        L.adg_ligand_set_stream_id.argtypes = [_vp, C.c_int64]
+        _fp = C.POINTER(C.c_float)
+        L.adg_mlp_nparams.argtypes = [_i]
+        L.adg_mlp_create.argtypes = [_vp, _i, C.c_uint64, C.POINTER(_vp)]
+        L.adg_mlp_destroy.argtypes = [_vp]
+        L.adg_mlp_get_params.argtypes = [_vp, _vp, _fp]
+        L.adg_mlp_set_params.argtypes = [_vp, _vp, _fp]
+        L.adg_mlp_set_norm.argtypes = [_vp, _fp, _fp, C.c_float, C.c_float]
+        L.adg_mlp_forward.argtypes = [_vp, _vp, _vp, _i, _vp]
+        L.adg_mlp_grad.argtypes = [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp]
+        L.adg_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _i, C.c_float, _vp]
+        L.adg_mlp_fit.argtypes = [_vp, _vp, _vp, _vp, _i, _i, _i, C.c_float, C.c_uint64, _fp]
         L.adg_ctx_tuned.argtypes = [_vp, C.POINTER(adg_tuned_shape), _i, C.POINTER(C.c_int)]
         _lib = L
     return _lib
@@ -208,17 +227,34 @@ def search_params(**kw) -> adg_search_params:
 
 # ---------------------------------------------------------------- objects
 class Context:
-    """adg_ctx_create / adg_ctx_destroy.  `stream`: a torch.cuda.Stream (or
-    None for a library-owned stream)."""
+    """adg_ctx_create / adg_ctx_destroy on a torch.cuda.Stream (a new one when
+    `stream` is None).  Calls that take device tensors order the context's
+    stream after the caller's current stream on entry, and the current stream
+    after the context's stream on exit, so tensors are safe to use on either
+    side without a host synchronisation."""
 
     def __init__(self, device: int = 0, stream=None):
+        import torch
         L = load()
+        if stream is None:
+            stream = torch.cuda.Stream(device=device)
         h = C.c_void_p()
-        sp = None if stream is None else C.c_void_p(stream.cuda_stream)
-        _check(L.adg_ctx_create(C.byref(h), device, sp), "adg_ctx_create")
+        _check(L.adg_ctx_create(C.byref(h), device, C.c_void_p(stream.cuda_stream)), "adg_ctx_create")
         self.handle = h
         self.device = device
         self.stream = stream
+
+    def _enter(self):
+        import torch
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            self.stream.wait_stream(cur)
+
+    def _leave(self):
+        import torch
+        cur = torch.cuda.current_stream(self.device)
+        if cur != self.stream:
+            cur.wait_stream(self.stream)
 
     def sync(self):
         _check(load().adg_sync(self.handle), "adg_sync", self)
@@ -269,8 +305,10 @@ def maps_build(ctx: Context, ff: dict, grid, rec: "synth.Receptor"):
     typ = np.ascontiguousarray(rec.type, np.int32)
     q = np.ascontiguousarray(rec.charge, np.float32)
     ffs, gs = forcefield_struct(ff), grid_struct(grid)
+    ctx._enter()
     _check(load().adg_maps_build(ctx.handle, C.byref(ffs), C.byref(gs), len(typ), xyz.ctypes.data, typ.ctypes.data,
                                  q.ctypes.data, _ptr(out)), "adg_maps_build", ctx)
+    ctx._leave()
     return out
 
 
@@ -286,6 +324,7 @@ class Receptor:
             m = np.ascontiguousarray(maps, np.float32)
             rc = load().adg_receptor_create(ctx.handle, C.byref(gs), m.ctypes.data, 0, C.byref(h))
         else:
+            ctx._enter()
             rc = load().adg_receptor_create(ctx.handle, C.byref(gs), _ptr(maps), 1, C.byref(h))
         _check(rc, "adg_receptor_create", ctx)
         self.handle = h
@@ -330,6 +369,19 @@ class Ligand:
         _check(load().adg_ligand_info(h, C.byref(st)), "adg_ligand_info", ctx)
         self.natoms, self.ntors, self.npairs = st.natoms, st.ntors, st.npairs
         self.sum_moving, self.device_bytes = st.sum_moving, st.device_bytes
+        self.stream_id = None
+
+    def set_stream_id(self, sid: int):
+        """adg_ligand_set_stream_id: fixed Philox ligand word (-1: index-based default)."""
+        _check(load().adg_ligand_set_stream_id(self.handle, int(sid)), "adg_ligand_set_stream_id")
+        self.stream_id = None if sid < 0 else int(sid)
+
+    def descriptors(self) -> np.ndarray:
+        """adg_ligand_descriptors: [NDESC] float32."""
+        out = np.zeros(NDESC, np.float32)
+        _check(load().adg_ligand_descriptors(self.handle, out.ctypes.data_as(C.POINTER(C.c_float))),
+               "adg_ligand_descriptors")
+        return out
 
     def close(self):
         if self.handle:
@@ -353,8 +405,10 @@ def score(ctx: Context, rec: Receptor, lig: Ligand, genes, grad_kind: int = GRAD
     if grad_kind != GRAD_NONE and grad is None:
         width = 7 + lig.ntors if grad_kind == GRAD_GENES else 6 + lig.ntors
         grad = torch.empty((n, width), dtype=torch.float32, device=genes.device)
+    ctx._enter()
     _check(load().adg_score(ctx.handle, rec.handle, lig.handle, _ptr(genes), n, _ptr(energy),
                             _ptr(grad) if grad is not None else None, grad_kind), "adg_score", ctx)
+    ctx._leave()
     return energy, grad
 
 
@@ -362,7 +416,9 @@ def pose(ctx: Context, lig: Ligand, genes):
     import torch
     n = genes.shape[0]
     xyz = torch.empty((n, lig.natoms, 3), dtype=torch.float32, device=genes.device)
+    ctx._enter()
     _check(load().adg_pose(ctx.handle, lig.handle, _ptr(genes), n, _ptr(xyz)), "adg_pose", ctx)
+    ctx._leave()
     return xyz
 
 
@@ -370,14 +426,27 @@ def philox(ctx: Context, ctr, key: int):
     """ctr: uint32-compatible int32 CUDA tensor [n, 4] -> same shape output."""
     import torch
     out = torch.empty_like(ctr)
+    ctx._enter()
     _check(load().adg_philox(ctx.handle, _ptr(ctr), ctr.shape[0], key, _ptr(out)), "adg_philox", ctx)
+    ctx._leave()
     return out
 
 
-def dock(ctx: Context, rec: Receptor, ligs, params: adg_search_params, trace_ngen: int = 0):
-    """adg_dock.  Returns a list (per ligand) of dicts with arrays over runs:
-    best_energy [nrun], genes [nrun, 7+T], xyz [nrun, natoms, 3], evals, generations;
-    plus a trace dict when trace_ngen > 0 (one ligand only)."""
+def _result_dtype():
+    f = adg_result
+    return np.dtype({"names": ["best_energy", "generations", "evals", "genes", "xyz"],
+                     "formats": [np.float32, np.int32, np.int64, (np.float32, MAX_GENES), (np.float32, 3 * MAX_ATOMS)],
+                     "offsets": [f.best_energy.offset, f.generations.offset, f.evals.offset, f.genes.offset,
+                                 f.xyz.offset],
+                     "itemsize": C.sizeof(adg_result)})
+
+
+def dock(ctx: Context, rec: Receptor, ligs, params: adg_search_params, trace_ngen: int = 0, best_trace: int = 0):
+    """adg_dock (adg_dock_traced when best_trace > 0).  Returns a list (per
+    ligand) of dicts with arrays over runs: best_energy [nrun], genes
+    [nrun, 7+T], xyz [nrun, natoms, 3], evals, generations, and best_trace
+    [nrun, best_trace] when asked; plus a trace dict when trace_ngen > 0 (one
+    ligand only)."""
     if isinstance(ligs, Ligand):
         ligs = [ligs]
     n = len(ligs)
@@ -386,6 +455,8 @@ def dock(ctx: Context, rec: Receptor, ligs, params: adg_search_params, trace_nge
     hs = (C.c_void_p * n)(*[l.handle.value for l in ligs])
     tr = None
     trace = None
+    if trace_ngen > 0 and best_trace > 0:
+        raise ValueError("trace_ngen and best_trace are exclusive")
     if trace_ngen > 0:
         G = 7 + ligs[0].ntors
         dec = np.zeros((nrun, trace_ngen, pop, TRACE_WIDTH), np.int32)
@@ -401,19 +472,26 @@ def dock(ctx: Context, rec: Receptor, ligs, params: adg_search_params, trace_nge
         tr.init_genes = ig.ctypes.data_as(C.POINTER(C.c_float))
         tr.init_energies = ie.ctypes.data_as(C.POINTER(C.c_float))
         trace = dict(decisions=dec, genes=tg, energies=te, init_genes=ig, init_energies=ie)
-    _check(load().adg_dock(ctx.handle, rec.handle, hs, n, C.byref(params), res,
-                           C.byref(tr) if tr is not None else None), "adg_dock", ctx)
-    raw = np.frombuffer(res, dtype=np.uint8).reshape(n * nrun, C.sizeof(adg_result))
+    bt = None
+    if best_trace > 0:
+        bt = np.zeros((n, nrun, best_trace), np.float32)
+        _check(load().adg_dock_traced(ctx.handle, rec.handle, hs, n, C.byref(params), res,
+                                      bt.ctypes.data_as(C.POINTER(C.c_float)), int(best_trace)),
+               "adg_dock_traced", ctx)
+    else:
+        _check(load().adg_dock(ctx.handle, rec.handle, hs, n, C.byref(params), res,
+                               C.byref(tr) if tr is not None else None), "adg_dock", ctx)
+    rec_arr = np.frombuffer(res, dtype=_result_dtype()).reshape(n, nrun)
     out = []
     for li, lig in enumerate(ligs):
         G, N = 7 + lig.ntors, lig.natoms
-        rr = [res[li * nrun + r] for r in range(nrun)]
-        out.append(dict(best_energy=np.array([r.best_energy for r in rr], np.float32),
-                        genes=np.array([r.genes[:G] for r in rr], np.float32),
-                        xyz=np.array([r.xyz[:3 * N] for r in rr], np.float32).reshape(nrun, N, 3),
-                        evals=np.array([r.evals for r in rr], np.int64),
-                        generations=np.array([r.generations for r in rr], np.int32)))
-    del raw
+        r = rec_arr[li]
+        d = dict(best_energy=r["best_energy"].copy(), genes=r["genes"][:, :G].copy(),
+                 xyz=r["xyz"][:, :3 * N].reshape(nrun, N, 3).copy(), evals=r["evals"].copy(),
+                 generations=r["generations"].copy())
+        if bt is not None:
+            d["best_trace"] = bt[li]
+        out.append(d)
     return (out, trace) if trace_ngen > 0 else out
 
 
@@ -431,3 +509,92 @@ def dock_noalloc(rec: Receptor, lig: Ligand, params: adg_search_params, stream=N
                 xyz=np.array([r.xyz[:3 * N] for r in res], np.float32).reshape(nrun, N, 3),
                 evals=np.array([r.evals for r in res], np.int64),
                 generations=np.array([r.generations for r in res], np.int32))
+
+
+class MLP:
+    """The triage network (adg_mlp_*): nin -> 256 -> 256 -> 1, ReLU, BF16
+    weights with FP32 accumulation, trained by Adam.  Tensors are CUDA
+    float32 (PyTorch supplies the memory; every step runs in libadg.so)."""
+
+    HIDDEN = 256
+    NIN_MAX = 32
+
+    def __init__(self, ctx: Context, nin: int, seed: int = 0):
+        self.ctx = ctx
+        self.nin = int(nin)
+        h = C.c_void_p()
+        _check(load().adg_mlp_create(ctx.handle, self.nin, int(seed), C.byref(h)), "adg_mlp_create", ctx)
+        self.handle = h
+        self.nparams = load().adg_mlp_nparams(self.nin)
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.nparams, np.float32)
+        _check(load().adg_mlp_get_params(self.ctx.handle, self.handle, out.ctypes.data_as(C.POINTER(C.c_float))),
+               "adg_mlp_get_params", self.ctx)
+        return out
+
+    def set_params(self, theta):
+        th = np.ascontiguousarray(theta, np.float32)
+        if th.size != self.nparams:
+            raise ValueError("expected %d parameters" % self.nparams)
+        _check(load().adg_mlp_set_params(self.ctx.handle, self.handle, th.ctypes.data_as(C.POINTER(C.c_float))),
+               "adg_mlp_set_params", self.ctx)
+
+    def set_norm(self, mu, sigma, mu_y: float, sigma_y: float):
+        m = np.ascontiguousarray(mu, np.float32)
+        sg = np.ascontiguousarray(sigma, np.float32)
+        _check(load().adg_mlp_set_norm(self.handle, m.ctypes.data_as(C.POINTER(C.c_float)),
+                                       sg.ctypes.data_as(C.POINTER(C.c_float)), float(mu_y), float(sigma_y)),
+               "adg_mlp_set_norm")
+
+    def forward(self, x):
+        import torch
+        y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+        self.ctx._enter()
+        _check(load().adg_mlp_forward(self.ctx.handle, self.handle, _ptr(x), x.shape[0], _ptr(y)),
+               "adg_mlp_forward", self.ctx)
+        self.ctx._leave()
+        return y
+
+    def grad(self, x, t, idx=None):
+        """(gradient [nparams] CUDA tensor, loss CUDA scalar) of the batch loss."""
+        import torch
+        g = torch.empty(self.nparams, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        n = x.shape[0] if idx is None else idx.shape[0]
+        self.ctx._enter()
+        _check(load().adg_mlp_grad(self.ctx.handle, self.handle, _ptr(x), _ptr(t),
+                                   _ptr(idx) if idx is not None else None, n, _ptr(g), _ptr(loss)),
+               "adg_mlp_grad", self.ctx)
+        self.ctx._leave()
+        return g, loss
+
+    def train_step(self, x, t, lr: float, idx=None):
+        import torch
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        n = x.shape[0] if idx is None else idx.shape[0]
+        self.ctx._enter()
+        _check(load().adg_mlp_train_step(self.ctx.handle, self.handle, _ptr(x), _ptr(t),
+                                         _ptr(idx) if idx is not None else None, n, float(lr), _ptr(loss)),
+               "adg_mlp_train_step", self.ctx)
+        self.ctx._leave()
+        return loss
+
+    def fit(self, x, t, batch: int, epochs: int, lr: float, seed: int = 0) -> np.ndarray:
+        out = np.zeros(max(epochs, 1), np.float32)
+        self.ctx._enter()
+        _check(load().adg_mlp_fit(self.ctx.handle, self.handle, _ptr(x), _ptr(t), x.shape[0], int(batch), int(epochs),
+                                  float(lr), int(seed), out.ctypes.data_as(C.POINTER(C.c_float))),
+               "adg_mlp_fit", self.ctx)
+        return out[:epochs]
+
+    def close(self):
+        if self.handle:
+            load().adg_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

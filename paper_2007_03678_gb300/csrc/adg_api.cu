@@ -23,26 +23,6 @@ namespace adg {
 void pair_coefs(const adg_forcefield& ff, int ti, int tj, float* c12, float* c6, float* c10);
 }
 
-struct adg_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    bool own_stream = false;
-    std::string last_error;
-    void* arena = nullptr;
-    size_t arena_bytes = 0;
-    int* host_active = nullptr;  // pinned
-    // measurement
-    bool timing = false;
-    adg_stats stats{};
-    std::vector<cudaEvent_t> ev_free;                       // reusable events
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
-    std::vector<cudaStream_t> class_streams;  // extra streams for concurrent ligand groups
-    // launch geometry of adg_dock
-    int geo_mode = ADG_GEO_TUNED;
-    std::map<uint32_t, adg_tuned_shape> tuned;  // by shape bucket
-    void* tune_buf = nullptr;                    // probe poses and energies
-    size_t tune_bytes = 0;
-};
 
 namespace {
 
@@ -667,8 +647,55 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     L->apl = apl_for(N);
     L->bytes = bytes;
     for (int k = 0; k < T; ++k) L->sum_moving += shi[k] - slo[k];
+    // descriptors of the ligand for the triage network (see adg_ligand_descriptors)
+    {
+        float* D = L->desc;
+        for (int q = 0; q < ADG_NDESC; ++q) D[q] = 0.f;
+        D[0] = (float)N;
+        D[1] = (float)T;
+        D[2] = (float)P;
+        double cx = 0, cy = 0, cz = 0, sq = 0, sq2 = 0;
+        for (int i = 0; i < N; ++i) {
+            D[3 + d->type[i]] += 1.f;
+            cx += d->xyz[3 * i];
+            cy += d->xyz[3 * i + 1];
+            cz += d->xyz[3 * i + 2];
+            sq += fabs((double)d->charge[i]);
+            sq2 += (double)d->charge[i] * d->charge[i];
+        }
+        cx /= N;
+        cy /= N;
+        cz /= N;
+        double rg = 0, rmax = 0;
+        for (int i = 0; i < N; ++i) {
+            const double dx = d->xyz[3 * i] - cx, dy = d->xyz[3 * i + 1] - cy, dz = d->xyz[3 * i + 2] - cz;
+            const double r2 = dx * dx + dy * dy + dz * dz;
+            rg += r2;
+            rmax = std::max(rmax, sqrt(r2));
+        }
+        D[10] = (float)sq;
+        D[11] = (float)sq2;
+        D[12] = (float)sqrt(rg / N);
+        D[13] = (float)rmax;
+        D[14] = (float)nf;
+        D[15] = T > 0 ? (float)L->sum_moving / (float)T : 0.f;
+    }
     ctx->stats.h2d_bytes += (int64_t)bytes;
     *out = L;
+    return ADG_OK;
+}
+
+int adg_ligand_set_stream_id(adg_ligand* lig, int64_t id)
+{
+    if (!lig || id < -1 || id > (int64_t)0xffffffffu) return ADG_EINVAL;
+    lig->stream_id = id;
+    return ADG_OK;
+}
+
+int adg_ligand_descriptors(const adg_ligand* lig, float* out)
+{
+    if (!lig || !out) return ADG_EINVAL;
+    for (int q = 0; q < ADG_NDESC; ++q) out[q] = lig->desc[q];
     return ADG_OK;
 }
 
@@ -970,6 +997,8 @@ cudaError_t build_class_graph(adg_ctx* ctx, ClassRun& c, const MapsDev& M, const
     cudaMemsetAsync(c.D.evals, 0, sizeof(unsigned long long) * 2 * nruns, cs);
     cudaMemsetAsync(c.D.gen_done, 0, sizeof(int) * nruns, cs);
     cudaMemsetAsync(c.D.stopped, 0, sizeof(int) * nruns, cs);
+    if (c.D.best_trace)  // all-ones words: NaN until a generation writes the entry
+        cudaMemsetAsync(c.D.best_trace, 0xff, sizeof(float) * nruns * c.D.best_trace_len, cs);
     cudaMemsetAsync(c.d_active, 0, sizeof(int), cs);
     cudaMemsetAsync(c.d_gen, 0, sizeof(int), cs);  // generations completed by the loop
     launch_dock_init(cs, M, S, c.D, c.geo);
@@ -1020,10 +1049,13 @@ cudaError_t build_class_graph(adg_ctx* ctx, ClassRun& c, const MapsDev& M, const
 
 }  // namespace
 
-int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig,
-             const adg_search_params* p, adg_result* out, adg_dock_trace* trace)
+namespace {
+
+int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig,
+              const adg_search_params* p, adg_result* out, adg_dock_trace* trace, float* best_trace, int ntrace)
 {
     if (!ctx || !rec || !ligs || nlig <= 0 || !p || !out) return ADG_EINVAL;
+    if (ntrace < 0 || (ntrace > 0 && !best_trace)) return ADG_EINVAL;
     if (p->nrun <= 0 || p->nrun > 65535 || p->pop_size < 2 || p->pop_size > 65535 || p->nev < 0 || p->max_gen < 0 ||
         p->ls_max_iters < 0 || p->elitism < 0 || p->elitism > 1 || p->ls_method < 0 || p->ls_method > 2)
         return ADG_EINVAL;
@@ -1047,7 +1079,7 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         return o;
     };
     struct Offs {
-        size_t g0, g1, e0, e1, ev, gd, hist, stop, act, gen, lr, id, res;
+        size_t g0, g1, e0, e1, ev, gd, hist, stop, act, gen, lr, id, res, bt;
     };
     std::vector<Offs> offs(cls.size());
     for (size_t k = 0; k < cls.size(); ++k) {
@@ -1066,6 +1098,7 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         o.lr = take(sizeof(LigandRef) * cls[k].ligs.size());
         o.id = take(sizeof(uint32_t) * cls[k].ligs.size());
         o.res = take(sizeof(ResultDev) * nruns);
+        o.bt = take(sizeof(float) * nruns * ntrace);
     }
     const size_t o_td = take(sizeof(int) * ADG_TRACE_WIDTH * tr_slots);
     const size_t o_tg = take(sizeof(float) * kGeneStride * tr_slots);
@@ -1113,6 +1146,8 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         D.gen_done = (int*)(A + o.gd);
         D.best_hist = (float*)(A + o.hist);
         D.stopped = (int*)(A + o.stop);
+        D.best_trace = ntrace > 0 ? (float*)(A + o.bt) : nullptr;
+        D.best_trace_len = ntrace;
         D.trace_ngen = tr_ngen;
         D.tr_dec = (int*)(A + o_td);
         D.tr_genes = (float*)(A + o_tg);
@@ -1122,7 +1157,7 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         c.d_res = (ResultDev*)(A + o.res);
         for (int i : c.ligs) {
             lr[k].push_back(ligs[i]->ref);
-            ids[k].push_back(p->lig_id + (uint32_t)i);
+            ids[k].push_back(ligs[i]->stream_id >= 0 ? (uint32_t)ligs[i]->stream_id : p->lig_id + (uint32_t)i);
         }
         CK(ctx, cudaMemcpyAsync(A + o.lr, lr[k].data(), sizeof(LigandRef) * c.ligs.size(), cudaMemcpyHostToDevice,
                                 c.stream));
@@ -1139,6 +1174,7 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         ctx->stats.kernel_launches += 2;  // initial population and final poses; the loop adds 3 per generation
     }
     std::vector<std::vector<ResultDev>> res(cls.size());
+    std::vector<std::vector<float>> btr(cls.size());
     std::vector<int> gens_dev(cls.size(), 0);
     for (size_t k = 0; k < cls.size(); ++k) {
         ClassRun& c = cls[k];
@@ -1147,6 +1183,12 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         CK(ctx, cudaMemcpyAsync(res[k].data(), c.d_res, sizeof(ResultDev) * nruns, cudaMemcpyDeviceToHost, c.stream));
         CK(ctx, cudaMemcpyAsync(&gens_dev[k], c.d_gen, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
         ctx->stats.d2h_bytes += (int64_t)(sizeof(ResultDev) * nruns + sizeof(int));
+        if (ntrace > 0) {
+            btr[k].resize((size_t)nruns * ntrace);
+            CK(ctx, cudaMemcpyAsync(btr[k].data(), c.D.best_trace, sizeof(float) * nruns * ntrace,
+                                    cudaMemcpyDeviceToHost, c.stream));
+            ctx->stats.d2h_bytes += (int64_t)(sizeof(float) * nruns * ntrace);
+        }
     }
     std::vector<int> tdec;
     std::vector<float> tg, te, init_g, init_e;
@@ -1211,6 +1253,13 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
                 o.evals = sr.evals;
                 for (int q = 0; q < G; ++q) o.genes[q] = sr.genes[q];
                 for (int q = 0; q < 3 * N; ++q) o.xyz[q] = sr.xyz[q];
+                if (ntrace > 0) {
+                    // generations after the run's last repeat its final best energy
+                    const float* src = btr[k].data() + ((long)li * p->nrun + run) * ntrace;
+                    float* dst = best_trace + ((long)lig * p->nrun + run) * ntrace;
+                    for (int q = 0; q < ntrace; ++q)
+                        dst[q] = q < sr.generations ? src[q] : (q > 0 ? dst[q - 1] : sr.best_energy);
+                }
             }
         }
     }
@@ -1229,6 +1278,21 @@ int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* lig
         if (trace->init_energies) memcpy(trace->init_energies, init_e.data(), sizeof(float) * nind);
     }
     return ADG_OK;
+}
+
+}  // namespace
+
+int adg_dock(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig,
+             const adg_search_params* p, adg_result* out, adg_dock_trace* trace)
+{
+    return dock_impl(ctx, rec, ligs, nlig, p, out, trace, nullptr, 0);
+}
+
+int adg_dock_traced(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig,
+                    const adg_search_params* p, adg_result* out, float* best_trace, int ntrace)
+{
+    if (ntrace <= 0 || !best_trace) return ADG_EINVAL;
+    return dock_impl(ctx, rec, ligs, nlig, p, out, nullptr, best_trace, ntrace);
 }
 
 }  // extern "C"

@@ -5,6 +5,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <map>
+#include <string>
+#include <utility>
+#include <vector>
+
 #include "adg.h"
 
 namespace adg {
@@ -112,7 +117,9 @@ struct DockDev {
     int* gen_done;             // [nlig*nrun]
     float* best_hist;          // [nlig*nrun][10] best energy of the last 10 generations (ring)
     int* stopped;              // [nlig*nrun] autostop fired
-    // optional trace (one ligand): decisions [nrun][ngen][pop][8], genes [nrun][ngen][pop][kGeneStride], e
+    float* best_trace;         // optional [nlig*nrun][best_trace_len]: best energy after generations 1..len
+    int best_trace_len;
+    // optional trace (one ligand): decisions [nrun][ngen][pop][12], genes [nrun][ngen][pop][kGeneStride], e
     int trace_ngen;
     int* tr_dec;
     float* tr_genes;
@@ -191,4 +198,28 @@ struct adg_ligand {
     adg::LigandRef ref{};
     int natoms = 0, ntors = 0, npairs = 0, apl = 1, sum_moving = 0, nslots = 0;
     size_t bytes = 0;
+    float desc[ADG_NDESC] = {};  // adg_ligand_descriptors
+    int64_t stream_id = -1;      // adg_ligand_set_stream_id
+};
+
+// The context: device, stream, reusable device memory and counters.
+struct adg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::string last_error;
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    int* host_active = nullptr;  // pinned
+    // measurement
+    bool timing = false;
+    adg_stats stats{};
+    std::vector<cudaEvent_t> ev_free;                       // reusable events
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
+    std::vector<cudaStream_t> class_streams;  // extra streams for concurrent ligand groups
+    // launch geometry of adg_dock
+    int geo_mode = ADG_GEO_TUNED;
+    std::map<uint32_t, adg_tuned_shape> tuned;  // by shape bucket
+    void* tune_buf = nullptr;                    // probe poses and energies
+    size_t tune_bytes = 0;
 };

@@ -1049,6 +1049,7 @@ __global__ void k_dock_bookkeep(SearchDev S, DockDev Dk, int gen_arg, const int*
         for (int i = 1; i < S.pop; ++i) b = fminf(b, Pe[i]);
         float* h = Dk.best_hist + 10 * r;
         h[(gen - 1) % 10] = b;
+        if (gen <= Dk.best_trace_len) Dk.best_trace[(long)r * Dk.best_trace_len + gen - 1] = b;
         if (S.autostop && gen >= 10) {
             float m = 0.f, v = 0.f;
             for (int k = 0; k < 10; ++k) m += h[k];

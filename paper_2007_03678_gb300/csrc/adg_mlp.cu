@@ -1,0 +1,786 @@
+// adg_mlp.cu -- the triage network of the screening pipeline: a three-layer
+// perceptron nin -> 256 -> 256 -> 1 with ReLU, BF16 weights and FP32
+// accumulation on the tensor cores (warp-level mma m16n8k16, BF16 inputs,
+// FP32 accumulators), trained on the GPU by these kernels (forward, backward,
+// Adam).  The paper has no learned part; the network predicts a ligand's
+// final best docking energy from its descriptors and the first generations
+// of its best-energy trace, so that ligands predicted hopeless can skip the
+// full search.
+//
+// Numerics (what is stored in BF16, what stays FP32):
+//   x_hat = (x - mu) / sigma                 FP32, stored BF16 (operand)
+//   h1 = relu(W1 x_hat + b1)                 FP32 accumulate, stored BF16 (operand)
+//   h2 = relu(W2 h1 + b2)                    FP32
+//   y  = w3 . h2 + b3                        FP32 (w3 BF16)
+//   dh2 = dy w3 [h2 > 0]                     FP32 (bias gradient), BF16 as operand
+//   dh1 = (dh2 W2) [h1 > 0]                  FP32 (bias gradient), BF16 as operand
+//   dW2 = dh2^T h1, dW1 = dh1^T x_hat        FP32 accumulate over the batch
+// Master weights and Adam moments are FP32; the BF16 copies are rewritten
+// after every update (round to nearest even).
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "adg_internal.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+constexpr int H = ADG_MLP_HIDDEN;   // 256
+constexpr int KIN = ADG_MLP_NIN_MAX;  // 32: input width padded for the k = 16 steps
+constexpr int TR = 32;              // rows per tile of the activation kernel
+constexpr int LW2 = H + 8;          // shared-memory row strides (bf16 elements)
+constexpr int LW1 = KIN + 8;
+constexpr int LX = KIN + 8;
+constexpr int LH = H + 8;
+constexpr int LF = H + 4;           // float rows
+constexpr size_t kActSmem = sizeof(bf16) * ((size_t)H * LW2 + (size_t)H * LW1 + TR * LX + 2 * TR * LH) +
+                            sizeof(float) * ((size_t)TR * LF + TR);
+
+struct Norm {
+    float mu[KIN], sigma[KIN];
+    float mu_y, sigma_y;
+};
+
+struct Offs {
+    int w1, b1, w2, b2, w3, b3, n;
+};
+
+Offs offsets(int nin)
+{
+    Offs o;
+    o.w1 = 0;
+    o.b1 = H * nin;
+    o.w2 = o.b1 + H;
+    o.b2 = o.w2 + H * H;
+    o.w3 = o.b2 + H;
+    o.b3 = o.w3 + H;
+    o.n = o.b3 + 1;
+    return o;
+}
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi)
+{
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// acc (16x8, FP32) += A (16x16) * B (16x8), operands BF16 in shared memory.
+// AK: A(m,k) = a[m*lda + k], else a[k*lda + m].
+// BK: B(k,n) = b[n*ldb + k], else b[k*ldb + n].
+// Fragment layout of mma.m16n8k16 (g = lane/4, t = lane%4): A regs hold
+// (g,2t..2t+1), (g+8,2t..), (g,2t+8..), (g+8,2t+8..); B regs (2t..2t+1, g),
+// (2t+8..2t+9, g); C holds (g,2t), (g,2t+1), (g+8,2t), (g+8,2t+1).
+template <bool AK, bool BK>
+__device__ __forceinline__ void mma16816(float (&c)[4], const bf16* a, int lda, const bf16* b, int ldb, int lane)
+{
+    const int g = lane >> 2, t = lane & 3;
+    uint32_t a0, a1, a2, a3, b0, b1;
+    if (AK) {
+        a0 = *reinterpret_cast<const uint32_t*>(a + g * lda + 2 * t);
+        a1 = *reinterpret_cast<const uint32_t*>(a + (g + 8) * lda + 2 * t);
+        a2 = *reinterpret_cast<const uint32_t*>(a + g * lda + 2 * t + 8);
+        a3 = *reinterpret_cast<const uint32_t*>(a + (g + 8) * lda + 2 * t + 8);
+    } else {
+        a0 = pack2(a[(2 * t) * lda + g], a[(2 * t + 1) * lda + g]);
+        a1 = pack2(a[(2 * t) * lda + g + 8], a[(2 * t + 1) * lda + g + 8]);
+        a2 = pack2(a[(2 * t + 8) * lda + g], a[(2 * t + 9) * lda + g]);
+        a3 = pack2(a[(2 * t + 8) * lda + g + 8], a[(2 * t + 9) * lda + g + 8]);
+    }
+    if (BK) {
+        b0 = *reinterpret_cast<const uint32_t*>(b + g * ldb + 2 * t);
+        b1 = *reinterpret_cast<const uint32_t*>(b + g * ldb + 2 * t + 8);
+    } else {
+        b0 = pack2(b[(2 * t) * ldb + g], b[(2 * t + 1) * ldb + g]);
+        b1 = pack2(b[(2 * t + 8) * ldb + g], b[(2 * t + 9) * ldb + g]);
+    }
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ float wsum(float v)
+{
+#pragma unroll
+    for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+struct ActArgs {
+    const float* theta;  // FP32 master parameters (biases read from here)
+    const bf16* w1;      // [H][KIN]
+    const bf16* w2;      // [H][H]
+    const bf16* w3;      // [H]
+    Offs o;
+    int nin;
+    Norm nm;
+    const float* x;      // [*][nin]
+    const float* t;      // [*] raw targets (training)
+    const int* idx;      // rows of x / t to use, or NULL (identity)
+    int B;
+    float* y;            // forward: denormalised predictions [B]
+    // training
+    bf16* xh;            // [Bpad][KIN]
+    bf16* h1;            // [Bpad][H]
+    bf16* dh2;           // [Bpad][H]
+    bf16* dh1;           // [Bpad][H]
+    float* part;         // per tile: b1 [H], b2 [H], w3 [H], b3, sum of squared residuals (kPart floats)
+    float inv_B;
+};
+
+constexpr int kPart = 3 * H + 2;  // partial sums per tile
+
+// Forward (and, TRAIN, the backward pass down to the activations) of 32-row
+// tiles; persistent CTAs keep W1 and W2 in shared memory across tiles.  The
+// bias / w3 gradients and the loss leave as per-tile partial sums, reduced
+// in tile order by k_mlp_wgrad, so training is bit-reproducible.
+template <bool TRAIN>
+__global__ void __launch_bounds__(256, 1) k_mlp_act(ActArgs A)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    bf16* W2s = reinterpret_cast<bf16*>(smem);
+    bf16* W1s = W2s + H * LW2;
+    bf16* Xs = W1s + H * LW1;
+    bf16* H1s = Xs + TR * LX;
+    bf16* D2s = H1s + TR * LH;
+    float* H2s = reinterpret_cast<float*>(D2s + TR * LH);
+    float* dys = H2s + TR * LF;
+    __shared__ float wloss[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    for (int i = tid; i < H * H / 8; i += 256) {
+        const int r = i >> 5, c8 = i & 31;
+        *reinterpret_cast<uint4*>(W2s + r * LW2 + c8 * 8) = *reinterpret_cast<const uint4*>(A.w2 + r * H + c8 * 8);
+    }
+    for (int i = tid; i < H * KIN / 8; i += 256) {
+        const int r = i >> 2, c8 = i & 3;
+        *reinterpret_cast<uint4*>(W1s + r * LW1 + c8 * 8) = *reinterpret_cast<const uint4*>(A.w1 + r * KIN + c8 * 8);
+    }
+    const float* b1 = A.theta + A.o.b1;
+    const float* b2 = A.theta + A.o.b2;
+    const float b3 = A.theta[A.o.b3];
+    __syncthreads();
+    const int ntiles = (A.B + TR - 1) / TR;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int r0 = tile * TR;
+        // 1. normalised inputs
+        for (int i = tid; i < TR * KIN; i += 256) {
+            const int r = i / KIN, k = i % KIN, row = r0 + r;
+            float v = 0.f;
+            if (row < A.B && k < A.nin) {
+                const int src = A.idx ? A.idx[row] : row;
+                v = (A.x[(long)src * A.nin + k] - A.nm.mu[k]) / A.nm.sigma[k];
+            }
+            const bf16 hv = __float2bfloat16_rn(v);
+            Xs[r * LX + k] = hv;
+            if (TRAIN) A.xh[(long)row * KIN + k] = hv;
+        }
+        __syncthreads();
+        // 2. h1 = relu(x_hat W1^T + b1); warp w owns columns [32w, 32w+32)
+        {
+            float acc[2][4][4] = {};
+#pragma unroll
+            for (int ks = 0; ks < KIN; ks += 16)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt)
+                        mma16816<true, true>(acc[mt][nt], Xs + mt * 16 * LX + ks, LX,
+                                             W1s + (warp * 32 + nt * 8) * LW1 + ks, LW1, lane);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int r = mt * 16 + g + (q >> 1) * 8, j = warp * 32 + nt * 8 + 2 * t4 + (q & 1);
+                        const bf16 hv = __float2bfloat16_rn(fmaxf(acc[mt][nt][q] + b1[j], 0.f));
+                        H1s[r * LH + j] = hv;
+                        if (TRAIN) A.h1[(long)(r0 + r) * H + j] = hv;
+                    }
+        }
+        __syncthreads();
+        // 3. h2 = relu(h1 W2^T + b2), FP32 in shared memory
+        {
+            float acc[2][4][4] = {};
+#pragma unroll 4
+            for (int ks = 0; ks < H; ks += 16)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt)
+                        mma16816<true, true>(acc[mt][nt], H1s + mt * 16 * LH + ks, LH,
+                                             W2s + (warp * 32 + nt * 8) * LW2 + ks, LW2, lane);
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int r = mt * 16 + g + (q >> 1) * 8, j = warp * 32 + nt * 8 + 2 * t4 + (q & 1);
+                        H2s[r * LF + j] = fmaxf(acc[mt][nt][q] + b2[j], 0.f);
+                    }
+        }
+        __syncthreads();
+        // 4. y = w3 . h2 + b3; warp w owns rows 4w..4w+3
+        float lsum = 0.f;
+        for (int q = 0; q < 4; ++q) {
+            const int r = warp * 4 + q, row = r0 + r;
+            float s = 0.f;
+            for (int j = lane; j < H; j += 32) s += H2s[r * LF + j] * __bfloat162float(A.w3[j]);
+            const float y = wsum(s) + b3;
+            if (!TRAIN) {
+                if (lane == 0 && row < A.B) A.y[row] = y * A.nm.sigma_y + A.nm.mu_y;
+            } else {
+                float res = 0.f;
+                if (row < A.B) {
+                    const int src = A.idx ? A.idx[row] : row;
+                    res = y - (A.t[src] - A.nm.mu_y) / A.nm.sigma_y;
+                }
+                if (lane == 0) dys[r] = 2.f * res * A.inv_B;
+                lsum += res * res;
+            }
+        }
+        if (!TRAIN) {
+            __syncthreads();
+            continue;
+        }
+        float* part = A.part + (long)tile * kPart;
+        if (lane == 0) wloss[warp] = lsum;
+        __syncthreads();
+        if (tid == 0) {
+            float l = 0.f;
+            for (int w = 0; w < 8; ++w) l += wloss[w];
+            part[3 * H + 1] = l;
+        }
+        // 5. per column j: dW3, dh2 = dy w3 [h2 > 0], db2
+        {
+            const int j = tid;
+            const float w3j = __bfloat162float(A.w3[j]);
+            float gw3 = 0.f, gb2 = 0.f, gb3 = 0.f;
+            for (int r = 0; r < TR; ++r) {
+                const float h = H2s[r * LF + j], d = dys[r];
+                gw3 += d * h;
+                gb3 += d;
+                const float dh = h > 0.f ? d * w3j : 0.f;
+                gb2 += dh;
+                const bf16 db = __float2bfloat16_rn(dh);
+                D2s[r * LH + j] = db;
+                A.dh2[(long)(r0 + r) * H + j] = db;
+            }
+            part[2 * H + j] = gw3;
+            part[H + j] = gb2;
+            if (j == 0) part[3 * H] = gb3;
+        }
+        __syncthreads();
+        // 6. dh1 = (dh2 W2) [h1 > 0], db1; warp w owns columns [32w, 32w+32)
+        {
+            float acc[2][4][4] = {};
+#pragma unroll 4
+            for (int ks = 0; ks < H; ks += 16)
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int nt = 0; nt < 4; ++nt)
+                        mma16816<true, false>(acc[mt][nt], D2s + mt * 16 * LH + ks, LH,
+                                              W2s + ks * LW2 + warp * 32 + nt * 8, LW2, lane);
+#pragma unroll
+            for (int nt = 0; nt < 4; ++nt)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const int i = warp * 32 + nt * 8 + 2 * t4 + c;
+                    float colsum = 0.f;
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                        for (int hh = 0; hh < 2; ++hh) {
+                            const int r = mt * 16 + g + hh * 8;
+                            const float v = __bfloat162float(H1s[r * LH + i]) > 0.f ? acc[mt][nt][hh * 2 + c] : 0.f;
+                            colsum += v;
+                            A.dh1[(long)(r0 + r) * H + i] = __float2bfloat16_rn(v);
+                        }
+                    // sum over the 8 row groups g (lanes t4, t4+4, ..., t4+28)
+                    colsum += __shfl_xor_sync(0xffffffffu, colsum, 4);
+                    colsum += __shfl_xor_sync(0xffffffffu, colsum, 8);
+                    colsum += __shfl_xor_sync(0xffffffffu, colsum, 16);
+                    if (g == 0) part[i] = colsum;
+                }
+        }
+        __syncthreads();
+    }
+}
+
+struct WgradArgs {
+    const bf16* dh2;  // [Bpad][H]
+    const bf16* h1;   // [Bpad][H]
+    const bf16* dh1;  // [Bpad][H]
+    const bf16* xh;   // [Bpad][KIN]
+    int Bpad, nin;
+    Offs o;
+    float* grad;
+    const float* part;  // [Bpad / 32][kPart] from k_mlp_act
+    float* loss;        // += sum of squared residuals * loss_scale
+    float loss_scale;
+};
+
+// Weight gradients summed over the batch (rows r):
+//   dW2[j][i] = sum_r dh2[r][j] h1[r][i]   (16 CTAs, 64x64 tiles)
+//   dW1[j][k] = sum_r dh1[r][j] xh[r][k]   (4 CTAs, 64x32 tiles)
+// Each output element is produced by one CTA (plain stores, no atomics).
+// CTA 20 sums the per-tile partials (biases, w3, loss) in tile order.
+__global__ void __launch_bounds__(256) k_mlp_wgrad(WgradArgs A)
+{
+    if (blockIdx.x == 20) {
+        const int ntiles = A.Bpad / 32;
+        for (int c = threadIdx.x; c < kPart; c += blockDim.x) {
+            float sum = 0.f;
+            for (int t = 0; t < ntiles; ++t) sum += A.part[(long)t * kPart + c];
+            if (c < H) A.grad[A.o.b1 + c] = sum;
+            else if (c < 2 * H) A.grad[A.o.b2 + c - H] = sum;
+            else if (c < 3 * H) A.grad[A.o.w3 + c - 2 * H] = sum;
+            else if (c == 3 * H) A.grad[A.o.b3] = sum;
+            else *A.loss += sum * A.loss_scale;
+        }
+        return;
+    }
+    constexpr int RC = 32;                 // rows per chunk
+    constexpr int LA = 64 + 8, LB = 64 + 8;
+    __shared__ __align__(16) bf16 As[RC * LA];
+    __shared__ __align__(16) bf16 Bs[RC * LB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = lane >> 2, t4 = lane & 3;
+    const bool w1part = blockIdx.x >= 16;
+    const int jt = w1part ? (int)blockIdx.x - 16 : (int)blockIdx.x / 4;
+    const int it = w1part ? 0 : (int)blockIdx.x % 4;
+    const int ncols = w1part ? KIN : 64;   // output columns of this tile
+    const bf16* Asrc = w1part ? A.dh1 : A.dh2;
+    const bf16* Bsrc = w1part ? A.xh : A.h1;
+    const int ldb_src = w1part ? KIN : H;
+    const int mtile = warp & 3, nhalf = warp >> 2;
+    const int nnt = ncols / 16;            // n-tiles (of 8) per warp: 4 for 64 columns, 2 for 32
+    float acc[4][4] = {};
+    for (int rc = 0; rc < A.Bpad; rc += RC) {
+        for (int i = tid; i < RC * 8; i += 256) {  // A chunk: 32 rows x 64 columns j
+            const int r = i >> 3, c8 = i & 7;
+            *reinterpret_cast<uint4*>(As + r * LA + c8 * 8) =
+                *reinterpret_cast<const uint4*>(Asrc + (long)(rc + r) * H + jt * 64 + c8 * 8);
+        }
+        for (int i = tid; i < RC * (ncols / 8); i += 256) {  // B chunk: 32 rows x ncols columns
+            const int r = i / (ncols / 8), c8 = i % (ncols / 8);
+            *reinterpret_cast<uint4*>(Bs + r * LB + c8 * 8) =
+                *reinterpret_cast<const uint4*>(Bsrc + (long)(rc + r) * ldb_src + it * 64 + c8 * 8);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < RC; ks += 16)
+            for (int nt = 0; nt < nnt; ++nt)
+                mma16816<false, false>(acc[nt], As + ks * LA + mtile * 16, LA,
+                                       Bs + ks * LB + nhalf * (ncols / 2) + nt * 8, LB, lane);
+        __syncthreads();
+    }
+    for (int nt = 0; nt < nnt; ++nt)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int j = jt * 64 + mtile * 16 + g + (q >> 1) * 8;
+            const int c = it * 64 + nhalf * (ncols / 2) + nt * 8 + 2 * t4 + (q & 1);
+            if (w1part) {
+                if (c < A.nin) A.grad[A.o.w1 + j * A.nin + c] = acc[nt][q];
+            } else {
+                A.grad[A.o.w2 + j * H + c] = acc[nt][q];
+            }
+        }
+}
+
+// Adam on the FP32 master parameters (update != 0), then the BF16 copies.
+__global__ void k_mlp_adam(float* __restrict__ theta, float* __restrict__ m, float* __restrict__ v,
+                           const float* __restrict__ grad, Offs o, int nin, int update, float lr, float c1, float c2,
+                           bf16* __restrict__ w1, bf16* __restrict__ w2, bf16* __restrict__ w3)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= o.n) return;
+    float th = theta[p];
+    if (update) {
+        const float gr = grad[p];
+        const float mm = 0.9f * m[p] + 0.1f * gr;
+        const float vv = 0.999f * v[p] + 0.001f * gr * gr;
+        m[p] = mm;
+        v[p] = vv;
+        th -= lr * (mm * c1) / (sqrtf(vv * c2) + 1e-8f);
+        theta[p] = th;
+    }
+    if (p < o.b1) w1[(p / nin) * KIN + p % nin] = __float2bfloat16_rn(th);
+    else if (p >= o.w2 && p < o.b2) w2[p - o.w2] = __float2bfloat16_rn(th);
+    else if (p >= o.w3 && p < o.b3) w3[p - o.w3] = __float2bfloat16_rn(th);
+}
+
+uint64_t splitmix64(uint64_t& s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+}  // namespace
+
+struct adg_mlp {
+    int device = 0;
+    int nin = 0;
+    Offs o{};
+    float* theta = nullptr;  // FP32 master parameters [n]
+    float* m = nullptr;      // Adam moments [n]
+    float* v = nullptr;
+    float* grad = nullptr;   // [n]
+    float* loss = nullptr;   // device scratch [1]
+    bf16* w1 = nullptr;      // [H][KIN], zero beyond nin
+    bf16* w2 = nullptr;      // [H][H]
+    bf16* w3 = nullptr;      // [H]
+    Norm nm{};
+    long step = 0;
+    void* act = nullptr;     // training activations
+    size_t act_bytes = 0;
+    int* idx = nullptr;      // fit(): permutation of the training rows
+    size_t idx_n = 0;
+    float* eloss = nullptr;  // fit(): loss per epoch
+    size_t eloss_n = 0;
+};
+
+namespace {
+
+int mlp_fail(adg_ctx* ctx, cudaError_t e)
+{
+    (void)ctx;
+    return e == cudaErrorMemoryAllocation ? ADG_ENOMEM : ADG_ECUDA;
+}
+
+#define MCK(call)                                      \
+    do {                                               \
+        cudaError_t _e = (call);                       \
+        if (_e != cudaSuccess) return mlp_fail(ctx, _e); \
+    } while (0)
+
+cudaError_t sync_bf16(cudaStream_t st, adg_mlp* M)
+{
+    k_mlp_adam<<<(M->o.n + 255) / 256, 256, 0, st>>>(M->theta, M->m, M->v, M->grad, M->o, M->nin, 0, 0.f, 0.f, 0.f,
+                                                     M->w1, M->w2, M->w3);
+    return cudaGetLastError();
+}
+
+ActArgs act_args(const adg_mlp* M, const float* x, int B)
+{
+    ActArgs a{};
+    a.theta = M->theta;
+    a.w1 = M->w1;
+    a.w2 = M->w2;
+    a.w3 = M->w3;
+    a.o = M->o;
+    a.nin = M->nin;
+    a.nm = M->nm;
+    a.x = x;
+    a.B = B;
+    return a;
+}
+
+unsigned act_blocks(int B, int device)
+{
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    const int ntiles = (B + TR - 1) / TR;
+    return (unsigned)std::max(1, std::min(ntiles, nsm));
+}
+
+// Gradient of the batch loss into M->grad (and the loss, scaled, into *loss).
+int backprop(adg_ctx* ctx, adg_mlp* M, cudaStream_t st, const float* x, const float* t, const int* idx, int B,
+             float* loss, float loss_scale)
+{
+    const int Bpad = (B + TR - 1) / TR * TR;
+    const size_t act_b = sizeof(bf16) * (size_t)Bpad * (KIN + 3 * H);
+    const size_t need = act_b + sizeof(float) * (size_t)(Bpad / TR) * kPart;
+    if (need > M->act_bytes) {
+        MCK(cudaStreamSynchronize(st));
+        if (M->act) cudaFree(M->act);
+        M->act = nullptr;
+        M->act_bytes = 0;
+        MCK(cudaMalloc(&M->act, need));
+        M->act_bytes = need;
+    }
+    bf16* xh = (bf16*)M->act;
+    bf16* h1 = xh + (size_t)Bpad * KIN;
+    bf16* dh2 = h1 + (size_t)Bpad * H;
+    bf16* dh1 = dh2 + (size_t)Bpad * H;
+    float* part = (float*)((char*)M->act + act_b);
+    ActArgs a = act_args(M, x, B);
+    a.t = t;
+    a.idx = idx;
+    a.xh = xh;
+    a.h1 = h1;
+    a.dh2 = dh2;
+    a.dh1 = dh1;
+    a.part = part;
+    a.inv_B = 1.f / (float)B;
+    MCK(cudaFuncSetAttribute(k_mlp_act<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kActSmem));
+    k_mlp_act<true><<<act_blocks(B, M->device), 256, kActSmem, st>>>(a);
+    MCK(cudaGetLastError());
+    WgradArgs w{};
+    w.dh2 = dh2;
+    w.h1 = h1;
+    w.dh1 = dh1;
+    w.xh = xh;
+    w.Bpad = Bpad;
+    w.nin = M->nin;
+    w.o = M->o;
+    w.grad = M->grad;
+    w.part = part;
+    w.loss = loss;
+    w.loss_scale = loss_scale;
+    k_mlp_wgrad<<<21, 256, 0, st>>>(w);
+    MCK(cudaGetLastError());
+    ctx->stats.kernel_launches += 2;
+    return ADG_OK;
+}
+
+int adam_step(adg_ctx* ctx, adg_mlp* M, cudaStream_t st, float lr)
+{
+    M->step += 1;
+    const float c1 = (float)(1.0 / (1.0 - pow(0.9, (double)M->step)));
+    const float c2 = (float)(1.0 / (1.0 - pow(0.999, (double)M->step)));
+    k_mlp_adam<<<(M->o.n + 255) / 256, 256, 0, st>>>(M->theta, M->m, M->v, M->grad, M->o, M->nin, 1, lr, c1, c2,
+                                                     M->w1, M->w2, M->w3);
+    MCK(cudaGetLastError());
+    ctx->stats.kernel_launches += 1;
+    return ADG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int adg_mlp_nparams(int nin)
+{
+    if (nin < 1 || nin > ADG_MLP_NIN_MAX) return ADG_EINVAL;
+    return offsets(nin).n;
+}
+
+int adg_mlp_create(adg_ctx* ctx, int nin, uint64_t seed, adg_mlp** out)
+{
+    if (!ctx || !out || nin < 1 || nin > ADG_MLP_NIN_MAX) return ADG_EINVAL;
+    *out = nullptr;
+    if (cudaSetDevice(ctx->device) != cudaSuccess) return ADG_ECUDA;
+    adg_mlp* M = new (std::nothrow) adg_mlp();
+    if (!M) return ADG_ENOMEM;
+    M->device = ctx->device;
+    M->nin = nin;
+    M->o = offsets(nin);
+    const size_t n = (size_t)M->o.n;
+    for (int k = 0; k < KIN; ++k) {
+        M->nm.mu[k] = 0.f;
+        M->nm.sigma[k] = 1.f;
+    }
+    M->nm.mu_y = 0.f;
+    M->nm.sigma_y = 1.f;
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = cudaMalloc(&M->theta, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&M->m, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&M->v, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&M->grad, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&M->loss, sizeof(float) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&M->w1, sizeof(bf16) * H * KIN);
+    if (e == cudaSuccess) e = cudaMalloc(&M->w2, sizeof(bf16) * H * H);
+    if (e == cudaSuccess) e = cudaMalloc(&M->w3, sizeof(bf16) * H);
+    // He-uniform initial weights (bound sqrt(6 / fan_in)), zero biases
+    std::vector<float> th(n, 0.f);
+    uint64_t s = seed;
+    auto uni = [&](float bound) { return bound * (2.f * (float)((splitmix64(s) >> 40) * (1.0 / 16777216.0)) - 1.f); };
+    for (int i = 0; i < H * nin; ++i) th[M->o.w1 + i] = uni(sqrtf(6.f / nin));
+    for (int i = 0; i < H * H; ++i) th[M->o.w2 + i] = uni(sqrtf(6.f / H));
+    for (int i = 0; i < H; ++i) th[M->o.w3 + i] = uni(sqrtf(6.f / H));
+    cudaStream_t st = ctx->stream;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(M->theta, th.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M->m, 0, sizeof(float) * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M->v, 0, sizeof(float) * n, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(M->w1, 0, sizeof(bf16) * H * KIN, st);
+    if (e == cudaSuccess) e = sync_bf16(st, M);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        adg_mlp_destroy(M);
+        return e == cudaErrorMemoryAllocation ? ADG_ENOMEM : ADG_ECUDA;
+    }
+    ctx->stats.h2d_bytes += (int64_t)(sizeof(float) * n);
+    *out = M;
+    return ADG_OK;
+}
+
+int adg_mlp_destroy(adg_mlp* M)
+{
+    if (!M) return ADG_EINVAL;
+    cudaSetDevice(M->device);
+    cudaFree(M->theta);
+    cudaFree(M->m);
+    cudaFree(M->v);
+    cudaFree(M->grad);
+    cudaFree(M->loss);
+    cudaFree(M->w1);
+    cudaFree(M->w2);
+    cudaFree(M->w3);
+    cudaFree(M->act);
+    cudaFree(M->idx);
+    cudaFree(M->eloss);
+    delete M;
+    return ADG_OK;
+}
+
+int adg_mlp_get_params(adg_ctx* ctx, const adg_mlp* M, float* out)
+{
+    if (!ctx || !M || !out) return ADG_EINVAL;
+    MCK(cudaSetDevice(M->device));
+    MCK(cudaMemcpyAsync(out, M->theta, sizeof(float) * M->o.n, cudaMemcpyDeviceToHost, ctx->stream));
+    MCK(cudaStreamSynchronize(ctx->stream));
+    ctx->stats.d2h_bytes += (int64_t)(sizeof(float) * M->o.n);
+    return ADG_OK;
+}
+
+int adg_mlp_set_params(adg_ctx* ctx, adg_mlp* M, const float* in)
+{
+    if (!ctx || !M || !in) return ADG_EINVAL;
+    MCK(cudaSetDevice(M->device));
+    cudaStream_t st = ctx->stream;
+    MCK(cudaMemcpyAsync(M->theta, in, sizeof(float) * M->o.n, cudaMemcpyHostToDevice, st));
+    MCK(cudaMemsetAsync(M->m, 0, sizeof(float) * M->o.n, st));
+    MCK(cudaMemsetAsync(M->v, 0, sizeof(float) * M->o.n, st));
+    MCK(sync_bf16(st, M));
+    MCK(cudaStreamSynchronize(st));
+    M->step = 0;
+    ctx->stats.h2d_bytes += (int64_t)(sizeof(float) * M->o.n);
+    ctx->stats.kernel_launches += 1;
+    return ADG_OK;
+}
+
+int adg_mlp_set_norm(adg_mlp* M, const float* mu, const float* sigma, float mu_y, float sigma_y)
+{
+    if (!M || !mu || !sigma || !(sigma_y > 0.f)) return ADG_EINVAL;
+    for (int k = 0; k < M->nin; ++k)
+        if (!(sigma[k] > 0.f)) return ADG_EINVAL;
+    for (int k = 0; k < KIN; ++k) {
+        M->nm.mu[k] = k < M->nin ? mu[k] : 0.f;
+        M->nm.sigma[k] = k < M->nin ? sigma[k] : 1.f;
+    }
+    M->nm.mu_y = mu_y;
+    M->nm.sigma_y = sigma_y;
+    return ADG_OK;
+}
+
+int adg_mlp_forward(adg_ctx* ctx, const adg_mlp* M, const float* x, int B, float* y)
+{
+    if (!ctx || !M || B < 0 || (B > 0 && (!x || !y))) return ADG_EINVAL;
+    if (B == 0) return ADG_OK;
+    MCK(cudaSetDevice(M->device));
+    ActArgs a = act_args(M, x, B);
+    a.y = y;
+    MCK(cudaFuncSetAttribute(k_mlp_act<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kActSmem));
+    k_mlp_act<false><<<act_blocks(B, M->device), 256, kActSmem, ctx->stream>>>(a);
+    MCK(cudaGetLastError());
+    ctx->stats.kernel_launches += 1;
+    return ADG_OK;
+}
+
+int adg_mlp_grad(adg_ctx* ctx, adg_mlp* M, const float* x, const float* t, const int* idx, int B, float* grad,
+                 float* loss)
+{
+    if (!ctx || !M || !x || !t || !grad || B <= 0) return ADG_EINVAL;
+    MCK(cudaSetDevice(M->device));
+    cudaStream_t st = ctx->stream;
+    MCK(cudaMemsetAsync(M->loss, 0, sizeof(float), st));
+    const int rc = backprop(ctx, M, st, x, t, idx, B, M->loss, 1.f / (float)B);
+    if (rc != ADG_OK) return rc;
+    MCK(cudaMemcpyAsync(grad, M->grad, sizeof(float) * M->o.n, cudaMemcpyDeviceToDevice, st));
+    if (loss) MCK(cudaMemcpyAsync(loss, M->loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return ADG_OK;
+}
+
+int adg_mlp_train_step(adg_ctx* ctx, adg_mlp* M, const float* x, const float* t, const int* idx, int B, float lr,
+                       float* loss)
+{
+    if (!ctx || !M || !x || !t || B <= 0 || !(lr >= 0.f)) return ADG_EINVAL;
+    MCK(cudaSetDevice(M->device));
+    cudaStream_t st = ctx->stream;
+    MCK(cudaMemsetAsync(M->loss, 0, sizeof(float), st));
+    int rc = backprop(ctx, M, st, x, t, idx, B, M->loss, 1.f / (float)B);
+    if (rc != ADG_OK) return rc;
+    rc = adam_step(ctx, M, st, lr);
+    if (rc != ADG_OK) return rc;
+    if (loss) MCK(cudaMemcpyAsync(loss, M->loss, sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return ADG_OK;
+}
+
+int adg_mlp_fit(adg_ctx* ctx, adg_mlp* M, const float* x, const float* t, int n, int batch, int epochs, float lr,
+                uint64_t seed, float* epoch_loss)
+{
+    if (!ctx || !M || !x || !t || n <= 0 || batch <= 0 || epochs < 0 || !(lr >= 0.f)) return ADG_EINVAL;
+    MCK(cudaSetDevice(M->device));
+    cudaStream_t st = ctx->stream;
+    if ((size_t)n > M->idx_n) {
+        MCK(cudaStreamSynchronize(st));
+        cudaFree(M->idx);
+        M->idx = nullptr;
+        M->idx_n = 0;
+        MCK(cudaMalloc(&M->idx, sizeof(int) * n));
+        M->idx_n = (size_t)n;
+    }
+    if ((size_t)epochs > M->eloss_n) {
+        MCK(cudaStreamSynchronize(st));
+        cudaFree(M->eloss);
+        M->eloss = nullptr;
+        M->eloss_n = 0;
+        MCK(cudaMalloc(&M->eloss, sizeof(float) * std::max(epochs, 1)));
+        M->eloss_n = (size_t)epochs;
+    }
+    if (epochs == 0) return ADG_OK;
+    MCK(cudaMemsetAsync(M->eloss, 0, sizeof(float) * epochs, st));
+    // one permutation per epoch (Fisher-Yates on a splitmix64 stream), uploaded
+    // before the epoch's steps; the host buffer is pinned so the copy is async
+    int* perm = nullptr;
+    MCK(cudaMallocHost(&perm, sizeof(int) * (size_t)n * 2));
+    uint64_t s = seed;
+    int rc = ADG_OK;
+    for (int ep = 0; ep < epochs && rc == ADG_OK; ++ep) {
+        int* hp = perm + (size_t)(ep & 1) * n;
+        if (ep >= 2) {
+            // the copy that used this half two epochs ago has finished once the stream passed it
+            if (cudaStreamSynchronize(st) != cudaSuccess) {
+                rc = ADG_ECUDA;
+                break;
+            }
+        }
+        for (int i = 0; i < n; ++i) hp[i] = i;
+        for (int i = n - 1; i > 0; --i) {
+            const int j = (int)(splitmix64(s) % (uint64_t)(i + 1));
+            std::swap(hp[i], hp[j]);
+        }
+        if (cudaMemcpyAsync(M->idx, hp, sizeof(int) * n, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+            rc = ADG_ECUDA;
+            break;
+        }
+        ctx->stats.h2d_bytes += (int64_t)(sizeof(int) * n);
+        for (int b0 = 0; b0 < n && rc == ADG_OK; b0 += batch) {
+            const int B = std::min(batch, n - b0);
+            rc = backprop(ctx, M, st, x, t, M->idx + b0, B, M->eloss + ep, 1.f / (float)n);
+            if (rc == ADG_OK) rc = adam_step(ctx, M, st, lr);
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (rc == ADG_OK && e != cudaSuccess) rc = ADG_ECUDA;
+    if (rc == ADG_OK && epoch_loss) {
+        e = cudaMemcpy(epoch_loss, M->eloss, sizeof(float) * epochs, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) rc = ADG_ECUDA;
+    }
+    cudaFreeHost(perm);
+    return rc;
+}
+
+}  // extern "C"

@@ -129,6 +129,8 @@ extern "C" int adg_dock_noalloc(const adg_receptor* rec, const adg_ligand* lig, 
     D.gen_done = (int*)(A + o_gd);
     D.best_hist = (float*)(A + o_hist);
     D.stopped = (int*)(A + o_stop);
+    D.best_trace = nullptr;
+    D.best_trace_len = 0;
     D.trace_ngen = 0;
     D.tr_dec = nullptr;
     D.tr_genes = nullptr;
@@ -139,7 +141,7 @@ extern "C" int adg_dock_noalloc(const adg_receptor* rec, const adg_ligand* lig, 
     const MapsDev& M = rec->maps;
     // host values live on this stack frame until the final synchronize below
     const LigandRef lr = lig->ref;
-    const uint32_t id = p->lig_id;
+    const uint32_t id = lig->stream_id >= 0 ? (uint32_t)lig->stream_id : p->lig_id;
     int active = 0;
 #define NA_CK(call)                                 \
     do {                                            \

@@ -15,6 +15,7 @@ types plus electrostatic and desolvation maps.
 from __future__ import annotations
 
 import math
+import os
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -178,9 +179,12 @@ class Ligand:
 _MAXDEG = {T_C: 4, T_A: 3, T_N: 3, T_NA: 2, T_OA: 2, T_S: 2, T_HD: 1}
 
 
+_COS100 = math.cos(math.radians(100.0))
+
+
 def _unit(rng):
     v = rng.normal(size=3)
-    return v / np.linalg.norm(v)
+    return v / math.sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2])
 
 
 def make_ligand(n_heavy: int, n_tors: int, seed: int, n_hd: int | None = None,
@@ -205,27 +209,40 @@ def make_ligand(n_heavy: int, n_tors: int, seed: int, n_hd: int | None = None,
         types = [int(rng.choice(heavy_types, p=heavy_p))]
         # make sure there are enough donor sites for the polar hydrogens
         xyz = [np.zeros(3)]
+        X = np.zeros((n_heavy + n_hd, 3))  # the same coordinates as one array (distance checks)
         nbr = [[]]
+
+        dirs = {}  # atom -> unit vectors to its bonded neighbours (dropped when a bond is added)
+
+        def bond_dirs(i):
+            u = dirs.get(i)
+            if u is None:
+                v = X[nbr[i]] - X[i]
+                u = dirs[i] = v / np.sqrt((v * v).sum(axis=1))[:, None]
+            return u
+
         failed = False
         for a in range(1, n_heavy):
             t = int(rng.choice(heavy_types, p=heavy_p))
             placed = False
+            cand = [i for i in range(a) if len(nbr[i]) < _MAXDEG[types[i]]]
             for _ in range(400):
-                cand = [i for i in range(a) if len(nbr[i]) < _MAXDEG[types[i]]]
                 if not cand:
                     break
-                p = int(rng.choice(cand))
+                p = cand[int(rng.integers(0, len(cand)))]
                 d = _unit(rng)
-                ok = all(np.dot(d, (xyz[j] - xyz[p]) / np.linalg.norm(xyz[j] - xyz[p])) <= math.cos(math.radians(100.0))
-                         for j in nbr[p])
-                if not ok:
+                if len(nbr[p]) and (bond_dirs(p) @ d > _COS100).any():
                     continue
                 x = xyz[p] + d * rng.uniform(1.40, 1.54)
-                if any(np.linalg.norm(x - xyz[j]) < 2.0 for j in range(a) if j != p):
+                r = np.sqrt(((X[:a] - x) ** 2).sum(axis=1))
+                r[p] = np.inf
+                if (r < 2.0).any():
                     continue
                 xyz.append(x)
+                X[a] = x
                 nbr.append([p])
                 nbr[p].append(a)
+                dirs.pop(p, None)
                 types.append(t)
                 placed = True
                 break
@@ -251,15 +268,18 @@ def make_ligand(n_heavy: int, n_tors: int, seed: int, n_hd: int | None = None,
             placed = False
             for _ in range(400):
                 d = _unit(rng)
-                if not all(np.dot(d, (xyz[j] - xyz[s]) / np.linalg.norm(xyz[j] - xyz[s])) <= math.cos(math.radians(100.0))
-                           for j in nbr[s]):
+                if len(nbr[s]) and (bond_dirs(s) @ d > _COS100).any():
                     continue
                 x = xyz[s] + d * 1.0
-                if any(np.linalg.norm(x - xyz[j]) < 1.6 for j in range(len(xyz)) if j != s):
+                r = np.sqrt(((X[:len(xyz)] - x) ** 2).sum(axis=1))
+                r[s] = np.inf
+                if (r < 1.6).any():
                     continue
+                X[len(xyz)] = x
                 xyz.append(x)
                 nbr.append([s])
                 nbr[s].append(len(xyz) - 1)
+                dirs.pop(s, None)
                 types.append(T_HD)
                 placed = True
                 break
@@ -326,21 +346,51 @@ def workload_inputs(w: dict, lig_index: int = 0):
     return grid, rec, lig
 
 
-def make_batch(n: int, seed: int, heavy=(10, 60), tors=(0, 15)):
+def _grow(job):
+    """Ligand k of a batch: the most torsions <= nt that a grown tree offers."""
+    nh, nt, lseed = job
+    for t in range(nt, -1, -1):
+        try:
+            return make_ligand(nh, t, lseed)
+        except RuntimeError:
+            continue
+    return None
+
+
+def make_batch(n: int, seed: int, heavy=(10, 60), tors=(0, 15), workers: int | None = None):
     """Seeded batch of drug-like ligands with heavy atoms uniform in `heavy`
     and torsions uniform in `tors` (clipped to the rotatable bonds a grown
-    tree offers)."""
+    tree offers).  Ligand k depends only on (seed, k), so a batch can be
+    grown by a pool of `workers` processes (0: the host's cores) with the
+    same result as one process; the pool is started with "spawn", so the
+    calling script needs the usual `if __name__ == "__main__":` guard."""
     rng = np.random.default_rng(seed)
+    if workers is None:
+        workers = 1
+    elif workers == 0:
+        workers = min(os.cpu_count() or 1, 32)
     out = []
     k = 0
-    while len(out) < n:
-        nh = int(rng.integers(heavy[0], heavy[1] + 1))
-        nt = int(rng.integers(tors[0], tors[1] + 1))
-        for t in range(nt, -1, -1):
-            try:
-                out.append(make_ligand(nh, t, seed * 100003 + k))
-                break
-            except RuntimeError:
-                continue
-        k += 1
-    return out
+    pool = None
+    try:
+        while len(out) < n:
+            need = n - len(out)
+            jobs = []
+            for _ in range(need):
+                nh = int(rng.integers(heavy[0], heavy[1] + 1))
+                nt = int(rng.integers(tors[0], tors[1] + 1))
+                jobs.append((nh, nt, seed * 100003 + k))
+                k += 1
+            if workers > 1 and len(jobs) >= 2 * workers:
+                if pool is None:
+                    import multiprocessing as mp
+                    from concurrent.futures import ProcessPoolExecutor
+                    pool = ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn"))
+                grown = list(pool.map(_grow, jobs, chunksize=max(1, len(jobs) // (4 * workers))))
+            else:
+                grown = [_grow(j) for j in jobs]
+            out.extend(g for g in grown if g is not None)
+    finally:
+        if pool is not None:
+            pool.shutdown()
+    return out[:n]

@@ -1,0 +1,171 @@
+"""Triage network kernels (adg_mlp_*) against the FP64 oracle of
+oracle/mlp.py with BF16 storage rounding at the same points.
+
+Tolerances.  Both sides round the same quantities to BF16; they differ in
+FP32 vs FP64 accumulation (a few FP32 ulps) and, where such a difference
+straddles a BF16 rounding boundary (probability ~1e-4 per stored element),
+in one BF16 ulp (2^-8 relative) of one activation.  One such flip moves the
+normalised output by at most 2^-8 |h| sum_i |w3_i W2_ij| (about 6e-3 for
+these weights).  So: almost every row agrees to 1e-4, every row to 3e-2;
+gradient blocks agree to 1e-2 of their largest component, their median
+element to 1e-4."""
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+
+NIN = 22
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_03678_gb300 import adg, build
+    build.build()
+    c = adg.Context(0)
+    yield c
+    c.close()
+
+
+def _problem(seed, B):
+    rng = np.random.default_rng(seed)
+    x = rng.normal(0, 2, (B, NIN)).astype(np.float32)
+    t = rng.normal(-9, 3, B).astype(np.float32)
+    mu = rng.normal(0, 0.5, NIN).astype(np.float32)
+    sig = rng.uniform(1, 3, NIN).astype(np.float32)
+    return x, t, mu, sig
+
+
+def _net(ctx, seed, mu, sig, my=-9.0, sy=3.0):
+    from paper_2007_03678_gb300 import adg
+    net = adg.MLP(ctx, NIN, seed=seed)
+    rng = np.random.default_rng(seed + 1)
+    th = net.get_params().astype(np.float64)
+    o = M.unpack(th, NIN)
+    # non-zero biases so every term is exercised
+    th = M.pack(o[0], rng.normal(0, 0.1, 256), o[2], rng.normal(0, 0.1, 256), o[4], 0.25).astype(np.float32)
+    net.set_params(th)
+    net.set_norm(mu, sig, my, sy)
+    return net, th.astype(np.float64)
+
+
+def _blocks(nin):
+    H = M.HIDDEN
+    e = np.cumsum([0, H * nin, H, H * H, H, H, 1])
+    return dict(zip(("W1", "b1", "W2", "b2", "w3", "b3"), [slice(a, b) for a, b in zip(e[:-1], e[1:])]))
+
+
+@pytest.mark.parametrize("B", [1, 32, 300])
+def test_forward_matches_oracle(ctx, B):
+    import torch
+    x, t, mu, sig = _problem(10 + B, B)
+    net, th = _net(ctx, 3, mu, sig)
+    y = net.forward(torch.from_numpy(x).cuda()).cpu().numpy().astype(np.float64)
+    yr, _ = M.forward(th, x.astype(np.float64), NIN, mu.astype(np.float64), sig.astype(np.float64), True)
+    yn = (y + 9.0) / 3.0
+    err = np.abs(yn - yr)
+    assert err.max() <= 3e-2, err.max()
+    assert (err <= 1e-4).mean() >= 0.95, np.sort(err)[-10:]
+
+
+@pytest.mark.parametrize("B", [7, 300, 1000])
+def test_gradient_matches_oracle(ctx, B):
+    import torch
+    x, t, mu, sig = _problem(20 + B, B)
+    net, th = _net(ctx, 4, mu, sig)
+    g, loss = net.grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    lr, gr = M.loss_and_grad(th, x.astype(np.float64), t.astype(np.float64), NIN, mu.astype(np.float64),
+                             sig.astype(np.float64), -9.0, 3.0, True)
+    assert abs(float(loss.cpu()) - lr) <= 1e-3 * lr
+    for name, sl in _blocks(NIN).items():
+        d = np.abs(g[sl] - gr[sl])
+        scale = np.abs(gr[sl]).max()
+        assert d.max() <= 1e-2 * scale, (name, d.max(), scale)
+        assert np.median(d) <= 1e-4 * scale + 1e-9, (name, np.median(d), scale)
+
+
+def test_row_selection_and_adam_step(ctx):
+    """train_step with an index list equals the gradient of the selected rows
+    followed by the Adam update (first step: theta - lr g / (|g| + eps))."""
+    import torch
+    x, t, mu, sig = _problem(30, 200)
+    net, th = _net(ctx, 5, mu, sig)
+    idx = np.random.default_rng(31).permutation(200)[:77].astype(np.int32)
+    xd, td, idd = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda(), torch.from_numpy(idx).cuda()
+    g, _ = net.grad(xd, td, idd)
+    g = g.cpu().numpy().astype(np.float64)
+    _, gr = M.loss_and_grad(th, x[idx].astype(np.float64), t[idx].astype(np.float64), NIN, mu.astype(np.float64),
+                            sig.astype(np.float64), -9.0, 3.0, True)
+    assert np.abs(g - gr).max() <= 1e-2 * np.abs(gr).max()
+    lr = 1e-3
+    net.train_step(xd, td, lr, idd)
+    th1 = net.get_params().astype(np.float64)
+    want, _, _ = M.adam(th, np.zeros_like(th), np.zeros_like(th), g, 1, lr)
+    assert np.abs(th1 - want).max() <= 1e-6
+
+
+def _oracle_fit(x, t, mu, sig, my, sy, epochs, batch, lr, seed):
+    """The same training in FP64 (oracle network and Adam, own shuffling)."""
+    H, n = M.HIDDEN, len(x)
+    r = np.random.default_rng(seed)
+    th = M.pack(r.uniform(-1, 1, (H, NIN)) * np.sqrt(6 / NIN), np.zeros(H),
+                r.uniform(-1, 1, (H, H)) * np.sqrt(6 / H), np.zeros(H), r.uniform(-1, 1, H) * np.sqrt(6 / H), 0.0)
+    m, v, step = np.zeros_like(th), np.zeros_like(th), 0
+    for _ in range(epochs):
+        perm = r.permutation(n)
+        for b in range(0, n, batch):
+            idx = perm[b:b + batch]
+            _, g = M.loss_and_grad(th, x[idx], t[idx], NIN, mu, sig, my, sy, False)
+            step += 1
+            th, m, v = M.adam(th, m, v, g, step, lr)
+    return th
+
+
+def test_training_reduces_loss(ctx):
+    """A smooth synthetic target learned by adg_mlp_fit: the epoch loss falls
+    tenfold, and the held-out error is that of the same training run in FP64
+    by the oracle (within 15%) and below a least-squares linear fit's."""
+    import torch
+    from paper_2007_03678_gb300 import adg
+    rng = np.random.default_rng(40)
+    n = 4096
+    x = rng.normal(0, 1, (n, NIN)).astype(np.float32)
+    w = rng.normal(0, 1, NIN)
+    t = (np.tanh(x @ w / 3) * 4 + 0.5 * x[:, 0] ** 2 - 10).astype(np.float32)
+    net = adg.MLP(ctx, NIN, seed=7)
+    net.set_norm(x.mean(0), x.std(0), float(t.mean()), float(t.std()))
+    xd, td = torch.from_numpy(x[:3584]).cuda(), torch.from_numpy(t[:3584]).cuda()
+    hist = net.fit(xd, td, batch=256, epochs=40, lr=2e-3, seed=1)
+    assert hist[-1] < 0.1 * hist[0], hist
+    pred = net.forward(torch.from_numpy(x[3584:]).cuda()).cpu().numpy()
+    rmse = np.sqrt(np.mean((pred - t[3584:]) ** 2))
+    x64, t64 = x.astype(np.float64), t.astype(np.float64)
+    mu, sig = x64.mean(0), x64.std(0)
+    th = _oracle_fit(x64[:3584], t64[:3584], mu, sig, t64.mean(), t64.std(), 40, 256, 2e-3, 8)
+    y, _ = M.forward(th, x64[3584:], NIN, mu, sig, False)
+    rmse_ref = np.sqrt(np.mean((y * t64.std() + t64.mean() - t64[3584:]) ** 2))
+    c, *_ = np.linalg.lstsq(np.c_[x64[:3584], np.ones(3584)], t64[:3584], rcond=None)
+    rmse_lin = np.sqrt(np.mean((np.c_[x64[3584:], np.ones(512)] @ c - t64[3584:]) ** 2))
+    assert rmse <= 1.15 * rmse_ref and rmse < rmse_lin, (rmse, rmse_ref, rmse_lin)
+
+
+def test_training_is_bit_reproducible(ctx):
+    """Bias and loss partial sums are reduced in tile order (no atomics), so
+    the same data, seeds and schedule give the same parameters bit for bit."""
+    import torch
+    from paper_2007_03678_gb300 import adg
+    x, t, mu, sig = _problem(50, 700)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    out = []
+    for _ in range(2):
+        net = adg.MLP(ctx, NIN, seed=11)
+        net.set_norm(mu, sig, -9.0, 3.0)
+        h = net.fit(xd, td, batch=96, epochs=5, lr=1e-3, seed=2)
+        out.append((net.get_params(), h))
+        net.close()
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
