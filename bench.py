@@ -202,6 +202,83 @@ def workload_config(nrun=None, nev=None) -> dict:
 
 
 TRIAGE_TRAIN, TRIAGE_STREAM = 1200, 2000
+# DRAM bytes (read + write) per full-size launch of the generation kernel, from
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
+#       -k regex:k_dock_generation -s 60 -c 2 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
+#       --no-e2e --no-batching --no-triage --no-graphs
+# (mean of the two launches); None whenever the kernel has changed since that capture.
+GEN_TRAFFIC_BYTES = 24.8e6
+
+
+def run_plain_config(ctx, ff, reps=5):
+    """The plain configuration: 40^3 maps of a 600-atom pseudo-receptor, one
+    16+2-atom ligand with 3 torsions, 10 runs x pop 150 x 50,000 evals,
+    Solis-Wets.  Device-timed per docking call (best of `reps`)."""
+    import numpy as np
+    import torch
+    from paper_2007_03678_gb300 import adg, synth as S
+    grid, rec, lig = S.workload_inputs(S.PLAIN)
+    maps = adg.maps_build(ctx, ff, grid, rec)
+    R = adg.Receptor(ctx, grid, maps)
+    L = adg.Ligand(ctx, ff, lig)
+    p = adg.search_params(nrun=S.PLAIN["nrun"], pop_size=S.PLAIN["pop"], nev=S.PLAIN["nev"],
+                          ls_method=adg.LS_SOLIS_WETS, seed=S.SEARCH_SEED)
+    adg.dock(ctx, R, L, p)
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        r = adg.dock(ctx, R, L, p)[0]
+        e1.record(ctx.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    ev = int(r["evals"].sum())
+    return {"workload": "plain: 40^3 maps, 600-atom pseudo-receptor, 16+2 atoms, 3 torsions, 10 runs x 150 x "
+                        "50,000 evals, Solis-Wets", "evals_per_s": ev / (best / 1e3), "ligands_per_s": 1e3 / best,
+            "ms_per_ligand": best, "best_energy_median": float(np.median(r["best_energy"]))}
+
+
+def run_differentiation(ctx, R, ff, reps=5):
+    """65,536 random poses across 256 ligands (20-50 atoms, 2-12 torsions):
+    energy + gene gradient through the torch.autograd.Function, forward and
+    backward, device-timed over all 256 ligands (best of `reps`)."""
+    import numpy as np
+    import torch
+    from paper_2007_03678_gb300 import adg, synth as S
+    from paper_2007_03678_gb300.autograd import score
+    rng = np.random.default_rng(2024)
+    ligs, seed = [], 30000
+    while len(ligs) < 256:
+        seed += 1
+        try:
+            lig = S.make_ligand(int(rng.integers(18, 46)), int(rng.integers(2, 13)), seed)
+        except RuntimeError:
+            continue
+        if 20 <= lig.natoms <= 50:
+            ligs.append(lig)
+    grid = S.make_grid(S.PAPER["grid_n"])
+    L = [adg.Ligand(ctx, ff, l) for l in ligs]
+    X = [torch.from_numpy(S.random_genes(l, 256, grid, 40000 + i, spread=0.3).astype(np.float32)).cuda()
+         for i, l in enumerate(ligs)]
+    best = None
+    for _ in range(reps + 1):
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for Lg, x in zip(L, X):
+            x.requires_grad_(True)
+            score(x, ctx, R, Lg).sum().backward()
+            x.grad = None
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    for Lg in L:
+        Lg.close()
+    return {"workload": "65,536 poses over 256 ligands (20-50 atoms, 2-12 torsions), energy + gene gradient, "
+                        "forward + backward through torch.autograd", "poses_per_s": 65536 / (best / 1e3),
+            "ms": best}
 
 
 def run_triage(ctx, R, ff):
@@ -251,6 +328,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end pass (profiling runs)")
     ap.add_argument("--no-batching", action="store_true", help="skip the batching comparison (profiling runs)")
     ap.add_argument("--no-triage", action="store_true", help="skip the learned-triage screen")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="host-driven generation loop (kernel profilers cannot see kernels in conditional graphs)")
     ap.add_argument("--nrun", type=int, default=None, help="override the run count (small profiling cases)")
     ap.add_argument("--nev", type=int, default=None, help="override the evaluation budget (small profiling cases)")
     args = ap.parse_args()
@@ -277,6 +356,8 @@ def main():
     grid, rec, lig_desc = S.workload_inputs(w, lig_index=rank)
     stream = torch.cuda.Stream()
     ctx = adg.Context(local, stream=stream)
+    if args.no_graphs:
+        ctx.set_graphs(False)
     maps = adg.maps_build(ctx, ff, grid, rec)
     R = adg.Receptor(ctx, grid, maps)
     ctx.sync()
@@ -329,7 +410,8 @@ def main():
     achieved = flops_per_launch / (gen_ms_per_launch / 1e3) / 1e12
     peak, peak_src = fp32_peak_tflops()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "k_dock_generation<2,ADADELTA>",
+                "traffic": GEN_TRAFFIC_BYTES, "traffic_unit": "bytes per launch (dram read + write)",
+                "kernel": "k_dock_generation<2,ADADELTA>",
                 "launch_ms": gen_ms_per_launch, "flops_per_launch": flops_per_launch,
                 "gen_share_of_step": st["gen_kernel_ms"] / total_ms if world == 1 else None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peak_src}"}
@@ -396,6 +478,10 @@ def main():
     triage = None
     if not args.no_triage:
         triage = run_triage(ctx, R, ff)
+    plain = differentiation = None
+    if not args.no_batching:
+        plain = run_plain_config(ctx, ff)
+        differentiation = run_differentiation(ctx, R, ff)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -416,7 +502,8 @@ def main():
                 "config": workload_config(args.nrun, args.nev), "ligands_per_s": ligands_per_s,
                 "best_energy_median": float(np.median(results["best_energy"])),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "batching": batching,
-                "triage": triage, "gpu_launches": st["kernel_launches"]}
+                "triage": triage, "plain": plain, "differentiation": differentiation,
+                "gpu_launches": st["kernel_launches"]}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

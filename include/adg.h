@@ -290,6 +290,16 @@ int adg_ctx_set_timing(adg_ctx* ctx, int enable);
  * stream when timing is on (to read the events). */
 int adg_ctx_stats(adg_ctx* ctx, adg_stats* out, int reset);
 
+/* How adg_dock drives its generation loop (no counterpart in the paper).
+ * enable != 0 (default): one CUDA graph per ligand group -- initial
+ * population, a device-side WHILE loop of (generation, bookkeeping, loop
+ * control) that runs until no run of the group is active, final poses -- so
+ * the host launches once per group.  enable == 0: the same kernels launched
+ * from the host, each group reading its active-run count every four
+ * generations (for tools that cannot see kernels inside conditional graphs,
+ * such as kernel profilers).  Results are identical. */
+int adg_ctx_set_graphs(adg_ctx* ctx, int enable);
+
 /* Launch geometry of adg_dock (no counterpart in the paper, whose kernels
  * have one fixed block shape per ligand).  The generation kernel runs one
  * individual per warp; per launch it chooses the warps per block and whether

@@ -106,7 +106,8 @@ EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_c
            "adg_ctx_set_timing", "adg_ctx_stats", "adg_dock_noalloc", "adg_ctx_set_geometry", "adg_ctx_tuned",
            "adg_dock_traced", "adg_ligand_descriptors", "adg_mlp_nparams", "adg_mlp_create", "adg_mlp_destroy",
            "adg_mlp_get_params", "adg_mlp_set_params", "adg_mlp_set_norm", "adg_mlp_forward", "adg_mlp_grad",
-           "adg_mlp_train_step", "adg_mlp_fit", "adg_ligand_set_stream_id")
+           "adg_mlp_train_step", "adg_mlp_fit", "adg_ligand_set_stream_id",
+           "adg_ctx_set_graphs")
 
 _lib = None
 
@@ -146,6 +147,7 @@ def load(path: str | None = None):
         L.adg_dock_noalloc.argtypes = [_vp, _vp, C.POINTER(adg_search_params), C.POINTER(adg_result), _vp]
         L.adg_ctx_stats.argtypes = [_vp, C.POINTER(adg_stats), _i]
         L.adg_ctx_set_geometry.argtypes = [_vp, _i]
+        L.adg_ctx_set_graphs.argtypes = [_vp, _i]
         L.adg_dock_traced.argtypes = [_vp, _vp, C.POINTER(_vp), _i, C.POINTER(adg_search_params),
                                       C.POINTER(adg_result), C.POINTER(C.c_float), _i]
         L.adg_ligand_descriptors.argtypes = [_vp, C.POINTER(C.c_float)]
@@ -261,6 +263,10 @@ class Context:
 
     def set_timing(self, enable: bool):
         _check(load().adg_ctx_set_timing(self.handle, int(enable)), "adg_ctx_set_timing", self)
+
+    def set_graphs(self, enable: bool):
+        """Generation loop of dock as device-side graph loops (default) or host launches."""
+        _check(load().adg_ctx_set_graphs(self.handle, int(enable)), "adg_ctx_set_graphs", self)
 
     def set_geometry(self, mode: int):
         """GEO_HEURISTIC or GEO_TUNED (default) launch geometry for dock."""

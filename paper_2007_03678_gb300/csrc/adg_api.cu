@@ -190,6 +190,13 @@ int adg_ctx_set_timing(adg_ctx* ctx, int enable)
     return ADG_OK;
 }
 
+int adg_ctx_set_graphs(adg_ctx* ctx, int enable)
+{
+    if (!ctx) return ADG_EINVAL;
+    ctx->use_graphs = enable != 0;
+    return ADG_OK;
+}
+
 int adg_ctx_set_geometry(adg_ctx* ctx, int mode)
 {
     if (!ctx || (mode != ADG_GEO_HEURISTIC && mode != ADG_GEO_TUNED)) return ADG_EINVAL;
@@ -1169,9 +1176,53 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
             CK(ctx, take_event(ctx, &c.t1));
         }
         const int nruns = (int)c.ligs.size() * p->nrun;
-        CK(ctx, build_class_graph(ctx, c, M, S, need_loop, ctx->timing, nruns));
-        CK(ctx, cudaGraphLaunch(c.exec, c.stream));
+        if (ctx->use_graphs) {
+            CK(ctx, build_class_graph(ctx, c, M, S, need_loop, ctx->timing, nruns));
+            CK(ctx, cudaGraphLaunch(c.exec, c.stream));
+        } else {
+            cudaStream_t cs = c.stream;
+            CK(ctx, cudaMemsetAsync(c.D.evals, 0, sizeof(unsigned long long) * 2 * nruns, cs));
+            CK(ctx, cudaMemsetAsync(c.D.gen_done, 0, sizeof(int) * nruns, cs));
+            CK(ctx, cudaMemsetAsync(c.D.stopped, 0, sizeof(int) * nruns, cs));
+            if (c.D.best_trace)
+                CK(ctx, cudaMemsetAsync(c.D.best_trace, 0xff, sizeof(float) * nruns * c.D.best_trace_len, cs));
+            CK(ctx, launch_dock_init(cs, M, S, c.D, c.geo));
+            if (ctx->timing) CK(ctx, cudaEventRecord(c.t0, cs));
+        }
         ctx->stats.kernel_launches += 2;  // initial population and final poses; the loop adds 3 per generation
+    }
+    // host-driven generation loop (graphs off): every group advances four
+    // generations between reads of its active-run count
+    std::vector<int> host_gens(cls.size(), 0);
+    if (!ctx->use_graphs) {
+        std::vector<char> live(cls.size(), need_loop ? 1 : 0);
+        std::vector<int> act(cls.size(), 0);
+        for (;;) {
+            bool any = false;
+            for (size_t k = 0; k < cls.size(); ++k) {
+                if (!live[k]) continue;
+                any = true;
+                ClassRun& c = cls[k];
+                for (int q = 0; q < 4 && host_gens[k] < p->max_gen; ++q) {
+                    const int gen = ++host_gens[k];
+                    CK(ctx, cudaMemsetAsync(c.d_active, 0, sizeof(int), c.stream));
+                    CK(ctx, launch_dock_generation(c.stream, M, S, c.D, c.geo, gen));
+                    CK(ctx, launch_dock_count_active(c.stream, S, c.D, gen, c.d_active));
+                }
+                CK(ctx, cudaMemcpyAsync(&act[k], c.d_active, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+            }
+            if (!any) break;
+            for (size_t k = 0; k < cls.size(); ++k) {
+                if (!live[k]) continue;
+                CK(ctx, cudaStreamSynchronize(cls[k].stream));
+                if (act[k] == 0 || host_gens[k] >= p->max_gen) live[k] = 0;
+            }
+        }
+        for (size_t k = 0; k < cls.size(); ++k) {
+            ClassRun& c = cls[k];
+            if (ctx->timing) CK(ctx, cudaEventRecord(c.t1, c.stream));
+            CK(ctx, launch_dock_finalize(c.stream, M, S, c.D, c.geo, c.d_res));
+        }
     }
     std::vector<std::vector<ResultDev>> res(cls.size());
     std::vector<std::vector<float>> btr(cls.size());
@@ -1181,8 +1232,13 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
         const long nruns = (long)c.ligs.size() * p->nrun;
         res[k].resize(nruns);
         CK(ctx, cudaMemcpyAsync(res[k].data(), c.d_res, sizeof(ResultDev) * nruns, cudaMemcpyDeviceToHost, c.stream));
-        CK(ctx, cudaMemcpyAsync(&gens_dev[k], c.d_gen, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
-        ctx->stats.d2h_bytes += (int64_t)(sizeof(ResultDev) * nruns + sizeof(int));
+        if (ctx->use_graphs) {
+            CK(ctx, cudaMemcpyAsync(&gens_dev[k], c.d_gen, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
+            ctx->stats.d2h_bytes += (int64_t)sizeof(int);
+        } else {
+            gens_dev[k] = host_gens[k];
+        }
+        ctx->stats.d2h_bytes += (int64_t)(sizeof(ResultDev) * nruns);
         if (ntrace > 0) {
             btr[k].resize((size_t)nruns * ntrace);
             CK(ctx, cudaMemcpyAsync(btr[k].data(), c.D.best_trace, sizeof(float) * nruns * ntrace,
@@ -1207,7 +1263,7 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
         }
         if (c.t0) ctx->ev_free.push_back(c.t0);
         if (c.t1) ctx->ev_free.push_back(c.t1);
-        cudaGraphExecDestroy(c.exec);
+        if (c.exec) cudaGraphExecDestroy(c.exec);
     }
     ctx->ev_free.push_back(fork);
     if (trace) {

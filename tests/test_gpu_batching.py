@@ -76,3 +76,22 @@ def test_geometry_modes_agree_and_tuning_table(ctx, ff):
     ctx.stats(reset=True)
     adg.dock(ctx, R, L, p)
     assert ctx.stats()["tune_launches"] == 0
+
+
+def test_graph_and_host_loops_agree(ctx, ff):
+    """The device-side graph loop and the host-driven loop give the same runs."""
+    from paper_2007_03678_gb300 import adg
+    grid, rec, _, maps64, maps32 = problem("paper")
+    R = adg.Receptor(ctx, grid, maps32)
+    L = [adg.Ligand(ctx, ff, l) for l in S.make_batch(7, seed=13)]
+    p = adg.search_params(nrun=3, pop_size=40, nev=9000, ls_method=adg.LS_SOLIS_WETS, ls_max_iters=30, seed=23,
+                          autostop=1)
+    ref = adg.dock(ctx, R, L, p, best_trace=6)
+    ctx.set_graphs(False)
+    try:
+        got = adg.dock(ctx, R, L, p, best_trace=6)
+    finally:
+        ctx.set_graphs(True)
+    for a, b in zip(ref, got):
+        for key in ("best_energy", "genes", "xyz", "evals", "generations", "best_trace"):
+            assert np.array_equal(a[key], b[key]), key
