@@ -207,7 +207,7 @@ TRIAGE_TRAIN, TRIAGE_STREAM = 1200, 2000
 #       -k regex:k_dock_generation -s 60 -c 2 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
 #       --no-e2e --no-batching --no-triage --no-graphs
 # (mean of the two launches); None whenever the kernel has changed since that capture.
-GEN_TRAFFIC_BYTES = 24.8e6
+GEN_TRAFFIC_BYTES = None
 
 
 def run_plain_config(ctx, ff, reps=5):

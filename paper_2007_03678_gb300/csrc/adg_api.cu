@@ -481,46 +481,81 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         for (int j = i + 1; j < N; ++j)
             if (frag[i] != frag[j] && !near[i][j]) pairs.emplace_back(std::min(nw[i], nw[j]), std::max(nw[i], nw[j]));
     const int P = (int)pairs.size();
-    // --- lane schedule: 32 pairs per step, greedily without a repeated atom
-    std::vector<int> slots;
-    {
-        std::vector<char> taken(P, 0);
-        int left = P;
-        std::vector<int> used(N, -1);
-        int step = 0;
-        while (left > 0) {
-            std::vector<int> cur;
-            for (int p = 0; p < P && (int)cur.size() < 32; ++p) {
-                if (taken[p]) continue;
-                if (used[pairs[p].first] == step || used[pairs[p].second] == step) continue;
-                cur.push_back(p);
-                used[pairs[p].first] = used[pairs[p].second] = step;
-                taken[p] = 1;
-            }
-            for (int p = 0; p < P && (int)cur.size() < 32; ++p)
-                if (!taken[p]) {
-                    cur.push_back(p);
-                    taken[p] = 1;
-                }
-            left -= (int)cur.size();
-            while ((int)cur.size() < 32) cur.push_back(-1);
-            slots.insert(slots.end(), cur.begin(), cur.end());
-            ++step;
-        }
+    // --- lane schedule.  Rows: a lane takes the not yet owned atom with the
+    // most unscheduled pairs and runs (up to its share of) those pairs as that
+    // atom's row, first the pairs whose partner already owns a row elsewhere
+    // (no row could take them later).  A row lives on one lane, so the lane
+    // sums the owner's force in registers.  Pairs left when every lane holds
+    // its share go, unowned, to the least loaded lanes.
+    std::vector<std::vector<int>> inc_p(N);  // pairs by atom
+    for (int p = 0; p < P; ++p) {
+        inc_p[pairs[p].first].push_back(p);
+        inc_p[pairs[p].second].push_back(p);
     }
-    const int nsteps = (int)slots.size() / 32;
-    // --- force-gather program: every atom's (slot, partner) list goes to one
-    // lane as a segment -- a header (atom | groups << 7) then its entries
-    // (partner | slot << 7) padded to a multiple of 4 with entries that point
-    // back at the atom itself (they add c * 0); atoms are dealt longest
-    // segment first to the least loaded lane
+    std::vector<int> owner(P, -1);                 // owning atom, -1: not owned
+    std::vector<char> sched(P, 0), done(N, 0);
+    std::vector<std::vector<int>> col(32);         // pair ids per lane, in slot order
+    std::vector<std::vector<char>> rowend(32);
+    const int share = (P + 31) / 32;
+    for (;;) {
+        int lane = 0;
+        for (int l = 1; l < 32; ++l)
+            if (col[l].size() < col[lane].size()) lane = l;
+        const int room = share - (int)col[lane].size();
+        if (room <= 0) break;
+        int best = -1, best_n = 0;
+        for (int a2 = 0; a2 < N; ++a2) {
+            if (done[a2]) continue;
+            int n2 = 0;
+            for (int p : inc_p[a2]) n2 += !sched[p];
+            if (n2 > best_n) { best = a2; best_n = n2; }
+        }
+        if (best < 0) break;
+        std::vector<int> cand;
+        for (int p : inc_p[best])  // partner already owns a row: only this row can take the pair
+            if (!sched[p] && done[pairs[p].first + pairs[p].second - best]) cand.push_back(p);
+        for (int p : inc_p[best])
+            if (!sched[p] && !done[pairs[p].first + pairs[p].second - best]) cand.push_back(p);
+        const int take = std::min(room, (int)cand.size());
+        for (int q = 0; q < take; ++q) {
+            owner[cand[q]] = best;
+            sched[cand[q]] = 1;
+            col[lane].push_back(cand[q]);
+            rowend[lane].push_back(q + 1 == take);
+        }
+        done[best] = 1;
+    }
+    for (int p = 0; p < P; ++p) {
+        if (sched[p]) continue;
+        int lane = 0;
+        for (int l = 1; l < 32; ++l)
+            if (col[l].size() < col[lane].size()) lane = l;
+        col[lane].push_back(p);
+        rowend[lane].push_back(0);
+        sched[p] = 1;
+    }
+    int nsteps = 0;
+    for (auto& v : col) nsteps = std::max(nsteps, (int)v.size());
+    nsteps += nsteps & 1;  // the kernel runs two slots per step
+    std::vector<int> slots((size_t)nsteps * 32, -1);
+    std::vector<int> slot_flags((size_t)nsteps * 32, 0);
+    for (int l = 0; l < 32; ++l)
+        for (size_t k = 0; k < col[l].size(); ++k) {
+            slots[k * 32 + l] = col[l][k];
+            slot_flags[k * 32 + l] = (owner[col[l][k]] >= 0 ? kPairOwned : 0) | (rowend[l][k] ? kPairRowEnd : 0);
+        }
+    // --- force-gather program: every atom's (slot, partner) entries that its
+    // row does not cover go to one lane as a segment -- a header
+    // (atom | groups << 7) then its entries (partner | slot << 7) padded to a
+    // multiple of 4 with entries that point back at the atom itself (they add
+    // c * 0); atoms are dealt longest segment first to the least loaded lane
     std::vector<std::vector<uint32_t>> inc(N);
     for (int sl = 0; sl < (int)slots.size(); ++sl) {
         const int p = slots[sl];
         if (p < 0) continue;
         const int i = pairs[p].first, j = pairs[p].second;
-        inc[i].push_back((uint32_t)j | ((uint32_t)sl << 7));
-        inc[j].push_back((uint32_t)i | ((uint32_t)sl << 7));
+        if (owner[p] != i) inc[i].push_back((uint32_t)j | ((uint32_t)sl << 7));
+        if (owner[p] != j) inc[j].push_back((uint32_t)i | ((uint32_t)sl << 7));
     }
     std::vector<int> by_deg(N);
     for (int i = 0; i < N; ++i) by_deg[i] = i;
@@ -602,12 +637,14 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     for (int s = 0; s < ns; ++s) {
         const int p = slots[s];
         if (p < 0) continue;
-        const int i = pairs[p].first, j = pairs[p].second;  // internal
+        // the owner, if any, goes first: the kernel sums the force on ij & 127
+        const int i = owner[p] == pairs[p].second ? pairs[p].second : pairs[p].first;
+        const int j = pairs[p].first + pairs[p].second - i;  // internal
         const int ti = d->type[old_of[i]], tj = d->type[old_of[j]];
         const double qi = d->charge[old_of[i]], qj = d->charge[old_of[j]];
         float c12, c6, c10;
         pair_coefs(*ff, ti, tj, &c12, &c6, &c10);
-        ij[s] = i | (j << 16);
+        ij[s] = i | (j << 16) | slot_flags[s];
         coef[s] = make_float4(c12, c6, c10, (float)(wq * qi * qj));
         cd[s] = (float)((double)ff->w_desolv * (((double)ff->solpar[ti] + (double)ff->qasp * fabs(qi)) * ff->vol[tj] +
                                                 ((double)ff->solpar[tj] + (double)ff->qasp * fabs(qj)) * ff->vol[ti]));

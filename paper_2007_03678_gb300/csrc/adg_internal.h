@@ -45,7 +45,7 @@ struct Geo {
 // indexed by their genotype index k (theta_k = genes[7 + k]); fragment f > 0
 // hangs from fragment fpar[f] on torsion ftor[f], at depth flev[f].
 struct LigandDev {
-    int natoms, ntors, npairs, nsteps;   // nsteps = ceil(npairs / 32) pair slots per lane
+    int natoms, ntors, npairs, nsteps;   // nsteps: pair slots per lane (even)
     int gsteps;                          // length of the longest per-lane force-gather list
     int nfrag, maxlev;                   // fragments (ntors + 1) and the deepest level
     // the blob: this header, then the pair and gather arrays at these byte offsets
@@ -64,15 +64,21 @@ struct LigandDev {
 };
 
 // Intramolecular pairs, lane-interleaved: slot (step, lane) = step * 32 + lane.
-// ij = i | j << 16 (an empty slot pairs atom 0 with itself, with zero
-// coefficients).  coef = (c12, c6, c10, cq):
+// ij = i | j << 16 | kPairOwned | kPairRowEnd (an empty slot pairs atom 0 with
+// itself, with zero coefficients, and no flag).  coef = (c12, c6, c10, cq):
 // E_pair = min(c12 r^-12 - c6 r^-6 - c10 r^-10, e_cap) + cq / (eps(r) r) + cd exp(-r^2/(2 s^2)).
-// Force gather: after the pair pass has stored c_p = (dE/dr)/r of every slot,
-// lane l walks its list gent[k * 32 + l]: segments of a header
-// atom | groups << 7 followed by 4 * groups entries partner | slot << 7
-// (padded with entries whose partner is the atom itself), ended by
-// kGatherPad, and sums f_atom = sum c_p (x_atom - x_partner).  Atoms are dealt
-// to lanes by segment length, longest first to the least loaded lane.
+// Forces.  Most pairs are owned by atom i: the pairs a lane runs are grouped
+// into rows, one row per owning atom, each row on one lane only, so the lane
+// sums c_p (x_i - x_j) in registers and stores it to f[i] at the row's last
+// slot (kPairRowEnd).  Everything else -- the partner side of owned pairs, and
+// both sides of the few pairs no row could take -- goes through the force
+// gather: after the pair pass has stored c_p of every slot, lane l walks its
+// list gent[k * 32 + l]: segments of a header atom | groups << 7 followed by
+// 4 * groups entries partner | slot << 7 (padded with entries whose partner
+// is the atom itself), ended by kGatherPad, and adds sum c_p (x_atom -
+// x_partner) to f[atom].
+constexpr int kPairOwned = 1 << 15;
+constexpr int kPairRowEnd = 1 << 14;
 struct PairsDev {
     const int* ij;
     const float4* coef;

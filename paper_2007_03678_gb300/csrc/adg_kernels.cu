@@ -290,6 +290,15 @@ __device__ __forceinline__ LigandRef stage_ligand(const LigandRef& g, int lig_by
     return r;
 }
 
+// Two-wide FP32 arithmetic: one instruction computes both halves of a float2
+// (each rounded to nearest, as the scalar operation would be).
+__device__ __forceinline__ float2 v2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 s2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -442,52 +451,85 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
             if (GRAD) ws.f[a] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
     }
-    // intramolecular pairs
+    if (GRAD) __syncwarp();  // rows below store into f of atoms other lanes cleared
+    // intramolecular pairs, two slots per step in two-wide FP32 arithmetic
+    // (one instruction for both); the force on a row owner accumulates in
+    // registers and is stored at the row's end
     const float cap = L->e_cap, rmin2 = L->rmin2, msA = L->ms_A, msB = L->ms_B, msk = L->ms_k, mslb = L->ms_lb;
     const float inv_2s2 = L->inv_2s2, inv_s2 = L->inv_s2;
-    const int nsteps = L->nsteps;
-#pragma unroll 2
-    for (int stp = 0; stp < nsteps; ++stp) {
-        const int idx = stp * 32 + lane;
-        const int ij = P.ij[idx];
-        const int i = ij & 0xffff, j = ij >> 16;
-        const float4 xi = ws.xyz[i], xj = ws.xyz[j];
-        const float dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
-        const float r2 = dx * dx + dy * dy + dz * dz;
-        const float4 c = P.coef[idx];
-        const float cd = P.cd[idx];
-        const bool fl = r2 < rmin2;
-        const float rr2 = fl ? rmin2 : r2;
-        const float ri = rsqrtf(rr2);
-        const float r = rr2 * ri;
-        const float ri2 = ri * ri;
-        const float ri6 = ri2 * ri2 * ri2, ri12 = ri6 * ri6, ri10 = ri6 * ri2 * ri2;
-        const float elj = c.x * ri12 - c.y * ri6 - c.z * ri10;
-        const float ex = __expf(-mslb * r);
-        const float den = 1.f + msk * ex;
-        const float D = msA * den + msB;  // eps(r) = D / den
-        const float rD = __fdividef(1.f, D);
-        const float eel = c.w * den * ri * rD;
-        const float gs = __expf(-rr2 * inv_2s2);
-        const float eds = cd * gs;
+    const int nsteps = L->nsteps;  // even
+    float rfx = 0.f, rfy = 0.f, rfz = 0.f;
+    float2 e2 = s2(0.f);
+    for (int stp = 0; stp < nsteps; stp += 2) {
+        const int ia = stp * 32 + lane, ib = ia + 32;
+        const int ija = P.ij[ia], ijb = P.ij[ib];
+        const float4 xia = ws.xyz[ija & 127], xja = ws.xyz[(ija >> 16) & 127];
+        const float4 xib = ws.xyz[ijb & 127], xjb = ws.xyz[(ijb >> 16) & 127];
+        const float2 dx = sub2(v2(xia.x, xib.x), v2(xja.x, xjb.x));
+        const float2 dy = sub2(v2(xia.y, xib.y), v2(xja.y, xjb.y));
+        const float2 dz = sub2(v2(xia.z, xib.z), v2(xja.z, xjb.z));
+        const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
+        const float4 ca = P.coef[ia], cb = P.coef[ib];
+        const float2 c12 = v2(ca.x, cb.x), c6 = v2(ca.y, cb.y), c10 = v2(ca.z, cb.z), cq = v2(ca.w, cb.w);
+        const float2 cd = v2(P.cd[ia], P.cd[ib]);
+        const bool fla = r2.x < rmin2, flb = r2.y < rmin2;
+        const float2 rr2 = v2(fla ? rmin2 : r2.x, flb ? rmin2 : r2.y);
+        const float2 ri = v2(rsqrtf(rr2.x), rsqrtf(rr2.y));
+        const float2 r = mul2(rr2, ri);
+        const float2 ri2 = mul2(ri, ri);
+        const float2 ri4 = mul2(ri2, ri2);
+        const float2 ri6 = mul2(ri4, ri2), ri12 = mul2(ri6, ri6), ri10 = mul2(ri6, ri4);
+        const float2 a12 = mul2(c12, ri12), a6 = mul2(c6, ri6), a10 = mul2(c10, ri10);
+        const float2 elj = sub2(sub2(a12, a6), a10);
+        const float2 ex = v2(__expf(-mslb * r.x), __expf(-mslb * r.y));
+        const float2 den = fma2(s2(msk), ex, s2(1.f));
+        const float2 D = fma2(s2(msA), den, s2(msB));  // eps(r) = D / den
+        const float2 rD = v2(__fdividef(1.f, D.x), __fdividef(1.f, D.y));
+        const float2 u = mul2(ri, rD);
+        const float2 eel = mul2(mul2(cq, den), u);
+        const float2 gs = v2(__expf(-rr2.x * inv_2s2), __expf(-rr2.y * inv_2s2));
+        const float2 eds = mul2(cd, gs);
         if (GRAD) {
-            float dlj = (-12.f * c.x * ri12 + 6.f * c.y * ri6 + 10.f * c.z * ri10) * ri2;  // (dE/dr) / r
-            if (elj > cap) dlj = 0.f;
-            const float dden = -mslb * msk * ex;
-            const float deel = c.w * (dden * rD * ri - den * rD * rD * ri * ri * (msA * dden * r + D)) * ri;
-            const float dds = -eds * inv_s2;
-            ws.c[idx] = fl ? 0.f : (dlj + deel + dds);
+            // (dE/dr) / r of the three terms
+            float2 dlj = mul2(fma2(s2(10.f), a10, fma2(s2(6.f), a6, mul2(s2(-12.f), a12))), ri2);
+            if (elj.x > cap) dlj.x = 0.f;
+            if (elj.y > cap) dlj.y = 0.f;
+            const float2 dden = mul2(s2(-mslb * msk), ex);
+            const float2 w = fma2(mul2(s2(msA), dden), r, D);
+            const float2 deel = mul2(mul2(cq, sub2(mul2(dden, u), mul2(mul2(den, mul2(u, u)), w))), ri);
+            const float2 dds = mul2(eds, s2(-inv_s2));
+            const float2 cp = add2(add2(dlj, deel), dds);
+            const float cpa = fla ? 0.f : cp.x, cpb = flb ? 0.f : cp.y;
+            ws.c[ia] = cpa;
+            ws.c[ib] = cpb;
+            const float coa = (ija & kPairOwned) ? cpa : 0.f;
+            rfx = fmaf(coa, dx.x, rfx);
+            rfy = fmaf(coa, dy.x, rfy);
+            rfz = fmaf(coa, dz.x, rfz);
+            if (ija & kPairRowEnd) {
+                ws.f[ija & 127] = make_float4(rfx, rfy, rfz, 0.f);
+                rfx = rfy = rfz = 0.f;
+            }
+            const float cob = (ijb & kPairOwned) ? cpb : 0.f;
+            rfx = fmaf(cob, dx.y, rfx);
+            rfy = fmaf(cob, dy.y, rfy);
+            rfz = fmaf(cob, dz.y, rfz);
+            if (ijb & kPairRowEnd) {
+                ws.f[ijb & 127] = make_float4(rfx, rfy, rfz, 0.f);
+                rfx = rfy = rfz = 0.f;
+            }
         }
-        e += fminf(elj, cap) + eel + eds;
+        e2 = add2(e2, add2(add2(v2(fminf(elj.x, cap), fminf(elj.y, cap)), eel), eds));
     }
+    e += e2.x + e2.y;
     ScoreOut out;
     out.e = warp_sum(e);
     out.gtan = 0.f;
     out.tx = out.ty = out.tz = 0.f;
     if (!GRAD) return out;
     __syncwarp();
-    // force gather: f_atom = sum over its pairs of c_p (x_atom - x_partner),
-    // four independent entries per step
+    // force gather: f_atom += sum over its pairs that its row did not cover of
+    // c_p (x_atom - x_partner), four independent entries per step
     for (int k = 0;;) {
         const uint32_t hdr = P.gent[k * 32 + lane];
         if (hdr == kGatherPad) break;
@@ -504,7 +546,8 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
             ay += c0 * (xa.y - x0.y) + c1 * (xa.y - x1.y) + c2 * (xa.y - x2.y) + c3 * (xa.y - x3.y);
             az += c0 * (xa.z - x0.z) + c1 * (xa.z - x1.z) + c2 * (xa.z - x2.z) + c3 * (xa.z - x3.z);
         }
-        ws.f[atom] = make_float4(ax, ay, az, 0.f);
+        const float4 fr = ws.f[atom];  // the atom's row sum (or zero)
+        ws.f[atom] = make_float4(fr.x + ax, fr.y + ay, fr.z + az, 0.f);
     }
     __syncwarp();
     // Per atom: total force f and moment m = (x - t) x f.  Inclusive prefix
