@@ -481,102 +481,217 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         for (int j = i + 1; j < N; ++j)
             if (frag[i] != frag[j] && !near[i][j]) pairs.emplace_back(std::min(nw[i], nw[j]), std::max(nw[i], nw[j]));
     const int P = (int)pairs.size();
-    // --- lane schedule.  Rows: a lane takes the not yet owned atom with the
-    // most unscheduled pairs and runs (up to its share of) those pairs as that
-    // atom's row, first the pairs whose partner already owns a row elsewhere
-    // (no row could take them later).  A row lives on one lane, so the lane
-    // sums the owner's force in registers.  Pairs left when every lane holds
-    // its share go, unowned, to the least loaded lanes.
+    // --- lane schedule.  Rows: the not yet owned atom with the most
+    // unscheduled pairs takes (up to a lane's share of) those pairs as its row,
+    // first the pairs whose partner already owns a row (no row could take them
+    // later).  A row runs on one lane, which keeps the owner's coordinates and
+    // force in registers.  Pairs no row takes run as one-pair rows, unowned.
     std::vector<std::vector<int>> inc_p(N);  // pairs by atom
     for (int p = 0; p < P; ++p) {
         inc_p[pairs[p].first].push_back(p);
         inc_p[pairs[p].second].push_back(p);
     }
-    std::vector<int> owner(P, -1);                 // owning atom, -1: not owned
-    std::vector<char> sched(P, 0), done(N, 0);
-    std::vector<std::vector<int>> col(32);         // pair ids per lane, in slot order
-    std::vector<std::vector<char>> rowend(32);
-    const int share = (P + 31) / 32;
-    for (;;) {
-        int lane = 0;
-        for (int l = 1; l < 32; ++l)
-            if (col[l].size() < col[lane].size()) lane = l;
-        const int room = share - (int)col[lane].size();
-        if (room <= 0) break;
-        int best = -1, best_n = 0;
-        for (int a2 = 0; a2 < N; ++a2) {
-            if (done[a2]) continue;
-            int n2 = 0;
-            for (int p : inc_p[a2]) n2 += !sched[p];
-            if (n2 > best_n) { best = a2; best_n = n2; }
+    struct Row {
+        int owner;               // -1: one unowned pair
+        std::vector<int> ps;     // pair ids
+    };
+    std::vector<Row> rows;
+    std::vector<int> owner(P, -1);
+    {
+        std::vector<char> sched(P, 0), done(N, 0);
+        std::vector<int> load(32, 0);
+        const int share = (P + 31) / 32;
+        for (;;) {
+            const int lane = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            const int room = share - load[lane];
+            if (room <= 0) break;
+            int best = -1, best_n = 0;
+            for (int a2 = 0; a2 < N; ++a2) {
+                if (done[a2]) continue;
+                int n2 = 0;
+                for (int p : inc_p[a2]) n2 += !sched[p];
+                if (n2 > best_n) { best = a2; best_n = n2; }
+            }
+            if (best < 0) break;
+            Row r{best, {}};
+            for (int p : inc_p[best])
+                if (!sched[p] && done[pairs[p].first + pairs[p].second - best]) r.ps.push_back(p);
+            for (int p : inc_p[best])
+                if (!sched[p] && !done[pairs[p].first + pairs[p].second - best]) r.ps.push_back(p);
+            r.ps.resize(std::min((int)r.ps.size(), room));
+            for (int p : r.ps) {
+                owner[p] = best;
+                sched[p] = 1;
+            }
+            load[lane] += (int)r.ps.size();
+            done[best] = 1;
+            rows.push_back(r);
         }
-        if (best < 0) break;
-        std::vector<int> cand;
-        for (int p : inc_p[best])  // partner already owns a row: only this row can take the pair
-            if (!sched[p] && done[pairs[p].first + pairs[p].second - best]) cand.push_back(p);
-        for (int p : inc_p[best])
-            if (!sched[p] && !done[pairs[p].first + pairs[p].second - best]) cand.push_back(p);
-        const int take = std::min(room, (int)cand.size());
-        for (int q = 0; q < take; ++q) {
-            owner[cand[q]] = best;
-            sched[cand[q]] = 1;
-            col[lane].push_back(cand[q]);
-            rowend[lane].push_back(q + 1 == take);
-        }
-        done[best] = 1;
+        for (int p = 0; p < P; ++p)
+            if (!sched[p]) rows.push_back(Row{-1, {p}});
     }
-    for (int p = 0; p < P; ++p) {
-        if (sched[p]) continue;
-        int lane = 0;
-        for (int l = 1; l < 32; ++l)
-            if (col[l].size() < col[lane].size()) lane = l;
-        col[lane].push_back(p);
-        rowend[lane].push_back(0);
-        sched[p] = 1;
+    // Rows to lanes, longest first to the least loaded lane; among those,
+    // one whose quarter-warp holds no owner with the same atom index mod 8
+    // (a 16-byte shared-memory load by eight lanes is conflict-free when their
+    // atoms differ mod 8).
+    std::vector<std::vector<int>> lane_rows(32);
+    {
+        std::vector<int> order(rows.size());
+        for (size_t r = 0; r < rows.size(); ++r) order[r] = (int)r;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int x, int y) { return rows[x].ps.size() > rows[y].ps.size(); });
+        std::vector<int> load(32, 0);
+        std::vector<int> qres(4, 0);  // residues held per quarter (bit mask)
+        for (int r : order) {
+            const int m = *std::min_element(load.begin(), load.end());
+            const int res = rows[r].owner >= 0 ? rows[r].owner % 8 : -1;
+            int lane = -1;
+            for (int l = 0; l < 32 && lane < 0; ++l)
+                if (load[l] == m && (res < 0 || !(qres[l / 8] >> res & 1))) lane = l;
+            if (lane < 0)
+                for (int l = 0; l < 32 && lane < 0; ++l)
+                    if (load[l] == m) lane = l;
+            lane_rows[lane].push_back(r);
+            load[lane] += (int)rows[r].ps.size();
+            if (res >= 0) qres[lane / 8] |= 1 << res;
+        }
     }
     int nsteps = 0;
-    for (auto& v : col) nsteps = std::max(nsteps, (int)v.size());
+    for (int l = 0; l < 32; ++l) {
+        int n2 = 0;
+        for (int r : lane_rows[l]) n2 += (int)rows[r].ps.size();
+        nsteps = std::max(nsteps, n2);
+    }
     nsteps += nsteps & 1;  // the kernel runs two slots per step
+    // Slots, step by step: each lane takes the next pair of its current row,
+    // choosing among the row's remaining pairs a partner whose index mod 8 no
+    // earlier lane of its quarter-warp uses in this step.
     std::vector<int> slots((size_t)nsteps * 32, -1);
     std::vector<int> slot_flags((size_t)nsteps * 32, 0);
-    for (int l = 0; l < 32; ++l)
-        for (size_t k = 0; k < col[l].size(); ++k) {
-            slots[k * 32 + l] = col[l][k];
-            slot_flags[k * 32 + l] = (owner[col[l][k]] >= 0 ? kPairOwned : 0) | (rowend[l][k] ? kPairRowEnd : 0);
-        }
-    // --- force-gather program: every atom's (slot, partner) entries that its
-    // row does not cover go to one lane as a segment -- a header
-    // (atom | groups << 7) then its entries (partner | slot << 7) padded to a
-    // multiple of 4 with entries that point back at the atom itself (they add
-    // c * 0); atoms are dealt longest segment first to the least loaded lane
-    std::vector<std::vector<uint32_t>> inc(N);
+    {
+        std::vector<int> ri(32, 0), pi(32, 0);  // row index in the lane's list, position in the row
+        std::vector<std::vector<int>> rem(32);  // remaining pairs of the current row
+        for (int st = 0; st < nsteps; ++st)
+            for (int qd = 0; qd < 4; ++qd) {
+                int used = 0;  // partner residues taken in this quarter and step
+                for (int l = qd * 8; l < qd * 8 + 8; ++l) {
+                    if (ri[l] >= (int)lane_rows[l].size()) continue;
+                    const Row& r = rows[lane_rows[l][ri[l]]];
+                    if (pi[l] == 0) rem[l] = r.ps;
+                    const int i0 = r.owner >= 0 ? r.owner : pairs[r.ps[0]].first;
+                    int pick = 0;
+                    for (size_t k = 0; k < rem[l].size(); ++k) {
+                        const int pt = pairs[rem[l][k]].first + pairs[rem[l][k]].second - i0;
+                        if (!(used >> (pt % 8) & 1)) {
+                            pick = (int)k;
+                            break;
+                        }
+                    }
+                    const int p = rem[l][pick];
+                    rem[l].erase(rem[l].begin() + pick);
+                    const int pt = pairs[p].first + pairs[p].second - i0;
+                    used |= 1 << (pt % 8);
+                    slots[(size_t)st * 32 + l] = p;
+                    int fl = r.owner >= 0 ? kPairOwned : 0;
+                    if (pi[l] == 0) fl |= kPairRowStart;
+                    if (rem[l].empty()) {
+                        if (r.owner >= 0) fl |= kPairRowEnd;
+                        ++ri[l];
+                        pi[l] = 0;
+                    } else {
+                        ++pi[l];
+                    }
+                    slot_flags[(size_t)st * 32 + l] = fl;
+                }
+            }
+    }
+    // --- force-gather program: every atom's (partner, slot) entries that its
+    // row does not cover go to one lane, in groups of four (the last group
+    // padded with entries whose partner is the atom itself: they add c * 0).
+    // Atoms are dealt longest list first to the least loaded lane, preferring a
+    // quarter-warp without an atom of the same index mod 8; within an atom's
+    // entries, each group position takes the entry whose partner (mod 8, in
+    // the quarter) and pair slot (mod 32, the c bank, in the warp) earlier
+    // lanes have used least.  Entry = partner | atom << 7 | slot << 14, bit 30
+    // on the first entry of an atom's first group, bit 31 on the last entry
+    // of its last group.  Every lane runs the same number of groups (empty
+    // groups are all zero and never stored).
+    std::vector<std::vector<std::pair<int, int>>> inc(N);
     for (int sl = 0; sl < (int)slots.size(); ++sl) {
         const int p = slots[sl];
         if (p < 0) continue;
         const int i = pairs[p].first, j = pairs[p].second;
-        if (owner[p] != i) inc[i].push_back((uint32_t)j | ((uint32_t)sl << 7));
-        if (owner[p] != j) inc[j].push_back((uint32_t)i | ((uint32_t)sl << 7));
+        if (owner[p] != i) inc[i].emplace_back(j, sl);
+        if (owner[p] != j) inc[j].emplace_back(i, sl);
     }
     std::vector<int> by_deg(N);
     for (int i = 0; i < N; ++i) by_deg[i] = i;
     std::stable_sort(by_deg.begin(), by_deg.end(), [&](int x, int y) { return inc[x].size() > inc[y].size(); });
-    std::vector<std::vector<uint32_t>> lane_list(32);
-    for (int i : by_deg) {
-        if (inc[i].empty()) continue;
-        const uint32_t groups = (uint32_t)((inc[i].size() + 3) / 4);
-        int best = 0;
-        for (int l = 1; l < 32; ++l)
-            if (lane_list[l].size() < lane_list[best].size()) best = l;
-        auto& v = lane_list[best];
-        v.push_back((uint32_t)i | (groups << 7));
-        v.insert(v.end(), inc[i].begin(), inc[i].end());
-        for (size_t k = inc[i].size(); k < 4 * groups; ++k) v.push_back((uint32_t)i);  // partner = itself, slot 0
+    std::vector<std::vector<int>> lane_atoms(32);
+    std::vector<int> gload(32, 0);
+    {
+        std::vector<int> qres(4, 0);
+        for (int i : by_deg) {
+            if (inc[i].empty()) continue;
+            const int m = *std::min_element(gload.begin(), gload.end());
+            int lane = -1;
+            for (int l = 0; l < 32 && lane < 0; ++l)
+                if (gload[l] == m && !(qres[l / 8] >> (i % 8) & 1)) lane = l;
+            if (lane < 0)
+                for (int l = 0; l < 32 && lane < 0; ++l)
+                    if (gload[l] == m) lane = l;
+            lane_atoms[lane].push_back(i);
+            gload[lane] += (int)(inc[i].size() + 3) / 4;
+            qres[lane / 8] |= 1 << (i % 8);
+        }
     }
-    int gsteps = 1;  // room for the terminating pad
-    for (auto& v : lane_list) gsteps = std::max(gsteps, (int)v.size() + 1);
-    std::vector<uint32_t> gent((size_t)gsteps * 32, kGatherPad);
-    for (int l = 0; l < 32; ++l)
-        for (size_t k = 0; k < lane_list[l].size(); ++k) gent[k * 32 + l] = lane_list[l][k];
+    const int ngroups = *std::max_element(gload.begin(), gload.end());
+    std::vector<uint32_t> gent((size_t)ngroups * 128, 0u);
+    {
+        std::vector<int> ai(32, 0), left(32, 0);           // atom index in the lane's list, groups left
+        std::vector<std::vector<std::pair<int, int>>> pool(32);  // entries of the current atom not yet placed
+        for (int k = 0; k < ngroups; ++k) {
+            std::vector<int> first(32, 0);
+            for (int l = 0; l < 32; ++l) {
+                if (ai[l] >= (int)lane_atoms[l].size()) continue;
+                if (left[l] == 0) {
+                    const int a2 = lane_atoms[l][ai[l]];
+                    pool[l] = inc[a2];
+                    while (pool[l].size() % 4) pool[l].emplace_back(a2, 0);  // self entries add c * 0
+                    left[l] = (int)pool[l].size() / 4;
+                    first[l] = 1;
+                }
+            }
+            for (int q = 0; q < 4; ++q) {
+                std::vector<int> cbank(32, 0);
+                std::vector<std::vector<int>> res(4, std::vector<int>(8, 0));
+                for (int l = 0; l < 32; ++l) {
+                    if (ai[l] >= (int)lane_atoms[l].size()) continue;
+                    const int a2 = lane_atoms[l][ai[l]];
+                    int pick = 0, best_cost = 1 << 30;
+                    for (size_t t = 0; t < pool[l].size(); ++t) {
+                        const int cost = 4 * res[l / 8][pool[l][t].first % 8] + cbank[pool[l][t].second % 32];
+                        if (cost < best_cost) {
+                            best_cost = cost;
+                            pick = (int)t;
+                        }
+                    }
+                    const std::pair<int, int> en = pool[l][pick];
+                    pool[l].erase(pool[l].begin() + pick);
+                    res[l / 8][en.first % 8] += 1;
+                    cbank[en.second % 32] += 1;
+                    uint32_t e = (uint32_t)en.first | ((uint32_t)a2 << 7) | ((uint32_t)en.second << 14);
+                    if (q == 0 && first[l]) e |= 0x40000000u;
+                    if (q == 3 && left[l] == 1) e |= 0x80000000u;
+                    gent[(size_t)k * 128 + q * 32 + l] = e;
+                }
+            }
+            for (int l = 0; l < 32; ++l) {
+                if (ai[l] >= (int)lane_atoms[l].size()) continue;
+                if (--left[l] == 0) ++ai[l];
+            }
+        }
+    }
     // --- device header
     LigandDev h;
     memset(&h, 0, sizeof(h));
@@ -584,7 +699,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     h.ntors = T;
     h.npairs = P;
     h.nsteps = nsteps;
-    h.gsteps = gsteps;
+    h.gsteps = ngroups;
     double c[3] = {0, 0, 0};
     for (int i = 0; i < N; ++i)
         for (int a = 0; a < 3; ++a) c[a] += d->xyz[3 * i + a];

@@ -18,7 +18,6 @@ constexpr int kMaxAtoms = ADG_MAX_ATOMS;
 constexpr int kMaxTors = ADG_MAX_TORS;
 constexpr int kGeneStride = 24;  // population rows are padded to 24 floats (>= 7 + 16)
 constexpr int kMaxWarpsPerBlock = 12;
-constexpr uint32_t kGatherPad = 0xffffffffu;
 
 // Per-warp shared memory (floats): xyz[na], f[na] and pm[na] (float4 each),
 // the fragment transforms W[52] (float4, three rows per fragment), genes,
@@ -46,7 +45,7 @@ struct Geo {
 // hangs from fragment fpar[f] on torsion ftor[f], at depth flev[f].
 struct LigandDev {
     int natoms, ntors, npairs, nsteps;   // nsteps: pair slots per lane (even)
-    int gsteps;                          // length of the longest per-lane force-gather list
+    int gsteps;                          // force-gather groups per lane
     int nfrag, maxlev;                   // fragments (ntors + 1) and the deepest level
     // the blob: this header, then the pair and gather arrays at these byte offsets
     int blob_bytes, off_ij, off_coef, off_cd, off_gent;
@@ -64,21 +63,24 @@ struct LigandDev {
 };
 
 // Intramolecular pairs, lane-interleaved: slot (step, lane) = step * 32 + lane.
-// ij = i | j << 16 | kPairOwned | kPairRowEnd (an empty slot pairs atom 0 with
-// itself, with zero coefficients, and no flag).  coef = (c12, c6, c10, cq):
+// ij = i | j << 16 | kPairOwned | kPairRowEnd | kPairRowStart (an empty slot is
+// 0: zero coefficients, no flag).  Atom i is the same for a whole row, so a
+// lane reads its coordinates only at the row's first slot.  coef = (c12, c6, c10, cq):
 // E_pair = min(c12 r^-12 - c6 r^-6 - c10 r^-10, e_cap) + cq / (eps(r) r) + cd exp(-r^2/(2 s^2)).
 // Forces.  Most pairs are owned by atom i: the pairs a lane runs are grouped
 // into rows, one row per owning atom, each row on one lane only, so the lane
 // sums c_p (x_i - x_j) in registers and stores it to f[i] at the row's last
 // slot (kPairRowEnd).  Everything else -- the partner side of owned pairs, and
 // both sides of the few pairs no row could take -- goes through the force
-// gather: after the pair pass has stored c_p of every slot, lane l walks its
-// list gent[k * 32 + l]: segments of a header atom | groups << 7 followed by
-// 4 * groups entries partner | slot << 7 (padded with entries whose partner
-// is the atom itself), ended by kGatherPad, and adds sum c_p (x_atom -
-// x_partner) to f[atom].
+// gather: after the pair pass has stored c_p of every slot, lane l runs
+// gsteps groups of four entries gent[(k * 4 + q) * 32 + l] = partner |
+// atom << 7 | slot << 14 (one atom per group; bit 30 on the first entry of the
+// atom's first group, bit 31 on the last entry of its last group; lists padded
+// with entries whose partner is the atom itself, and all-zero groups at the
+// end), and adds sum c_p (x_atom - x_partner) to f[atom].
 constexpr int kPairOwned = 1 << 15;
 constexpr int kPairRowEnd = 1 << 14;
+constexpr int kPairRowStart = 1 << 13;  // first slot of a row: (re)load atom i's coordinates
 struct PairsDev {
     const int* ij;
     const float4* coef;

@@ -459,12 +459,15 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     const float inv_2s2 = L->inv_2s2, inv_s2 = L->inv_s2;
     const int nsteps = L->nsteps;  // even
     float rfx = 0.f, rfy = 0.f, rfz = 0.f;
+    float4 xr = make_float4(0.f, 0.f, 0.f, 0.f);  // atom i of the current row
     float2 e2 = s2(0.f);
     for (int stp = 0; stp < nsteps; stp += 2) {
         const int ia = stp * 32 + lane, ib = ia + 32;
         const int ija = P.ij[ia], ijb = P.ij[ib];
-        const float4 xia = ws.xyz[ija & 127], xja = ws.xyz[(ija >> 16) & 127];
-        const float4 xib = ws.xyz[ijb & 127], xjb = ws.xyz[(ijb >> 16) & 127];
+        if (ija & kPairRowStart) xr = ws.xyz[ija & 127];
+        const float4 xia = xr, xja = ws.xyz[(ija >> 16) & 127];
+        if (ijb & kPairRowStart) xr = ws.xyz[ijb & 127];
+        const float4 xib = xr, xjb = ws.xyz[(ijb >> 16) & 127];
         const float2 dx = sub2(v2(xia.x, xib.x), v2(xja.x, xjb.x));
         const float2 dy = sub2(v2(xia.y, xib.y), v2(xja.y, xjb.y));
         const float2 dz = sub2(v2(xia.z, xib.z), v2(xja.z, xjb.z));
@@ -529,25 +532,28 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     if (!GRAD) return out;
     __syncwarp();
     // force gather: f_atom += sum over its pairs that its row did not cover of
-    // c_p (x_atom - x_partner), four independent entries per step
-    for (int k = 0;;) {
-        const uint32_t hdr = P.gent[k * 32 + lane];
-        if (hdr == kGatherPad) break;
-        const int atom = hdr & 127, groups = hdr >> 7;
-        ++k;
-        const float4 xa = ws.xyz[atom];
-        float ax = 0.f, ay = 0.f, az = 0.f;
-        for (int q = 0; q < groups; ++q, k += 4) {
-            const uint32_t e0 = P.gent[k * 32 + lane], e1 = P.gent[(k + 1) * 32 + lane],
-                           e2 = P.gent[(k + 2) * 32 + lane], e3 = P.gent[(k + 3) * 32 + lane];
-            const float c0 = ws.c[e0 >> 7], c1 = ws.c[e1 >> 7], c2 = ws.c[e2 >> 7], c3 = ws.c[e3 >> 7];
-            const float4 x0 = ws.xyz[e0 & 127], x1 = ws.xyz[e1 & 127], x2 = ws.xyz[e2 & 127], x3 = ws.xyz[e3 & 127];
-            ax += c0 * (xa.x - x0.x) + c1 * (xa.x - x1.x) + c2 * (xa.x - x2.x) + c3 * (xa.x - x3.x);
-            ay += c0 * (xa.y - x0.y) + c1 * (xa.y - x1.y) + c2 * (xa.y - x2.y) + c3 * (xa.y - x3.y);
-            az += c0 * (xa.z - x0.z) + c1 * (xa.z - x1.z) + c2 * (xa.z - x2.z) + c3 * (xa.z - x3.z);
+    // c_p (x_atom - x_partner); every lane runs the same number of groups of
+    // four entries, so consecutive groups' loads overlap
+    const int ngroups = L->gsteps;
+    float ax = 0.f, ay = 0.f, az = 0.f;
+    float4 xa = make_float4(0.f, 0.f, 0.f, 0.f);  // the current atom
+#pragma unroll 2
+    for (int k = 0; k < ngroups; ++k) {
+        const uint32_t* ge = P.gent + k * 128 + lane;
+        const uint32_t e0 = ge[0], e1 = ge[32], e2 = ge[64], e3 = ge[96];
+        const int atom = (e0 >> 7) & 127;
+        if (e0 & 0x40000000u) xa = ws.xyz[atom];
+        const float c0 = ws.c[(e0 >> 14) & 0xffff], c1 = ws.c[(e1 >> 14) & 0xffff],
+                    c2 = ws.c[(e2 >> 14) & 0xffff], c3 = ws.c[(e3 >> 14) & 0xffff];
+        const float4 x0 = ws.xyz[e0 & 127], x1 = ws.xyz[e1 & 127], x2 = ws.xyz[e2 & 127], x3 = ws.xyz[e3 & 127];
+        ax += c0 * (xa.x - x0.x) + c1 * (xa.x - x1.x) + c2 * (xa.x - x2.x) + c3 * (xa.x - x3.x);
+        ay += c0 * (xa.y - x0.y) + c1 * (xa.y - x1.y) + c2 * (xa.y - x2.y) + c3 * (xa.y - x3.y);
+        az += c0 * (xa.z - x0.z) + c1 * (xa.z - x1.z) + c2 * (xa.z - x2.z) + c3 * (xa.z - x3.z);
+        if (e3 >> 31) {  // the atom's last group: add to its row sum (or zero)
+            const float4 fr = ws.f[atom];
+            ws.f[atom] = make_float4(fr.x + ax, fr.y + ay, fr.z + az, 0.f);
+            ax = ay = az = 0.f;
         }
-        const float4 fr = ws.f[atom];  // the atom's row sum (or zero)
-        ws.f[atom] = make_float4(fr.x + ax, fr.y + ay, fr.z + az, 0.f);
     }
     __syncwarp();
     // Per atom: total force f and moment m = (x - t) x f.  Inclusive prefix
