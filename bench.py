@@ -207,7 +207,11 @@ TRIAGE_TRAIN, TRIAGE_STREAM = 1200, 2000
 #       -k regex:k_dock_generation -s 60 -c 2 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
 #       --no-e2e --no-batching --no-triage --no-graphs
 # (mean of the two launches); None whenever the kernel has changed since that capture.
-GEN_TRAFFIC_BYTES = None
+GEN_TRAFFIC_BYTES = 30.8e6
+# The pipe that bounds the kernel, from the full-section capture of the same
+# kernel (l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed):
+# the L1 / shared-memory data pipe.  None whenever the kernel has changed.
+GEN_L1_PIPE_FRAC = 0.715
 
 
 def run_plain_config(ctx, ff, reps=5):
@@ -411,6 +415,7 @@ def main():
     peak, peak_src = fp32_peak_tflops()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": GEN_TRAFFIC_BYTES, "traffic_unit": "bytes per launch (dram read + write)",
+                "l1_shared_pipe_frac_ncu": GEN_L1_PIPE_FRAC,
                 "kernel": "k_dock_generation<2,ADADELTA>",
                 "launch_ms": gen_ms_per_launch, "flops_per_launch": flops_per_launch,
                 "gen_share_of_step": st["gen_kernel_ms"] / total_ms if world == 1 else None,
