@@ -716,6 +716,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     h.inv_2s2 = (float)(1.0 / (2.0 * (double)ff->sigma * ff->sigma));
     h.inv_s2 = (float)(1.0 / ((double)ff->sigma * ff->sigma));
     h.k_out = ff->k_out;
+    h.wq = (float)((double)ff->w_elec * ff->coulomb);
     for (int n = 0; n < N; ++n) {
         const int i = old_of[n];
         h.ref[n] = make_float4(d->xyz[3 * i], d->xyz[3 * i + 1], d->xyz[3 * i + 2], d->charge[i]);
@@ -743,12 +744,9 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         h.tpt[k] = make_float4(pa[0], pa[1], pa[2], 0.f);
         h.tax[k] = make_float4((float)(u[0] / un), (float)(u[1] / un), (float)(u[2] / un), 0.f);
     }
-    // --- pair arrays in slot order
+    // --- pair records in slot order
     const int ns = nsteps * 32;
-    std::vector<int> ij(ns, 0);  // empty slots: atom 0 with itself, zero coefficients (adds 0)
-    std::vector<float4> coef(ns, make_float4(0, 0, 0, 0));
-    std::vector<float> cd(ns, 0.f);
-    const double wq = (double)ff->w_elec * ff->coulomb;
+    std::vector<float4> pk(ns, make_float4(0, 0, 0, 0));  // empty slots: all zero (add 0)
     for (int s = 0; s < ns; ++s) {
         const int p = slots[s];
         if (p < 0) continue;
@@ -759,29 +757,26 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         const double qi = d->charge[old_of[i]], qj = d->charge[old_of[j]];
         float c12, c6, c10;
         pair_coefs(*ff, ti, tj, &c12, &c6, &c10);
-        ij[s] = i | (j << 16) | slot_flags[s];
-        coef[s] = make_float4(c12, c6, c10, (float)(wq * qi * qj));
-        cd[s] = (float)((double)ff->w_desolv * (((double)ff->solpar[ti] + (double)ff->qasp * fabs(qi)) * ff->vol[tj] +
-                                                ((double)ff->solpar[tj] + (double)ff->qasp * fabs(qj)) * ff->vol[ti]));
+        const bool hb = c10 != 0.f;
+        const int ij = i | (j << 16) | slot_flags[s] | (hb ? kPairHB : 0);
+        const float cd = (float)((double)ff->w_desolv * (((double)ff->solpar[ti] + (double)ff->qasp * fabs(qi)) * ff->vol[tj] +
+                                                         ((double)ff->solpar[tj] + (double)ff->qasp * fabs(qj)) * ff->vol[ti]));
+        float ijf;
+        memcpy(&ijf, &ij, sizeof(float));
+        pk[s] = make_float4(c12, hb ? c10 : c6, cd, ijf);
     }
-    const size_t off_ij = align_up(sizeof(LigandDev), 256);
-    const size_t off_coef = align_up(off_ij + sizeof(int) * ns, 256);
-    const size_t off_cd = align_up(off_coef + sizeof(float4) * ns, 256);
-    const size_t off_gent = align_up(off_cd + sizeof(float) * ns, 256);
+    const size_t off_pk = align_up(sizeof(LigandDev), 256);
+    const size_t off_gent = align_up(off_pk + sizeof(float4) * ns, 256);
     const size_t bytes = align_up(off_gent + sizeof(uint32_t) * gent.size(), 256);
     h.blob_bytes = (int)bytes;
-    h.off_ij = (int)off_ij;
-    h.off_coef = (int)off_coef;
-    h.off_cd = (int)off_cd;
+    h.off_pk = (int)off_pk;
     h.off_gent = (int)off_gent;
     CK(ctx, cudaSetDevice(ctx->device));
     adg_ligand* L = new (std::nothrow) adg_ligand();
     if (!L) return ADG_ENOMEM;
     std::vector<char> host(bytes, 0);
     memcpy(host.data(), &h, sizeof(h));
-    memcpy(host.data() + off_ij, ij.data(), sizeof(int) * ns);
-    memcpy(host.data() + off_coef, coef.data(), sizeof(float4) * ns);
-    memcpy(host.data() + off_cd, cd.data(), sizeof(float) * ns);
+    memcpy(host.data() + off_pk, pk.data(), sizeof(float4) * ns);
     memcpy(host.data() + off_gent, gent.data(), sizeof(uint32_t) * gent.size());
     cudaError_t e = cudaMalloc(&L->blob, bytes);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L->blob, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
@@ -795,9 +790,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     L->ctx = ctx;
     L->device = ctx->device;
     L->ref.hdr = (const LigandDev*)base;
-    L->ref.pairs.ij = (const int*)(base + off_ij);
-    L->ref.pairs.coef = (const float4*)(base + off_coef);
-    L->ref.pairs.cd = (const float*)(base + off_cd);
+    L->ref.pairs.pk = (const float4*)(base + off_pk);
     L->ref.pairs.gent = (const uint32_t*)(base + off_gent);
     L->nslots = ns;
     L->natoms = N;

@@ -48,10 +48,11 @@ struct LigandDev {
     int gsteps;                          // force-gather groups per lane
     int nfrag, maxlev;                   // fragments (ntors + 1) and the deepest level
     // the blob: this header, then the pair and gather arrays at these byte offsets
-    int blob_bytes, off_ij, off_coef, off_cd, off_gent;
+    int blob_bytes, off_pk, off_gent;
     float cx, cy, cz;                    // reference centroid
     // scoring constants (from the force field)
     float e_cap, rmin2, ms_A, ms_B, ms_k, ms_lb, inv_2s2, inv_s2, k_out;
+    float wq;                            // w_elec * Coulomb constant: cq = wq q_i q_j
     float4 ref[kMaxAtoms];               // reference x, y, z and charge q (internal order)
     int tf[kMaxAtoms];                   // map type | fragment << 8
     int old_of_new[kMaxAtoms];           // caller's index of internal atom i
@@ -62,11 +63,14 @@ struct LigandDev {
     int fpar[kMaxTors + 1], ftor[kMaxTors + 1], flev[kMaxTors + 1];
 };
 
-// Intramolecular pairs, lane-interleaved: slot (step, lane) = step * 32 + lane.
-// ij = i | j << 16 | kPairOwned | kPairRowEnd | kPairRowStart (an empty slot is
-// 0: zero coefficients, no flag).  Atom i is the same for a whole row, so a
-// lane reads its coordinates only at the row's first slot.  coef = (c12, c6, c10, cq):
-// E_pair = min(c12 r^-12 - c6 r^-6 - c10 r^-10, e_cap) + cq / (eps(r) r) + cd exp(-r^2/(2 s^2)).
+// Intramolecular pairs, lane-interleaved: slot (step, lane) = step * 32 + lane,
+// one 16-byte record per slot: pk = (c12, cm, cd, ij as bits) with
+// ij = i | j << 16 | kPairOwned | kPairRowEnd | kPairRowStart | kPairHB (an
+// empty slot is all zero: zero coefficients, no flag).  Atom i is the same for
+// a whole row, so a lane reads its coordinates only at the row's first slot.
+// With m = 10 for H-bond pairs (kPairHB) and 6 otherwise, and cq = wq q_i q_j
+// from the charges the posed coordinates carry in .w:
+// E_pair = min(c12 r^-12 - cm r^-m, e_cap) + cq / (eps(r) r) + cd exp(-r^2/(2 s^2)).
 // Forces.  Most pairs are owned by atom i: the pairs a lane runs are grouped
 // into rows, one row per owning atom, each row on one lane only, so the lane
 // sums c_p (x_i - x_j) in registers and stores it to f[i] at the row's last
@@ -81,10 +85,9 @@ struct LigandDev {
 constexpr int kPairOwned = 1 << 15;
 constexpr int kPairRowEnd = 1 << 14;
 constexpr int kPairRowStart = 1 << 13;  // first slot of a row: (re)load atom i's coordinates
+constexpr int kPairHB = 1 << 12;        // 12-10 H-bond pair (else 12-6)
 struct PairsDev {
-    const int* ij;
-    const float4* coef;
-    const float* cd;
+    const float4* pk;
     const uint32_t* gent;
 };
 

@@ -283,9 +283,7 @@ __device__ __forceinline__ LigandRef stage_ligand(const LigandRef& g, int lig_by
     const LigandDev* L = reinterpret_cast<const LigandDev*>(b);
     LigandRef r;
     r.hdr = L;
-    r.pairs.ij = reinterpret_cast<const int*>(b + L->off_ij);
-    r.pairs.coef = reinterpret_cast<const float4*>(b + L->off_coef);
-    r.pairs.cd = reinterpret_cast<const float*>(b + L->off_cd);
+    r.pairs.pk = reinterpret_cast<const float4*>(b + L->off_pk);
     r.pairs.gent = reinterpret_cast<const uint32_t*>(b + L->off_gent);
     return r;
 }
@@ -366,7 +364,7 @@ __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const
             const int f = L->tf[a] >> 8;
             const float4 w0 = ws.W[3 * f], w1 = ws.W[3 * f + 1], w2 = ws.W[3 * f + 2];
             ws.xyz[a] = make_float4(w0.x * r.x + w0.y * r.y + w0.z * r.z + w0.w, w1.x * r.x + w1.y * r.y + w1.z * r.z + w1.w,
-                                    w2.x * r.x + w2.y * r.y + w2.z * r.z + w2.w, 0.f);
+                                    w2.x * r.x + w2.y * r.y + w2.z * r.z + w2.w, r.w);  // .w: the charge
         }
     }
     __syncwarp();
@@ -456,14 +454,15 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     // (one instruction for both); the force on a row owner accumulates in
     // registers and is stored at the row's end
     const float cap = L->e_cap, rmin2 = L->rmin2, msA = L->ms_A, msB = L->ms_B, msk = L->ms_k, mslb = L->ms_lb;
-    const float inv_2s2 = L->inv_2s2, inv_s2 = L->inv_s2;
+    const float inv_2s2 = L->inv_2s2, inv_s2 = L->inv_s2, wq = L->wq;
     const int nsteps = L->nsteps;  // even
     float rfx = 0.f, rfy = 0.f, rfz = 0.f;
     float4 xr = make_float4(0.f, 0.f, 0.f, 0.f);  // atom i of the current row
     float2 e2 = s2(0.f);
     for (int stp = 0; stp < nsteps; stp += 2) {
         const int ia = stp * 32 + lane, ib = ia + 32;
-        const int ija = P.ij[ia], ijb = P.ij[ib];
+        const float4 pa = P.pk[ia], pb = P.pk[ib];
+        const int ija = __float_as_int(pa.w), ijb = __float_as_int(pb.w);
         if (ija & kPairRowStart) xr = ws.xyz[ija & 127];
         const float4 xia = xr, xja = ws.xyz[(ija >> 16) & 127];
         if (ijb & kPairRowStart) xr = ws.xyz[ijb & 127];
@@ -472,9 +471,9 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const float2 dy = sub2(v2(xia.y, xib.y), v2(xja.y, xjb.y));
         const float2 dz = sub2(v2(xia.z, xib.z), v2(xja.z, xjb.z));
         const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-        const float4 ca = P.coef[ia], cb = P.coef[ib];
-        const float2 c12 = v2(ca.x, cb.x), c6 = v2(ca.y, cb.y), c10 = v2(ca.z, cb.z), cq = v2(ca.w, cb.w);
-        const float2 cd = v2(P.cd[ia], P.cd[ib]);
+        const float2 c12 = v2(pa.x, pb.x), cm = v2(pa.y, pb.y), cd = v2(pa.z, pb.z);
+        // cq = wq q_i q_j; an empty slot (ij == 0; a real pair has i != j) adds nothing
+        const float2 cq = mul2(mul2(v2(ija ? wq : 0.f, ijb ? wq : 0.f), v2(xia.w, xib.w)), v2(xja.w, xjb.w));
         const bool fla = r2.x < rmin2, flb = r2.y < rmin2;
         const float2 rr2 = v2(fla ? rmin2 : r2.x, flb ? rmin2 : r2.y);
         const float2 ri = v2(rsqrtf(rr2.x), rsqrtf(rr2.y));
@@ -482,8 +481,10 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const float2 ri2 = mul2(ri, ri);
         const float2 ri4 = mul2(ri2, ri2);
         const float2 ri6 = mul2(ri4, ri2), ri12 = mul2(ri6, ri6), ri10 = mul2(ri6, ri4);
-        const float2 a12 = mul2(c12, ri12), a6 = mul2(c6, ri6), a10 = mul2(c10, ri10);
-        const float2 elj = sub2(sub2(a12, a6), a10);
+        const float2 rim = v2((ija & kPairHB) ? ri10.x : ri6.x, (ijb & kPairHB) ? ri10.y : ri6.y);
+        const float2 km = v2((ija & kPairHB) ? 10.f : 6.f, (ijb & kPairHB) ? 10.f : 6.f);
+        const float2 a12 = mul2(c12, ri12), am = mul2(cm, rim);
+        const float2 elj = sub2(a12, am);
         const float2 ex = v2(__expf(-mslb * r.x), __expf(-mslb * r.y));
         const float2 den = fma2(s2(msk), ex, s2(1.f));
         const float2 D = fma2(s2(msA), den, s2(msB));  // eps(r) = D / den
@@ -494,7 +495,7 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const float2 eds = mul2(cd, gs);
         if (GRAD) {
             // (dE/dr) / r of the three terms
-            float2 dlj = mul2(fma2(s2(10.f), a10, fma2(s2(6.f), a6, mul2(s2(-12.f), a12))), ri2);
+            float2 dlj = mul2(fma2(km, am, mul2(s2(-12.f), a12)), ri2);
             if (elj.x > cap) dlj.x = 0.f;
             if (elj.y > cap) dlj.y = 0.f;
             const float2 dden = mul2(s2(-mslb * msk), ex);
