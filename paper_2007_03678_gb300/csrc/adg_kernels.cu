@@ -1055,9 +1055,17 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
         nev = 1;
     }
     // local search on this individual with probability ls_rate (Lamarckian write-back)
-    int ls_applied = 0;
-    if (LS != ADG_LS_NONE && ptest(rng.block(P_LSPICK, 0).x, S.thr_ls)) {
-        ls_applied = 1;
+    const bool ls_applied = LS != ADG_LS_NONE && ptest(rng.block(P_LSPICK, 0).x, S.thr_ls);
+    // the decision record is written before the local search, so none of its
+    // fields stays live across it
+    const bool traced = Dk.trace_ngen > 0 && gen <= Dk.trace_ngen && lig == 0;
+    const long slot = ((long)run * Dk.trace_ngen + (gen - 1)) * pop + ind;
+    if (traced && lane == 0) {
+        int* d = Dk.tr_dec + slot * ADG_TRACE_WIDTH;
+        d[0] = p1; d[1] = p2; d[2] = lo; d[3] = hi; d[4] = mmask; d[5] = ls_applied ? 1 : 0;
+        d[6] = a1; d[7] = b1; d[8] = a2; d[9] = b2; d[10] = 0; d[11] = 0;
+    }
+    if (ls_applied) {
         if (LS == ADG_LS_SOLIS_WETS) nev += warp_solis_wets<APL>(L, LR.pairs, M, S, rng, ws, e, lane);
         else nev += warp_adadelta<APL>(L, LR.pairs, M, S, ws, e, lane);
     }
@@ -1067,14 +1075,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
         Dk.pop_e[gen & 1][(long)run_g * pop + ind] = e;
         atomicAdd(&Dk.evals[nruns + run_g], (unsigned long long)nev);
     }
-    if (Dk.trace_ngen > 0 && gen <= Dk.trace_ngen && lig == 0) {
-        const long slot = ((long)run * Dk.trace_ngen + (gen - 1)) * pop + ind;
-        if (lane == 0) {
-            int* d = Dk.tr_dec + slot * ADG_TRACE_WIDTH;
-            d[0] = p1; d[1] = p2; d[2] = lo; d[3] = hi; d[4] = mmask; d[5] = ls_applied;
-            d[6] = a1; d[7] = b1; d[8] = a2; d[9] = b2; d[10] = 0; d[11] = 0;
-            Dk.tr_e[slot] = e;
-        }
+    if (traced) {
+        if (lane == 0) Dk.tr_e[slot] = e;
         if (lane < G) Dk.tr_genes[slot * kGeneStride + lane] = ws.genes[lane];
     }
 }
