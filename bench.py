@@ -152,7 +152,7 @@ def oracle_maps_file() -> str:
 
 
 ORACLE_SAMPLE_NEV = 150 + 45150  # initial population + one ADADELTA generation
-BATCH_LIGANDS, BATCH_NRUN, BATCH_NEV = 64, 20, 100_000
+BATCH_LIGANDS, BATCH_NRUN, BATCH_NEV = 256, 20, 100_000
 
 
 def cpu_cores() -> int:
@@ -441,7 +441,7 @@ def main():
     # batching (shape classes on concurrent streams, one graph each) against one call per ligand
     batching = None
     if not args.no_batching:
-        bl = S.make_batch(BATCH_LIGANDS, seed=7)
+        bl = S.make_batch(BATCH_LIGANDS, seed=7, workers=0)
         BL = [adg.Ligand(ctx, ff, l) for l in bl]
         bp = adg.search_params(nrun=BATCH_NRUN, pop_size=150, nev=BATCH_NEV, ls_method=adg.LS_ADADELTA,
                                seed=S.SEARCH_SEED)

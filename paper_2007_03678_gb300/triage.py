@@ -32,13 +32,13 @@ NTRACE_FEATURES = 2  # per early generation: best over runs, mean over runs
 class TriageConfig:
     nrun: int = 10
     pop: int = 150
-    max_gen: int = 30          # the full search
-    early_gen: int = 3         # the early search: the first tenth of the generations
+    max_gen: int = 50          # the full search
+    early_gen: int = 5         # the early search: the first tenth of the generations
     ls_max_iters: int = 20
     ls_method: int = adg.LS_ADADELTA
     seed: int = 42
     top_frac: float = 0.01     # the screen's hits: the best 1% by final energy
-    keep_frac: float = 0.25    # full search for the best-predicted quarter of a stream
+    keep_frac: float = 0.10    # full search for the best-predicted tenth of a stream
     epochs: int = 100
     batch: int = 64
     lr: float = 1e-3
