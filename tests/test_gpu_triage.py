@@ -95,3 +95,25 @@ def test_triage_pipeline_recall_and_gain(ctx, ff):
     # the early features of the screen are those of the full runs' first generations
     feats, _, _ = T.dock_early(ctx, R, LS[:50], cfg)
     assert np.array_equal(feats, x_st[:50])
+
+
+def test_best_trace_after_autostop_and_rigid_descriptors(ctx, ff):
+    """A run that autostop ends early repeats its final best energy in the
+    rest of the trace; a rigid ligand has one fragment and no moving atoms."""
+    from paper_2007_03678_gb300 import adg
+    grid, rec, _, _, maps32 = problem("paper")
+    R = adg.Receptor(ctx, grid, maps32)
+    L = adg.Ligand(ctx, ff, S.make_ligand(20, 3, 7100))
+    K = 40
+    p = adg.search_params(nrun=6, pop_size=40, nev=10 ** 7, max_gen=K, ls_method=adg.LS_SOLIS_WETS,
+                          ls_max_iters=20, seed=3, autostop=1, stopstd=1.0)
+    r = adg.dock(ctx, R, L, p, best_trace=K)[0]
+    tr = r["best_trace"]
+    assert (r["generations"] < K).any()  # autostop fired somewhere
+    for run in range(6):
+        g = int(r["generations"][run])
+        assert np.all(tr[run, g - 1:] == r["best_energy"][run])
+        assert np.all(np.diff(tr[run, :g]) <= 0)
+    rigid = adg.Ligand(ctx, ff, S.make_ligand(15, 0, 7200))
+    d = rigid.descriptors()
+    assert d[1] == 0 and d[14] == 1 and d[15] == 0

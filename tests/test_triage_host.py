@@ -1,0 +1,52 @@
+"""Host-side logic of the triage pipeline (no GPU): the energy squash, the
+feature rows, the survival rule and the recall measure."""
+import numpy as np
+
+from paper_2007_03678_gb300 import triage as T
+
+
+def test_squash_is_monotone_and_keeps_the_bound_region():
+    e = np.array([-20.0, -3.5, -1e-9, 0.0, 1e-9, 0.5, 10.0, 1e5])
+    s = T.squash(e)
+    assert np.all(np.diff(s) > 0) or np.all(np.diff(s) >= 0)
+    assert np.array_equal(s[:4], e[:4])
+    assert np.isclose(s[-1], np.log1p(1e5))
+    assert np.isclose(s[5], np.log1p(0.5))
+
+
+def test_features_layout():
+    rng = np.random.default_rng(0)
+    n, nrun, K = 5, 4, 3
+    desc = rng.normal(size=(n, 16))
+    tr = -np.sort(rng.uniform(0, 10, size=(n, nrun, 7)), axis=2)  # non-increasing traces
+    tr[0, 2, :] = 1e4                                              # a run stuck in a clash
+    x = T.features(desc, tr, K)
+    assert x.shape == (n, 16 + 2 * K) and x.dtype == np.float32
+    assert np.allclose(x[:, :16], desc, atol=1e-6)
+    sq = T.squash(tr[:, :, :K])
+    assert np.allclose(x[:, 16:16 + K], sq.min(axis=1), atol=1e-5)
+    assert np.allclose(x[:, 16 + K:], sq.mean(axis=1), atol=1e-5)
+    assert x[0, 16 + K] < 5  # the clash run enters the mean as log(1 + 1e4), not 1e4
+
+
+def test_keep_best_and_recall():
+    score = np.array([3.0, -1.0, 2.0, -5.0, 0.0, -5.0])
+    keep = T.keep_best(score, 0.5)
+    assert keep.sum() == 3 and keep[3] and keep[5] and keep[1]
+    assert T.keep_best(score, 0.0).sum() == 0 and T.keep_best(score, 1.0).all()
+    true_e = np.arange(100, dtype=float)          # ligand 0 is the best
+    keep = np.zeros(100, bool)
+    keep[:1] = True
+    assert T.recall(true_e, keep, 0.01) == 1.0    # top 1 % = ligand 0
+    assert T.recall(true_e, keep, 0.02) == 0.5
+    assert T.recall(true_e, ~keep, 0.01) == 0.0
+
+
+def test_config_defaults():
+    from paper_2007_03678_gb300 import build
+    build.build()  # search_params reads the library's defaults
+    cfg = T.TriageConfig()
+    assert cfg.early_gen * 10 == cfg.max_gen       # the early search is the first tenth
+    assert cfg.nin == 16 + 2 * cfg.early_gen <= 32  # fits the network's input width
+    p = cfg.params(cfg.early_gen)
+    assert p.max_gen == cfg.early_gen and p.nrun == cfg.nrun and p.ls_method == cfg.ls_method

@@ -54,3 +54,30 @@ def test_noalloc_rejects_oversized_requests(ctx, ff):
         with pytest.raises(adg.AdgError) as ei:
             adg.dock_noalloc(R, L, p)
         assert ei.value.code == -3
+
+
+def test_no_alloc_docking_keeps_a_fixed_stream_id():
+    """adg_ligand_set_stream_id applies to the no-allocation entry point too."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2007_03678_gb300 import adg, build
+    from paper_2007_03678_gb300 import synth as S
+    from gpu_common import problem
+    build.build()
+    ctx = adg.Context(0)
+    ff = S.forcefield()
+    grid, rec, lig, _, maps32 = problem("plain")
+    R = adg.Receptor(ctx, grid, maps32)
+    L = adg.Ligand(ctx, ff, lig)
+    L.set_stream_id(4242)
+    p = adg.search_params(nrun=3, pop_size=40, nev=4000, ls_method=adg.LS_SOLIS_WETS, ls_max_iters=20, seed=8,
+                          lig_id=7)
+    a = adg.dock_noalloc(R, L, p, stream=ctx.stream)
+    L.set_stream_id(-1)
+    q = adg.search_params(nrun=3, pop_size=40, nev=4000, ls_method=adg.LS_SOLIS_WETS, ls_max_iters=20, seed=8,
+                          lig_id=4242)
+    b = adg.dock(ctx, R, L, q)[0]
+    for key in ("best_energy", "genes", "evals", "generations"):
+        assert np.array_equal(a[key], b[key]), key
+    ctx.close()
