@@ -426,10 +426,12 @@ struct ScoreOut {
 
 // Energy (and gradient) of the genotype in shared memory `g`.
 //  1. pose (lanes own atoms), 2. intermolecular gather (lanes own atoms),
-//  3. pair terms (lanes own pair slots; the gradient pass stores
-//     c_p = (dE/dr)/r per slot), 4. force gather per atom from c_p (no
-//     atomics: each atom belongs to one lane's gather list), 5. one
-//     transposed warp reduction of dE/dt, the torque and every dE/dtheta.
+//  3. pair terms (lanes own rows of pair slots; the gradient pass stores
+//     c_p = (dE/dr)/r per slot and sums each row owner's force in
+//     registers), 4. force gather of the partner sides from c_p (no
+//     atomics: each atom belongs to one lane's gather list), 5. prefix sums
+//     over the depth-first atom order and one transposed warp reduction of
+//     dE/dt, the torque and every dE/dtheta.
 template <int APL, bool GRAD>
 __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, const PairsDev& P, const MapsDev& M,
                                                const float* g, const WarpView& ws, int lane)
