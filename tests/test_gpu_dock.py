@@ -236,3 +236,30 @@ def test_autostop_applies_the_rule(ctx, A, ff):
         stopped += g < ngen
     assert stopped >= 1
     assert res_on[0]["evals"].sum() < res_off["evals"].sum()
+
+
+def test_paper_scale_bench_configuration_sampled_against_oracle(ctx, A, ff):
+    """The launch the bench times (paper-scale: 64^3 maps, 44 atoms, 8 torsions,
+    100 runs x 150 x 2.5 M evaluations, ADADELTA): properties that hold at any
+    size -- every run spends its budget, the best energy never rises along the
+    trace, the reported pose is the oracle's pose of the reported genotype --
+    and, on a sample of 20 runs, the reported best energy is the oracle's
+    energy of the reported genotype within the energy tolerance."""
+    grid, rec, lig, maps64, maps32 = problem("paper")
+    R = A.Receptor(ctx, grid, maps32)
+    Lg = A.Ligand(ctx, ff, lig)
+    nev = 2_500_000
+    p = A.search_params(nrun=100, pop_size=150, nev=nev, ls_method=A.LS_ADADELTA, seed=42)
+    res = A.dock(ctx, R, Lg, p, best_trace=64)[0]
+    assert (res["evals"] >= nev).all() and (res["evals"] < nev + 150 * 301).all()
+    assert (res["generations"] == res["generations"][0]).all()
+    assert np.all(np.diff(res["best_trace"], axis=1) <= 0)
+    L = O.Ligand(lig)
+    genes = res["genes"].astype(np.float64)
+    xyz_ref = O.pose(L, genes)
+    assert np.abs(res["xyz"] - xyz_ref).max() < 1e-3
+    sample = np.arange(0, 100, 5)
+    e_ref = O.score(ff, grid, maps64, L, genes[sample])[0]
+    forces = O.atom_gradients(ff, grid, maps64, L, genes[sample])
+    assert (np.abs(res["best_energy"][sample] - e_ref) <= energy_tol(e_ref, forces)).all()
+    assert (e_ref < 0).all()
