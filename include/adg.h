@@ -364,6 +364,15 @@ int adg_mlp_set_params(adg_ctx* ctx, adg_mlp* mlp, const float* in);
 int adg_mlp_set_norm(adg_mlp* mlp, const float* mu, const float* sigma, float mu_y, float sigma_y);
 /* y[b] = prediction for x[b] (x: [B][nin], y: [B]). */
 int adg_mlp_forward(adg_ctx* ctx, const adg_mlp* mlp, const float* x, int B, float* y);
+/* Engine of adg_mlp_forward: ADG_MLP_TCGEN05 (default) -- one CTA per 128 rows,
+ * tcgen05.mma with FP32 accumulators in tensor memory; ADG_MLP_MMA_SYNC --
+ * warp-level m16n8k16 MMAs, as the training kernels use.  Same numerics
+ * (BF16 operands and stored h1, FP32 accumulation and h2). */
+enum { ADG_MLP_MMA_SYNC = 0, ADG_MLP_TCGEN05 = 1 };
+int adg_mlp_set_engine(adg_mlp* mlp, int engine);
+/* Synchronous: ADG_ETIMEOUT if a bounded wait of the tcgen05 forward pass
+ * expired since the last check (those rows were written as NaN), else ADG_OK. */
+int adg_mlp_check(adg_ctx* ctx, adg_mlp* mlp);
 /* Gradient of the batch loss (1/B) sum_b (y_b - (t_b - mu_y)/sigma_y)^2 with
  * respect to the packed parameters into grad [nparams], and the loss into
  * *loss (nullable); idx (nullable) selects rows of x and t.  No update. */

@@ -28,6 +28,7 @@ ADG_OK = 0
 GRAD_NONE, GRAD_GENES, GRAD_TANGENT = 0, 1, 2
 LS_NONE, LS_SOLIS_WETS, LS_ADADELTA = 0, 1, 2
 GEO_HEURISTIC, GEO_TUNED = 0, 1
+MLP_MMA_SYNC, MLP_TCGEN05 = 0, 1
 NDESC = 16
 
 
@@ -107,7 +108,7 @@ EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_c
            "adg_dock_traced", "adg_ligand_descriptors", "adg_mlp_nparams", "adg_mlp_create", "adg_mlp_destroy",
            "adg_mlp_get_params", "adg_mlp_set_params", "adg_mlp_set_norm", "adg_mlp_forward", "adg_mlp_grad",
            "adg_mlp_train_step", "adg_mlp_fit", "adg_ligand_set_stream_id",
-           "adg_ctx_set_graphs")
+           "adg_ctx_set_graphs", "adg_mlp_set_engine", "adg_mlp_check")
 
 _lib = None
 
@@ -163,6 +164,8 @@ def load(path: str | None = None):
         L.adg_mlp_grad.argtypes = [_vp, _vp, _vp, _vp, _vp, _i, _vp, _vp]
         L.adg_mlp_train_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _i, C.c_float, _vp]
         L.adg_mlp_fit.argtypes = [_vp, _vp, _vp, _vp, _i, _i, _i, C.c_float, C.c_uint64, _fp]
+        L.adg_mlp_set_engine.argtypes = [_vp, _i]
+        L.adg_mlp_check.argtypes = [_vp, _vp]
         L.adg_ctx_tuned.argtypes = [_vp, C.POINTER(adg_tuned_shape), _i, C.POINTER(C.c_int)]
         _lib = L
     return _lib
@@ -552,6 +555,14 @@ class MLP:
         _check(load().adg_mlp_set_norm(self.handle, m.ctypes.data_as(C.POINTER(C.c_float)),
                                        sg.ctypes.data_as(C.POINTER(C.c_float)), float(mu_y), float(sigma_y)),
                "adg_mlp_set_norm")
+
+    def set_engine(self, engine: int):
+        """MLP_TCGEN05 (default) or MLP_MMA_SYNC for forward()."""
+        _check(load().adg_mlp_set_engine(self.handle, int(engine)), "adg_mlp_set_engine")
+
+    def check(self):
+        """Raise if a bounded wait of the tcgen05 forward expired (synchronous)."""
+        _check(load().adg_mlp_check(self.ctx.handle, self.handle), "adg_mlp_check", self.ctx)
 
     def forward(self, x):
         import torch

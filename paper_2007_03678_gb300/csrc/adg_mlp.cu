@@ -419,6 +419,198 @@ __global__ void k_mlp_adam(float* __restrict__ theta, float* __restrict__ m, flo
     else if (p >= o.w3 && p < o.b3) w3[p - o.w3] = __float2bfloat16_rn(th);
 }
 
+
+// ------------------------------------------------------------------ tcgen05 forward
+// Inference on the 5th-generation tensor cores: one CTA (4 warps) per 128-row
+// tile.  x_hat, W1, h1 and W2 sit in shared memory in the canonical K-major
+// no-swizzle layout (8-row x 16-byte core matrices: element (r, k) of an
+// R x K operand at ((r/8)(K/8) + k/8) * 128 + (r%8) * 16 + (k%8) * 2 bytes);
+// one thread issues tcgen05.mma (M = 128, N = 256, K = 16 per instruction,
+// BF16 in, FP32 accumulators in tensor memory): x_hat W1^T into TMEM columns
+// 0-255, then h1 W2^T into columns 256-511.  Each thread owns one row (its
+// TMEM lane), reads its accumulators back with tcgen05.ld, and finishes the
+// row (bias, ReLU, BF16 h1; then bias, ReLU and the w3 dot product) alone.
+constexpr int TC_ROWS = 128;
+constexpr size_t kTcW2 = (size_t)H * H * 2;
+constexpr size_t kTcW1 = (size_t)H * KIN * 2;
+constexpr size_t kTcX = (size_t)TC_ROWS * KIN * 2;
+constexpr size_t kTcH1 = (size_t)TC_ROWS * H * 2;
+constexpr size_t kTcSmem = kTcW2 + kTcW1 + kTcX + kTcH1 + 3 * H * sizeof(float) + 16;
+constexpr long long kTcWaitNs = 1000000000ll;  // bounded wait on the MMA completion barrier (1 s)
+
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;      // leading byte offset: next core matrix along K
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;      // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                            // descriptor version of this architecture
+    return d;                                          // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, int accumulate)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ long long global_ns()
+{
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the given phase parity of an mbarrier, for at most kTcWaitNs.
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
+{
+    const long long t0 = global_ns();
+    for (;;) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > kTcWaitNs) return false;
+    }
+}
+
+// 32 consecutive FP32 accumulator columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
+{
+    uint32_t r[32];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(ActArgs A, int* status)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* W2s = smem;
+    unsigned char* W1s = W2s + kTcW2;
+    unsigned char* Xs = W1s + kTcW1;
+    unsigned char* H1s = Xs + kTcX;
+    float* b1s = reinterpret_cast<float*>(H1s + kTcH1);
+    float* b2s = b1s + H;
+    float* w3s = b2s + H;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(w3s + H);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t s_base = smem_u32(smem), s_mbar = smem_u32(mbar);
+    if (warp == 0) {  // 512 TMEM columns: layer 1 in 0-255, layer 2 in 256-511
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < H * H / 8; i += TC_ROWS) {
+        const int n = i >> 5, k8 = i & 31;
+        *reinterpret_cast<uint4*>(W2s + (((n >> 3) * (H / 8) + k8) << 7) + ((n & 7) << 4)) =
+            *reinterpret_cast<const uint4*>(A.w2 + n * H + k8 * 8);
+    }
+    for (int i = tid; i < H * KIN / 8; i += TC_ROWS) {
+        const int n = i >> 2, k8 = i & 3;
+        *reinterpret_cast<uint4*>(W1s + (((n >> 3) * (KIN / 8) + k8) << 7) + ((n & 7) << 4)) =
+            *reinterpret_cast<const uint4*>(A.w1 + n * KIN + k8 * 8);
+    }
+    for (int j = tid; j < H; j += TC_ROWS) {
+        b1s[j] = A.theta[A.o.b1 + j];
+        b2s[j] = A.theta[A.o.b2 + j];
+        w3s[j] = __bfloat162float(A.w3[j]);
+    }
+    const int row = blockIdx.x * TC_ROWS + tid;  // this thread's row = its TMEM lane
+#pragma unroll
+    for (int k8 = 0; k8 < KIN / 8; ++k8) {
+        uint32_t pk[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int k = k8 * 8 + 2 * q;
+            float v0 = 0.f, v1 = 0.f;
+            if (row < A.B) {
+                const int src = A.idx ? A.idx[row] : row;
+                if (k < A.nin) v0 = (A.x[(long)src * A.nin + k] - A.nm.mu[k]) / A.nm.sigma[k];
+                if (k + 1 < A.nin) v1 = (A.x[(long)src * A.nin + k + 1] - A.nm.mu[k + 1]) / A.nm.sigma[k + 1];
+            }
+            pk[q] = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
+        }
+        *reinterpret_cast<uint4*>(Xs + (((tid >> 3) * (KIN / 8) + k8) << 7) + ((tid & 7) << 4)) =
+            make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // smem writes visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = *tslot;
+    // kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N = 256, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) |
+                           ((uint32_t)(TC_ROWS >> 4) << 24);
+    if (tid == 0) {
+        for (int s = 0; s < KIN / 16; ++s)
+            tc_mma(tbase, tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1) + s * 256, 128, (KIN / 8) * 128),
+                   tc_smem_desc(s_base + (uint32_t)kTcW2 + s * 256, 128, (KIN / 8) * 128), idesc, s > 0);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar)
+                     : "memory");
+    }
+    bool ok = tc_wait(s_mbar, 0);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+    for (int c = 0; c < H / 32; ++c) {  // h1 = relu(x_hat W1^T + b1) -> BF16, row-major K = 256
+        float v[32];
+        tc_ld32(trow + c * 32, v);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t pk[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int j = c * 32 + q * 8 + 2 * e;
+                pk[e] = pack2(__float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e] + b1s[j], 0.f)),
+                              __float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e + 1] + b1s[j + 1], 0.f)));
+            }
+            *reinterpret_cast<uint4*>(H1s + (((tid >> 3) * (H / 8) + c * 4 + q) << 7) + ((tid & 7) << 4)) =
+                make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (tid == 0) {
+        for (int s = 0; s < H / 16; ++s)
+            tc_mma(tbase + H, tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1 + kTcX) + s * 256, 128, (H / 8) * 128),
+                   tc_smem_desc(s_base + s * 256, 128, (H / 8) * 128), idesc, s > 0);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar)
+                     : "memory");
+    }
+    ok = tc_wait(s_mbar, 1) && ok;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    float acc = A.theta[A.o.b3];
+    for (int c = 0; c < H / 32; ++c) {  // y = w3 . relu(h1 W2^T + b2) + b3, FP32
+        float v[32];
+        tc_ld32(trow + H + c * 32, v);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) acc += fmaxf(v[e] + b2s[c * 32 + e], 0.f) * w3s[c * 32 + e];
+    }
+    if (row < A.B) A.y[row] = ok ? acc * A.nm.sigma_y + A.nm.mu_y : __int_as_float(0x7fc00000);
+    if (!ok) atomicOr(status, 1);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
+}
+
 uint64_t splitmix64(uint64_t& s)
 {
     uint64_t z = (s += 0x9E3779B97F4A7C15ull);
@@ -449,6 +641,8 @@ struct adg_mlp {
     size_t idx_n = 0;
     float* eloss = nullptr;  // fit(): loss per epoch
     size_t eloss_n = 0;
+    int engine = ADG_MLP_TCGEN05;  // forward pass engine
+    int* status = nullptr;   // device: bit 0 set when a bounded wait of the tcgen05 forward expired
 };
 
 namespace {
@@ -593,6 +787,8 @@ int adg_mlp_create(adg_ctx* ctx, int nin, uint64_t seed, adg_mlp** out)
     if (e == cudaSuccess) e = cudaMalloc(&M->w1, sizeof(bf16) * H * KIN);
     if (e == cudaSuccess) e = cudaMalloc(&M->w2, sizeof(bf16) * H * H);
     if (e == cudaSuccess) e = cudaMalloc(&M->w3, sizeof(bf16) * H);
+    if (e == cudaSuccess) e = cudaMalloc(&M->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(M->status, 0, sizeof(int), ctx->stream);
     // He-uniform initial weights (bound sqrt(6 / fan_in)), zero biases
     std::vector<float> th(n, 0.f);
     uint64_t s = seed;
@@ -631,6 +827,7 @@ int adg_mlp_destroy(adg_mlp* M)
     cudaFree(M->act);
     cudaFree(M->idx);
     cudaFree(M->eloss);
+    cudaFree(M->status);
     delete M;
     return ADG_OK;
 }
@@ -682,11 +879,34 @@ int adg_mlp_forward(adg_ctx* ctx, const adg_mlp* M, const float* x, int B, float
     MCK(cudaSetDevice(M->device));
     ActArgs a = act_args(M, x, B);
     a.y = y;
-    MCK(cudaFuncSetAttribute(k_mlp_act<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kActSmem));
-    k_mlp_act<false><<<act_blocks(B, M->device), 256, kActSmem, ctx->stream>>>(a);
+    if (M->engine == ADG_MLP_TCGEN05) {
+        MCK(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+        k_mlp_fwd_tc<<<(unsigned)((B + TC_ROWS - 1) / TC_ROWS), TC_ROWS, kTcSmem, ctx->stream>>>(a, M->status);
+    } else {
+        MCK(cudaFuncSetAttribute(k_mlp_act<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kActSmem));
+        k_mlp_act<false><<<act_blocks(B, M->device), 256, kActSmem, ctx->stream>>>(a);
+    }
     MCK(cudaGetLastError());
     ctx->stats.kernel_launches += 1;
     return ADG_OK;
+}
+
+int adg_mlp_set_engine(adg_mlp* M, int engine)
+{
+    if (!M || (engine != ADG_MLP_MMA_SYNC && engine != ADG_MLP_TCGEN05)) return ADG_EINVAL;
+    M->engine = engine;
+    return ADG_OK;
+}
+
+int adg_mlp_check(adg_ctx* ctx, adg_mlp* M)
+{
+    if (!ctx || !M) return ADG_EINVAL;
+    MCK(cudaSetDevice(M->device));
+    int h = 0;
+    MCK(cudaMemcpyAsync(&h, M->status, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    MCK(cudaMemsetAsync(M->status, 0, sizeof(int), ctx->stream));
+    MCK(cudaStreamSynchronize(ctx->stream));
+    return h ? ADG_ETIMEOUT : ADG_OK;
 }
 
 int adg_mlp_grad(adg_ctx* ctx, adg_mlp* M, const float* x, const float* t, const int* idx, int B, float* grad,

@@ -169,3 +169,24 @@ def test_training_is_bit_reproducible(ctx):
         out.append((net.get_params(), h))
         net.close()
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("B", [1, 128, 300])
+def test_tcgen05_forward_matches_oracle_and_mma_sync(ctx, B):
+    """The tcgen05 (tensor-memory) forward pass against the oracle, with the
+    tolerances above, and against the warp-level MMA forward pass."""
+    import torch
+    from paper_2007_03678_gb300 import adg
+    x, t, mu, sig = _problem(60 + B, B)
+    net, th = _net(ctx, 9, mu, sig)
+    xd = torch.from_numpy(x).cuda()
+    net.set_engine(adg.MLP_TCGEN05)
+    y_tc = net.forward(xd).cpu().numpy().astype(np.float64)
+    net.check()
+    net.set_engine(adg.MLP_MMA_SYNC)
+    y_mma = net.forward(xd).cpu().numpy().astype(np.float64)
+    yr, _ = M.forward(th, x.astype(np.float64), NIN, mu.astype(np.float64), sig.astype(np.float64), True)
+    err = np.abs((y_tc + 9.0) / 3.0 - yr)
+    assert err.max() <= 3e-2, err.max()
+    assert (err <= 1e-4).mean() >= 0.95, np.sort(err)[-10:]
+    assert np.abs(y_tc - y_mma).max() <= 3e-2 * 3.0
