@@ -364,7 +364,7 @@ int adg_mlp_set_params(adg_ctx* ctx, adg_mlp* mlp, const float* in);
 int adg_mlp_set_norm(adg_mlp* mlp, const float* mu, const float* sigma, float mu_y, float sigma_y);
 /* y[b] = prediction for x[b] (x: [B][nin], y: [B]). */
 int adg_mlp_forward(adg_ctx* ctx, const adg_mlp* mlp, const float* x, int B, float* y);
-/* Engine of adg_mlp_forward: ADG_MLP_TCGEN05 (default) -- one CTA per 128 rows,
+/* Engine of adg_mlp_forward: ADG_MLP_TCGEN05 (default) -- persistent CTAs over 128-row tiles,
  * tcgen05.mma with FP32 accumulators in tensor memory; ADG_MLP_MMA_SYNC --
  * warp-level m16n8k16 MMAs, as the training kernels use.  Same numerics
  * (BF16 operands and stored h1, FP32 accumulation and h2). */

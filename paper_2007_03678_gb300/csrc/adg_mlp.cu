@@ -421,8 +421,8 @@ __global__ void k_mlp_adam(float* __restrict__ theta, float* __restrict__ m, flo
 
 
 // ------------------------------------------------------------------ tcgen05 forward
-// Inference on the 5th-generation tensor cores: one CTA (4 warps) per 128-row
-// tile.  x_hat, W1, h1 and W2 sit in shared memory in the canonical K-major
+// Inference on the 5th-generation tensor cores: persistent CTAs (4 warps, one
+// per SM) run 128-row tiles, W1 and W2 staged once per CTA.  x_hat, W1, h1 and W2 sit in shared memory in the canonical K-major
 // no-swizzle layout (8-row x 16-byte core matrices: element (r, k) of an
 // R x K operand at ((r/8)(K/8) + k/8) * 128 + (r%8) * 16 + (k%8) * 2 bytes);
 // one thread issues tcgen05.mma (M = 128, N = 256, K = 16 per instruction,
@@ -532,79 +532,95 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(ActArgs A, int* status)
         b2s[j] = A.theta[A.o.b2 + j];
         w3s[j] = __bfloat162float(A.w3[j]);
     }
-    const int row = blockIdx.x * TC_ROWS + tid;  // this thread's row = its TMEM lane
-#pragma unroll
-    for (int k8 = 0; k8 < KIN / 8; ++k8) {
-        uint32_t pk[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int k = k8 * 8 + 2 * q;
-            float v0 = 0.f, v1 = 0.f;
-            if (row < A.B) {
-                const int src = A.idx ? A.idx[row] : row;
-                if (k < A.nin) v0 = (A.x[(long)src * A.nin + k] - A.nm.mu[k]) / A.nm.sigma[k];
-                if (k + 1 < A.nin) v1 = (A.x[(long)src * A.nin + k + 1] - A.nm.mu[k + 1]) / A.nm.sigma[k + 1];
-            }
-            pk[q] = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
-        }
-        *reinterpret_cast<uint4*>(Xs + (((tid >> 3) * (KIN / 8) + k8) << 7) + ((tid & 7) << 4)) =
-            make_uint4(pk[0], pk[1], pk[2], pk[3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // smem writes visible to the tensor cores
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tbase = *tslot;
     // kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N = 256, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) |
                            ((uint32_t)(TC_ROWS >> 4) << 24);
-    if (tid == 0) {
-        for (int s = 0; s < KIN / 16; ++s)
-            tc_mma(tbase, tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1) + s * 256, 128, (KIN / 8) * 128),
-                   tc_smem_desc(s_base + (uint32_t)kTcW2 + s * 256, 128, (KIN / 8) * 128), idesc, s > 0);
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar)
-                     : "memory");
-    }
-    bool ok = tc_wait(s_mbar, 0);
+    bool ok = true;
+    uint32_t phase = 0;  // parity of the next completion of the MMA barrier
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // the TMEM address, the barrier and the staged weights are ready
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
-    for (int c = 0; c < H / 32; ++c) {  // h1 = relu(x_hat W1^T + b1) -> BF16, row-major K = 256
-        float v[32];
-        tc_ld32(trow + c * 32, v);
+    const uint32_t tbase = *tslot;
+    const int ntiles = (A.B + TC_ROWS - 1) / TC_ROWS;
+    // persistent CTAs: W1 and W2 stay in shared memory across tiles
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int row = tile * TC_ROWS + tid;  // this thread's row = its TMEM lane
 #pragma unroll
-        for (int q = 0; q < 4; ++q) {
+        for (int k8 = 0; k8 < KIN / 8; ++k8) {
             uint32_t pk[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int j = c * 32 + q * 8 + 2 * e;
-                pk[e] = pack2(__float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e] + b1s[j], 0.f)),
-                              __float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e + 1] + b1s[j + 1], 0.f)));
+            for (int q = 0; q < 4; ++q) {
+                const int k = k8 * 8 + 2 * q;
+                float v0 = 0.f, v1 = 0.f;
+                if (row < A.B) {
+                    const int src = A.idx ? A.idx[row] : row;
+                    if (k < A.nin) v0 = (A.x[(long)src * A.nin + k] - A.nm.mu[k]) / A.nm.sigma[k];
+                    if (k + 1 < A.nin) v1 = (A.x[(long)src * A.nin + k + 1] - A.nm.mu[k + 1]) / A.nm.sigma[k + 1];
+                }
+                pk[q] = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
             }
-            *reinterpret_cast<uint4*>(H1s + (((tid >> 3) * (H / 8) + c * 4 + q) << 7) + ((tid & 7) << 4)) =
+            *reinterpret_cast<uint4*>(Xs + (((tid >> 3) * (KIN / 8) + k8) << 7) + ((tid & 7) << 4)) =
                 make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (tid == 0) {
-        for (int s = 0; s < H / 16; ++s)
-            tc_mma(tbase + H, tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1 + kTcX) + s * 256, 128, (H / 8) * 128),
-                   tc_smem_desc(s_base + s * 256, 128, (H / 8) * 128), idesc, s > 0);
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar)
-                     : "memory");
-    }
-    ok = tc_wait(s_mbar, 1) && ok;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    float acc = A.theta[A.o.b3];
-    for (int c = 0; c < H / 32; ++c) {  // y = w3 . relu(h1 W2^T + b2) + b3, FP32
-        float v[32];
-        tc_ld32(trow + H + c * 32, v);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // smem writes visible to the tensor cores
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            for (int s = 0; s < KIN / 16; ++s)
+                tc_mma(tbase, tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1) + s * 256, 128, (KIN / 8) * 128),
+                       tc_smem_desc(s_base + (uint32_t)kTcW2 + s * 256, 128, (KIN / 8) * 128), idesc, s > 0);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar)
+                         : "memory");
+        }
+        ok = tc_wait(s_mbar, phase) && ok;
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+        for (int c = 0; c < H / 32; ++c) {  // h1 = relu(x_hat W1^T + b1) -> BF16, row-major K = 256
+            float v[32];
+            tc_ld32(trow + c * 32, v);
 #pragma unroll
-        for (int e = 0; e < 32; ++e) acc += fmaxf(v[e] + b2s[c * 32 + e], 0.f) * w3s[c * 32 + e];
+            for (int q = 0; q < 4; ++q) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int j = c * 32 + q * 8 + 2 * e;
+                    pk[e] = pack2(__float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e] + b1s[j], 0.f)),
+                                  __float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e + 1] + b1s[j + 1], 0.f)));
+                }
+                *reinterpret_cast<uint4*>(H1s + (((tid >> 3) * (H / 8) + c * 4 + q) << 7) + ((tid & 7) << 4)) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (tid == 0) {
+            for (int s = 0; s < H / 16; ++s)
+                tc_mma(tbase + H,
+                       tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1 + kTcX) + s * 256, 128, (H / 8) * 128),
+                       tc_smem_desc(s_base + s * 256, 128, (H / 8) * 128), idesc, s > 0);
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar)
+                         : "memory");
+        }
+        ok = tc_wait(s_mbar, phase) && ok;
+        phase ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float acc = A.theta[A.o.b3];
+        for (int c = 0; c < H / 32; ++c) {  // y = w3 . relu(h1 W2^T + b2) + b3, FP32
+            float v[32];
+            tc_ld32(trow + H + c * 32, v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) acc += fmaxf(v[e] + b2s[c * 32 + e], 0.f) * w3s[c * 32 + e];
+        }
+        if (row < A.B) A.y[row] = ok ? acc * A.nm.sigma_y + A.nm.mu_y : __int_as_float(0x7fc00000);
+        // the next tile rewrites x_hat, h1 and the accumulators only after every thread is done with them
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     }
-    if (row < A.B) A.y[row] = ok ? acc * A.nm.sigma_y + A.nm.mu_y : __int_as_float(0x7fc00000);
     if (!ok) atomicOr(status, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
@@ -881,7 +897,10 @@ int adg_mlp_forward(adg_ctx* ctx, const adg_mlp* M, const float* x, int B, float
     a.y = y;
     if (M->engine == ADG_MLP_TCGEN05) {
         MCK(cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-        k_mlp_fwd_tc<<<(unsigned)((B + TC_ROWS - 1) / TC_ROWS), TC_ROWS, kTcSmem, ctx->stream>>>(a, M->status);
+        int nsm = 148;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M->device);
+        const int ntiles = (B + TC_ROWS - 1) / TC_ROWS;
+        k_mlp_fwd_tc<<<(unsigned)std::min(ntiles, nsm), TC_ROWS, kTcSmem, ctx->stream>>>(a, M->status);
     } else {
         MCK(cudaFuncSetAttribute(k_mlp_act<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kActSmem));
         k_mlp_act<false><<<act_blocks(B, M->device), 256, kActSmem, ctx->stream>>>(a);
