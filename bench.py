@@ -214,6 +214,45 @@ GEN_TRAFFIC_BYTES = 27.6e6
 GEN_L1_PIPE_FRAC = 0.685
 
 
+def run_mlp_inference(ctx, rows=1_000_000, reps=10):
+    """Triage-network inference throughput on `rows` random feature rows, for
+    both engines (tcgen05 with tensor-memory accumulators, and warp-level
+    MMAs); device-timed, mean of `reps` launches."""
+    import json as _json
+    import numpy as np
+    import torch
+    from paper_2007_03678_gb300 import adg
+    nin = 26
+    net = adg.MLP(ctx, nin, seed=1)
+    net.set_norm(np.zeros(nin), np.ones(nin), 0.0, 1.0)
+    x = torch.randn(rows, nin, device=f"cuda:{ctx.device}")
+    flops = 2.0 * rows * (32 * 256 + 256 * 256 + 256)  # input width padded to 32 on the tensor cores
+    out = {"rows": rows, "network": f"{nin}-256-256-1, BF16 weights / FP32 accumulate", "flops_per_call": flops}
+    peak = None
+    try:
+        peak = float(_json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)),
+                                                  "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except Exception:
+        pass
+    for eng, name in ((adg.MLP_TCGEN05, "tcgen05"), (adg.MLP_MMA_SYNC, "mma_sync")):
+        net.set_engine(eng)
+        for _ in range(3):
+            net.forward(x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            net.forward(x)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "tflops": flops / ms / 1e9,
+                     "frac_of_bf16_peak": (flops / ms / 1e9 / peak) if peak else None}
+    net.check()
+    net.close()
+    return out
+
+
 def run_plain_config(ctx, ff, reps=5):
     """The plain configuration: 40^3 maps of a 600-atom pseudo-receptor, one
     16+2-atom ligand with 3 torsions, 10 runs x pop 150 x 50,000 evals,
@@ -480,9 +519,10 @@ def main():
                     "tuning": {"buckets": len(ctx.tuned()), "launches": tune_launches,
                                "first_call_s": round(t_tune, 3)}}
 
-    triage = None
+    triage = mlp = None
     if not args.no_triage:
         triage = run_triage(ctx, R, ff)
+        mlp = run_mlp_inference(ctx)
     plain = differentiation = None
     if not args.no_batching:
         plain = run_plain_config(ctx, ff)
@@ -507,7 +547,7 @@ def main():
                 "config": workload_config(args.nrun, args.nev), "ligands_per_s": ligands_per_s,
                 "best_energy_median": float(np.median(results["best_energy"])),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "batching": batching,
-                "triage": triage, "plain": plain, "differentiation": differentiation,
+                "triage": triage, "mlp_inference": mlp, "plain": plain, "differentiation": differentiation,
                 "gpu_launches": st["kernel_launches"]}
         print(json.dumps(line), flush=True)
     if dist is not None:
