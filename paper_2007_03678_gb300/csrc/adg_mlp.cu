@@ -421,21 +421,22 @@ __global__ void k_mlp_adam(float* __restrict__ theta, float* __restrict__ m, flo
 
 
 // ------------------------------------------------------------------ tcgen05 forward
-// Inference on the 5th-generation tensor cores: persistent CTAs (4 warps, one
+// Inference on the 5th-generation tensor cores: persistent CTAs (8 warps, one
 // per SM) run 128-row tiles, W1 and W2 staged once per CTA.  x_hat, W1, h1 and W2 sit in shared memory in the canonical K-major
 // no-swizzle layout (8-row x 16-byte core matrices: element (r, k) of an
 // R x K operand at ((r/8)(K/8) + k/8) * 128 + (r%8) * 16 + (k%8) * 2 bytes);
 // one thread issues tcgen05.mma (M = 128, N = 256, K = 16 per instruction,
 // BF16 in, FP32 accumulators in tensor memory): x_hat W1^T into TMEM columns
-// 0-255, then h1 W2^T into columns 256-511.  Each thread owns one row (its
-// TMEM lane), reads its accumulators back with tcgen05.ld, and finishes the
-// row (bias, ReLU, BF16 h1; then bias, ReLU and the w3 dot product) alone.
+// 0-255, then h1 W2^T into columns 256-511.  Two threads own a row (its TMEM
+// lane), one per half of the columns; they read their accumulators back with
+// tcgen05.ld and finish the row (bias, ReLU, BF16 h1; then bias, ReLU and the
+// w3 dot product, the halves summed through shared memory).
 constexpr int TC_ROWS = 128;
 constexpr size_t kTcW2 = (size_t)H * H * 2;
 constexpr size_t kTcW1 = (size_t)H * KIN * 2;
 constexpr size_t kTcX = (size_t)TC_ROWS * KIN * 2;
 constexpr size_t kTcH1 = (size_t)TC_ROWS * H * 2;
-constexpr size_t kTcSmem = kTcW2 + kTcW1 + kTcX + kTcH1 + 3 * H * sizeof(float) + 16;
+constexpr size_t kTcSmem = kTcW2 + kTcW1 + kTcX + kTcH1 + 3 * H * sizeof(float) + 32;
 constexpr long long kTcWaitNs = 1000000000ll;  // bounded wait on the MMA completion barrier (1 s)
 
 __device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
@@ -494,7 +495,9 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(ActArgs A, int* status)
+constexpr int TC_THREADS = 256;  // 8 warps: warps w and w + 4 share TMEM lanes 32 (w % 4).., split the columns
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* status)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* W2s = smem;
@@ -504,30 +507,34 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(ActArgs A, int* status)
     float* b1s = reinterpret_cast<float*>(H1s + kTcH1);
     float* b2s = b1s + H;
     float* w3s = b2s + H;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(w3s + H);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 1);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(w3s + H);  // [0]: layer-1 MMAs, [1]: layer-2 MMAs
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    __shared__ float part[TC_ROWS];  // the second column half's share of each row's output
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t s_base = smem_u32(smem), s_mbar = smem_u32(mbar);
+    const int r = (warp & 3) * 32 + (tid & 31);  // this thread's row = its TMEM lane
+    const int half = warp >> 2;                  // columns [128 half, 128 half + 128)
+    const uint32_t s_base = smem_u32(smem), s_mbar1 = smem_u32(mbar), s_mbar2 = smem_u32(mbar + 1);
     if (warp == 0) {  // 512 TMEM columns: layer 1 in 0-255, layer 2 in 256-511
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot))
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_mbar) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_mbar1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_mbar2) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int i = tid; i < H * H / 8; i += TC_ROWS) {
+    for (int i = tid; i < H * H / 8; i += TC_THREADS) {
         const int n = i >> 5, k8 = i & 31;
         *reinterpret_cast<uint4*>(W2s + (((n >> 3) * (H / 8) + k8) << 7) + ((n & 7) << 4)) =
             *reinterpret_cast<const uint4*>(A.w2 + n * H + k8 * 8);
     }
-    for (int i = tid; i < H * KIN / 8; i += TC_ROWS) {
+    for (int i = tid; i < H * KIN / 8; i += TC_THREADS) {
         const int n = i >> 2, k8 = i & 3;
         *reinterpret_cast<uint4*>(W1s + (((n >> 3) * (KIN / 8) + k8) << 7) + ((n & 7) << 4)) =
             *reinterpret_cast<const uint4*>(A.w1 + n * KIN + k8 * 8);
     }
-    for (int j = tid; j < H; j += TC_ROWS) {
+    for (int j = tid; j < H; j += TC_THREADS) {
         b1s[j] = A.theta[A.o.b1 + j];
         b2s[j] = A.theta[A.o.b2 + j];
         w3s[j] = __bfloat162float(A.w3[j]);
@@ -535,18 +542,11 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(ActArgs A, int* status)
     // kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N = 256, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) |
                            ((uint32_t)(TC_ROWS >> 4) << 24);
-    bool ok = true;
-    uint32_t phase = 0;  // parity of the next completion of the MMA barrier
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();  // the TMEM address, the barrier and the staged weights are ready
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tbase = *tslot;
-    const int ntiles = (A.B + TC_ROWS - 1) / TC_ROWS;
-    // persistent CTAs: W1 and W2 stay in shared memory across tiles
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int row = tile * TC_ROWS + tid;  // this thread's row = its TMEM lane
+    // x_hat of one tile (BF16, canonical layout, K = 32); each column half writes two of the four chunks
+    auto stage_x = [&](int tile) {
+        const int row = tile * TC_ROWS + r;
 #pragma unroll
-        for (int k8 = 0; k8 < KIN / 8; ++k8) {
+        for (int k8 = half * 2; k8 < half * 2 + 2; ++k8) {
             uint32_t pk[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -559,25 +559,37 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(ActArgs A, int* status)
                 }
                 pk[q] = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
             }
-            *reinterpret_cast<uint4*>(Xs + (((tid >> 3) * (KIN / 8) + k8) << 7) + ((tid & 7) << 4)) =
+            *reinterpret_cast<uint4*>(Xs + (((r >> 3) * (KIN / 8) + k8) << 7) + ((r & 7) << 4)) =
                 make_uint4(pk[0], pk[1], pk[2], pk[3]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // smem writes visible to the tensor cores
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+    };
+    auto issue_layer1 = [&](uint32_t tbase) {
+        for (int s = 0; s < KIN / 16; ++s)
+            tc_mma(tbase, tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1) + s * 256, 128, (KIN / 8) * 128),
+                   tc_smem_desc(s_base + (uint32_t)kTcW2 + s * 256, 128, (KIN / 8) * 128), idesc, s > 0);
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar1)
+                     : "memory");
+    };
+    bool ok = true;
+    uint32_t ph1 = 0, ph2 = 0;  // parity of the next completion of each barrier
+    const int ntiles = (A.B + TC_ROWS - 1) / TC_ROWS;
+    int tile = blockIdx.x;
+    if (tile < ntiles) stage_x(tile);
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();  // TMEM address, barriers, weights and the first x_hat are ready
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tbase = *tslot;
+    const uint32_t trow = tbase + ((uint32_t)((warp & 3) * 32) << 16);
+    if (tid == 0 && tile < ntiles) issue_layer1(tbase);
+    // persistent CTAs, W1 and W2 resident; the next tile's x_hat and layer-1 MMAs
+    // overlap this tile's layer-2 MMAs and epilogue
+    for (; tile < ntiles; tile += gridDim.x) {
+        const int row = tile * TC_ROWS + r;
+        ok = tc_wait(s_mbar1, ph1) && ok;
+        ph1 ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (tid == 0) {
-            for (int s = 0; s < KIN / 16; ++s)
-                tc_mma(tbase, tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1) + s * 256, 128, (KIN / 8) * 128),
-                       tc_smem_desc(s_base + (uint32_t)kTcW2 + s * 256, 128, (KIN / 8) * 128), idesc, s > 0);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar)
-                         : "memory");
-        }
-        ok = tc_wait(s_mbar, phase) && ok;
-        phase ^= 1u;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
-        for (int c = 0; c < H / 32; ++c) {  // h1 = relu(x_hat W1^T + b1) -> BF16, row-major K = 256
+        for (int c = half * 4; c < half * 4 + 4; ++c) {  // h1 = relu(x_hat W1^T + b1) -> BF16, row-major K = 256
             float v[32];
             tc_ld32(trow + c * 32, v);
 #pragma unroll
@@ -589,7 +601,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(ActArgs A, int* status)
                     pk[e] = pack2(__float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e] + b1s[j], 0.f)),
                                   __float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e + 1] + b1s[j + 1], 0.f)));
                 }
-                *reinterpret_cast<uint4*>(H1s + (((tid >> 3) * (H / 8) + c * 4 + q) << 7) + ((tid & 7) << 4)) =
+                *reinterpret_cast<uint4*>(H1s + (((r >> 3) * (H / 8) + c * 4 + q) << 7) + ((r & 7) << 4)) =
                     make_uint4(pk[0], pk[1], pk[2], pk[3]);
             }
         }
@@ -602,24 +614,34 @@ __global__ void __launch_bounds__(128, 1) k_mlp_fwd_tc(ActArgs A, int* status)
                 tc_mma(tbase + H,
                        tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1 + kTcX) + s * 256, 128, (H / 8) * 128),
                        tc_smem_desc(s_base + s * 256, 128, (H / 8) * 128), idesc, s > 0);
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar2)
                          : "memory");
         }
-        ok = tc_wait(s_mbar, phase) && ok;
-        phase ^= 1u;
+        // the next tile: x_hat (its buffer is free: layer 1 of this tile is done) and, once every thread has
+        // written it, its layer-1 MMAs into columns 0-255 (their accumulators were read above)
+        const int next = tile + gridDim.x;
+        if (next < ntiles) stage_x(next);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float acc = A.theta[A.o.b3];
-        for (int c = 0; c < H / 32; ++c) {  // y = w3 . relu(h1 W2^T + b2) + b3, FP32
+        if (tid == 0 && next < ntiles) issue_layer1(tbase);
+        ok = tc_wait(s_mbar2, ph2) && ok;
+        ph2 ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float acc = 0.f;
+        for (int c = half * 4; c < half * 4 + 4; ++c) {  // w3 . relu(h1 W2^T + b2) over this half's columns
             float v[32];
             tc_ld32(trow + H + c * 32, v);
 #pragma unroll
             for (int e = 0; e < 32; ++e) acc += fmaxf(v[e] + b2s[c * 32 + e], 0.f) * w3s[c * 32 + e];
         }
-        if (row < A.B) A.y[row] = ok ? acc * A.nm.sigma_y + A.nm.mu_y : __int_as_float(0x7fc00000);
-        // the next tile rewrites x_hat, h1 and the accumulators only after every thread is done with them
+        if (half == 1) part[r] = acc;
+        // h1 and columns 256-511 are rewritten for the next tile only after every thread is done with them
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (half == 0 && row < A.B)
+            A.y[row] = ok ? (acc + part[r] + A.theta[A.o.b3]) * A.nm.sigma_y + A.nm.mu_y : __int_as_float(0x7fc00000);
     }
     if (!ok) atomicOr(status, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -900,7 +922,7 @@ int adg_mlp_forward(adg_ctx* ctx, const adg_mlp* M, const float* x, int B, float
         int nsm = 148;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M->device);
         const int ntiles = (B + TC_ROWS - 1) / TC_ROWS;
-        k_mlp_fwd_tc<<<(unsigned)std::min(ntiles, nsm), TC_ROWS, kTcSmem, ctx->stream>>>(a, M->status);
+        k_mlp_fwd_tc<<<(unsigned)std::min(ntiles, nsm), TC_THREADS, kTcSmem, ctx->stream>>>(a, M->status);
     } else {
         MCK(cudaFuncSetAttribute(k_mlp_act<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kActSmem));
         k_mlp_act<false><<<act_blocks(B, M->device), 256, kActSmem, ctx->stream>>>(a);
