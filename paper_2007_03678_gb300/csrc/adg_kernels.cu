@@ -297,6 +297,30 @@ __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
+// The special-function unit's approximations with subnormals flushed: one
+// instruction each.  The pair terms never meet a subnormal (r >= sqrt(rmin2),
+// r bounded by the ligand's extent), and without .ftz each call carries the
+// scaling steps that preserve subnormal inputs and outputs.
+__device__ __forceinline__ float ex2_ftz(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float rcp_ftz(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+constexpr float kLog2e = 1.4426950408889634f;
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -457,6 +481,8 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     // registers and is stored at the row's end
     const float cap = L->e_cap, rmin2 = L->rmin2, msA = L->ms_A, msB = L->ms_B, msk = L->ms_k, mslb = L->ms_lb;
     const float inv_2s2 = L->inv_2s2, inv_s2 = L->inv_s2, wq = L->wq;
+    // exp(-lambda r) and exp(-r^2 / 2 sigma^2) as powers of two
+    const float kex = -mslb * kLog2e, kgs = -inv_2s2 * kLog2e;
     const int nsteps = L->nsteps;  // even
     float rfx = 0.f, rfy = 0.f, rfz = 0.f;
     float4 xr = make_float4(0.f, 0.f, 0.f, 0.f);  // atom i of the current row
@@ -478,7 +504,7 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const float2 cq = mul2(mul2(v2(ija ? wq : 0.f, ijb ? wq : 0.f), v2(xia.w, xib.w)), v2(xja.w, xjb.w));
         const bool fla = r2.x < rmin2, flb = r2.y < rmin2;
         const float2 rr2 = v2(fla ? rmin2 : r2.x, flb ? rmin2 : r2.y);
-        const float2 ri = v2(rsqrtf(rr2.x), rsqrtf(rr2.y));
+        const float2 ri = v2(rsqrt_ftz(rr2.x), rsqrt_ftz(rr2.y));
         const float2 r = mul2(rr2, ri);
         const float2 ri2 = mul2(ri, ri);
         const float2 ri4 = mul2(ri2, ri2);
@@ -487,13 +513,15 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const float2 km = v2((ija & kPairHB) ? 10.f : 6.f, (ijb & kPairHB) ? 10.f : 6.f);
         const float2 a12 = mul2(c12, ri12), am = mul2(cm, rim);
         const float2 elj = sub2(a12, am);
-        const float2 ex = v2(__expf(-mslb * r.x), __expf(-mslb * r.y));
+        const float2 tex = mul2(s2(kex), r);
+        const float2 ex = v2(ex2_ftz(tex.x), ex2_ftz(tex.y));
         const float2 den = fma2(s2(msk), ex, s2(1.f));
         const float2 D = fma2(s2(msA), den, s2(msB));  // eps(r) = D / den
-        const float2 rD = v2(__fdividef(1.f, D.x), __fdividef(1.f, D.y));
+        const float2 rD = v2(rcp_ftz(D.x), rcp_ftz(D.y));
         const float2 u = mul2(ri, rD);
         const float2 eel = mul2(mul2(cq, den), u);
-        const float2 gs = v2(__expf(-rr2.x * inv_2s2), __expf(-rr2.y * inv_2s2));
+        const float2 tgs = mul2(s2(kgs), rr2);
+        const float2 gs = v2(ex2_ftz(tgs.x), ex2_ftz(tgs.y));
         const float2 eds = mul2(cd, gs);
         if (GRAD) {
             // (dE/dr) / r of the three terms
