@@ -595,7 +595,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
                     int fl = r.owner >= 0 ? kPairOwned : 0;
                     if (pi[l] == 0) fl |= kPairRowStart;
                     if (rem[l].empty()) {
-                        if (r.owner >= 0) fl |= kPairRowEnd;
+                        fl |= kPairRowEnd;
                         ++ri[l];
                         pi[l] = 0;
                     } else {
@@ -744,9 +744,12 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         h.tpt[k] = make_float4(pa[0], pa[1], pa[2], 0.f);
         h.tax[k] = make_float4((float)(u[0] / un), (float)(u[1] / un), (float)(u[2] / un), 0.f);
     }
-    // --- pair records in slot order
+    // --- pair records: per slot (c12, cm, cd, ij), stored for the kernel's
+    // two-slot steps as pk[a] = (c12_a, c12_b, cm_a, cm_b) and
+    // pk[b] = (cd_a, cd_b, ij_a, ij_b), slots a = 2t * 32 + lane and b = a + 32,
+    // so each coefficient pair arrives as one two-wide operand
     const int ns = nsteps * 32;
-    std::vector<float4> pk(ns, make_float4(0, 0, 0, 0));  // empty slots: all zero (add 0)
+    std::vector<uint4> rec(ns, make_uint4(0, 0, 0, 0));  // empty slots: all zero (add 0); moved as bits
     for (int s = 0; s < ns; ++s) {
         const int p = slots[s];
         if (p < 0) continue;
@@ -758,15 +761,26 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         float c12, c6, c10;
         pair_coefs(*ff, ti, tj, &c12, &c6, &c10);
         const bool hb = c10 != 0.f;
-        const int ij = i | (j << 16) | slot_flags[s] | (hb ? kPairHB : 0);
+        const uint32_t tgt = (slot_flags[s] & kPairOwned) ? (uint32_t)i : (uint32_t)(32 * apl_for(N));
+        const int ij = (int)((uint32_t)(i | (j << 16) | slot_flags[s] | (hb ? kPairHB : 0)) | (tgt << 24));
         const float cd = (float)((double)ff->w_desolv * (((double)ff->solpar[ti] + (double)ff->qasp * fabs(qi)) * ff->vol[tj] +
                                                          ((double)ff->solpar[tj] + (double)ff->qasp * fabs(qj)) * ff->vol[ti]));
-        float ijf;
-        memcpy(&ijf, &ij, sizeof(float));
-        pk[s] = make_float4(c12, hb ? c10 : c6, cd, ijf);
+        const float cm = hb ? c10 : c6;
+        uint4& r = rec[s];
+        memcpy(&r.x, &c12, 4);
+        memcpy(&r.y, &cm, 4);
+        memcpy(&r.z, &cd, 4);
+        memcpy(&r.w, &ij, 4);
     }
+    std::vector<uint4> pk(ns);
+    for (int a = 0; a < ns; a += 64)
+        for (int l = 0; l < 32; ++l) {
+            const uint4 ra = rec[a + l], rb = rec[a + 32 + l];
+            pk[a + l] = make_uint4(ra.x, rb.x, ra.y, rb.y);
+            pk[a + 32 + l] = make_uint4(ra.z, rb.z, ra.w, rb.w);
+        }
     const size_t off_pk = align_up(sizeof(LigandDev), 256);
-    const size_t off_gent = align_up(off_pk + sizeof(float4) * ns, 256);
+    const size_t off_gent = align_up(off_pk + sizeof(uint4) * ns, 256);
     const size_t bytes = align_up(off_gent + sizeof(uint32_t) * gent.size(), 256);
     h.blob_bytes = (int)bytes;
     h.off_pk = (int)off_pk;
@@ -776,7 +790,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     if (!L) return ADG_ENOMEM;
     std::vector<char> host(bytes, 0);
     memcpy(host.data(), &h, sizeof(h));
-    memcpy(host.data() + off_pk, pk.data(), sizeof(float4) * ns);
+    memcpy(host.data() + off_pk, pk.data(), sizeof(uint4) * ns);
     memcpy(host.data() + off_gent, gent.data(), sizeof(uint32_t) * gent.size());
     cudaError_t e = cudaMalloc(&L->blob, bytes);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L->blob, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);

@@ -64,18 +64,25 @@ struct LigandDev {
 };
 
 // Intramolecular pairs, lane-interleaved: slot (step, lane) = step * 32 + lane,
-// one 16-byte record per slot: pk = (c12, cm, cd, ij as bits) with
-// ij = i | j << 16 | kPairOwned | kPairRowEnd | kPairRowStart | kPairHB (an
-// empty slot is all zero: zero coefficients, no flag).  Atom i is the same for
-// a whole row, so a lane reads its coordinates only at the row's first slot.
+// 16 bytes per slot, (c12, cm, cd, ij as bits), stored for two-slot steps:
+// slots a = 2t * 32 + lane and b = a + 32 hold pk[a] = (c12_a, c12_b, cm_a,
+// cm_b) and pk[b] = (cd_a, cd_b, ij_a, ij_b), with
+// ij = i | j << 16 | kPairOwned | kPairRowEnd | kPairRowStart | kPairHB |
+// target << 24 (an empty slot is all zero: zero coefficients, no flag).  Atom
+// i is the same for a whole row, so a lane reads its coordinates only at the
+// row's first slot.
 // With m = 10 for H-bond pairs (kPairHB) and 6 otherwise, and cq = wq q_i q_j
 // from the charges the posed coordinates carry in .w:
 // E_pair = min(c12 r^-12 - cm r^-m, e_cap) + cq / (eps(r) r) + cd exp(-r^2/(2 s^2)).
 // Forces.  Most pairs are owned by atom i: the pairs a lane runs are grouped
 // into rows, one row per owning atom, each row on one lane only, so the lane
-// sums c_p (x_i - x_j) in registers and stores it to f[i] at the row's last
-// slot (kPairRowEnd).  Everything else -- the partner side of owned pairs, and
-// both sides of the few pairs no row could take -- goes through the force
+// sums c_p (x_i - x_j) in registers and stores it to f[target] at the row's
+// last slot (kPairRowEnd), target = i.  A pair no row could take runs as a
+// row of its own (kPairOwned clear) whose target is 32 * atoms-per-lane: a
+// sink slot past the ligand's atoms (f of an unused atom, or the first moment
+// slot, both rewritten before they are read), so the kernel sums every slot
+// the same way.  Everything else -- the partner side of owned pairs, and
+// both sides of the unowned pairs -- goes through the force
 // gather: after the pair pass has stored c_p of every slot, lane l runs
 // gsteps groups of four entries gent[(k * 4 + q) * 32 + l] = partner |
 // atom << 7 | slot << 14 (one atom per group; bit 30 on the first entry of the

@@ -489,19 +489,21 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     float2 e2 = s2(0.f);
     for (int stp = 0; stp < nsteps; stp += 2) {
         const int ia = stp * 32 + lane, ib = ia + 32;
+        // (c12, cm) of both slots, then (cd, ij) of both slots
         const float4 pa = P.pk[ia], pb = P.pk[ib];
-        const int ija = __float_as_int(pa.w), ijb = __float_as_int(pb.w);
+        const int ija = __float_as_int(pb.z), ijb = __float_as_int(pb.w);
         if (ija & kPairRowStart) xr = ws.xyz[ija & 127];
         const float4 xia = xr, xja = ws.xyz[(ija >> 16) & 127];
         if (ijb & kPairRowStart) xr = ws.xyz[ijb & 127];
         const float4 xib = xr, xjb = ws.xyz[(ijb >> 16) & 127];
-        const float2 dx = sub2(v2(xia.x, xib.x), v2(xja.x, xjb.x));
-        const float2 dy = sub2(v2(xia.y, xib.y), v2(xja.y, xjb.y));
-        const float2 dz = sub2(v2(xia.z, xib.z), v2(xja.z, xjb.z));
+        // differences one slot at a time, so each lands in its half of a pair
+        const float2 dx = v2(xia.x - xja.x, xib.x - xjb.x);
+        const float2 dy = v2(xia.y - xja.y, xib.y - xjb.y);
+        const float2 dz = v2(xia.z - xja.z, xib.z - xjb.z);
         const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
-        const float2 c12 = v2(pa.x, pb.x), cm = v2(pa.y, pb.y), cd = v2(pa.z, pb.z);
+        const float2 c12 = v2(pa.x, pa.y), cm = v2(pa.z, pa.w), cd = v2(pb.x, pb.y);
         // cq = wq q_i q_j; an empty slot (ij == 0; a real pair has i != j) adds nothing
-        const float2 cq = mul2(mul2(v2(ija ? wq : 0.f, ijb ? wq : 0.f), v2(xia.w, xib.w)), v2(xja.w, xjb.w));
+        const float2 cq = v2((ija ? wq : 0.f) * xia.w * xja.w, (ijb ? wq : 0.f) * xib.w * xjb.w);
         const bool fla = r2.x < rmin2, flb = r2.y < rmin2;
         const float2 rr2 = v2(fla ? rmin2 : r2.x, flb ? rmin2 : r2.y);
         const float2 ri = v2(rsqrt_ftz(rr2.x), rsqrt_ftz(rr2.y));
@@ -536,20 +538,20 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
             const float cpa = fla ? 0.f : cp.x, cpb = flb ? 0.f : cp.y;
             ws.c[ia] = cpa;
             ws.c[ib] = cpb;
-            const float coa = (ija & kPairOwned) ? cpa : 0.f;
+            const float coa = cpa;
             rfx = fmaf(coa, dx.x, rfx);
             rfy = fmaf(coa, dy.x, rfy);
             rfz = fmaf(coa, dz.x, rfz);
             if (ija & kPairRowEnd) {
-                ws.f[ija & 127] = make_float4(rfx, rfy, rfz, 0.f);
+                ws.f[(uint32_t)ija >> 24] = make_float4(rfx, rfy, rfz, 0.f);
                 rfx = rfy = rfz = 0.f;
             }
-            const float cob = (ijb & kPairOwned) ? cpb : 0.f;
+            const float cob = cpb;
             rfx = fmaf(cob, dx.y, rfx);
             rfy = fmaf(cob, dy.y, rfy);
             rfz = fmaf(cob, dz.y, rfz);
             if (ijb & kPairRowEnd) {
-                ws.f[ijb & 127] = make_float4(rfx, rfy, rfz, 0.f);
+                ws.f[(uint32_t)ijb >> 24] = make_float4(rfx, rfy, rfz, 0.f);
                 rfx = rfy = rfz = 0.f;
             }
         }
