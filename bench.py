@@ -460,6 +460,30 @@ def main():
                 "gen_share_of_step": st["gen_kernel_ms"] / total_ms if world == 1 else None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peak_src}"}
 
+    # the same kernel against its three unit limits as measured on this GPU
+    # (FP32 flops, special-function results, L2 random gathers), after the
+    # timed region; the binding one is the evaluation's roofline
+    if rank == 0:
+        pk = adg.probe_peaks(ctx)
+        evals_per_launch = p.nrun * ((p.pop_size - 1) + p.pop_size * iters)
+        # per pair two exponentials (ex2) and one rsqrt and one reciprocal (rsqrt rate)
+        per_eval = {"flops": flops_per_launch / evals_per_launch, "mufu": 4.0 * L.npairs,
+                    "l2_bytes": 96.0 * L.natoms}
+        t_unit = {"fp32": per_eval["flops"] / (pk["fp32_tflops"] * 1e12),
+                  "mufu": 2.0 * L.npairs / (pk["mufu_gops"] * 1e9) + 2.0 * L.npairs / (pk["mufu_rsqrt_gops"] * 1e9),
+                  "l2_gather": per_eval["l2_bytes"] / (pk["l2_gather_gbs"] * 1e9)}
+        binding = max(t_unit, key=t_unit.get)
+        limit = 1.0 / t_unit[binding]
+        got = evals_per_launch / (gen_ms_per_launch / 1e3)
+        roofline["measured_units"] = {
+            "fp32_tflops": pk["fp32_tflops"], "fp32_scalar_tflops": pk["fp32_scalar_tflops"],
+            "fp32x2_tflops": pk["fp32x2_tflops"], "mufu_ex2_gops": pk["mufu_gops"],
+            "mufu_rsqrt_gops": pk["mufu_rsqrt_gops"],
+            "l2_gather_gbs": pk["l2_gather_gbs"], "gather_buffer_bytes": pk["gather_bytes"],
+            "frac_of_measured_fp32": achieved / pk["fp32_tflops"],
+            "per_eval": per_eval, "binding_unit": binding, "evals_per_s_limit": limit,
+            "evals_per_s_kernel": got, "frac_of_limit": got / limit}
+
     # end to end through the public API with host buffers: ligand upload + dock + results read back
     ctx.stats(reset=True)
     e2e_t, e2e_evals = 1e-30, 0

@@ -420,6 +420,27 @@ int adg_dock_noalloc(const adg_receptor* rec, const adg_ligand* lig, const adg_s
  * ctr and out: device, 4*n uint32, each 16-byte aligned (ADG_EINVAL otherwise). */
 int adg_philox(adg_ctx* ctx, const uint32_t* ctr, int n, uint64_t key, uint32_t* out);
 
+/* Measured throughput of the units that bound one scoring evaluation (the
+ * roofline terms of the evaluation: FP32 flops, special-function results for
+ * the pair terms' exp / rsqrt / reciprocal, and random gathers of the
+ * L2-resident maps).  Each probe is one launch of 8 blocks of 256 threads
+ * per SM, timed with CUDA events on the context's stream after one untimed
+ * launch; about 20 ms of GPU time in all.  Allocates and frees an 8 MiB
+ * device buffer.  out: host, caller-allocated.  Returns ADG_EINVAL on a null
+ * argument, ADG_ECUDA (text in adg_ctx_last_error) on a CUDA failure. */
+typedef struct adg_peaks {
+    double fp32_tflops;        /* the larger of the two FMA probes; FMA = 2 flops */
+    double fp32_scalar_tflops; /* 16 independent scalar FMA chains per thread */
+    double fp32x2_tflops;      /* 8 independent two-wide FMA chains per thread */
+    double mufu_gops;          /* ex2.approx results per second, 1e9 */
+    double mufu_rsqrt_gops;    /* rsqrt.approx results per second, 1e9 */
+    double l2_gather_gbs;      /* 16-byte random loads over gather_bytes, 1e9 bytes per second */
+    int64_t gather_bytes;      /* size of the gathered buffer */
+    int32_t sms;               /* multiprocessors */
+    int32_t sm_clock_mhz;      /* maximum SM clock the device reports */
+} adg_peaks;
+int adg_probe_peaks(adg_ctx* ctx, adg_peaks* out);
+
 #ifdef __cplusplus
 }
 #endif

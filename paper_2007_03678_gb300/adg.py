@@ -100,6 +100,12 @@ class adg_ligand_stats(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
+class adg_peaks(C.Structure):
+    _fields_ = [("fp32_tflops", C.c_double), ("fp32_scalar_tflops", C.c_double), ("fp32x2_tflops", C.c_double),
+                ("mufu_gops", C.c_double), ("mufu_rsqrt_gops", C.c_double), ("l2_gather_gbs", C.c_double), ("gather_bytes", C.c_int64),
+                ("sms", C.c_int32), ("sm_clock_mhz", C.c_int32)]
+
+
 # The full exported symbol list of include/adg.h.
 EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_ctx_destroy", "adg_sync",
            "adg_ctx_last_error", "adg_maps_build", "adg_receptor_create", "adg_receptor_destroy", "adg_ligand_create",
@@ -108,7 +114,7 @@ EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_c
            "adg_dock_traced", "adg_ligand_descriptors", "adg_mlp_nparams", "adg_mlp_create", "adg_mlp_destroy",
            "adg_mlp_get_params", "adg_mlp_set_params", "adg_mlp_set_norm", "adg_mlp_forward", "adg_mlp_grad",
            "adg_mlp_train_step", "adg_mlp_fit", "adg_ligand_set_stream_id",
-           "adg_ctx_set_graphs", "adg_mlp_set_engine", "adg_mlp_check")
+           "adg_ctx_set_graphs", "adg_mlp_set_engine", "adg_mlp_check", "adg_probe_peaks")
 
 _lib = None
 
@@ -167,6 +173,7 @@ def load(path: str | None = None):
         L.adg_mlp_set_engine.argtypes = [_vp, _i]
         L.adg_mlp_check.argtypes = [_vp, _vp]
         L.adg_ctx_tuned.argtypes = [_vp, C.POINTER(adg_tuned_shape), _i, C.POINTER(C.c_int)]
+        L.adg_probe_peaks.argtypes = [_vp, C.POINTER(adg_peaks)]
         _lib = L
     return _lib
 
@@ -439,6 +446,16 @@ def philox(ctx: Context, ctr, key: int):
     _check(load().adg_philox(ctx.handle, _ptr(ctr), ctr.shape[0], key, _ptr(out)), "adg_philox", ctx)
     ctx._leave()
     return out
+
+
+def probe_peaks(ctx: Context) -> dict:
+    """Measured FP32 (TFLOP/s), special-function (G results/s) and L2 random
+    gather (GB/s) throughput of the context's GPU (adg_probe_peaks)."""
+    out = adg_peaks()
+    ctx._enter()
+    _check(load().adg_probe_peaks(ctx.handle, C.byref(out)), "adg_probe_peaks", ctx)
+    ctx._leave()
+    return {f: getattr(out, f) for f, _ in adg_peaks._fields_}
 
 
 def _result_dtype():

@@ -20,7 +20,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libadg.so")
-SOURCES = ["adg_kernels.cu", "adg_api.cu", "adg_noalloc.cu", "adg_mlp.cu"]
+SOURCES = ["adg_kernels.cu", "adg_api.cu", "adg_noalloc.cu", "adg_mlp.cu", "adg_peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
