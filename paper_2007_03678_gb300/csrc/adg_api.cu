@@ -563,6 +563,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         nsteps = std::max(nsteps, n2);
     }
     nsteps += nsteps & 1;  // the kernel runs two slots per step
+    if (32 * nsteps == P) nsteps += 2;  // keep one empty slot: its c_p is exactly 0 (padding below)
     // Slots, step by step: each lane takes the next pair of its current row,
     // choosing among the row's remaining pairs a partner whose index mod 8 no
     // earlier lane of its quarter-warp uses in this step.
@@ -607,15 +608,19 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     }
     // --- force-gather program: every atom's (partner, slot) entries that its
     // row does not cover go to one lane, in groups of four (the last group
-    // padded with entries whose partner is the atom itself: they add c * 0).
+    // padded with entries whose partner is the atom itself and whose slot is
+    // an empty one, c_p = 0: they add exactly nothing).
     // Atoms are dealt longest list first to the least loaded lane, preferring a
     // quarter-warp without an atom of the same index mod 8; within an atom's
     // entries, each group position takes the entry whose partner (mod 8, in
     // the quarter) and pair slot (mod 32, the c bank, in the warp) earlier
-    // lanes have used least.  Entry = partner | atom << 7 | slot << 14, bit 30
-    // on the first entry of an atom's first group, bit 31 on the last entry
-    // of its last group.  Every lane runs the same number of groups (empty
-    // groups are all zero and never stored).
+    // lanes have used least.  Entry = partner | atom << 7 | slot << 14, bit 31
+    // on the last entry of the atom's last group.  Every lane runs the same
+    // number of groups (empty groups are all zero and never stored).
+    int zero_slot = -1;
+    for (int sl = 0; sl < (int)slots.size() && zero_slot < 0; ++sl)
+        if (slots[sl] < 0) zero_slot = sl;
+    if (zero_slot < 0) return ADG_EINVAL;  // unreachable: nsteps keeps one slot empty
     std::vector<std::vector<std::pair<int, int>>> inc(N);
     for (int sl = 0; sl < (int)slots.size(); ++sl) {
         const int p = slots[sl];
@@ -651,15 +656,13 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         std::vector<int> ai(32, 0), left(32, 0);           // atom index in the lane's list, groups left
         std::vector<std::vector<std::pair<int, int>>> pool(32);  // entries of the current atom not yet placed
         for (int k = 0; k < ngroups; ++k) {
-            std::vector<int> first(32, 0);
             for (int l = 0; l < 32; ++l) {
                 if (ai[l] >= (int)lane_atoms[l].size()) continue;
                 if (left[l] == 0) {
                     const int a2 = lane_atoms[l][ai[l]];
                     pool[l] = inc[a2];
-                    while (pool[l].size() % 4) pool[l].emplace_back(a2, 0);  // self entries add c * 0
+                    while (pool[l].size() % 4) pool[l].emplace_back(a2, zero_slot);
                     left[l] = (int)pool[l].size() / 4;
-                    first[l] = 1;
                 }
             }
             for (int q = 0; q < 4; ++q) {
@@ -681,7 +684,6 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
                     res[l / 8][en.first % 8] += 1;
                     cbank[en.second % 32] += 1;
                     uint32_t e = (uint32_t)en.first | ((uint32_t)a2 << 7) | ((uint32_t)en.second << 14);
-                    if (q == 0 && first[l]) e |= 0x40000000u;
                     if (q == 3 && left[l] == 1) e |= 0x80000000u;
                     gent[(size_t)k * 128 + q * 32 + l] = e;
                 }

@@ -85,10 +85,12 @@ struct LigandDev {
 // both sides of the unowned pairs -- goes through the force
 // gather: after the pair pass has stored c_p of every slot, lane l runs
 // gsteps groups of four entries gent[(k * 4 + q) * 32 + l] = partner |
-// atom << 7 | slot << 14 (one atom per group; bit 30 on the first entry of the
-// atom's first group, bit 31 on the last entry of its last group; lists padded
-// with entries whose partner is the atom itself, and all-zero groups at the
-// end), and adds sum c_p (x_atom - x_partner) to f[atom].
+// atom << 7 | slot << 14 (one atom per group; bit 31 on the last entry of
+// the atom's last group; lists padded with entries whose partner is the atom
+// itself and whose slot is an empty one, c_p = 0, and all-zero groups at the
+// end), sums c_p and c_p x_partner over the atom's entries, and at its last
+// group adds x_atom sum c_p - sum c_p x_partner to f[atom].  Every ligand has
+// at least one empty slot.
 constexpr int kPairOwned = 1 << 15;
 constexpr int kPairRowEnd = 1 << 14;
 constexpr int kPairRowStart = 1 << 13;  // first slot of a row: (re)load atom i's coordinates

@@ -521,7 +521,8 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const float2 D = fma2(s2(msA), den, s2(msB));  // eps(r) = D / den
         const float2 rD = v2(rcp_ftz(D.x), rcp_ftz(D.y));
         const float2 u = mul2(ri, rD);
-        const float2 eel = mul2(mul2(cq, den), u);
+        const float2 cqu = mul2(cq, u);
+        const float2 eel = mul2(cqu, den);
         const float2 tgs = mul2(s2(kgs), rr2);
         const float2 gs = v2(ex2_ftz(tgs.x), ex2_ftz(tgs.y));
         const float2 eds = mul2(cd, gs);
@@ -530,11 +531,12 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
             float2 dlj = mul2(fma2(km, am, mul2(s2(-12.f), a12)), ri2);
             if (elj.x > cap) dlj.x = 0.f;
             if (elj.y > cap) dlj.y = 0.f;
+            // with u = 1 / (r D) and den' = -lambda k e^(-lambda r):
+            // (dE_el/dr) / r = cq u / r (den' - den (A den' / D + 1 / r))
             const float2 dden = mul2(s2(-mslb * msk), ex);
-            const float2 w = fma2(mul2(s2(msA), dden), r, D);
-            const float2 deel = mul2(mul2(cq, sub2(mul2(dden, u), mul2(mul2(den, mul2(u, u)), w))), ri);
-            const float2 dds = mul2(eds, s2(-inv_s2));
-            const float2 cp = add2(add2(dlj, deel), dds);
+            const float2 s = fma2(mul2(s2(-mslb * msk * msA), ex), rD, ri);
+            const float2 deel = mul2(mul2(cqu, ri), fma2(mul2(den, s2(-1.f)), s, dden));
+            const float2 cp = add2(fma2(eds, s2(-inv_s2), dlj), deel);
             const float cpa = fla ? 0.f : cp.x, cpb = flb ? 0.f : cp.y;
             ws.c[ia] = cpa;
             ws.c[ib] = cpb;
@@ -565,27 +567,27 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     if (!GRAD) return out;
     __syncwarp();
     // force gather: f_atom += sum over its pairs that its row did not cover of
-    // c_p (x_atom - x_partner); every lane runs the same number of groups of
+    // c_p (x_atom - x_partner), formed as x_atom sum c_p - sum c_p x_partner
+    // at the atom's last group; every lane runs the same number of groups of
     // four entries, so consecutive groups' loads overlap
     const int ngroups = L->gsteps;
-    float ax = 0.f, ay = 0.f, az = 0.f;
-    float4 xa = make_float4(0.f, 0.f, 0.f, 0.f);  // the current atom
+    float sc = 0.f, bx = 0.f, by = 0.f, bz = 0.f;  // sum c_p and sum c_p x_partner of the current atom
 #pragma unroll 2
     for (int k = 0; k < ngroups; ++k) {
         const uint32_t* ge = P.gent + k * 128 + lane;
         const uint32_t e0 = ge[0], e1 = ge[32], e2 = ge[64], e3 = ge[96];
-        const int atom = (e0 >> 7) & 127;
-        if (e0 & 0x40000000u) xa = ws.xyz[atom];
         const float c0 = ws.c[(e0 >> 14) & 0xffff], c1 = ws.c[(e1 >> 14) & 0xffff],
                     c2 = ws.c[(e2 >> 14) & 0xffff], c3 = ws.c[(e3 >> 14) & 0xffff];
         const float4 x0 = ws.xyz[e0 & 127], x1 = ws.xyz[e1 & 127], x2 = ws.xyz[e2 & 127], x3 = ws.xyz[e3 & 127];
-        ax += c0 * (xa.x - x0.x) + c1 * (xa.x - x1.x) + c2 * (xa.x - x2.x) + c3 * (xa.x - x3.x);
-        ay += c0 * (xa.y - x0.y) + c1 * (xa.y - x1.y) + c2 * (xa.y - x2.y) + c3 * (xa.y - x3.y);
-        az += c0 * (xa.z - x0.z) + c1 * (xa.z - x1.z) + c2 * (xa.z - x2.z) + c3 * (xa.z - x3.z);
-        if (e3 >> 31) {  // the atom's last group: add to its row sum (or zero)
-            const float4 fr = ws.f[atom];
-            ws.f[atom] = make_float4(fr.x + ax, fr.y + ay, fr.z + az, 0.f);
-            ax = ay = az = 0.f;
+        sc += (c0 + c1) + (c2 + c3);
+        bx = fmaf(c3, x3.x, fmaf(c2, x2.x, fmaf(c1, x1.x, fmaf(c0, x0.x, bx))));
+        by = fmaf(c3, x3.y, fmaf(c2, x2.y, fmaf(c1, x1.y, fmaf(c0, x0.y, by))));
+        bz = fmaf(c3, x3.z, fmaf(c2, x2.z, fmaf(c1, x1.z, fmaf(c0, x0.z, bz))));
+        if (e3 >> 31) {  // the atom's last group: add x_atom sum c_p - sum c_p x_partner to its row sum
+            const int atom = (e0 >> 7) & 127;
+            const float4 xa = ws.xyz[atom], fr = ws.f[atom];
+            ws.f[atom] = make_float4(fr.x + fmaf(xa.x, sc, -bx), fr.y + fmaf(xa.y, sc, -by), fr.z + fmaf(xa.z, sc, -bz), 0.f);
+            sc = bx = by = bz = 0.f;
         }
     }
     __syncwarp();
