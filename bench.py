@@ -197,7 +197,7 @@ def workload_config(nrun=None, nev=None) -> dict:
                         f"{w['nrun']} LGA runs x pop 150 x {w['nev']:,} evals, ADADELTA local search",
             "grid": w["grid_n"], "receptor_atoms": w["rec_atoms"], "ligand_atoms": w["n_heavy"] + w["n_hd"],
             "torsions": w["n_tors"], "nrun": w["nrun"], "pop": w["pop"], "nev": w["nev"], "local_search": "adadelta",
-            "l2": "flushed between steps (256 MB write); maps (29 MB packed) are meant to stay L2-resident within a step",
+            "l2": "flushed between steps (256 MB write); maps (58.7 MB packed) are meant to stay L2-resident within a step",
             "parallelism": "replicas"}
 
 
@@ -207,11 +207,11 @@ TRIAGE_TRAIN, TRIAGE_STREAM = 1200, 2000
 #       -k regex:k_dock_generation -s 60 -c 2 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
 #       --no-e2e --no-batching --no-triage --no-graphs
 # (mean of the two launches); None whenever the kernel has changed since that capture.
-GEN_TRAFFIC_BYTES = 26.5e6
+GEN_TRAFFIC_BYTES = None
 # The pipe that bounds the kernel, from the full-section capture of the same
 # kernel (l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed):
 # the L1 / shared-memory data pipe.  None whenever the kernel has changed.
-GEN_L1_PIPE_FRAC = 0.742
+GEN_L1_PIPE_FRAC = None
 
 
 def run_mlp_inference(ctx, rows=1_000_000, reps=10):

@@ -278,7 +278,7 @@ int adg_receptor_create(adg_ctx* ctx, const adg_grid_desc* grid, const float* ma
     r->ctx = ctx;
     r->device = ctx->device;
     r->grid = *grid;
-    cudaError_t e = cudaMalloc(&r->packed, sizeof(float4) * ADG_NTYPES * npt);
+    cudaError_t e = cudaMalloc(&r->packed, 2 * sizeof(float4) * ADG_NTYPES * npt);
     if (e != cudaSuccess) {
         delete r;
         return cuda_fail(ctx, e, "cudaMalloc(packed maps)");
@@ -685,7 +685,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
                     cbank[en.second % 32] += 1;
                     uint32_t e = (uint32_t)en.first | ((uint32_t)a2 << 7) | ((uint32_t)en.second << 14);
                     if (q == 3 && left[l] == 1) e |= 0x80000000u;
-                    gent[(size_t)k * 128 + q * 32 + l] = e;
+                    gent[((size_t)k * 32 + l) * 4 + q] = e;
                 }
             }
             for (int l = 0; l < 32; ++l) {

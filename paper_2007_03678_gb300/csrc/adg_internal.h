@@ -84,7 +84,7 @@ struct LigandDev {
 // the same way.  Everything else -- the partner side of owned pairs, and
 // both sides of the unowned pairs -- goes through the force
 // gather: after the pair pass has stored c_p of every slot, lane l runs
-// gsteps groups of four entries gent[(k * 4 + q) * 32 + l] = partner |
+// gsteps groups of four entries gent[(k * 32 + l) * 4 + q] (one 16-byte load) = partner |
 // atom << 7 | slot << 14 (one atom per group; bit 31 on the last entry of
 // the atom's last group; lists padded with entries whose partner is the atom
 // itself and whose slot is an empty one, c_p = 0, and all-zero groups at the
@@ -105,9 +105,12 @@ struct LigandRef {
     PairsDev pairs;
 };
 
-// Receptor maps, packed per ligand atom type t: node = (M_t, M_elec, M_desolv, 0).
+// Receptor maps, packed per ligand atom type t as one 32-byte record per node
+// holding both x-corners of the cell edge that starts there:
+// (M_t, M_elec, M_desolv, 0) at (x, y, z) and at (x + 1, y, z) (the last
+// node of a row repeats itself), so a trilinear lookup is four 32-byte loads.
 struct MapsDev {
-    const float4* packed;  // [7][nz][ny][nx]
+    const float4* packed;  // [7][nz][ny][nx][2]
     int nx, ny, nz;
     float ox, oy, oz;      // origin
     float h, inv_h;

@@ -221,19 +221,24 @@ cudaError_t launch_maps_build(cudaStream_t st, const adg_forcefield& ff, const a
     return cudaGetLastError();
 }
 
-__global__ void k_pack_maps(const float* __restrict__ maps, long npt, float4* __restrict__ packed)
+__global__ void k_pack_maps(const float* __restrict__ maps, long npt, int nx, float4* __restrict__ packed)
 {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= npt) return;
+    const long i1 = (i % nx == nx - 1) ? i : i + 1;  // the x + 1 neighbour (the last node repeats itself)
     const float e = maps[ADG_MAP_ELEC * npt + i], d = maps[ADG_MAP_DESOLV * npt + i];
+    const float e1 = maps[ADG_MAP_ELEC * npt + i1], d1 = maps[ADG_MAP_DESOLV * npt + i1];
 #pragma unroll
-    for (int t = 0; t < ADG_NTYPES; ++t) packed[t * npt + i] = make_float4(maps[t * npt + i], e, d, 0.f);
+    for (int t = 0; t < ADG_NTYPES; ++t) {
+        packed[2 * (t * npt + i)] = make_float4(maps[t * npt + i], e, d, 0.f);
+        packed[2 * (t * npt + i) + 1] = make_float4(maps[t * npt + i1], e1, d1, 0.f);
+    }
 }
 
 cudaError_t launch_pack_maps(cudaStream_t st, const float* maps, const adg_grid_desc& g, float4* packed)
 {
     const long npt = (long)g.n[0] * g.n[1] * g.n[2];
-    k_pack_maps<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(maps, npt, packed);
+    k_pack_maps<<<(unsigned)((npt + 255) / 256), 256, 0, st>>>(maps, npt, g.n[0], packed);
     return cudaGetLastError();
 }
 
@@ -394,6 +399,14 @@ __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const
     __syncwarp();
 }
 
+// Both x-corners of a cell edge, one 32-byte record: (M_t, M_e, M_d, 0) at x and at x + 1.
+__device__ __forceinline__ void ldg_pair(const float4* p, float4& a, float4& b)
+{
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(b.x), "=f"(b.y), "=f"(b.z), "=f"(b.w)
+        : "l"(p));
+}
+
 // Intermolecular energy of one atom: trilinear interpolation of
 // M_t + q M_e + |q| M_d at the point clamped into the box, plus k_out d^2
 // outside it; gradient accumulated into (gx, gy, gz).
@@ -415,12 +428,14 @@ __device__ __forceinline__ float atom_inter(const MapsDev& M, float k_out, int t
     int iy = min(max((int)floorf(uy), 0), M.ny - 2);
     int iz = min(max((int)floorf(uz), 0), M.nz - 2);
     const float fx = ux - ix, fy = uy - iy, fz = uz - iz;
-    const long nxy = (long)M.nx * M.ny;
-    const float4* p = M.packed + (long)t * nxy * M.nz + (iz * nxy + (long)iy * M.nx + ix);
+    const int nxy = M.nx * M.ny;
+    const float4* p = M.packed + 2 * ((long)t * nxy * M.nz + (iz * nxy + iy * M.nx + ix));
     const float aq = fabsf(q);
-    const float4 c000 = __ldg(p), c100 = __ldg(p + 1), c010 = __ldg(p + M.nx), c110 = __ldg(p + M.nx + 1);
-    const float4 c001 = __ldg(p + nxy), c101 = __ldg(p + nxy + 1), c011 = __ldg(p + nxy + M.nx),
-                 c111 = __ldg(p + nxy + M.nx + 1);
+    float4 c000, c100, c010, c110, c001, c101, c011, c111;
+    ldg_pair(p, c000, c100);
+    ldg_pair(p + 2 * M.nx, c010, c110);
+    ldg_pair(p + 2 * nxy, c001, c101);
+    ldg_pair(p + 2 * (nxy + M.nx), c011, c111);
     const float v000 = c000.x + q * c000.y + aq * c000.z, v100 = c100.x + q * c100.y + aq * c100.z;
     const float v010 = c010.x + q * c010.y + aq * c010.z, v110 = c110.x + q * c110.y + aq * c110.z;
     const float v001 = c001.x + q * c001.y + aq * c001.z, v101 = c101.x + q * c101.y + aq * c101.z;
@@ -574,8 +589,8 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     float sc = 0.f, bx = 0.f, by = 0.f, bz = 0.f;  // sum c_p and sum c_p x_partner of the current atom
 #pragma unroll 2
     for (int k = 0; k < ngroups; ++k) {
-        const uint32_t* ge = P.gent + k * 128 + lane;
-        const uint32_t e0 = ge[0], e1 = ge[32], e2 = ge[64], e3 = ge[96];
+        const uint4 ge = reinterpret_cast<const uint4*>(P.gent)[k * 32 + lane];
+        const uint32_t e0 = ge.x, e1 = ge.y, e2 = ge.z, e3 = ge.w;
         const float c0 = ws.c[(e0 >> 14) & 0xffff], c1 = ws.c[(e1 >> 14) & 0xffff],
                     c2 = ws.c[(e2 >> 14) & 0xffff], c3 = ws.c[(e3 >> 14) & 0xffff];
         const float4 x0 = ws.xyz[e0 & 127], x1 = ws.xyz[e1 & 127], x2 = ws.xyz[e2 & 127], x3 = ws.xyz[e3 & 127];
