@@ -415,6 +415,29 @@ int adg_mlp_fit(adg_ctx* ctx, adg_mlp* mlp, const float* x, const float* t, int 
 int adg_dock_noalloc(const adg_receptor* rec, const adg_ligand* lig, const adg_search_params* p, adg_result* out,
                      void* stream);
 
+/* The schedule adg_ligand_create builds for a ligand, reported without a
+ * device or a context: pair-loop steps (slots per lane; the kernel runs two
+ * per step) and force-gather groups per lane, the empty slots, and the
+ * shared-memory wavefronts one energy+gradient evaluation of the scoring
+ * kernel spends in the pair loop (pair records, row and partner coordinates,
+ * c_p stores, row-end force stores) and in the force gather (entries, c_p,
+ * partner coordinates, the per-atom flush), modelled from the schedule: a
+ * 16-byte access by a warp runs as four quarter-warp phases, each taking as
+ * many wavefronts as the most distinct 16-byte words on one of its eight bank
+ * groups; a 4-byte access takes as many as the most distinct words on one of
+ * the 32 banks; lanes on the same word share it.  *_ideal: the same accesses
+ * without bank conflicts.  Same validation and error codes as
+ * adg_ligand_create; out: host, caller-allocated. */
+typedef struct adg_schedule_stats {
+    int32_t natoms, npairs;
+    int32_t nsteps;       /* pair slots per lane */
+    int32_t gsteps;       /* force-gather groups of four entries per lane */
+    int32_t empty_slots;  /* 32 * nsteps - npairs, at least 1 */
+    int32_t pair_wavefronts, pair_wavefronts_ideal;
+    int32_t gather_wavefronts, gather_wavefronts_ideal;
+} adg_schedule_stats;
+int adg_ligand_schedule(const adg_forcefield* ff, const adg_ligand_desc* d, adg_schedule_stats* out);
+
 /* Philox4x32-10 (Salmon et al., SC'11) on the device: out[4i..4i+3] =
  * Philox(counter ctr[4i..4i+3], key = (key & 0xffffffff, key >> 32)).
  * ctr and out: device, 4*n uint32, each 16-byte aligned (ADG_EINVAL otherwise). */

@@ -100,6 +100,11 @@ class adg_ligand_stats(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
+class adg_schedule_stats(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("natoms", "npairs", "nsteps", "gsteps", "empty_slots", "pair_wavefronts",
+                                         "pair_wavefronts_ideal", "gather_wavefronts", "gather_wavefronts_ideal")]
+
+
 class adg_peaks(C.Structure):
     _fields_ = [("fp32_tflops", C.c_double), ("fp32_scalar_tflops", C.c_double), ("fp32x2_tflops", C.c_double),
                 ("mufu_gops", C.c_double), ("mufu_rsqrt_gops", C.c_double), ("l2_gather_gbs", C.c_double), ("gather_bytes", C.c_int64),
@@ -114,7 +119,7 @@ EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_c
            "adg_dock_traced", "adg_ligand_descriptors", "adg_mlp_nparams", "adg_mlp_create", "adg_mlp_destroy",
            "adg_mlp_get_params", "adg_mlp_set_params", "adg_mlp_set_norm", "adg_mlp_forward", "adg_mlp_grad",
            "adg_mlp_train_step", "adg_mlp_fit", "adg_ligand_set_stream_id",
-           "adg_ctx_set_graphs", "adg_mlp_set_engine", "adg_mlp_check", "adg_probe_peaks")
+           "adg_ctx_set_graphs", "adg_mlp_set_engine", "adg_mlp_check", "adg_probe_peaks", "adg_ligand_schedule")
 
 _lib = None
 
@@ -174,6 +179,8 @@ def load(path: str | None = None):
         L.adg_mlp_check.argtypes = [_vp, _vp]
         L.adg_ctx_tuned.argtypes = [_vp, C.POINTER(adg_tuned_shape), _i, C.POINTER(C.c_int)]
         L.adg_probe_peaks.argtypes = [_vp, C.POINTER(adg_peaks)]
+        L.adg_ligand_schedule.argtypes = [C.POINTER(adg_forcefield), C.POINTER(adg_ligand_desc),
+                                          C.POINTER(adg_schedule_stats)]
         _lib = L
     return _lib
 
@@ -357,26 +364,44 @@ class Receptor:
             pass
 
 
+def ligand_desc(lig):
+    """adg_ligand_desc of a synth.Ligand-like object, and the arrays it points
+    into (keep them alive while the descriptor is used)."""
+    xyz = np.ascontiguousarray(lig.xyz, np.float32).reshape(-1)
+    typ = np.ascontiguousarray(lig.type, np.int32)
+    q = np.ascontiguousarray(lig.charge, np.float32)
+    bonds = np.ascontiguousarray(lig.bonds, np.int32).reshape(-1)
+    tors = np.ascontiguousarray(lig.tors, np.int32).reshape(-1)
+    d = adg_ligand_desc()
+    d.natoms = len(typ)
+    d.xyz = xyz.ctypes.data_as(C.POINTER(C.c_float))
+    d.type = typ.ctypes.data_as(C.POINTER(C.c_int32))
+    d.charge = q.ctypes.data_as(C.POINTER(C.c_float))
+    d.nbonds = len(bonds) // 2
+    d.bonds = bonds.ctypes.data_as(C.POINTER(C.c_int32))
+    d.ntors = len(tors) // 2
+    d.tors = tors.ctypes.data_as(C.POINTER(C.c_int32))
+    d.root = int(lig.root)
+    return d, (xyz, typ, q, bonds, tors)
+
+
+def ligand_schedule(ff: dict, lig) -> dict:
+    """adg_ligand_schedule: the pair-loop and force-gather schedule the library
+    builds for `lig`, with its modelled shared-memory wavefronts per
+    energy+gradient evaluation (host only, no GPU)."""
+    d, _keep = ligand_desc(lig)
+    ffs = forcefield_struct(ff)
+    out = adg_schedule_stats()
+    _check(load().adg_ligand_schedule(C.byref(ffs), C.byref(d), C.byref(out)), "adg_ligand_schedule")
+    return {f: getattr(out, f) for f, _ in adg_schedule_stats._fields_}
+
+
 class Ligand:
     """adg_ligand_create from a synth.Ligand-like object (xyz, type, charge, bonds, tors, root)."""
 
     def __init__(self, ctx: Context, ff: dict, lig):
         self.ctx = ctx
-        xyz = np.ascontiguousarray(lig.xyz, np.float32).reshape(-1)
-        typ = np.ascontiguousarray(lig.type, np.int32)
-        q = np.ascontiguousarray(lig.charge, np.float32)
-        bonds = np.ascontiguousarray(lig.bonds, np.int32).reshape(-1)
-        tors = np.ascontiguousarray(lig.tors, np.int32).reshape(-1)
-        d = adg_ligand_desc()
-        d.natoms = len(typ)
-        d.xyz = xyz.ctypes.data_as(C.POINTER(C.c_float))
-        d.type = typ.ctypes.data_as(C.POINTER(C.c_int32))
-        d.charge = q.ctypes.data_as(C.POINTER(C.c_float))
-        d.nbonds = len(bonds) // 2
-        d.bonds = bonds.ctypes.data_as(C.POINTER(C.c_int32))
-        d.ntors = len(tors) // 2
-        d.tors = tors.ctypes.data_as(C.POINTER(C.c_int32))
-        d.root = int(lig.root)
+        d, _keep = ligand_desc(lig)
         ffs = forcefield_struct(ff)
         h = C.c_void_p()
         _check(load().adg_ligand_create(ctx.handle, C.byref(ffs), C.byref(d), C.byref(h)), "adg_ligand_create", ctx)

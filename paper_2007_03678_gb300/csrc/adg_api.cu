@@ -328,10 +328,49 @@ int adg_receptor_destroy(adg_receptor* rec)
     return ADG_OK;
 }
 
-int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_desc* d, adg_ligand** out)
+}  // extern "C"
+
+namespace {
+
+// The distinct words one shared-memory access reads, by bank: a 16-byte
+// access by a quarter-warp (8 groups of four banks) or a 4-byte access by a
+// warp (32 banks).  cost(w) = the wavefronts reading w as well would add.
+template <int BANKS>
+struct WordSet {
+    int words[32];
+    int n = 0, mx = 0;
+    int cnt[BANKS] = {};
+    bool has(int w) const
+    {
+        for (int k = 0; k < n; ++k)
+            if (words[k] == w) return true;
+        return false;
+    }
+    int cost(int w) const { return has(w) ? 0 : std::max(0, cnt[w % BANKS] + 1 - mx); }
+    // ranks a choice: added wavefronts first, then a word already read (shared
+    // for free) over a new one, then the fuller its bank would get
+    int rank(int w) const { return has(w) ? 0 : 64 * cost(w) + 1 + cnt[w % BANKS]; }
+    void add(int w)
+    {
+        if (has(w)) return;
+        words[n++] = w;
+        mx = std::max(mx, ++cnt[w % BANKS]);
+    }
+};
+
+// Host-side plan of a ligand: the device header, the pair records and the
+// force-gather program the scoring kernel runs, built without touching a
+// device (adg_ligand_create uploads it; adg_ligand_schedule reports on it).
+struct LigandPlan {
+    LigandDev h;
+    std::vector<uint4> pk;
+    std::vector<uint32_t> gent;
+    int nf = 0, sum_moving = 0;
+};
+
+int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& pl)
 {
-    if (!ctx || !ff || !d || !out || !d->xyz || !d->type || !d->charge) return ADG_EINVAL;
-    *out = nullptr;
+    if (!ff || !d || !d->xyz || !d->type || !d->charge) return ADG_EINVAL;
     const int N = d->natoms, T = d->ntors;
     if (N < 1 || T < 0 || d->nbonds < 0) return ADG_EINVAL;
     if (N > ADG_MAX_ATOMS || T > ADG_MAX_TORS) return ADG_ETOOBIG;
@@ -565,8 +604,10 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     nsteps += nsteps & 1;  // the kernel runs two slots per step
     if (32 * nsteps == P) nsteps += 2;  // keep one empty slot: its c_p is exactly 0 (padding below)
     // Slots, step by step: each lane takes the next pair of its current row,
-    // choosing among the row's remaining pairs a partner whose index mod 8 no
-    // earlier lane of its quarter-warp uses in this step.
+    // choosing among the row's remaining pairs the partner that adds the fewest
+    // shared-memory wavefronts to its quarter-warp's partner load in this step
+    // (a partner another lane already reads is free); lanes with the fewest
+    // pairs left choose first.  A lane past its last row reads atom 0.
     std::vector<int> slots((size_t)nsteps * 32, -1);
     std::vector<int> slot_flags((size_t)nsteps * 32, 0);
     {
@@ -574,24 +615,32 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
         std::vector<std::vector<int>> rem(32);  // remaining pairs of the current row
         for (int st = 0; st < nsteps; ++st)
             for (int qd = 0; qd < 4; ++qd) {
-                int used = 0;  // partner residues taken in this quarter and step
+                WordSet<8> ph;  // partners this quarter reads in this step
+                int order[8], no = 0;
                 for (int l = qd * 8; l < qd * 8 + 8; ++l) {
-                    if (ri[l] >= (int)lane_rows[l].size()) continue;
+                    if (ri[l] >= (int)lane_rows[l].size()) {
+                        ph.add(0);
+                        continue;
+                    }
+                    if (pi[l] == 0) rem[l] = rows[lane_rows[l][ri[l]]].ps;
+                    order[no++] = l;
+                }
+                std::stable_sort(order, order + no, [&](int x, int y) { return rem[x].size() < rem[y].size(); });
+                for (int t = 0; t < no; ++t) {
+                    const int l = order[t];
                     const Row& r = rows[lane_rows[l][ri[l]]];
-                    if (pi[l] == 0) rem[l] = r.ps;
                     const int i0 = r.owner >= 0 ? r.owner : pairs[r.ps[0]].first;
-                    int pick = 0;
+                    int pick = 0, best = 1 << 30;
                     for (size_t k = 0; k < rem[l].size(); ++k) {
-                        const int pt = pairs[rem[l][k]].first + pairs[rem[l][k]].second - i0;
-                        if (!(used >> (pt % 8) & 1)) {
+                        const int rk = ph.rank(pairs[rem[l][k]].first + pairs[rem[l][k]].second - i0);
+                        if (rk < best) {
+                            best = rk;
                             pick = (int)k;
-                            break;
                         }
                     }
                     const int p = rem[l][pick];
                     rem[l].erase(rem[l].begin() + pick);
-                    const int pt = pairs[p].first + pairs[p].second - i0;
-                    used |= 1 << (pt % 8);
+                    ph.add(pairs[p].first + pairs[p].second - i0);
                     slots[(size_t)st * 32 + l] = p;
                     int fl = r.owner >= 0 ? kPairOwned : 0;
                     if (pi[l] == 0) fl |= kPairRowStart;
@@ -608,15 +657,16 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     }
     // --- force-gather program: every atom's (partner, slot) entries that its
     // row does not cover go to one lane, in groups of four (the last group
-    // padded with entries whose partner is the atom itself and whose slot is
-    // an empty one, c_p = 0: they add exactly nothing).
-    // Atoms are dealt longest list first to the least loaded lane, preferring a
-    // quarter-warp without an atom of the same index mod 8; within an atom's
-    // entries, each group position takes the entry whose partner (mod 8, in
-    // the quarter) and pair slot (mod 32, the c bank, in the warp) earlier
-    // lanes have used least.  Entry = partner | atom << 7 | slot << 14, bit 31
-    // on the last entry of the atom's last group.  Every lane runs the same
-    // number of groups (empty groups are all zero and never stored).
+    // padded with entries on an empty slot, c_p = 0, which add exactly nothing
+    // whatever their partner).  Atoms are dealt longest list first to the
+    // least loaded lane, preferring a quarter-warp without an atom of the same
+    // index mod 8.  Group by group and position by position, each lane (fewest
+    // entries left first) takes the entry that adds the fewest shared-memory
+    // wavefronts to the position's partner load (its quarter-warp) and c_p
+    // load (the warp); a padding entry reads a partner its quarter already
+    // reads.  Entry = partner | atom << 7 | slot << 14, bit 31 on the last
+    // entry of the atom's last group.  Every lane runs the same number of
+    // groups (empty groups are all zero and never stored).
     int zero_slot = -1;
     for (int sl = 0; sl < (int)slots.size() && zero_slot < 0; ++sl)
         if (slots[sl] < 0) zero_slot = sl;
@@ -666,23 +716,40 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
                 }
             }
             for (int q = 0; q < 4; ++q) {
-                std::vector<int> cbank(32, 0);
-                std::vector<std::vector<int>> res(4, std::vector<int>(8, 0));
+                WordSet<32> cb;    // c_p slots the warp reads at this position
+                WordSet<8> ph[4];  // partners each quarter reads at this position
+                int order[32], no = 0;
                 for (int l = 0; l < 32; ++l) {
-                    if (ai[l] >= (int)lane_atoms[l].size()) continue;
+                    if (ai[l] >= (int)lane_atoms[l].size()) {  // an all-zero entry: slot 0, atom 0
+                        cb.add(0);
+                        ph[l / 8].add(0);
+                        continue;
+                    }
+                    order[no++] = l;
+                }
+                std::stable_sort(order, order + no, [&](int x, int y) { return pool[x].size() < pool[y].size(); });
+                for (int t = 0; t < no; ++t) {
+                    const int l = order[t];
                     const int a2 = lane_atoms[l][ai[l]];
-                    int pick = 0, best_cost = 1 << 30;
-                    for (size_t t = 0; t < pool[l].size(); ++t) {
-                        const int cost = 4 * res[l / 8][pool[l][t].first % 8] + cbank[pool[l][t].second % 32];
-                        if (cost < best_cost) {
-                            best_cost = cost;
-                            pick = (int)t;
+                    WordSet<8>& pq = ph[l / 8];
+                    // a padding entry (empty slot, c_p = 0) adds nothing whatever its
+                    // partner: it reads an atom its quarter already reads, if any
+                    const int pad_partner = pq.n > 0 ? pq.words[0] : a2;
+                    int pick = 0, best = 1 << 30;
+                    for (size_t c = 0; c < pool[l].size(); ++c) {
+                        const bool pad = pool[l][c].second == zero_slot;
+                        const int pt = pad ? pad_partner : pool[l][c].first;
+                        const int rk = pq.rank(pt) + cb.rank(pool[l][c].second);
+                        if (rk < best) {
+                            best = rk;
+                            pick = (int)c;
                         }
                     }
-                    const std::pair<int, int> en = pool[l][pick];
+                    std::pair<int, int> en = pool[l][pick];
                     pool[l].erase(pool[l].begin() + pick);
-                    res[l / 8][en.first % 8] += 1;
-                    cbank[en.second % 32] += 1;
+                    if (en.second == zero_slot) en.first = pad_partner;
+                    pq.add(en.first);
+                    cb.add(en.second);
                     uint32_t e = (uint32_t)en.first | ((uint32_t)a2 << 7) | ((uint32_t)en.second << 14);
                     if (q == 3 && left[l] == 1) e |= 0x80000000u;
                     gent[((size_t)k * 32 + l) * 4 + q] = e;
@@ -787,13 +854,135 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     h.blob_bytes = (int)bytes;
     h.off_pk = (int)off_pk;
     h.off_gent = (int)off_gent;
+    pl.h = h;
+    pl.pk = std::move(pk);
+    pl.gent = std::move(gent);
+    pl.nf = nf;
+    pl.sum_moving = 0;
+    for (int k = 0; k < T; ++k) pl.sum_moving += shi[k] - slo[k];
+    return ADG_OK;
+}
+
+// Shared-memory wavefronts of one warp access, from the word each lane
+// touches (-1: lane inactive); lanes on the same word share it.  A 16-byte
+// access runs as four quarter-warp phases, each taking as many wavefronts as
+// the most distinct words on one of its eight 16-byte bank groups; a 4-byte
+// access takes as many as the most distinct words on one of the 32 banks.
+// `ideal` adds what the access would take without bank conflicts.
+int wavefronts(const int* w, bool wide, int* ideal)
+{
+    int tot = 0, best = 0;
+    const int nphase = wide ? 4 : 1, lanes = wide ? 8 : 32, banks = wide ? 8 : 32;
+    for (int ph = 0; ph < nphase; ++ph) {
+        int cnt[32] = {0}, any = 0, m = 0;
+        for (int l = ph * lanes; l < (ph + 1) * lanes; ++l) {
+            if (w[l] < 0) continue;
+            bool dup = false;
+            for (int k = ph * lanes; k < l && !dup; ++k) dup = w[k] == w[l];
+            if (dup) continue;
+            any = 1;
+            m = std::max(m, ++cnt[w[l] % banks]);
+        }
+        tot += m;
+        best += any;
+    }
+    *ideal += best;
+    return tot;
+}
+
+// The scoring kernel's shared-memory accesses in the pair loop and the force
+// gather of one energy+gradient evaluation, walked over the plan.
+void model_schedule(const LigandPlan& pl, adg_schedule_stats* out)
+{
+    const LigandDev& h = pl.h;
+    int w[32], pi = 0, gi = 0;
+    int pw = 0, gw = 0;
+    const int ns = h.nsteps * 32;
+    for (int a0 = 0; a0 < ns; a0 += 64) {
+        uint32_t ij[2][32];
+        for (int l = 0; l < 32; ++l) {
+            ij[0][l] = pl.pk[a0 + 32 + l].z;
+            ij[1][l] = pl.pk[a0 + 32 + l].w;
+        }
+        for (int r = 0; r < 2; ++r) {  // the two record loads: consecutive words
+            for (int l = 0; l < 32; ++l) w[l] = a0 + 32 * r + l;
+            pw += wavefronts(w, true, &pi);
+        }
+        for (int sl = 0; sl < 2; ++sl) {
+            for (int l = 0; l < 32; ++l) w[l] = (ij[sl][l] & kPairRowStart) ? (int)(ij[sl][l] & 127) : -1;
+            pw += wavefronts(w, true, &pi);  // row atom at the row's first slot
+            for (int l = 0; l < 32; ++l) w[l] = (int)((ij[sl][l] >> 16) & 127);
+            pw += wavefronts(w, true, &pi);  // partner
+        }
+        for (int sl = 0; sl < 2; ++sl) {  // c_p stores: consecutive
+            for (int l = 0; l < 32; ++l) w[l] = a0 + 32 * sl + l;
+            pw += wavefronts(w, false, &pi);
+        }
+        for (int sl = 0; sl < 2; ++sl) {  // row-end force stores
+            for (int l = 0; l < 32; ++l) w[l] = (ij[sl][l] & kPairRowEnd) ? (int)(ij[sl][l] >> 24) : -1;
+            pw += wavefronts(w, true, &pi);
+        }
+    }
+    for (int k = 0; k < h.gsteps; ++k) {
+        const uint32_t* e = pl.gent.data() + (size_t)k * 128;
+        for (int l = 0; l < 32; ++l) w[l] = k * 32 + l;
+        gw += wavefronts(w, true, &gi);  // the group's four entries
+        for (int q = 0; q < 4; ++q) {
+            for (int l = 0; l < 32; ++l) w[l] = (int)((e[l * 4 + q] >> 14) & 0xffff);
+            gw += wavefronts(w, false, &gi);  // c_p
+        }
+        for (int q = 0; q < 4; ++q) {
+            for (int l = 0; l < 32; ++l) w[l] = (int)(e[l * 4 + q] & 127);
+            gw += wavefronts(w, true, &gi);  // partner coordinates
+        }
+        // flush at the atom's last group: its coordinates and force read, the force written
+        for (int l = 0; l < 32; ++l) w[l] = (e[l * 4 + 3] >> 31) ? (int)((e[l * 4] >> 7) & 127) : -1;
+        for (int r = 0; r < 3; ++r) gw += wavefronts(w, true, &gi);
+    }
+    out->pair_wavefronts = pw;
+    out->pair_wavefronts_ideal = pi;
+    out->gather_wavefronts = gw;
+    out->gather_wavefronts_ideal = gi;
+}
+
+}  // namespace
+
+extern "C" {
+
+int adg_ligand_schedule(const adg_forcefield* ff, const adg_ligand_desc* d, adg_schedule_stats* out)
+{
+    if (!ff || !d || !out) return ADG_EINVAL;
+    LigandPlan pl;
+    const int rc = plan_ligand(ff, d, pl);
+    if (rc != ADG_OK) return rc;
+    memset(out, 0, sizeof(*out));
+    out->natoms = pl.h.natoms;
+    out->npairs = pl.h.npairs;
+    out->nsteps = pl.h.nsteps;
+    out->gsteps = pl.h.gsteps;
+    out->empty_slots = pl.h.nsteps * 32 - pl.h.npairs;
+    model_schedule(pl, out);
+    return ADG_OK;
+}
+
+int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_desc* d, adg_ligand** out)
+{
+    if (!ctx || !ff || !d || !out) return ADG_EINVAL;
+    *out = nullptr;
+    LigandPlan pl;
+    const int rc = plan_ligand(ff, d, pl);
+    if (rc != ADG_OK) return rc;
+    const LigandDev& h = pl.h;
+    const int N = h.natoms, T = h.ntors, P = h.npairs, nf = pl.nf;
+    const size_t bytes = (size_t)h.blob_bytes, off_pk = (size_t)h.off_pk, off_gent = (size_t)h.off_gent;
+    const int ns = (int)pl.pk.size();
     CK(ctx, cudaSetDevice(ctx->device));
     adg_ligand* L = new (std::nothrow) adg_ligand();
     if (!L) return ADG_ENOMEM;
     std::vector<char> host(bytes, 0);
     memcpy(host.data(), &h, sizeof(h));
-    memcpy(host.data() + off_pk, pk.data(), sizeof(uint4) * ns);
-    memcpy(host.data() + off_gent, gent.data(), sizeof(uint32_t) * gent.size());
+    memcpy(host.data() + off_pk, pl.pk.data(), sizeof(uint4) * ns);
+    memcpy(host.data() + off_gent, pl.gent.data(), sizeof(uint32_t) * pl.gent.size());
     cudaError_t e = cudaMalloc(&L->blob, bytes);
     if (e == cudaSuccess) e = cudaMemcpyAsync(L->blob, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
@@ -814,7 +1003,7 @@ int adg_ligand_create(adg_ctx* ctx, const adg_forcefield* ff, const adg_ligand_d
     L->npairs = P;
     L->apl = apl_for(N);
     L->bytes = bytes;
-    for (int k = 0; k < T; ++k) L->sum_moving += shi[k] - slo[k];
+    L->sum_moving = pl.sum_moving;
     // descriptors of the ligand for the triage network (see adg_ligand_descriptors)
     {
         float* D = L->desc;

@@ -86,9 +86,8 @@ struct LigandDev {
 // gather: after the pair pass has stored c_p of every slot, lane l runs
 // gsteps groups of four entries gent[(k * 32 + l) * 4 + q] (one 16-byte load) = partner |
 // atom << 7 | slot << 14 (one atom per group; bit 31 on the last entry of
-// the atom's last group; lists padded with entries whose partner is the atom
-// itself and whose slot is an empty one, c_p = 0, and all-zero groups at the
-// end), sums c_p and c_p x_partner over the atom's entries, and at its last
+// the atom's last group; lists padded with entries on an empty slot, c_p = 0,
+// whose partner is any posed atom, and all-zero groups at the end), sums c_p and c_p x_partner over the atom's entries, and at its last
 // group adds x_atom sum c_p - sum c_p x_partner to f[atom].  Every ligand has
 // at least one empty slot.
 constexpr int kPairOwned = 1 << 15;

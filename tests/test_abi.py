@@ -44,9 +44,10 @@ def test_struct_layouts_match_header():
 #include <stddef.h>
 #include "adg.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(adg_forcefield), sizeof(adg_grid_desc),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(adg_forcefield), sizeof(adg_grid_desc),
          sizeof(adg_ligand_desc), sizeof(adg_search_params), sizeof(adg_result), sizeof(adg_dock_trace),
-         sizeof(adg_stats), sizeof(adg_ligand_stats), sizeof(adg_tuned_shape), sizeof(adg_peaks));
+         sizeof(adg_stats), sizeof(adg_ligand_stats), sizeof(adg_tuned_shape), sizeof(adg_peaks),
+         sizeof(adg_schedule_stats));
   printf("%zu %zu %zu %zu %zu %zu\n", offsetof(adg_search_params, seed), offsetof(adg_search_params, mut_tors),
          offsetof(adg_result, genes), offsetof(adg_result, xyz), offsetof(adg_forcefield, k_out),
          offsetof(adg_peaks, gather_bytes));
@@ -59,12 +60,12 @@ int main(void) {
         open(src, "w").write(probe)
         subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe])
         out = subprocess.check_output([exe]).decode().split()
-    sizes = [int(x) for x in out[:10]]
-    offs = [int(x) for x in out[10:]]
+    sizes = [int(x) for x in out[:11]]
+    offs = [int(x) for x in out[11:]]
     assert sizes == [C.sizeof(adg.adg_forcefield), C.sizeof(adg.adg_grid_desc), C.sizeof(adg.adg_ligand_desc),
                      C.sizeof(adg.adg_search_params), C.sizeof(adg.adg_result), C.sizeof(adg.adg_dock_trace),
                      C.sizeof(adg.adg_stats), C.sizeof(adg.adg_ligand_stats), C.sizeof(adg.adg_tuned_shape),
-                     C.sizeof(adg.adg_peaks)]
+                     C.sizeof(adg.adg_peaks), C.sizeof(adg.adg_schedule_stats)]
     assert offs == [adg.adg_search_params.seed.offset, adg.adg_search_params.mut_tors.offset,
                     adg.adg_result.genes.offset, adg.adg_result.xyz.offset, adg.adg_forcefield.k_out.offset,
                     adg.adg_peaks.gather_bytes.offset]
