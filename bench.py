@@ -202,11 +202,12 @@ def workload_config(nrun=None, nev=None) -> dict:
 
 
 TRIAGE_TRAIN, TRIAGE_STREAM = 1200, 2000
-# DRAM bytes (read + write) per full-size launch of the generation kernel, from
+# DRAM bytes (read + write) per generation of all 100 runs (two launches of the
+# generation kernel, 50 runs each), from
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
 #       -k regex:k_dock_generation -s 60 -c 2 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
 #       --no-e2e --no-batching --no-triage --no-graphs
-# (mean of the two launches); None whenever the kernel has changed since that capture.
+# (the sum of the two launches); None whenever the kernel has changed since that capture.
 GEN_TRAFFIC_BYTES = None
 # The pipe that bounds the kernel, from the full-section capture of the same
 # kernel (l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed):
@@ -442,21 +443,23 @@ def main():
     value = evals / (total_ms / 1e3)
     ligands_per_s = world * args.steps / (total_ms / 1e3)
 
-    # roofline of the dominant kernel (the GA-generation kernel: selection + ADADELTA)
+    # roofline of the dominant kernel (the GA-generation kernel: selection + ADADELTA).  One
+    # generation of the 100 runs is two concurrent launches of 50 runs each (the library docks
+    # one ligand's runs as concurrent halves); the figures are per generation of all runs.
     gens = int(results["generations"][0])
     iters = p.ls_max_iters
     f_eg = flops_per_eval(L.natoms, L.npairs, L.sum_moving, True)
     f_e = flops_per_eval(L.natoms, L.npairs, L.sum_moving, False)
     gen_flops_per_step = p.nrun * gens * ((p.pop_size - 1) * f_e + p.pop_size * iters * f_eg)
-    gen_ms_per_launch = st["gen_kernel_ms"] / max(1, st["gen_timed"])
-    flops_per_launch = gen_flops_per_step / gens
-    achieved = flops_per_launch / (gen_ms_per_launch / 1e3) / 1e12
+    gen_ms = st["gen_kernel_ms"] / max(1, st["gen_timed"])
+    flops_per_gen = gen_flops_per_step / gens
+    achieved = flops_per_gen / (gen_ms / 1e3) / 1e12
     peak, peak_src = fp32_peak_tflops()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": GEN_TRAFFIC_BYTES, "traffic_unit": "bytes per launch (dram read + write)",
+                "traffic": GEN_TRAFFIC_BYTES, "traffic_unit": "bytes per generation of all runs (dram read + write)",
                 "l1_shared_pipe_frac_ncu": GEN_L1_PIPE_FRAC,
                 "kernel": "k_dock_generation<2,ADADELTA>",
-                "launch_ms": gen_ms_per_launch, "flops_per_launch": flops_per_launch,
+                "generation_ms": gen_ms, "flops_per_generation": flops_per_gen,
                 "gen_share_of_step": st["gen_kernel_ms"] / total_ms if world == 1 else None,
                 "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {peak_src}"}
 
@@ -465,16 +468,16 @@ def main():
     # timed region; the binding one is the evaluation's roofline
     if rank == 0:
         pk = adg.probe_peaks(ctx)
-        evals_per_launch = p.nrun * ((p.pop_size - 1) + p.pop_size * iters)
+        evals_per_gen = p.nrun * ((p.pop_size - 1) + p.pop_size * iters)
         # per pair two exponentials (ex2) and one rsqrt and one reciprocal (rsqrt rate)
-        per_eval = {"flops": flops_per_launch / evals_per_launch, "mufu": 4.0 * L.npairs,
+        per_eval = {"flops": flops_per_gen / evals_per_gen, "mufu": 4.0 * L.npairs,
                     "l2_bytes": 96.0 * L.natoms}
         t_unit = {"fp32": per_eval["flops"] / (pk["fp32_tflops"] * 1e12),
                   "mufu": 2.0 * L.npairs / (pk["mufu_gops"] * 1e9) + 2.0 * L.npairs / (pk["mufu_rsqrt_gops"] * 1e9),
                   "l2_gather": per_eval["l2_bytes"] / (pk["l2_gather_gbs"] * 1e9)}
         binding = max(t_unit, key=t_unit.get)
         limit = 1.0 / t_unit[binding]
-        got = evals_per_launch / (gen_ms_per_launch / 1e3)
+        got = evals_per_gen / (gen_ms / 1e3)
         roofline["measured_units"] = {
             "fp32_tflops": pk["fp32_tflops"], "fp32_scalar_tflops": pk["fp32_scalar_tflops"],
             "fp32x2_tflops": pk["fp32x2_tflops"], "mufu_ex2_gops": pk["mufu_gops"],

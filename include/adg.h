@@ -272,13 +272,16 @@ int adg_dock_traced(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* con
 
 /* Launch accounting of a context, for measurement.  Counts every kernel the
  * library launched on the context since the last reset; when timing is on
- * (adg_ctx_set_timing), each GA-generation launch of adg_dock is bracketed
- * by CUDA events on the context's stream and gen_kernel_ms is their sum. */
+ * (adg_ctx_set_timing), the generation loops of each adg_dock call are
+ * bracketed by CUDA events: gen_kernel_ms adds the span from the first
+ * group's loop start to the last group's loop end (the groups of a call run
+ * concurrently), gen_timed the generations of its longest group, so
+ * gen_kernel_ms / gen_timed is the time of one generation of all its runs. */
 typedef struct {
     int64_t kernel_launches;  /* all kernels launched by the library       */
     int64_t gen_launches;     /* generation kernels (selection + LS) only  */
-    double gen_kernel_ms;     /* summed event time of generation launches  */
-    int64_t gen_timed;        /* generation launches included in that sum  */
+    double gen_kernel_ms;     /* event-timed span of the generation loops  */
+    int64_t gen_timed;        /* generation rounds in that span            */
     int64_t h2d_bytes;        /* host -> device bytes copied by the library */
     int64_t d2h_bytes;        /* device -> host bytes copied by the library */
     int64_t dock_groups;      /* ligand groups (one graph each) of adg_dock */

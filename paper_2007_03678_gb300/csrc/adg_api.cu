@@ -1125,7 +1125,12 @@ struct ClassRun {
     cudaStream_t stream = nullptr;
     cudaGraphExec_t exec = nullptr;
     cudaEvent_t t0 = nullptr, t1 = nullptr;  // around the generation loop (timing mode)
+    SearchDev S;   // the call's search parameters, nrun = this group's runs per ligand
+    int run0 = 0;  // the group's first run
 };
+
+// A single ligand's runs go out in this many concurrent groups (see dock_impl).
+constexpr int kRunParts = 2;
 
 void fill_search(const adg_search_params* p, SearchDev& S)
 {
@@ -1425,6 +1430,23 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
     std::vector<ClassRun> cls;
     int rc = group_ligands(ctx, rec, ligs, nlig, p->ls_method, cls);
     if (rc != ADG_OK) return rc;
+    SearchDev S;
+    fill_search(p, S);
+    for (ClassRun& c : cls) c.S = S;
+    // One ligand's runs in two halves on two concurrent graphs: the last,
+    // partly filled wave of one half's generation launch overlaps the other
+    // half's next generation.  Runs are independent and their random streams
+    // are keyed by the run index, so the results do not change.
+    if (!trace && cls.size() == 1 && cls[0].ligs.size() == 1 && p->nrun >= 4 * kRunParts) {
+        const ClassRun one = cls[0];
+        cls.clear();
+        for (int q = 0, r0 = 0; q < kRunParts; ++q) {
+            cls.push_back(one);
+            cls.back().run0 = r0;
+            cls.back().S.nrun = (p->nrun + kRunParts - 1 - q) / kRunParts;
+            r0 += cls.back().S.nrun;
+        }
+    }
     ctx->stats.dock_groups += (int64_t)cls.size();
     const int tr_ngen = trace ? trace->ngen : 0;
     const long tr_slots = trace ? (long)p->nrun * tr_ngen * p->pop_size : 0;
@@ -1440,7 +1462,7 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
     };
     std::vector<Offs> offs(cls.size());
     for (size_t k = 0; k < cls.size(); ++k) {
-        const long nruns = (long)cls[k].ligs.size() * p->nrun, nind = nruns * p->pop_size;
+        const long nruns = (long)cls[k].ligs.size() * cls[k].S.nrun, nind = nruns * p->pop_size;
         Offs& o = offs[k];
         o.g0 = take(sizeof(float) * nind * kGeneStride);
         o.g1 = take(sizeof(float) * nind * kGeneStride);
@@ -1471,8 +1493,6 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
         ctx->arena_bytes = off;
     }
     char* A = (char*)ctx->arena;
-    SearchDev S;
-    fill_search(p, S);
     const MapsDev& M = rec->maps;
     const bool need_loop = p->max_gen > 0 && p->pop_size < p->nev;
     // streams: the first class runs on the context's stream, others on their own, joined by events
@@ -1495,6 +1515,7 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
         D.ligs = (const LigandRef*)(A + o.lr);
         D.lig_id = (const uint32_t*)(A + o.id);
         D.nlig = (int)c.ligs.size();
+        D.run0 = c.run0;
         D.pop_genes[0] = (float*)(A + o.g0);
         D.pop_genes[1] = (float*)(A + o.g1);
         D.pop_e[0] = (float*)(A + o.e0);
@@ -1525,9 +1546,9 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
             CK(ctx, take_event(ctx, &c.t0));
             CK(ctx, take_event(ctx, &c.t1));
         }
-        const int nruns = (int)c.ligs.size() * p->nrun;
+        const int nruns = (int)c.ligs.size() * c.S.nrun;
         if (ctx->use_graphs) {
-            CK(ctx, build_class_graph(ctx, c, M, S, need_loop, ctx->timing, nruns));
+            CK(ctx, build_class_graph(ctx, c, M, c.S, need_loop, ctx->timing, nruns));
             CK(ctx, cudaGraphLaunch(c.exec, c.stream));
         } else {
             cudaStream_t cs = c.stream;
@@ -1536,7 +1557,7 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
             CK(ctx, cudaMemsetAsync(c.D.stopped, 0, sizeof(int) * nruns, cs));
             if (c.D.best_trace)
                 CK(ctx, cudaMemsetAsync(c.D.best_trace, 0xff, sizeof(float) * nruns * c.D.best_trace_len, cs));
-            CK(ctx, launch_dock_init(cs, M, S, c.D, c.geo));
+            CK(ctx, launch_dock_init(cs, M, c.S, c.D, c.geo));
             if (ctx->timing) CK(ctx, cudaEventRecord(c.t0, cs));
         }
         ctx->stats.kernel_launches += 2;  // initial population and final poses; the loop adds 3 per generation
@@ -1556,8 +1577,8 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
                 for (int q = 0; q < 4 && host_gens[k] < p->max_gen; ++q) {
                     const int gen = ++host_gens[k];
                     CK(ctx, cudaMemsetAsync(c.d_active, 0, sizeof(int), c.stream));
-                    CK(ctx, launch_dock_generation(c.stream, M, S, c.D, c.geo, gen));
-                    CK(ctx, launch_dock_count_active(c.stream, S, c.D, gen, c.d_active));
+                    CK(ctx, launch_dock_generation(c.stream, M, c.S, c.D, c.geo, gen));
+                    CK(ctx, launch_dock_count_active(c.stream, c.S, c.D, gen, c.d_active));
                 }
                 CK(ctx, cudaMemcpyAsync(&act[k], c.d_active, sizeof(int), cudaMemcpyDeviceToHost, c.stream));
             }
@@ -1571,7 +1592,7 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
         for (size_t k = 0; k < cls.size(); ++k) {
             ClassRun& c = cls[k];
             if (ctx->timing) CK(ctx, cudaEventRecord(c.t1, c.stream));
-            CK(ctx, launch_dock_finalize(c.stream, M, S, c.D, c.geo, c.d_res));
+            CK(ctx, launch_dock_finalize(c.stream, M, c.S, c.D, c.geo, c.d_res));
         }
     }
     std::vector<std::vector<ResultDev>> res(cls.size());
@@ -1579,7 +1600,7 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
     std::vector<int> gens_dev(cls.size(), 0);
     for (size_t k = 0; k < cls.size(); ++k) {
         ClassRun& c = cls[k];
-        const long nruns = (long)c.ligs.size() * p->nrun;
+        const long nruns = (long)c.ligs.size() * c.S.nrun;
         res[k].resize(nruns);
         CK(ctx, cudaMemcpyAsync(res[k].data(), c.d_res, sizeof(ResultDev) * nruns, cudaMemcpyDeviceToHost, c.stream));
         if (ctx->use_graphs) {
@@ -1599,18 +1620,29 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
     std::vector<int> tdec;
     std::vector<float> tg, te, init_g, init_e;
     for (size_t k = 0; k < cls.size(); ++k) CK(ctx, cudaStreamSynchronize(cls[k].stream));
+    if (ctx->timing && need_loop) {
+        // the groups' generation loops run concurrently: time their span, from
+        // the first loop's start to the last one's end (both measured from the
+        // fork every group waited on), over the longest group's generations
+        float lo = 0.f, hi = 0.f;
+        int rounds = 0;
+        for (size_t k = 0; k < cls.size(); ++k) {
+            float a = 0.f, b = 0.f;
+            CK(ctx, cudaEventElapsedTime(&a, fork, cls[k].t0));
+            CK(ctx, cudaEventElapsedTime(&b, fork, cls[k].t1));
+            lo = k == 0 ? a : std::min(lo, a);
+            hi = std::max(hi, b);
+            rounds = std::max(rounds, gens_dev[k]);
+        }
+        ctx->stats.gen_kernel_ms += hi - lo;
+        ctx->stats.gen_timed += rounds;
+    }
     for (size_t k = 0; k < cls.size(); ++k) {
         ClassRun& c = cls[k];
         // generations executed by the device loop (the counter counts passes)
         const int ran = need_loop ? gens_dev[k] : 0;
         ctx->stats.gen_launches += ran;
         ctx->stats.kernel_launches += 3 * (int64_t)ran;
-        if (ctx->timing && need_loop) {
-            float ms = 0.f;
-            CK(ctx, cudaEventElapsedTime(&ms, c.t0, c.t1));
-            ctx->stats.gen_kernel_ms += ms;
-            ctx->stats.gen_timed += ran;
-        }
         if (c.t0) ctx->ev_free.push_back(c.t0);
         if (c.t1) ctx->ev_free.push_back(c.t1);
         if (c.exec) cudaGraphExecDestroy(c.exec);
@@ -1636,7 +1668,7 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
             DockDev D1 = c.D;
             D1.pop_genes[0] = c.D.pop_genes[1];
             D1.pop_e[0] = c.D.pop_e[1];
-            CK(ctx, launch_dock_init(st, M, S, D1, c.geo));
+            CK(ctx, launch_dock_init(st, M, c.S, D1, c.geo));
             init_g.resize((size_t)nind * kGeneStride);
             init_e.resize(nind);
             CK(ctx, cudaMemcpyAsync(init_g.data(), D1.pop_genes[0], sizeof(float) * nind * kGeneStride,
@@ -1650,9 +1682,10 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
         for (size_t li = 0; li < c.ligs.size(); ++li) {
             const int lig = c.ligs[li];
             const int G = 7 + ligs[lig]->ntors, N = ligs[lig]->natoms;
-            for (int run = 0; run < p->nrun; ++run) {
+            for (int r = 0; r < c.S.nrun; ++r) {
+                const int run = c.run0 + r;
                 adg_result& o = out[(long)lig * p->nrun + run];
-                const ResultDev& sr = res[k][(long)li * p->nrun + run];
+                const ResultDev& sr = res[k][(long)li * c.S.nrun + r];
                 memset(&o, 0, sizeof(o));
                 o.best_energy = sr.best_energy;
                 o.generations = sr.generations;
@@ -1661,7 +1694,7 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
                 for (int q = 0; q < 3 * N; ++q) o.xyz[q] = sr.xyz[q];
                 if (ntrace > 0) {
                     // generations after the run's last repeat its final best energy
-                    const float* src = btr[k].data() + ((long)li * p->nrun + run) * ntrace;
+                    const float* src = btr[k].data() + ((long)li * c.S.nrun + r) * ntrace;
                     float* dst = best_trace + ((long)lig * p->nrun + run) * ntrace;
                     for (int q = 0; q < ntrace; ++q)
                         dst[q] = q < sr.generations ? src[q] : (q > 0 ? dst[q - 1] : sr.best_energy);

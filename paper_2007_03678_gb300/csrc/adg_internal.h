@@ -133,6 +133,7 @@ struct DockDev {
     const LigandRef* ligs;     // [nlig]
     const uint32_t* lig_id;    // Philox counter word 0 per ligand
     int nlig;
+    int run0;                  // run index of this launch's first run (its runs are run0 .. run0 + nrun - 1)
     float* pop_genes[2];       // [nlig*nrun][pop][kGeneStride], double-buffered by generation parity
     float* pop_e[2];           // [nlig*nrun][pop]
     unsigned long long* evals; // [nlig*nrun]

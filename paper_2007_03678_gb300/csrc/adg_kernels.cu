@@ -986,7 +986,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
     const int run_g = lig * S.nrun + run;
     const LigandDev* L = LR.hdr;
     const int T = L->ntors, G = 7 + T;
-    const Rng rng{S.key0, S.key1, Dk.lig_id[lig], (uint32_t)run, (uint32_t)ind, 0u};
+    const Rng rng{S.key0, S.key1, Dk.lig_id[lig], (uint32_t)(Dk.run0 + run), (uint32_t)ind, 0u};
     float v = 0.f;
     if (lane < 3) {
         const uint4 wd = rng.block(P_INIT, 0);
@@ -1043,7 +1043,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
     const WarpView ws = warp_view(na, nslots, lig_bytes);
     const LigandDev* L = LR.hdr;
     const int T = L->ntors, G = 7 + T, nb = 2 + T, pop = S.pop;
-    const Rng rng{S.key0, S.key1, Dk.lig_id[lig], (uint32_t)run, (uint32_t)ind, (uint32_t)gen};
+    const Rng rng{S.key0, S.key1, Dk.lig_id[lig], (uint32_t)(Dk.run0 + run), (uint32_t)ind, (uint32_t)gen};
     const float* Pg = Dk.pop_genes[(gen - 1) & 1] + (long)run_g * pop * kGeneStride;
     const float* Pe = Dk.pop_e[(gen - 1) & 1] + (long)run_g * pop;
 

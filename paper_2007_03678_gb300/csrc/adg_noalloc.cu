@@ -121,6 +121,7 @@ extern "C" int adg_dock_noalloc(const adg_receptor* rec, const adg_ligand* lig, 
     D.ligs = (const LigandRef*)(A + o_lr);
     D.lig_id = (const uint32_t*)(A + o_id);
     D.nlig = 1;
+    D.run0 = 0;
     D.pop_genes[0] = (float*)(A + o_g0);
     D.pop_genes[1] = (float*)(A + o_g1);
     D.pop_e[0] = (float*)(A + o_e0);

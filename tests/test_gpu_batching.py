@@ -95,3 +95,22 @@ def test_graph_and_host_loops_agree(ctx, ff):
     for a, b in zip(ref, got):
         for key in ("best_energy", "genes", "xyz", "evals", "generations", "best_trace"):
             assert np.array_equal(a[key], b[key]), key
+
+
+def test_run_halves_equal_one_group(ctx, ff):
+    """One ligand with 8 or more runs docks as two concurrent groups of run
+    halves; every run's result (and best-energy trace) equals the same run
+    docked inside a single group (the ligand batched with another)."""
+    from paper_2007_03678_gb300 import adg
+    grid, rec, lig, maps64, maps32 = problem("paper")
+    R = adg.Receptor(ctx, grid, maps32)
+    L = adg.Ligand(ctx, ff, lig)
+    other = adg.Ligand(ctx, ff, S.make_ligand(20, 3, 777))
+    p = adg.search_params(nrun=9, pop_size=40, nev=4000, ls_method=adg.LS_ADADELTA, ls_max_iters=20, lig_id=300,
+                          seed=5)
+    ctx.stats(reset=True)
+    alone = adg.dock(ctx, R, L, p, best_trace=6)[0]
+    assert ctx.stats()["dock_groups"] == 2
+    both = adg.dock(ctx, R, [L, other], p, best_trace=6)[0]
+    for key in ("best_energy", "genes", "xyz", "evals", "generations", "best_trace"):
+        assert np.array_equal(alone[key], both[key]), key
