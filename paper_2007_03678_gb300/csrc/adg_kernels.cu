@@ -343,31 +343,36 @@ template <int APL>
 __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, const WarpView& ws, int lane)
 {
     const int N = L->natoms, NF = L->nfrag;
-    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;  // this lane's rotation about its torsion axis
-    if (lane == 0) {
-        float qw = g[3], qx = g[4], qy = g[5], qz = g[6];
-        const float qi = 1.f / sqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
-        qw *= qi; qx *= qi; qy *= qi; qz *= qi;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;  // this lane's map: rotation rows | translation
+    if (lane < NF) {
+        // lane 0: x' = R(q/|q|)(x - c) + t; lane f > 0: the rotation by theta
+        // about fragment f's torsion axis through o, x' = R(x - o) + o, with R
+        // from the unit quaternion (cos theta/2, sin theta/2 u).  One
+        // quaternion-to-matrix path for both, so the lanes do not diverge.
+        const int k = lane > 0 ? L->ftor[lane] : 0;
+        float s, c;
+        sincosf(lane > 0 ? 0.5f * g[7 + k] : 0.f, &s, &c);
+        const float4 u = L->tax[k], o = L->tpt[k];
+        float qw = c, qx = s * u.x, qy = s * u.y, qz = s * u.z;
+        float px = o.x, py = o.y, pz = o.z, tx = o.x, ty = o.y, tz = o.z;
+        if (lane == 0) {
+            qw = g[3]; qx = g[4]; qy = g[5]; qz = g[6];
+            const float qi = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+            qw *= qi; qx *= qi; qy *= qi; qz *= qi;
+            px = L->cx; py = L->cy; pz = L->cz;
+            tx = g[0]; ty = g[1]; tz = g[2];
+        }
         const float R00 = 1.f - 2.f * (qy * qy + qz * qz), R01 = 2.f * (qx * qy - qw * qz), R02 = 2.f * (qx * qz + qw * qy);
         const float R10 = 2.f * (qx * qy + qw * qz), R11 = 1.f - 2.f * (qx * qx + qz * qz), R12 = 2.f * (qy * qz - qw * qx);
         const float R20 = 2.f * (qx * qz - qw * qy), R21 = 2.f * (qy * qz + qw * qx), R22 = 1.f - 2.f * (qx * qx + qy * qy);
-        const float cx = L->cx, cy = L->cy, cz = L->cz;
-        ws.W[0] = make_float4(R00, R01, R02, g[0] - (R00 * cx + R01 * cy + R02 * cz));
-        ws.W[1] = make_float4(R10, R11, R12, g[1] - (R10 * cx + R11 * cy + R12 * cz));
-        ws.W[2] = make_float4(R20, R21, R22, g[2] - (R20 * cx + R21 * cy + R22 * cz));
-    } else if (lane < NF) {
-        const int k = L->ftor[lane];
-        float s, c;
-        sincosf(g[7 + k], &s, &c);
-        const float4 u = L->tax[k], o = L->tpt[k];
-        const float oc = 1.f - c;
-        // Rodrigues: R = c I + s [u]x + (1 - c) u u^T, about the line through o
-        r0 = make_float4(c + oc * u.x * u.x, oc * u.x * u.y - s * u.z, oc * u.x * u.z + s * u.y, 0.f);
-        r1 = make_float4(oc * u.x * u.y + s * u.z, c + oc * u.y * u.y, oc * u.y * u.z - s * u.x, 0.f);
-        r2 = make_float4(oc * u.x * u.z - s * u.y, oc * u.y * u.z + s * u.x, c + oc * u.z * u.z, 0.f);
-        r0.w = o.x - (r0.x * o.x + r0.y * o.y + r0.z * o.z);
-        r1.w = o.y - (r1.x * o.x + r1.y * o.y + r1.z * o.z);
-        r2.w = o.z - (r2.x * o.x + r2.y * o.y + r2.z * o.z);
+        r0 = make_float4(R00, R01, R02, tx - (R00 * px + R01 * py + R02 * pz));
+        r1 = make_float4(R10, R11, R12, ty - (R10 * px + R11 * py + R12 * pz));
+        r2 = make_float4(R20, R21, R22, tz - (R20 * px + R21 * py + R22 * pz));
+        if (lane == 0) {
+            ws.W[0] = r0;
+            ws.W[1] = r1;
+            ws.W[2] = r2;
+        }
     }
     __syncwarp();
     const int maxlev = L->maxlev;
@@ -414,15 +419,12 @@ template <bool GRAD>
 __device__ __forceinline__ float atom_inter(const MapsDev& M, float k_out, int t, float q, float x, float y, float z,
                                             float& gx, float& gy, float& gz)
 {
-    float pen = 0.f, pgx = 0.f, pgy = 0.f, pgz = 0.f;
-    bool clx = false, cly = false, clz = false;
-    float xc = x, yc = y, zc = z;
-    if (x < M.ox) { pen += (M.ox - x) * (M.ox - x); pgx = 2.f * k_out * (x - M.ox); xc = M.ox; clx = true; }
-    if (x > M.hx) { pen += (x - M.hx) * (x - M.hx); pgx = 2.f * k_out * (x - M.hx); xc = M.hx; clx = true; }
-    if (y < M.oy) { pen += (M.oy - y) * (M.oy - y); pgy = 2.f * k_out * (y - M.oy); yc = M.oy; cly = true; }
-    if (y > M.hy) { pen += (y - M.hy) * (y - M.hy); pgy = 2.f * k_out * (y - M.hy); yc = M.hy; cly = true; }
-    if (z < M.oz) { pen += (M.oz - z) * (M.oz - z); pgz = 2.f * k_out * (z - M.oz); zc = M.oz; clz = true; }
-    if (z > M.hz) { pen += (z - M.hz) * (z - M.hz); pgz = 2.f * k_out * (z - M.hz); zc = M.hz; clz = true; }
+    // the point clamped into the box and its distance outside, per axis
+    const float xc = fminf(fmaxf(x, M.ox), M.hx), yc = fminf(fmaxf(y, M.oy), M.hy), zc = fminf(fmaxf(z, M.oz), M.hz);
+    const float ex = x - xc, ey = y - yc, ez = z - zc;
+    const float pen = ex * ex + ey * ey + ez * ez;
+    const float pgx = 2.f * k_out * ex, pgy = 2.f * k_out * ey, pgz = 2.f * k_out * ez;
+    const bool clx = ex != 0.f, cly = ey != 0.f, clz = ez != 0.f;
     const float ux = (xc - M.ox) * M.inv_h, uy = (yc - M.oy) * M.inv_h, uz = (zc - M.oz) * M.inv_h;
     int ix = min(max((int)floorf(ux), 0), M.nx - 2);
     int iy = min(max((int)floorf(uy), 0), M.ny - 2);
@@ -633,8 +635,11 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
             const float u0 = __shfl_up_sync(FULL_MASK, v0, o), u1 = __shfl_up_sync(FULL_MASK, v1, o),
                         u2 = __shfl_up_sync(FULL_MASK, v2, o), u3 = __shfl_up_sync(FULL_MASK, v3, o),
                         u4 = __shfl_up_sync(FULL_MASK, v4, o), u5 = __shfl_up_sync(FULL_MASK, v5, o);
-            if (lane >= o) {
-                v0 += u0; v1 += u1; v2 += u2; v3 += u3; v4 += u4; v5 += u5;
+            if (lane >= o) {  // two-wide adds
+                const float2 a = __fadd2_rn(make_float2(v0, v1), make_float2(u0, u1));
+                const float2 b = __fadd2_rn(make_float2(v2, v3), make_float2(u2, u3));
+                const float2 d = __fadd2_rn(make_float2(v4, v5), make_float2(u4, u5));
+                v0 = a.x; v1 = a.y; v2 = b.x; v3 = b.y; v4 = d.x; v5 = d.y;
             }
         }
         v0 += cf0; v1 += cf1; v2 += cf2; v3 += cm0; v4 += cm1; v5 += cm2;
