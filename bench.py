@@ -208,11 +208,11 @@ TRIAGE_TRAIN, TRIAGE_STREAM = 1200, 2000
 #       -k regex:k_dock_generation -s 60 -c 2 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
 #       --no-e2e --no-batching --no-triage --no-graphs
 # (the sum of the two launches); None whenever the kernel has changed since that capture.
-GEN_TRAFFIC_BYTES = None
+GEN_TRAFFIC_BYTES = 38.5e6
 # The pipe that bounds the kernel, from the full-section capture of the same
 # kernel (l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed):
 # the L1 / shared-memory data pipe.  None whenever the kernel has changed.
-GEN_L1_PIPE_FRAC = None
+GEN_L1_PIPE_FRAC = 0.694
 
 
 def run_mlp_inference(ctx, rows=1_000_000, reps=10):
