@@ -249,6 +249,23 @@ enum { ADG_GRAD_NONE = 0, ADG_GRAD_GENES = 1, ADG_GRAD_TANGENT = 2 };
 int adg_score(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* lig, const float* genes, int npose,
               float* energy, float* grad, int grad_kind);
 
+/* adg_score over the poses of several ligands in one launch per
+ * atoms-per-lane width (the ligands of a differentiable batch).  Ligand i
+ * owns npose[i] consecutive rows, in ligand order (host array [nlig]); every
+ * row is ADG_MAX_GENES floats:
+ *   genes:  device [total][ADG_MAX_GENES]; a row holds its ligand's 7+T genes
+ *           in front, the rest is ignored
+ *   energy: device [total]
+ *   grad:   device [total][ADG_MAX_GENES], NULL when grad_kind ==
+ *           ADG_GRAD_NONE; a row gets 7+T (ADG_GRAD_GENES) or 6+T
+ *           (ADG_GRAD_TANGENT) values in front, the rest is left as it was
+ * Each pose gets the same values as adg_score gives it.  The launch tables
+ * live in a stream-ordered device buffer (cudaMallocAsync) freed after the
+ * launch.  ADG_EINVAL on a null argument, a negative count or a ligand of
+ * another context; asynchronous on the context's stream. */
+int adg_score_multi(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig, const int* npose,
+                    const float* genes, float* energy, float* grad, int grad_kind);
+
 /* Posed coordinates of npose genotypes: xyz device [npose][natoms][3]. */
 int adg_pose(adg_ctx* ctx, const adg_ligand* lig, const float* genes, int npose, float* xyz);
 

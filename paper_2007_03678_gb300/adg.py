@@ -119,7 +119,7 @@ EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_c
            "adg_dock_traced", "adg_ligand_descriptors", "adg_mlp_nparams", "adg_mlp_create", "adg_mlp_destroy",
            "adg_mlp_get_params", "adg_mlp_set_params", "adg_mlp_set_norm", "adg_mlp_forward", "adg_mlp_grad",
            "adg_mlp_train_step", "adg_mlp_fit", "adg_ligand_set_stream_id",
-           "adg_ctx_set_graphs", "adg_mlp_set_engine", "adg_mlp_check", "adg_probe_peaks", "adg_ligand_schedule")
+           "adg_ctx_set_graphs", "adg_mlp_set_engine", "adg_mlp_check", "adg_probe_peaks", "adg_ligand_schedule", "adg_score_multi")
 
 _lib = None
 
@@ -151,6 +151,7 @@ def load(path: str | None = None):
         L.adg_ligand_destroy.argtypes = [_vp]
         L.adg_ligand_info.argtypes = [_vp, C.POINTER(adg_ligand_stats)]
         L.adg_score.argtypes = [_vp, _vp, _vp, _vp, _i, _vp, _vp, _i]
+        L.adg_score_multi.argtypes = [_vp, _vp, C.POINTER(_vp), _i, C.POINTER(C.c_int), _vp, _vp, _vp, _i]
         L.adg_pose.argtypes = [_vp, _vp, _vp, _i, _vp]
         L.adg_dock.argtypes = [_vp, _vp, C.POINTER(_vp), _i, C.POINTER(adg_search_params), C.POINTER(adg_result),
                                C.POINTER(adg_dock_trace)]
@@ -449,6 +450,28 @@ def score(ctx: Context, rec: Receptor, lig: Ligand, genes, grad_kind: int = GRAD
     ctx._enter()
     _check(load().adg_score(ctx.handle, rec.handle, lig.handle, _ptr(genes), n, _ptr(energy),
                             _ptr(grad) if grad is not None else None, grad_kind), "adg_score", ctx)
+    ctx._leave()
+    return energy, grad
+
+
+def score_multi(ctx: Context, rec: Receptor, ligs, genes, npose, grad_kind: int = GRAD_NONE):
+    """adg_score_multi: genes float32 [sum(npose), MAX_GENES] on the device,
+    ligand i owning npose[i] consecutive rows (its 7+T genes in front).
+    Returns (energy [total], grad [total, MAX_GENES] or None)."""
+    import torch
+    n = len(ligs)
+    counts = (C.c_int * n)(*[int(k) for k in npose])
+    total = int(sum(int(k) for k in npose))
+    if genes.shape != (total, MAX_GENES) or genes.dtype != torch.float32:
+        raise ValueError(f"genes must be float32 [{total}, {MAX_GENES}]")
+    energy = torch.empty(total, dtype=torch.float32, device=genes.device)
+    grad = None
+    if grad_kind != GRAD_NONE:
+        grad = torch.zeros((total, MAX_GENES), dtype=torch.float32, device=genes.device)
+    hs = (C.c_void_p * n)(*[l.handle.value for l in ligs])
+    ctx._enter()
+    _check(load().adg_score_multi(ctx.handle, rec.handle, hs, n, counts, _ptr(genes), _ptr(energy),
+                                  _ptr(grad) if grad is not None else None, grad_kind), "adg_score_multi", ctx)
     ctx._leave()
     return energy, grad
 

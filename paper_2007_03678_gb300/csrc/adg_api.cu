@@ -1090,6 +1090,84 @@ int adg_score(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* lig, cons
     return ADG_OK;
 }
 
+int adg_score_multi(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig, const int* npose,
+                    const float* genes, float* energy, float* grad, int grad_kind)
+{
+    if (!ctx || !rec || !ligs || nlig < 0 || (nlig > 0 && !npose)) return ADG_EINVAL;
+    if (grad_kind != ADG_GRAD_NONE && grad_kind != ADG_GRAD_GENES && grad_kind != ADG_GRAD_TANGENT) return ADG_EINVAL;
+    long total = 0;
+    for (int i = 0; i < nlig; ++i) {
+        if (!ligs[i] || ligs[i]->ctx != ctx || npose[i] < 0) return ADG_EINVAL;
+        total += npose[i];
+    }
+    if (total > 0 && (!genes || !energy || (grad_kind != ADG_GRAD_NONE && !grad))) return ADG_EINVAL;
+    if (total == 0) return ADG_OK;
+    if (total > (1l << 30)) return ADG_ETOOBIG;
+    CK(ctx, cudaSetDevice(ctx->device));
+    // one launch per atoms-per-lane width; rows keep the caller's ligand order
+    std::vector<long> row0(nlig);
+    for (int i = 0, r = 0; i < nlig; ++i) {
+        row0[i] = r;
+        r += npose[i];
+    }
+    for (int apl = 1; apl <= 4; ++apl) {
+        std::vector<int> members;
+        int nslots = 32;
+        size_t lig_bytes = 0;
+        for (int i = 0; i < nlig; ++i)
+            if (ligs[i]->apl == apl && npose[i] > 0) {
+                members.push_back(i);
+                nslots = std::max(nslots, ligs[i]->nslots);
+                lig_bytes = std::max(lig_bytes, ligs[i]->bytes);
+            }
+        if (members.empty()) continue;
+        const Geo g = make_geo(apl, nslots, lig_bytes);
+        const int nm = (int)members.size();
+        std::vector<LigandRef> refs(nm);
+        std::vector<int> blk0(nm), rows(nm), np(nm), blk_lig;
+        for (int m = 0; m < nm; ++m) {
+            const int i = members[m];
+            refs[m] = ligs[i]->ref;
+            blk0[m] = (int)blk_lig.size();
+            rows[m] = (int)row0[i];
+            np[m] = npose[i];
+            const int nb = (npose[i] + g.wpb - 1) / g.wpb;
+            for (int b = 0; b < nb; ++b) blk_lig.push_back(m);
+        }
+        // the launch's tables in one stream-ordered device buffer, freed after the launch
+        const size_t o_ref = 0, o_bl = align_up(sizeof(LigandRef) * nm, 256),
+                     o_b0 = align_up(o_bl + sizeof(int) * blk_lig.size(), 256),
+                     o_r0 = align_up(o_b0 + sizeof(int) * nm, 256), o_np = align_up(o_r0 + sizeof(int) * nm, 256),
+                     bytes = align_up(o_np + sizeof(int) * nm, 256);
+        std::vector<char> host(bytes, 0);
+        memcpy(host.data() + o_ref, refs.data(), sizeof(LigandRef) * nm);
+        memcpy(host.data() + o_bl, blk_lig.data(), sizeof(int) * blk_lig.size());
+        memcpy(host.data() + o_b0, blk0.data(), sizeof(int) * nm);
+        memcpy(host.data() + o_r0, rows.data(), sizeof(int) * nm);
+        memcpy(host.data() + o_np, np.data(), sizeof(int) * nm);
+        char* dev = nullptr;
+        CK(ctx, cudaMallocAsync((void**)&dev, bytes, ctx->stream));
+        cudaError_t e = cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
+        if (e == cudaSuccess) {
+            ScoreMultiDev J;
+            J.ligs = (const LigandRef*)(dev + o_ref);
+            J.blk_lig = (const int*)(dev + o_bl);
+            J.lig_blk0 = (const int*)(dev + o_b0);
+            J.lig_row0 = (const int*)(dev + o_r0);
+            J.lig_npose = (const int*)(dev + o_np);
+            J.stride = ADG_MAX_GENES;
+            e = launch_score_multi(ctx->stream, rec->maps, J, (int)blk_lig.size(), g, genes, energy,
+                                   grad_kind == ADG_GRAD_NONE ? nullptr : grad, grad_kind);
+        }
+        const cudaError_t e2 = cudaFreeAsync(dev, ctx->stream);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "adg_score_multi");
+        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaFreeAsync");
+        ctx->stats.h2d_bytes += (int64_t)bytes;
+        ctx->stats.kernel_launches += 1;
+    }
+    return ADG_OK;
+}
+
 int adg_pose(adg_ctx* ctx, const adg_ligand* lig, const float* genes, int npose, float* xyz)
 {
     if (!ctx || !lig || npose < 0 || (npose > 0 && (!genes || !xyz))) return ADG_EINVAL;
@@ -1438,13 +1516,16 @@ int dock_impl(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* li
     // half's next generation.  Runs are independent and their random streams
     // are keyed by the run index, so the results do not change.
     if (!trace && cls.size() == 1 && cls[0].ligs.size() == 1 && p->nrun >= 4 * kRunParts) {
-        const ClassRun one = cls[0];
-        cls.clear();
+        const int lig0 = cls[0].ligs[0];
+        const Geo geo0 = cls[0].geo;
+        cls.resize(kRunParts);
         for (int q = 0, r0 = 0; q < kRunParts; ++q) {
-            cls.push_back(one);
-            cls.back().run0 = r0;
-            cls.back().S.nrun = (p->nrun + kRunParts - 1 - q) / kRunParts;
-            r0 += cls.back().S.nrun;
+            cls[q].ligs.assign(1, lig0);
+            cls[q].geo = geo0;
+            cls[q].S = S;
+            cls[q].run0 = r0;
+            cls[q].S.nrun = (p->nrun + kRunParts - 1 - q) / kRunParts;
+            r0 += cls[q].S.nrun;
         }
     }
     ctx->stats.dock_groups += (int64_t)cls.size();

@@ -184,6 +184,19 @@ cudaError_t launch_probe_genes(cudaStream_t st, const MapsDev& m, int T, int npo
 // (grad != 0) or without the gradient; energy[pose] receives the last value.
 cudaError_t launch_tune(cudaStream_t st, const MapsDev& m, const LigandRef& l, const Geo& g, const float* genes,
                         int npose, int reps, int grad, float* energy);
+// Several ligands' poses in one launch (adg_score_multi): device arrays
+// over the launch's ligands and blocks; rows of genes / energy / grad are
+// `stride` floats apart.
+struct ScoreMultiDev {
+    const LigandRef* ligs;  // [nlig]
+    const int* blk_lig;     // [nblocks] ligand of each block
+    const int* lig_blk0;    // [nlig] first block of each ligand
+    const int* lig_row0;    // [nlig] first row of each ligand
+    const int* lig_npose;   // [nlig]
+    int stride;
+};
+cudaError_t launch_score_multi(cudaStream_t st, const MapsDev& m, const ScoreMultiDev& j, int nblocks, const Geo& g,
+                               const float* genes, float* energy, float* grad, int grad_kind);
 cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, const Geo& g, const float* genes,
                          int npose, float* energy, float* grad, int grad_kind);
 cudaError_t launch_pose(cudaStream_t st, const LigandRef& l, const Geo& g, const float* genes, int npose, float* xyz);

@@ -721,30 +721,27 @@ static cudaError_t allow_smem(K kernel, size_t bytes)
 static unsigned blocks_for(long nwarps, const Geo& g) { return (unsigned)((nwarps + g.wpb - 1) / g.wpb); }
 
 // ------------------------------------------------------------------ score / pose API kernels
+// One pose's energy and gradient into energy[0] and grad[0 ..]: the gene
+// gradient (dE/dt, dE/dq by the chain rule, dE/dtheta; 7 + T values) or the
+// tangent gradient (6 + T values).  gin: the pose's 7 + T genes.
 template <int APL>
-__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_score(MapsDev M, LigandRef LR, int na, int nslots, int lig_bytes,
-                                                                  const float* __restrict__ genes, int npose,
-                                                                  float* __restrict__ energy, float* __restrict__ grad,
-                                                                  int grad_kind)
+__device__ __forceinline__ void score_pose(const LigandRef& SL, const MapsDev& M, const WarpView& ws,
+                                           const float* __restrict__ gin, float* __restrict__ energy,
+                                           float* __restrict__ grad, int grad_kind, int lane)
 {
-    const int lane = threadIdx.x & 31;
-    const long pose = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const LigandRef SL = stage_ligand(LR, lig_bytes);
-    if (pose >= npose) return;
-    const WarpView ws = warp_view(na, nslots, lig_bytes);
     const LigandDev* L = SL.hdr;
     const int T = L->ntors, G = 7 + T, D = 6 + T;
-    if (lane < G) ws.genes[lane] = genes[pose * G + lane];
+    if (lane < G) ws.genes[lane] = gin[lane];
     __syncwarp();
     if (grad_kind == ADG_GRAD_NONE) {
         ScoreOut o = warp_score<APL, false>(L, SL.pairs, M, ws.genes, ws, lane);
-        if (lane == 0) energy[pose] = o.e;
+        if (lane == 0) energy[0] = o.e;
         return;
     }
     ScoreOut o = warp_score<APL, true>(L, SL.pairs, M, ws.genes, ws, lane);
-    if (lane == 0) energy[pose] = o.e;
+    if (lane == 0) energy[0] = o.e;
     if (grad_kind == ADG_GRAD_TANGENT) {
-        if (lane < D) grad[pose * D + lane] = o.gtan;
+        if (lane < D) grad[lane] = o.gtan;
         return;
     }
     // gene gradient: t and theta from the tangent gradient, q by the chain rule
@@ -762,7 +759,43 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_scor
         else if (lane == 5) val = 2.f * (qw * ty + (tz * qx - tx * qz)) * iq;
         else val = 2.f * (qw * tz + (tx * qy - ty * qx)) * iq;
     } else if (lane < G) val = prev;
-    if (lane < G) grad[pose * G + lane] = val;
+    if (lane < G) grad[lane] = val;
+}
+
+template <int APL>
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_score(MapsDev M, LigandRef LR, int na, int nslots, int lig_bytes,
+                                                                  const float* __restrict__ genes, int npose,
+                                                                  float* __restrict__ energy, float* __restrict__ grad,
+                                                                  int grad_kind)
+{
+    const int lane = threadIdx.x & 31;
+    const long pose = (long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const LigandRef SL = stage_ligand(LR, lig_bytes);
+    if (pose >= npose) return;
+    const WarpView ws = warp_view(na, nslots, lig_bytes);
+    const int T = SL.hdr->ntors, G = 7 + T, D = 6 + T;
+    score_pose<APL>(SL, M, ws, genes + pose * G, energy + pose,
+                    grad ? grad + pose * (grad_kind == ADG_GRAD_TANGENT ? D : G) : nullptr, grad_kind, lane);
+}
+
+// Poses of several ligands in one launch: block b serves ligand J.blk_lig[b]
+// (the ligand's blocks are consecutive, from J.lig_blk0); its warps take the
+// ligand's poses in order, rows J.lig_row0 .. of the row-strided arrays.
+template <int APL>
+__global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_score_multi(MapsDev M, ScoreMultiDev J, int na, int nslots,
+                                                                        int lig_bytes, const float* __restrict__ genes,
+                                                                        float* __restrict__ energy,
+                                                                        float* __restrict__ grad, int grad_kind)
+{
+    const int lane = threadIdx.x & 31;
+    const int lig = J.blk_lig[blockIdx.x];
+    const LigandRef SL = stage_ligand(J.ligs[lig], lig_bytes);
+    const int local = (blockIdx.x - J.lig_blk0[lig]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (local >= J.lig_npose[lig]) return;
+    const WarpView ws = warp_view(na, nslots, lig_bytes);
+    const long row = (long)J.lig_row0[lig] + local;
+    score_pose<APL>(SL, M, ws, genes + row * J.stride, energy + row, grad ? grad + row * J.stride : nullptr,
+                    grad_kind, lane);
 }
 
 cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, const Geo& g, const float* genes,
@@ -782,6 +815,25 @@ cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, 
     else if (g.apl == 3) { ADG_SCORE(3) }
     else { ADG_SCORE(4) }
 #undef ADG_SCORE
+    return cudaGetLastError();
+}
+
+cudaError_t launch_score_multi(cudaStream_t st, const MapsDev& m, const ScoreMultiDev& j, int nblocks, const Geo& g,
+                               const float* genes, float* energy, float* grad, int grad_kind)
+{
+    if (nblocks <= 0) return cudaSuccess;
+    const unsigned threads = g.wpb * 32;
+    cudaError_t e;
+#define ADG_SCORE_MULTI(A)                                                                                        \
+    e = allow_smem(k_score_multi<A>, g.smem);                                                                     \
+    if (e != cudaSuccess) return e;                                                                               \
+    k_score_multi<A><<<(unsigned)nblocks, threads, g.smem, st>>>(m, j, g.na, g.nslots, (int)g.lig_bytes, genes, energy, \
+                                                                 grad, grad_kind);
+    if (g.apl == 1) { ADG_SCORE_MULTI(1) }
+    else if (g.apl == 2) { ADG_SCORE_MULTI(2) }
+    else if (g.apl == 3) { ADG_SCORE_MULTI(3) }
+    else { ADG_SCORE_MULTI(4) }
+#undef ADG_SCORE_MULTI
     return cudaGetLastError();
 }
 

@@ -95,6 +95,7 @@ def test_null_arguments_are_rejected(lib):
     assert lib.adg_ctx_set_geometry(None, 1) == -1
     assert lib.adg_ctx_tuned(None, None, 0, None) == -1
     assert lib.adg_probe_peaks(None, None) == -1
+    assert lib.adg_score_multi(None, None, None, 0, None, None, None, None, 0) == -1
 
 
 def test_no_gpu_context_fails_cleanly(lib):

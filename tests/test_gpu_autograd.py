@@ -105,3 +105,56 @@ def test_autograd_matches_oracle_and_finite_differences(ctx, ff):
             fd_checked += int(use.sum())
     assert checked > 0.1 * NLIG * NPOSE
     assert fd_checked > 3000
+
+
+def test_batched_scoring_equals_per_ligand(ctx, ff):
+    """adg_score_multi (one launch per atoms-per-lane width over many
+    ligands) gives every pose the energy and gene gradient adg_score gives it,
+    bit for bit; the batched autograd function returns the same gradients as
+    the per-ligand one, including for a ligand with no poses."""
+    import torch
+    from paper_2007_03678_gb300 import adg
+    from paper_2007_03678_gb300.autograd import score, score_batch, score_rows
+    grid, rec, _, maps64, maps32 = problem("paper")
+    R = adg.Receptor(ctx, grid, maps32)
+    ligs = _ligands()[:12] + [S.make_ligand(80, 9, 5151), S.make_ligand(12, 2, 5252)]
+    assert len({(l.natoms + 31) // 32 for l in ligs}) >= 3  # several widths in one call
+    L = [adg.Ligand(ctx, ff, l) for l in ligs]
+    counts = [37 + 11 * i for i in range(len(ligs))]
+    counts[5] = 0
+    genes = [torch.from_numpy(S.random_genes(l, max(k, 1), grid, 60000 + i, spread=0.3)[:k].astype(np.float32)).cuda()
+             for i, (l, k) in enumerate(zip(ligs, counts))]
+    rows = torch.zeros((sum(counts), adg.MAX_GENES), dtype=torch.float32, device="cuda")
+    r = 0
+    for g in genes:
+        rows[r:r + g.shape[0], :g.shape[1]] = g
+        r += g.shape[0]
+    e_all, g_all = adg.score_multi(ctx, R, L, rows, counts, adg.GRAD_GENES)
+    ctx.sync()
+    packed = rows.clone().requires_grad_(True)
+    e_rows = score_rows(packed, ctx, R, L, counts)
+    e_rows.sum().backward()
+    assert torch.equal(e_rows.detach(), e_all) and torch.equal(packed.grad, g_all)
+    r = 0
+    for Lg, g in zip(L, genes):
+        n, w = g.shape
+        if n:
+            e1, g1 = adg.score(ctx, R, Lg, g.contiguous(), adg.GRAD_GENES)
+            ctx.sync()
+            assert torch.equal(e_all[r:r + n], e1)
+            assert torch.equal(g_all[r:r + n, :w], g1)
+            assert not g_all[r:r + n, w:].any()
+        r += n
+    # autograd through the batch against the per-ligand function
+    xs = [g.clone().requires_grad_(True) for g in genes]
+    energies = score_batch(xs, ctx, R, L)
+    torch.stack([e.sum() for e in energies]).sum().backward()
+    for Lg, g, x, e in zip(L, genes, xs, energies):
+        if g.shape[0] == 0:
+            assert e.numel() == 0
+            continue
+        y = g.clone().requires_grad_(True)
+        e1 = score(y, ctx, R, Lg)
+        e1.sum().backward()
+        assert torch.equal(e.detach(), e1.detach())
+        assert torch.equal(x.grad, y.grad)
