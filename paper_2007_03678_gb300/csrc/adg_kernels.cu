@@ -5,10 +5,11 @@
 // and warp shuffles reduce the energy and the genotype gradient.  A whole
 // GA generation of an individual -- selection, crossover, mutation, the
 // offspring evaluation and its local search (Solis-Wets or ADADELTA) -- runs
-// inside that one warp, so a generation of every run of every ligand is one
-// launch.  The receptor maps are packed per atom type as float4 nodes
-// (M_t, M_elec, M_desolv, 0) so that a trilinear gather is 8 16-byte loads
-// served from L2 (a 64^3 receptor is 29 MB packed, well inside the 126 MB L2).
+// inside that one warp, so a generation of every run of a ligand group is
+// one launch.  The receptor maps are packed per atom type as one 32-byte
+// record per node, (M_t, M_elec, M_desolv, 0) at x and at x + 1, so that a
+// trilinear gather is four 32-byte loads served from L2 (a 64^3 receptor is
+// 59 MB packed, inside the 126 MB L2).
 #include <math.h>
 #include <stdint.h>
 
@@ -221,6 +222,8 @@ cudaError_t launch_maps_build(cudaStream_t st, const adg_forcefield& ff, const a
     return cudaGetLastError();
 }
 
+// The caller's [map][z][y][x] maps -> per atom type t and node i the record
+// packed[2 (t npt + i)], packed[2 (t npt + i) + 1] = the node and its x + 1 neighbour.
 __global__ void k_pack_maps(const float* __restrict__ maps, long npt, int nx, float4* __restrict__ packed)
 {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
