@@ -17,6 +17,7 @@ the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import functools
 import json
 import os
 import subprocess
@@ -137,6 +138,70 @@ def oracle_sample(nev: int, cores: int, maps_path: str, run0: int = 0) -> dict:
         wall = time.perf_counter() - t0
     evals = sum(e for e, _ in out)
     return dict(evals=evals, wall=wall, rate=evals / wall)
+
+
+def _oracle_plain_worker(args):
+    maps_path, run = args
+    import numpy as np
+    import oracle as O
+    from paper_2007_03678_gb300 import synth as S
+    grid, rec, lig = S.workload_inputs(S.PLAIN)
+    maps = np.load(maps_path)
+    p = O.SearchParams(nrun=1, pop_size=S.PLAIN["pop"], nev=S.PLAIN["nev"], ls_method=1)
+    best, _, evals, gens, _ = O.lga_run(S.forcefield(), grid, maps, O.Ligand(lig), p, run=run)
+    return evals
+
+
+def _oracle_diff_worker(args):
+    maps_path, specs = args
+    import numpy as np
+    import oracle as O
+    from paper_2007_03678_gb300 import synth as S
+    grid = S.make_grid(S.PAPER["grid_n"])
+    maps = np.load(maps_path)
+    ff = S.forcefield()
+    n = 0
+    for n_heavy, n_tors, seed, i in specs:
+        lig = S.make_ligand(n_heavy, n_tors, seed)
+        genes = S.random_genes(lig, 256, grid, 40000 + i, spread=0.3).astype(np.float32).astype(np.float64)
+        O.score(ff, grid, maps, O.Ligand(lig), genes)
+        n += len(genes)
+    return n
+
+
+def oracle_other_configs(cores: int, paper_maps_path: str, diff_specs) -> dict:
+    """The FP64 oracle on the plain config (its 10 runs as 10 parallel
+    single-thread processes) and on the differentiation workload (energy +
+    gradient of its 65,536 poses, ligands spread over `cores` processes;
+    ligand set-up included in the time)."""
+    import multiprocessing as mp
+    import numpy as np
+    import oracle as O
+    from paper_2007_03678_gb300 import synth as S
+    grid, rec, lig = S.workload_inputs(S.PLAIN)
+    fd, plain_path = tempfile.mkstemp(suffix=".npy")
+    os.close(fd)
+    np.save(plain_path, O.maps_build(S.forcefield(), grid, rec).astype(np.float32).astype(np.float64))
+    try:
+        nrun = S.PLAIN["nrun"]
+        with mp.get_context("spawn").Pool(min(cores, nrun)) as pool:
+            pool.map(_oracle_plain_worker, [(plain_path, 0)])  # warm the workers' imports
+            t0 = time.perf_counter()
+            evals = sum(pool.map(_oracle_plain_worker, [(plain_path, r) for r in range(nrun)]))
+            t_plain = time.perf_counter() - t0
+        chunks = [diff_specs[i::cores] for i in range(cores)]
+        with mp.get_context("spawn").Pool(cores) as pool:
+            pool.map(_oracle_diff_worker, [(paper_maps_path, [])] * cores)
+            t0 = time.perf_counter()
+            poses = sum(pool.map(_oracle_diff_worker, [(paper_maps_path, c) for c in chunks]))
+            t_diff = time.perf_counter() - t0
+    finally:
+        os.unlink(plain_path)
+    return {"plain_config": {"ligands_per_s": 1.0 / t_plain, "evals_per_s": evals / t_plain, "seconds": t_plain,
+                             "cores": min(cores, nrun),
+                             "sample": f"the whole plain config: {nrun} single-thread oracle LGA runs in parallel"},
+            "differentiation": {"poses_per_s": poses / t_diff, "seconds": t_diff, "cores": cores,
+                                "sample": f"all {poses} poses of the differentiation workload, energy + gradient"}}
 
 
 def oracle_maps_file() -> str:
@@ -283,6 +348,27 @@ def run_plain_config(ctx, ff, reps=5):
             "ms_per_ligand": best, "best_energy_median": float(np.median(r["best_energy"]))}
 
 
+@functools.lru_cache(maxsize=1)
+def differentiation_ligands():
+    """The differentiation workload's 256 seeded ligands (20-50 atoms, 2-12
+    torsions) and the (heavy atoms, torsions, seed, index) that make each."""
+    import numpy as np
+    from paper_2007_03678_gb300 import synth as S
+    rng = np.random.default_rng(2024)
+    specs, ligs, seed = [], [], 30000
+    while len(ligs) < 256:
+        seed += 1
+        n_heavy, n_tors = int(rng.integers(18, 46)), int(rng.integers(2, 13))
+        try:
+            lig = S.make_ligand(n_heavy, n_tors, seed)
+        except RuntimeError:
+            continue
+        if 20 <= lig.natoms <= 50:
+            specs.append((n_heavy, n_tors, seed, len(ligs)))
+            ligs.append(lig)
+    return specs, ligs
+
+
 def run_differentiation(ctx, R, ff, reps=5):
     """65,536 random poses across 256 ligands (20-50 atoms, 2-12 torsions):
     energy + gene gradient through torch.autograd, forward and backward,
@@ -293,16 +379,7 @@ def run_differentiation(ctx, R, ff, reps=5):
     import torch
     from paper_2007_03678_gb300 import adg, synth as S
     from paper_2007_03678_gb300.autograd import score, score_batch, score_rows
-    rng = np.random.default_rng(2024)
-    ligs, seed = [], 30000
-    while len(ligs) < 256:
-        seed += 1
-        try:
-            lig = S.make_ligand(int(rng.integers(18, 46)), int(rng.integers(2, 13)), seed)
-        except RuntimeError:
-            continue
-        if 20 <= lig.natoms <= 50:
-            ligs.append(lig)
+    specs, ligs = differentiation_ligands()
     grid = S.make_grid(S.PAPER["grid_n"])
     L = [adg.Ligand(ctx, ff, l) for l in ligs]
     X = [torch.from_numpy(S.random_genes(l, 256, grid, 40000 + i, spread=0.3).astype(np.float32)).cuda()
@@ -590,11 +667,13 @@ def main():
         path = oracle_maps_file()
         try:
             r = oracle_sample(ORACLE_SAMPLE_NEV, cores, path)
+            others = oracle_other_configs(cores, path, differentiation_ligands()[0])
         finally:
             os.unlink(path)
         cpu = {"value": r["rate"], "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": f"{cores} parallel single-thread oracle LGA runs of the paper-scale ligand, each stopped "
-                         f"after {ORACLE_SAMPLE_NEV} evaluations ({r['evals']} evals in {r['wall']:.1f} s)"}
+                         f"after {ORACLE_SAMPLE_NEV} evaluations ({r['evals']} evals in {r['wall']:.1f} s)",
+               "other_configs": others}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
