@@ -306,8 +306,8 @@ typedef struct {
 } adg_stats;
 
 int adg_ctx_set_timing(adg_ctx* ctx, int enable);
-/* Copy the counters to *out; zero them when reset != 0.  Waits for the
- * stream when timing is on (to read the events). */
+/* Copy the counters to *out; zero them when reset != 0.  (adg_dock reads
+ * its timing events before it returns, so this does not wait.) */
 int adg_ctx_stats(adg_ctx* ctx, adg_stats* out, int reset);
 
 /* How adg_dock drives its generation loop (no counterpart in the paper).

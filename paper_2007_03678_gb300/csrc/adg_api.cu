@@ -156,10 +156,6 @@ int adg_ctx_destroy(adg_ctx* ctx)
     if (!ctx) return ADG_EINVAL;
     cudaSetDevice(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-    for (auto& pr : ctx->ev_pending) {
-        cudaEventDestroy(pr.first);
-        cudaEventDestroy(pr.second);
-    }
     for (auto ev : ctx->ev_free) cudaEventDestroy(ev);
     for (auto s2 : ctx->class_streams) {
         cudaStreamSynchronize(s2);
@@ -219,19 +215,6 @@ int adg_ctx_tuned(adg_ctx* ctx, adg_tuned_shape* out, int cap, int* n)
 int adg_ctx_stats(adg_ctx* ctx, adg_stats* out, int reset)
 {
     if (!ctx || !out) return ADG_EINVAL;
-    CK(ctx, cudaSetDevice(ctx->device));
-    if (!ctx->ev_pending.empty()) {
-        CK(ctx, cudaStreamSynchronize(ctx->stream));
-        for (auto& pr : ctx->ev_pending) {
-            float ms = 0.f;
-            CK(ctx, cudaEventElapsedTime(&ms, pr.first, pr.second));
-            ctx->stats.gen_kernel_ms += ms;
-            ctx->stats.gen_timed += 1;
-            ctx->ev_free.push_back(pr.first);
-            ctx->ev_free.push_back(pr.second);
-        }
-        ctx->ev_pending.clear();
-    }
     *out = ctx->stats;
     if (reset) ctx->stats = adg_stats{};
     return ADG_OK;

@@ -251,7 +251,6 @@ struct adg_ctx {
     bool timing = false;
     adg_stats stats{};
     std::vector<cudaEvent_t> ev_free;                       // reusable events
-    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;  // recorded, not yet read
     std::vector<cudaStream_t> class_streams;  // extra streams for concurrent ligand groups
     bool use_graphs = true;  // adg_ctx_set_graphs
     // launch geometry of adg_dock
