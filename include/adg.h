@@ -262,7 +262,8 @@ int adg_score(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* lig, cons
  * Each pose gets the same values as adg_score gives it.  The launch tables
  * live in a stream-ordered device buffer (cudaMallocAsync) freed after the
  * launch.  ADG_EINVAL on a null argument, a negative count or a ligand of
- * another context; asynchronous on the context's stream. */
+ * another context, ADG_ETOOBIG beyond 2^30 rows; asynchronous on the
+ * context's stream. */
 int adg_score_multi(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig, const int* npose,
                     const float* genes, float* energy, float* grad, int grad_kind);
 
