@@ -421,16 +421,18 @@ __global__ void k_mlp_adam(float* __restrict__ theta, float* __restrict__ m, flo
 
 
 // ------------------------------------------------------------------ tcgen05 forward
-// Inference on the 5th-generation tensor cores: persistent CTAs (8 warps, one
+// Inference on the 5th-generation tensor cores: persistent CTAs (16 warps, one
 // per SM) run 128-row tiles, W1 and W2 staged once per CTA.  x_hat, W1, h1 and W2 sit in shared memory in the canonical K-major
 // no-swizzle layout (8-row x 16-byte core matrices: element (r, k) of an
 // R x K operand at ((r/8)(K/8) + k/8) * 128 + (r%8) * 16 + (k%8) * 2 bytes);
 // one thread issues tcgen05.mma (M = 128, N = 256, K = 16 per instruction,
 // BF16 in, FP32 accumulators in tensor memory): x_hat W1^T into TMEM columns
-// 0-255, then h1 W2^T into columns 256-511.  Two threads own a row (its TMEM
-// lane), one per half of the columns; they read their accumulators back with
-// tcgen05.ld and finish the row (bias, ReLU, BF16 h1; then bias, ReLU and the
-// w3 dot product, the halves summed through shared memory).
+// 0-255, then h1 W2^T into columns 256-511.  Four threads own a row (its TMEM
+// lane), one per quarter of the columns (four warps per lane quarter keep the
+// epilogue's tensor-memory and shared-memory latencies covered); they read
+// their accumulators back with tcgen05.ld and finish the row (bias, ReLU,
+// BF16 h1; then bias, ReLU and the w3 dot product, the quarters summed
+// through shared memory).
 constexpr int TC_ROWS = 128;
 constexpr size_t kTcW2 = (size_t)H * H * 2;
 constexpr size_t kTcW1 = (size_t)H * KIN * 2;
@@ -495,7 +497,7 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-constexpr int TC_THREADS = 256;  // 8 warps: warps w and w + 4 share TMEM lanes 32 (w % 4).., split the columns
+constexpr int TC_THREADS = 512;  // 16 warps: warps w, w + 4, w + 8, w + 12 share TMEM lanes 32 (w % 4).., a column quarter each
 
 __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* status)
 {
@@ -509,10 +511,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
     float* w3s = b2s + H;
     uint64_t* mbar = reinterpret_cast<uint64_t*>(w3s + H);  // [0]: layer-1 MMAs, [1]: layer-2 MMAs
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
-    __shared__ float part[TC_ROWS];  // the second column half's share of each row's output
+    __shared__ float part[3][TC_ROWS];  // the other column quarters' shares of each row's output
     const int tid = threadIdx.x, warp = tid >> 5;
     const int r = (warp & 3) * 32 + (tid & 31);  // this thread's row = its TMEM lane
-    const int half = warp >> 2;                  // columns [128 half, 128 half + 128)
+    const int half = warp >> 2;                  // column quarter: columns [64 half, 64 half + 64)
     const uint32_t s_base = smem_u32(smem), s_mbar1 = smem_u32(mbar), s_mbar2 = smem_u32(mbar + 1);
     if (warp == 0) {  // 512 TMEM columns: layer 1 in 0-255, layer 2 in 256-511
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot))
@@ -546,7 +548,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
     auto stage_x = [&](int tile) {
         const int row = tile * TC_ROWS + r;
 #pragma unroll
-        for (int k8 = half * 2; k8 < half * 2 + 2; ++k8) {
+        for (int k8 = half; k8 < half + 1; ++k8) {
             uint32_t pk[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -589,7 +591,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
         ok = tc_wait(s_mbar1, ph1) && ok;
         ph1 ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int c = half * 4; c < half * 4 + 4; ++c) {  // h1 = relu(x_hat W1^T + b1) -> BF16, row-major K = 256
+        for (int c = half * 2; c < half * 2 + 2; ++c) {  // h1 = relu(x_hat W1^T + b1) -> BF16, row-major K = 256
             float v[32];
             tc_ld32(trow + c * 32, v);
 #pragma unroll
@@ -629,19 +631,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
         ph2 ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float acc = 0.f;
-        for (int c = half * 4; c < half * 4 + 4; ++c) {  // w3 . relu(h1 W2^T + b2) over this half's columns
+        for (int c = half * 2; c < half * 2 + 2; ++c) {  // w3 . relu(h1 W2^T + b2) over this quarter's columns
             float v[32];
             tc_ld32(trow + H + c * 32, v);
 #pragma unroll
             for (int e = 0; e < 32; ++e) acc += fmaxf(v[e] + b2s[c * 32 + e], 0.f) * w3s[c * 32 + e];
         }
-        if (half == 1) part[r] = acc;
+        if (half > 0) part[half - 1][r] = acc;
         // h1 and columns 256-511 are rewritten for the next tile only after every thread is done with them
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (half == 0 && row < A.B)
-            A.y[row] = ok ? (acc + part[r] + A.theta[A.o.b3]) * A.nm.sigma_y + A.nm.mu_y : __int_as_float(0x7fc00000);
+            A.y[row] = ok ? (acc + part[0][r] + part[1][r] + part[2][r] + A.theta[A.o.b3]) * A.nm.sigma_y + A.nm.mu_y
+                          : __int_as_float(0x7fc00000);
     }
     if (!ok) atomicOr(status, 1);
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
