@@ -127,6 +127,13 @@ def _declare(L):
     L.orc_lga_run.argtypes = [C.POINTER(FF), C.POINTER(GRID), _d, _vp, C.POINTER(PARAMS), C.c_int,
                               C.POINTER(RUNRES), C.c_int, _vp, _vp, _vp]
     L.orc_init_population.argtypes = [C.POINTER(GRID), C.POINTER(PARAMS), C.c_int, C.c_int, _d]
+    L.orc_score_xyz.argtypes = [C.POINTER(FF), C.POINTER(GRID), _d, _vp, _d, C.c_int, _d, _d, _vp]
+    L.orc_solis_wets_trace.argtypes = [C.POINTER(FF), C.POINTER(GRID), _d, _vp, C.POINTER(PARAMS), C.c_int,
+                                       C.c_int, C.c_int, _d, C.POINTER(C.c_double), _d,
+                                       C.POINTER(C.c_longlong)]
+    L.orc_solis_wets_trace.restype = C.c_int
+    L.orc_make_offspring.argtypes = [C.POINTER(PARAMS), C.c_int, C.c_int, C.c_int, C.c_int, _d, _d, _d,
+                                     C.POINTER(TRACE)]
 
 
 # ---------------------------------------------------------------- helpers
@@ -319,6 +326,20 @@ def score(ff, grid, maps, L: Ligand, genes: np.ndarray):
     return e, ei, gg, gt
 
 
+def score_xyz(ff, grid, maps, L: Ligand, xyz: np.ndarray, forces: bool = False):
+    """Energies (total, intermolecular) of posed coordinates xyz[npose, natoms, 3]
+    given directly, and with forces=True the per-atom gradients too."""
+    xyz = np.ascontiguousarray(np.asarray(xyz, np.float64).reshape(-1, L.natoms, 3))
+    n = xyz.shape[0]
+    e = np.zeros(n)
+    ei = np.zeros(n)
+    f = np.zeros((n, L.natoms, 3)) if forces else None
+    lib().orc_score_xyz(C.byref(make_ff(ff)), C.byref(make_grid(grid)),
+                        np.ascontiguousarray(maps, np.float64).reshape(-1), L.ptr, xyz, n, e, ei,
+                        f.ctypes.data if forces else None)
+    return (e, ei, f) if forces else (e, ei)
+
+
 def atom_gradients(ff, grid, maps, L: Ligand, genes: np.ndarray) -> np.ndarray:
     """dE/dx'_i per atom: [npose, natoms, 3]."""
     genes = np.ascontiguousarray(np.atleast_2d(genes), np.float64)
@@ -342,6 +363,40 @@ def local_search(ff, grid, maps, L, params: SearchParams, genes, energy, run=0, 
                                np.ascontiguousarray(maps, np.float64).reshape(-1), L.ptr, C.byref(params.to_c()),
                                run, ind, gen, g, C.byref(e))
     return g, e.value, n
+
+
+SW_TRACE_WIDTH = 3 + 2 * MAXGENES
+
+
+def solis_wets_trace(ff, grid, maps, L, params: SearchParams, genes, energy, run=0, ind=0, gen=1):
+    """Solis-Wets on one genotype with its trace.  Returns (genes, energy,
+    evaluations, trace) where trace has one row per iteration: rho, outcome
+    (+1 / -1 / 0), energy after it, xi[D], bias after it[D]."""
+    g = np.ascontiguousarray(genes, np.float64).copy()
+    e = C.c_double(energy)
+    nev = C.c_longlong(0)
+    D = 6 + L.ntors
+    buf = np.zeros((max(params.ls_max_iters, 1), SW_TRACE_WIDTH))
+    it = lib().orc_solis_wets_trace(C.byref(make_ff(ff)), C.byref(make_grid(grid)),
+                                    np.ascontiguousarray(maps, np.float64).reshape(-1), L.ptr,
+                                    C.byref(params.to_c()), run, ind, gen, g, C.byref(e), buf, C.byref(nev))
+    t = buf[:it]
+    trace = dict(rho=t[:, 0].copy(), outcome=t[:, 1].astype(int), energy=t[:, 2].copy(),
+                 xi=t[:, 3:3 + D].copy(), bias=t[:, 3 + MAXGENES:3 + MAXGENES + D].copy())
+    return g, e.value, nev.value, trace
+
+
+def make_offspring(params: SearchParams, ntors, pop_genes, pop_energy, run=0, ind=1, gen=1):
+    """One offspring of the GA (selection, two-point crossover, mutation).
+    Returns (child genes, decisions dict)."""
+    G = 7 + ntors
+    Pg = np.ascontiguousarray(pop_genes, np.float64).reshape(-1, G)
+    Pe = np.ascontiguousarray(pop_energy, np.float64).reshape(-1)
+    child = np.zeros(G)
+    tr = TRACE()
+    lib().orc_make_offspring(C.byref(params.to_c()), ntors, run, ind, gen, Pg, Pe, child, C.byref(tr))
+    dec = {f: getattr(tr, f) for f, _ in TRACE._fields_}
+    return child, dec
 
 
 def init_population(grid, params: SearchParams, ntors, run=0):

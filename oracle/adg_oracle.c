@@ -571,20 +571,16 @@ static double atom_inter(const orc_ff* ff, const orc_grid* g, const double* maps
     return vt + q * ve + fabs(q) * vd + pen;
 }
 
-/* Total energy E = E_inter + E_intra (the search objective; reading) and
- * its gradient.  g_i = dE/dx'_i.  Then
- *   dE/dt = sum_i g_i
- *   torque = sum_i (x'_i - t) x g_i                (tangent of a world-frame rotation)
- *   dE/dtheta_k = sum_{i in S_k} (u'_k x (x'_i - x'_{a_k})) . g_i, u'_k the posed axis
- *   dE/dq = 2 (-tau.v, w tau + tau x v) / |q|, with q/|q| = (w, v)   (chain rule
- *           through x' = q (0,x) q*, derived in DESIGN notes of the tests). */
-int orc_score(const orc_ff* ff, const orc_grid* g, const double* maps, const orc_ligand* L,
-              const double* genes, orc_score_out* out, double* xyz_out)
+/* Energy of posed coordinates x (natoms x 3): E_inter + E_intra (the search
+ * objective; reading) and the per-atom gradient f_i = dE/dx_i.  The
+ * intermolecular part sums, per atom, the trilinear maps plus the out-of-box
+ * restraint; the intramolecular part sums the three pair terms over the
+ * pair list, each pair's dE/dr applied along the unit vector between the
+ * two atoms (Sec. 1: vdW / H-bond, electrostatic and desolvation terms). */
+static void score_coords(const orc_ff* ff, const orc_grid* g, const double* maps, const orc_ligand* L,
+                         const double* x, double* e_inter_out, double* e_intra_out, double (*f)[3])
 {
     int n = L->natoms;
-    double x[ORC_MAXATOMS * 3];
-    double f[ORC_MAXATOMS][3];
-    orc_pose(L, genes, x);
     double e_inter = 0.0, e_intra = 0.0;
     for (int i = 0; i < n; ++i) {
         double gi[3];
@@ -608,6 +604,28 @@ int orc_score(const orc_ff* ff, const orc_grid* g, const double* maps, const orc
             }
         }
     }
+    *e_inter_out = e_inter;
+    *e_intra_out = e_intra;
+}
+
+/* Total energy of a genotype and its gradient: pose (orc_pose), then the
+ * energy of the posed coordinates (score_coords) with g_i = dE/dx'_i, then
+ *   dE/dt = sum_i g_i
+ *   torque = sum_i (x'_i - t) x g_i                (tangent of a world-frame rotation)
+ *   dE/dtheta_k = sum_{i in S_k} (u'_k x (x'_i - x'_{a_k})) . g_i, u'_k the posed axis
+ *   dE/dq = 2 (-tau.v, w tau + tau x v) / |q|, with q/|q| = (w, v)   (chain rule
+ *           through x' = q (0,x) q*: the derivative of a unit-quaternion rotation
+ *           with respect to q is a rotation generator, projected off the
+ *           radial direction by the normalisation). */
+int orc_score(const orc_ff* ff, const orc_grid* g, const double* maps, const orc_ligand* L,
+              const double* genes, orc_score_out* out, double* xyz_out)
+{
+    int n = L->natoms;
+    double x[ORC_MAXATOMS * 3];
+    double f[ORC_MAXATOMS][3];
+    orc_pose(L, genes, x);
+    double e_inter, e_intra;
+    score_coords(ff, g, maps, L, x, &e_inter, &e_intra, f);
     double gt[3] = {0, 0, 0}, tau[3] = {0, 0, 0};
     for (int i = 0; i < n; ++i) {
         double rel[3] = {x[3 * i] - genes[0], x[3 * i + 1] - genes[1], x[3 * i + 2] - genes[2]};
@@ -656,24 +674,28 @@ void orc_atom_gradients(const orc_ff* ff, const orc_grid* g, const double* maps,
 {
     int n = L->natoms, G = 7 + L->ntors;
     for (int p = 0; p < npose; ++p) {
-        double x[ORC_MAXATOMS * 3];
-        double* f = forces + (size_t)p * n * 3;
+        double x[ORC_MAXATOMS * 3], f[ORC_MAXATOMS][3], ei, ea;
         orc_pose(L, genes + (size_t)p * G, x);
-        for (int i = 0; i < n; ++i) atom_inter(ff, g, maps, L->type[i], L->q[i], x + 3 * i, f + 3 * i);
-        for (int q = 0; q < L->npairs; ++q) {
-            int i = L->pair_i[q], j = L->pair_j[q];
-            double d[3] = {x[3 * i] - x[3 * j], x[3 * i + 1] - x[3 * j + 1], x[3 * i + 2] - x[3 * j + 2]};
-            double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-            double d1, d2, d3;
-            orc_pair_lj(ff, L->type[i], L->type[j], r, &d1);
-            orc_pair_elec(ff, L->q[i] * L->q[j], r, &d2);
-            orc_pair_desolv(ff, L->type[i], L->q[i], L->type[j], L->q[j], r, &d3);
-            if (r > 0.0)
-                for (int a = 0; a < 3; ++a) {
-                    f[3 * i + a] += (d1 + d2 + d3) * d[a] / r;
-                    f[3 * j + a] -= (d1 + d2 + d3) * d[a] / r;
-                }
-        }
+        score_coords(ff, g, maps, L, x, &ei, &ea, f);
+        memcpy(forces + (size_t)p * n * 3, f, sizeof(double) * 3 * n);
+    }
+}
+
+/* Energies of npose sets of posed coordinates xyz[npose][natoms][3], given
+ * directly rather than as genotypes (the same sums as orc_score after its
+ * pose step): total and intermolecular energy per pose, and optionally the
+ * per-atom gradients forces[npose][natoms][3].  Lets the tests separate the
+ * rounding of the posed coordinates from the rounding of the scoring sums. */
+void orc_score_xyz(const orc_ff* ff, const orc_grid* g, const double* maps, const orc_ligand* L,
+                   const double* xyz, int npose, double* energy, double* e_inter, double* forces)
+{
+    int n = L->natoms;
+    for (int p = 0; p < npose; ++p) {
+        double f[ORC_MAXATOMS][3], ei, ea;
+        score_coords(ff, g, maps, L, xyz + (size_t)p * n * 3, &ei, &ea, f);
+        if (energy) energy[p] = ei + ea;
+        if (e_inter) e_inter[p] = ei;
+        if (forces) memcpy(forces + (size_t)p * n * 3, f, sizeof(double) * 3 * n);
     }
 }
 
@@ -791,16 +813,23 @@ static double ls_gauss(const orc_rng* r, int run, int ind, int gen, int iter, in
  * Accept x (+) xi if better (bias <- 0.4 xi + 0.2 bias), else try x (-) xi
  * (bias <- bias - 0.4 xi), else bias <- 0.5 bias.  rho doubles after
  * sw_succ consecutive successes and halves after sw_fail consecutive
- * failures; stop when rho < rho_min or after max_iters iterations. */
-static void solis_wets(orc_problem* P, const orc_params* prm, const orc_rng* r, int run, int ind, int gen,
-                       double* genes, double* energy)
+ * failures; stop when rho < rho_min or after max_iters iterations.
+ * trace (optional, for the tests): per iteration ORC_SW_TRACE_WIDTH doubles
+ * = rho of the iteration, outcome (+1 x (+) xi accepted, -1 x (-) xi
+ * accepted, 0 rejected), energy after it, xi[ORC_MAXGENES],
+ * bias after it[ORC_MAXGENES]. */
+#define ORC_SW_TRACE_WIDTH (3 + 2 * ORC_MAXGENES)
+static int solis_wets(orc_problem* P, const orc_params* prm, const orc_rng* r, int run, int ind, int gen,
+                      double* genes, double* energy, double* trace)
 {
     int T = P->L->ntors, D = 6 + T, G = 7 + T;
     double bias[ORC_MAXGENES] = {0}, xi[ORC_MAXGENES], cand[ORC_MAXGENES];
     double rho = prm->sw_rho0;
-    int succ = 0, fail = 0;
+    int succ = 0, fail = 0, it;
     double e = *energy;
-    for (int it = 0; it < prm->ls_max_iters && rho >= prm->sw_rho_min; ++it) {
+    for (it = 0; it < prm->ls_max_iters && rho >= prm->sw_rho_min; ++it) {
+        double rho_it = rho;
+        int outcome;
         for (int d = 0; d < D; ++d) {
             double s = d < 3 ? prm->sw_scale_t : (d < 6 ? prm->sw_scale_rot : prm->sw_scale_tors);
             xi[d] = bias[d] + rho * s * ls_gauss(r, run, ind, gen, it, d);
@@ -812,6 +841,7 @@ static void solis_wets(orc_problem* P, const orc_params* prm, const orc_rng* r, 
             e = e1;
             for (int d = 0; d < D; ++d) bias[d] = 0.4 * xi[d] + 0.2 * bias[d];
             ++succ; fail = 0;
+            outcome = 1;
         } else {
             orc_apply_step(T, genes, xi, -1.0, cand);
             double e2 = eval_energy(P, cand);
@@ -820,15 +850,26 @@ static void solis_wets(orc_problem* P, const orc_params* prm, const orc_rng* r, 
                 e = e2;
                 for (int d = 0; d < D; ++d) bias[d] = bias[d] - 0.4 * xi[d];
                 ++succ; fail = 0;
+                outcome = -1;
             } else {
                 for (int d = 0; d < D; ++d) bias[d] *= 0.5;
                 ++fail; succ = 0;
+                outcome = 0;
             }
         }
         if (succ >= prm->sw_succ) { rho *= prm->sw_expand; succ = 0; }
         if (fail >= prm->sw_fail) { rho *= prm->sw_contract; fail = 0; }
+        if (trace) {
+            double* t = trace + (size_t)it * ORC_SW_TRACE_WIDTH;
+            memset(t, 0, sizeof(double) * ORC_SW_TRACE_WIDTH);
+            t[0] = rho_it;
+            t[1] = outcome;
+            t[2] = e;
+            for (int d = 0; d < D; ++d) { t[3 + d] = xi[d]; t[3 + ORC_MAXGENES + d] = bias[d]; }
+        }
     }
     *energy = e;
+    return it;
 }
 
 /* ADADELTA (Zeiler 2012) in the tangent space: per iteration evaluate E and
@@ -870,9 +911,22 @@ long long orc_local_search(const orc_ff* ff, const orc_grid* g, const double* ma
 {
     orc_problem P = {ff, g, maps, L, 0};
     orc_rng r = {{prm->seed_lo, prm->seed_hi}, prm->lig_id};
-    if (prm->ls_method == 1) solis_wets(&P, prm, &r, run, ind, gen, genes, energy);
+    if (prm->ls_method == 1) solis_wets(&P, prm, &r, run, ind, gen, genes, energy, NULL);
     else if (prm->ls_method == 2) adadelta(&P, prm, genes, energy);
     return P.evals;
+}
+
+/* Solis-Wets on one genotype with its per-iteration trace (see solis_wets);
+ * returns the number of iterations, *nevals the energy evaluations. */
+int orc_solis_wets_trace(const orc_ff* ff, const orc_grid* g, const double* maps, const orc_ligand* L,
+                         const orc_params* prm, int run, int ind, int gen, double* genes, double* energy,
+                         double* trace, long long* nevals)
+{
+    orc_problem P = {ff, g, maps, L, 0};
+    orc_rng r = {{prm->seed_lo, prm->seed_hi}, prm->lig_id};
+    int iters = solis_wets(&P, prm, &r, run, ind, gen, genes, energy, trace);
+    *nevals = P.evals;
+    return iters;
 }
 
 /* ======================================================================== */
@@ -980,6 +1034,18 @@ static void make_offspring(const orc_rng* r, const orc_params* prm, int T, int r
     }
 }
 
+/* make_offspring exported for the tests: offspring `ind` of generation `gen`
+ * from the population genes Pg[pop][7+T] and energies Pe[pop]; the decision
+ * record goes to *tr. */
+void orc_make_offspring(const orc_params* prm, int T, int run, int ind, int gen, const double* Pg,
+                        const double* Pe, double* child, orc_trace* tr)
+{
+    orc_rng r = {{prm->seed_lo, prm->seed_hi}, prm->lig_id};
+    orc_trace t = {-1, -1, -1, -1, 0, 0, {-1, -1, -1, -1}, 0, 0};
+    make_offspring(&r, prm, T, run, ind, gen, Pg, Pe, child, &t);
+    *tr = t;
+}
+
 typedef struct {
     double best_energy;
     double best_genes[ORC_MAXGENES];
@@ -1034,7 +1100,7 @@ int orc_lga_run(const orc_ff* ff, const orc_grid* g, const double* maps, const o
             rng_block(&r, run, i, gen, PURPOSE_LSPICK, 0, w);
             if (prm->ls_method != 0 && ptest(w[0], thr_ls)) {
                 tr.ls_applied = 1;
-                if (prm->ls_method == 1) solis_wets(&P, prm, &r, run, i, gen, child, &Ne[i]);
+                if (prm->ls_method == 1) solis_wets(&P, prm, &r, run, i, gen, child, &Ne[i], NULL);
                 else adadelta(&P, prm, child, &Ne[i]);
             }
             if (trace && gen <= ntrace) trace[(size_t)(gen - 1) * pop + i] = tr;

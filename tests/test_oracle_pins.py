@@ -671,3 +671,220 @@ def test_autostop_rule(ff, plain_inputs, plain_maps):
     b = te[:g_on].min(axis=1)
     first = next((g for g in range(10, g_on + 1) if np.std(b[g - 10:g]) < 0.15), None)
     assert first == g_on < 60
+
+
+# ----------------------------------------------------------------- Solis-Wets, step by step
+def _sw_gaussians(params, lig_id, run, ind, gen, iters, D):
+    """The Solis-Wets normal draws from the pinned Philox stream and the
+    textbook Box-Muller transform: counter (ligand, run<<16 | individual,
+    generation, 5<<20 | iteration*8 + d/4); words (2p, 2p+1) with p = (d/2)
+    mod 2 give u1 in (0, 1] and u2 in [0, 1); z = sqrt(-2 ln u1) cos(2 pi u2)
+    for even d, sin for odd d."""
+    z = np.zeros((iters, D))
+    for it in range(iters):
+        for d in range(D):
+            ctr = np.array([[lig_id, (run << 16) | ind, gen, (5 << 20) | (it * 8 + d // 4)]], np.uint32)
+            w = O.philox(ctr, params.seed & 0xFFFFFFFF, params.seed >> 32)[0]
+            p = (d // 2) % 2
+            u1 = ((int(w[2 * p]) >> 8) + 1) / 2.0 ** 24
+            u2 = (int(w[2 * p + 1]) >> 8) / 2.0 ** 24
+            rad = math.sqrt(-2.0 * math.log(u1))
+            z[it, d] = rad * (math.cos(2 * math.pi * u2) if d % 2 == 0 else math.sin(2 * math.pi * u2))
+    return z
+
+
+def test_solis_wets_follows_the_published_rule(ff, plain_inputs, plain_maps):
+    """Every iteration of a Solis-Wets search (Solis & Wets 1981) on the plain
+    problem, checked against the rule: the trial is xi = bias + rho s (.) z
+    with z the Box-Muller normals of the Philox stream; x (+) xi is taken when
+    it lowers the energy (bias <- 0.4 xi + 0.2 bias), else x (-) xi when that
+    does (bias <- bias - 0.4 xi), else nothing moves (bias <- bias / 2); rho
+    doubles after 4 successes in a row and halves after 4 failures in a row.
+    The energies of both trials are recomputed with the scoring function and
+    the step with the tangent move (both pinned above)."""
+    grid, rec, lig = plain_inputs
+    L = O.Ligand(lig)
+    T, D = lig.ntors, 6 + lig.ntors
+    p = O.SearchParams(ls_method=1, ls_max_iters=80, seed=11, lig_id=3)
+    scale = np.array([p.sw_scale_t] * 3 + [p.sw_scale_rot] * 3 + [p.sw_scale_tors] * T)
+    g0 = S.random_genes(lig, 4, grid, 41, spread=0.2)[2]
+    e0 = O.score(ff, grid, plain_maps, L, g0)[0][0]
+    g_end, e_end, nev, tr = O.solis_wets_trace(ff, grid, plain_maps, L, p, g0, e0, run=2, ind=7, gen=3)
+    n = len(tr["rho"])
+    assert n == p.ls_max_iters or tr["rho"][-1] * 0.5 < p.sw_rho_min
+    z = _sw_gaussians(p, 3, 2, 7, 3, n, D)
+    x, e, bias, rho, succ, fail = g0.copy(), e0, np.zeros(D), 1.0, 0, 0
+    outcomes, evals = set(), 0
+    for it in range(n):
+        assert tr["rho"][it] == rho
+        xi = bias + rho * scale * z[it]
+        assert np.allclose(tr["xi"][it], xi, rtol=1e-12, atol=1e-14)
+        xi = tr["xi"][it]
+        plus, minus = O.apply_step(T, x, xi, 1.0), O.apply_step(T, x, xi, -1.0)
+        e_plus = O.score(ff, grid, plain_maps, L, plus)[0][0]
+        evals += 1
+        if e_plus < e:
+            want, x, e, bias = 1, plus, e_plus, 0.4 * xi + 0.2 * bias
+        else:
+            e_minus = O.score(ff, grid, plain_maps, L, minus)[0][0]
+            evals += 1
+            if e_minus < e:
+                want, x, e, bias = -1, minus, e_minus, bias - 0.4 * xi
+            else:
+                want, bias = 0, 0.5 * bias
+        assert tr["outcome"][it] == want, it
+        assert tr["energy"][it] == e
+        assert np.allclose(tr["bias"][it], bias, rtol=1e-12, atol=1e-14)
+        outcomes.add(want)
+        succ, fail = (succ + 1, 0) if want else (0, fail + 1)
+        if succ >= 4:
+            rho, succ = 2 * rho, 0
+        if fail >= 4:
+            rho, fail = 0.5 * rho, 0
+    assert outcomes == {1, -1, 0}  # the three branches all ran
+    assert nev == evals and e_end == e and np.array_equal(g_end, x)
+
+
+def test_solis_wets_at_a_strict_minimum_contracts_to_rho_min(ff):
+    """Started exactly on the minimum node of a convex bowl, every trial is
+    worse in both directions: the bias stays 0, rho halves after every 4
+    failures, 1 -> 2^-7 < 0.01 after 28 iterations = 56 evaluations, and the
+    genotype does not move."""
+    grid, maps, L, c = _bowl_problem(ff)
+    p = O.SearchParams(ls_method=1, ls_max_iters=300)
+    g0 = np.concatenate([c, [1, 0, 0, 0]])
+    e0 = O.score(ff, grid, maps, L, g0)[0][0]
+    g, e, nev, tr = O.solis_wets_trace(ff, grid, maps, L, p, g0, e0)
+    assert len(tr["rho"]) == 28 and nev == 56
+    assert (tr["outcome"] == 0).all() and (tr["bias"] == 0).all()
+    assert np.array_equal(tr["rho"], 0.5 ** (np.arange(28) // 4))
+    assert np.array_equal(g, g0) and e == e0
+
+
+def test_solis_wets_on_a_linear_field_always_succeeds(ff):
+    """One atom in a linear field E = b.x: for any trial one of x (+) xi and
+    x (-) xi is lower, and the lower one is the one with b.xi_t < 0.  So every
+    iteration succeeds, rho doubles every 4 iterations, and the translation
+    moves by exactly -sign(b.xi_t) xi_t each time."""
+    grid = S.Grid((61, 61, 61), (0.0, 0.0, 0.0), 1.0)
+    b = np.array([0.3, -0.2, 0.5])
+    maps = np.stack([_linear_map(grid, 0.0, b) for _ in range(S.NMAPS)])
+    lig = S.Ligand(np.zeros((1, 3)), np.array([S.T_C], np.int32), np.zeros(1), np.zeros((0, 2), np.int32),
+                   np.zeros((0, 2), np.int32), 0)
+    L = O.Ligand(lig)
+    p = O.SearchParams(ls_method=1, ls_max_iters=12, sw_scale_t=0.1)
+    g0 = np.array([30.0, 30.0, 30.0, 1, 0, 0, 0])
+    e0 = O.score(ff, grid, maps, L, g0)[0][0]
+    g, e, nev, tr = O.solis_wets_trace(ff, grid, maps, L, p, g0, e0)
+    assert len(tr["rho"]) == 12
+    assert np.array_equal(tr["rho"], 2.0 ** (np.arange(12) // 4))
+    want = -np.sign(tr["xi"][:, 0:3] @ b)
+    assert np.array_equal(tr["outcome"], want.astype(int))
+    assert nev == 12 + (want < 0).sum()
+    t = g0[0:3] + (want[:, None] * tr["xi"][:, 0:3]).sum(axis=0)
+    assert np.allclose(g[0:3], t, rtol=0, atol=1e-12)
+    assert e == pytest.approx(e0 + b @ (t - g0[0:3]), abs=1e-10)
+
+
+# ----------------------------------------------------------------- offspring
+def test_make_offspring_blocks_and_mutations():
+    """Selection, crossover and mutation of single offspring against the
+    operators' definitions, drawing from the pinned Philox stream:
+      - parents: binary tournaments over uniform indices floor(w pop / 2^32),
+        the lower energy (ties to the lower index) winning when the word's
+        top 24 bits fall below floor(0.6 * 2^24);
+      - two-point crossover over gene blocks [t][q][theta_1]..[theta_T]: the
+        blocks in [lo, hi) are parent 2's, all others parent 1's, q whole;
+      - mutation per block: t moves by mut_t (2u - 1) per component, theta by
+        mut_tors (2u - 1), q by a rotation of angle mut_rot (2u - 1) about a
+        uniform axis (checked with scipy's rotation algebra); blocks that do
+        not mutate keep their crossed-over values bit for bit."""
+    from scipy.spatial.transform import Rotation
+    rng = np.random.default_rng(5)
+    T, pop = 5, 40
+    G, nb = 7 + T, 2 + T
+    Pg = rng.normal(size=(pop, G))
+    Pg[:, 3:7] /= np.linalg.norm(Pg[:, 3:7], axis=1, keepdims=True)
+    Pe = rng.normal(size=pop)
+    Pe[7] = Pe[3]  # one tie, broken towards the lower index
+    base = O.SearchParams(pop_size=pop, mutation_rate=0.0, seed=99, lig_id=4)
+    mut = O.SearchParams(pop_size=pop, mutation_rate=0.5, seed=99, lig_id=4)
+    key = (base.seed & 0xFFFFFFFF, base.seed >> 32)
+    thr = lambda pr: math.floor(pr * 2 ** 24)
+
+    def words(run, ind, gen, purpose, blk):
+        return [int(v) for v in O.philox(np.array([[4, (run << 16) | ind, gen, (purpose << 20) | blk]], np.uint32),
+                                          *key)[0]]
+
+    seen_x = seen_m = 0
+    for k in range(400):
+        run, ind, gen = k % 3, 1 + k % (pop - 1), 1 + k // 7
+        c0, d0 = O.make_offspring(base, T, Pg, Pe, run, ind, gen)
+        c1, d1 = O.make_offspring(mut, T, Pg, Pe, run, ind, gen)
+        for f in ("parent1", "parent2", "xlo", "xhi", "a1", "b1", "a2", "b2"):
+            assert d0[f] == d1[f]
+        parents = []
+        for s in (0, 1):
+            w = words(run, ind, gen, 2, s)
+            a, b = (w[0] * pop) >> 32, (w[1] * pop) >> 32
+            better, worse = (a, b) if (Pe[a] < Pe[b] or (Pe[a] == Pe[b] and a <= b)) else (b, a)
+            parents.append(better if (w[2] >> 8) < thr(0.6) else worse)
+            assert (d0["a%d" % (s + 1)], d0["b%d" % (s + 1)]) == (a, b)
+        assert (d0["parent1"], d0["parent2"]) == tuple(parents)
+        p1, p2 = parents
+        w = words(run, ind, gen, 2, 2)
+        if (w[0] >> 8) < thr(0.8):
+            c1_, c2_ = (w[1] * (nb + 1)) >> 32, (w[2] * (nb + 1)) >> 32
+            lo, hi = min(c1_, c2_), max(c1_, c2_)
+            seen_x += hi > lo
+        else:
+            lo = hi = -1
+        assert (d0["xlo"], d0["xhi"]) == (lo, hi)
+        blocks = [slice(0, 3), slice(3, 7)] + [slice(7 + j, 8 + j) for j in range(T)]
+        for bidx, sl in enumerate(blocks):
+            src = p2 if lo <= bidx < hi else p1
+            assert np.array_equal(c0[sl], Pg[src, sl])
+        assert d0["mut_mask"] == 0
+        mask = 0
+        for bidx, sl in enumerate(blocks):
+            if (words(run, ind, gen, 2, 3 + bidx // 4)[bidx % 4] >> 8) >= thr(0.5):
+                assert np.array_equal(c1[sl], c0[sl])
+                continue
+            mask |= 1 << bidx
+            m = words(run, ind, gen, 3, bidx)
+            u = [(v >> 8) / 2.0 ** 24 for v in m]
+            if bidx == 0:
+                assert np.array_equal(c1[sl], c0[sl] + 2.0 * (2.0 * np.array(u[:3]) - 1.0))
+                assert np.abs(c1[sl] - c0[sl]).max() <= 2.0
+            elif bidx == 1:
+                zc, phi, ang = 2 * u[0] - 1, 2 * math.pi * u[1], (math.pi / 2) * (2 * u[2] - 1)
+                axis = np.array([math.sqrt(1 - zc * zc) * math.cos(phi), math.sqrt(1 - zc * zc) * math.sin(phi), zc])
+                want = Rotation.from_rotvec(ang * axis) * Rotation.from_quat([c0[4], c0[5], c0[6], c0[3]])
+                wq = want.as_quat()
+                got = np.array([c1[4], c1[5], c1[6], c1[3]])
+                assert min(np.abs(got - wq).max(), np.abs(got + wq).max()) < 1e-12
+                assert abs(np.dot(c1[3:7], c0[3:7])) >= math.cos(math.pi / 4) - 1e-12  # at most 90 degrees
+            else:
+                assert c1[sl][0] == c0[sl][0] + (math.pi / 2) * (2.0 * u[0] - 1.0)
+                assert abs(c1[sl][0] - c0[sl][0]) <= math.pi / 2
+        assert d1["mut_mask"] == mask
+        seen_m += mask != 0
+    assert seen_x > 200 and seen_m > 300
+
+
+def test_score_of_posed_coordinates_matches_genotype_scoring(ff, plain_inputs, plain_maps):
+    """orc_score_xyz on the oracle's own posed coordinates gives orc_score's
+    energies and per-atom gradients bit for bit; translating every atom by a
+    vector leaves the intramolecular part unchanged."""
+    grid, rec, lig = plain_inputs
+    L = O.Ligand(lig)
+    g = S.random_genes(lig, 40, grid, 43, spread=0.2)
+    e, ei, _, _ = O.score(ff, grid, plain_maps, L, g)
+    x = O.pose(L, g)
+    e2, ei2, f2 = O.score_xyz(ff, grid, plain_maps, L, x, forces=True)
+    assert np.array_equal(e, e2) and np.array_equal(ei, ei2)
+    assert np.array_equal(f2, O.atom_gradients(ff, grid, plain_maps, L, g))
+    zero = np.zeros_like(plain_maps)
+    a = O.score_xyz(ff, grid, zero, L, x)[0] - O.score_xyz(ff, grid, zero, L, x)[1]
+    b = O.score_xyz(ff, grid, zero, L, x + np.array([0.7, -0.4, 0.2]))
+    assert np.allclose(a, b[0] - b[1], rtol=1e-12, atol=1e-9)
