@@ -267,17 +267,37 @@ def workload_config(nrun=None, nev=None) -> dict:
 
 
 TRIAGE_TRAIN, TRIAGE_STREAM = 1200, 2000
-# DRAM bytes (read + write) per generation of all 100 runs (two launches of the
-# generation kernel, 50 runs each), from
-#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
-#       -k regex:k_dock_generation -s 60 -c 2 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
-#       --no-e2e --no-batching --no-triage --no-graphs
-# (the sum of the two launches); None whenever the kernel has changed since that capture.
-GEN_TRAFFIC_BYTES = 38.5e6
-# The pipe that bounds the kernel, from the full-section capture of the same
-# kernel (l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed):
-# the L1 / shared-memory data pipe.  None whenever the kernel has changed.
-GEN_L1_PIPE_FRAC = 0.694
+# Figures of the generation kernel taken from ncu captures, valid only for
+# the kernel source they were taken on: the bench reports them only while
+# the SHA-256 (first 16 hex digits) of adg_kernels.cu + adg_internal.h
+# equals `source_sha16`, and null otherwise.  The same hash heads the capture
+# summaries under profiles/.
+#   traffic_bytes: DRAM bytes (read + write) per generation of all 100 runs
+#     (both launches), from
+#     ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum --clock-control none
+#         -k regex:k_dock_generation -s 60 -c 2 python bench.py --steps 1 --warmup 3 --no-cpu-baseline
+#         --no-e2e --no-batching --no-triage --no-graphs
+#   l1_pipe_frac: the L1 / shared-memory data pipe's share of its peak
+#     (l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed) in
+#     the full-section capture of one launch.
+GEN_CAPTURE = {"source_sha16": None, "traffic_bytes": None, "l1_pipe_frac": None}
+
+
+def kernel_source_sha16() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("adg_kernels.cu", "adg_internal.h"):
+        with open(os.path.join(ROOT, "paper_2007_03678_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def gen_capture_figures() -> tuple:
+    """(traffic bytes, L1-pipe fraction) of the generation kernel if the
+    captures were taken on the current kernel source, else (None, None)."""
+    if GEN_CAPTURE["source_sha16"] != kernel_source_sha16():
+        return None, None
+    return GEN_CAPTURE["traffic_bytes"], GEN_CAPTURE["l1_pipe_frac"]
 
 
 def run_mlp_inference(ctx, rows=1_000_000, reps=10):
@@ -604,9 +624,10 @@ def main():
     flops_per_gen = gen_flops_per_step / gens
     achieved = flops_per_gen / (gen_ms / 1e3) / 1e12
     peak, peak_src = fp32_peak_tflops()
+    traffic, l1_frac = gen_capture_figures()
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": GEN_TRAFFIC_BYTES, "traffic_unit": "bytes per generation of all runs (dram read + write)",
-                "l1_shared_pipe_frac_ncu": GEN_L1_PIPE_FRAC,
+                "traffic": traffic, "traffic_unit": "bytes per generation of all runs (dram read + write)",
+                "l1_shared_pipe_frac_ncu": l1_frac, "kernel_source_sha16": kernel_source_sha16(),
                 "kernel": "k_dock_generation<2,ADADELTA>",
                 "generation_ms": gen_ms, "flops_per_generation": flops_per_gen,
                 "gen_share_of_step": st["gen_kernel_ms"] / total_ms if world == 1 else None,

@@ -392,8 +392,18 @@ int adg_mlp_forward(adg_ctx* ctx, const adg_mlp* mlp, const float* x, int B, flo
 enum { ADG_MLP_MMA_SYNC = 0, ADG_MLP_TCGEN05 = 1 };
 int adg_mlp_set_engine(adg_mlp* mlp, int engine);
 /* Synchronous: ADG_ETIMEOUT if a bounded wait of the tcgen05 forward pass
- * expired since the last check (those rows were written as NaN), else ADG_OK. */
+ * expired since the last check (the rows of the tiles concerned were written
+ * as NaN), else ADG_OK. */
 int adg_mlp_check(adg_ctx* ctx, adg_mlp* mlp);
+/* Bound, in nanoseconds, of each wait of the tcgen05 forward pass on its
+ * tensor-core MMAs (default 1e9; 0 = test the barrier once and give up if the
+ * MMAs are not done).  A wait that gives up sets the status adg_mlp_check
+ * reports and the rows of that tile become NaN; the kernel still waits for
+ * every MMA it issued, under its own 1 s bound, before it frees its tensor
+ * memory, so the context stays usable.  The paper has no counterpart: this
+ * is the failure-detection path of the device waits, exposed so that it can
+ * be exercised.  ns < 0: ADG_EINVAL. */
+int adg_mlp_set_wait_ns(adg_mlp* mlp, long long ns);
 /* Gradient of the batch loss (1/B) sum_b (y_b - (t_b - mu_y)/sigma_y)^2 with
  * respect to the packed parameters into grad [nparams], and the loss into
  * *loss (nullable); idx (nullable) selects rows of x and t.  No update. */
@@ -424,12 +434,16 @@ int adg_mlp_fit(adg_ctx* ctx, adg_mlp* mlp, const float* x, const float* t, int 
  *   rec, lig: built beforehand with adg_receptor_create / adg_ligand_create
  *   out:      host, caller-allocated [p->nrun], filled as by adg_dock
  *   stream:   cudaStream_t to run on (NULL: the legacy default stream)
- * The first call on a device looks up the array's device address on that
- * device (cudaGetSymbolAddress); make that first call before any stream
- * capture.  Every call reuses the same array and clears what must start at
- * zero; calls whose GPU work overlaps (on different streams or host threads)
- * race on it and must be serialized by the caller.  Returns when the results
- * are in `out`. */
+ * The first call on a device looks up the array's device address there
+ * (cudaGetSymbolAddress).  CUDA loads the code module holding the array
+ * lazily, so the GPU reserves the array's memory at that lookup, not when the
+ * library is loaded: make the first call on each device at set-up, before
+ * the application's own allocator takes the device's memory, and before any
+ * stream capture.  The call runs on rec's device and restores the caller's
+ * current device before it returns.  Every call reuses the same array and
+ * clears what must start at zero; calls whose GPU work overlaps (on
+ * different streams or host threads) race on it and must be serialized by
+ * the caller.  Returns when the results are in `out`. */
 #define ADG_NOALLOC_SCRATCH_BYTES (4u << 20)
 #define ADG_NOALLOC_MAX_RUNS 128
 #define ADG_NOALLOC_MAX_INDIVIDUALS 16384

@@ -119,7 +119,8 @@ EXPORTS = ("adg_strerror", "adg_search_params_default", "adg_ctx_create", "adg_c
            "adg_dock_traced", "adg_ligand_descriptors", "adg_mlp_nparams", "adg_mlp_create", "adg_mlp_destroy",
            "adg_mlp_get_params", "adg_mlp_set_params", "adg_mlp_set_norm", "adg_mlp_forward", "adg_mlp_grad",
            "adg_mlp_train_step", "adg_mlp_fit", "adg_ligand_set_stream_id",
-           "adg_ctx_set_graphs", "adg_mlp_set_engine", "adg_mlp_check", "adg_probe_peaks", "adg_ligand_schedule", "adg_score_multi")
+           "adg_ctx_set_graphs", "adg_mlp_set_engine", "adg_mlp_check", "adg_probe_peaks", "adg_ligand_schedule", "adg_score_multi",
+           "adg_mlp_set_wait_ns")
 
 _lib = None
 
@@ -178,6 +179,7 @@ def load(path: str | None = None):
         L.adg_mlp_fit.argtypes = [_vp, _vp, _vp, _vp, _i, _i, _i, C.c_float, C.c_uint64, _fp]
         L.adg_mlp_set_engine.argtypes = [_vp, _i]
         L.adg_mlp_check.argtypes = [_vp, _vp]
+        L.adg_mlp_set_wait_ns.argtypes = [_vp, C.c_longlong]
         L.adg_ctx_tuned.argtypes = [_vp, C.POINTER(adg_tuned_shape), _i, C.POINTER(C.c_int)]
         L.adg_probe_peaks.argtypes = [_vp, C.POINTER(adg_peaks)]
         L.adg_ligand_schedule.argtypes = [C.POINTER(adg_forcefield), C.POINTER(adg_ligand_desc),
@@ -624,6 +626,10 @@ class MLP:
     def set_engine(self, engine: int):
         """MLP_TCGEN05 (default) or MLP_MMA_SYNC for forward()."""
         _check(load().adg_mlp_set_engine(self.handle, int(engine)), "adg_mlp_set_engine")
+
+    def set_wait_ns(self, ns: int):
+        """Bound of each wait of the tcgen05 forward on its MMAs (ns; 0: no waiting)."""
+        _check(load().adg_mlp_set_wait_ns(self.handle, int(ns)), "adg_mlp_set_wait_ns")
 
     def check(self):
         """Raise if a bounded wait of the tcgen05 forward expired (synchronous)."""

@@ -432,7 +432,18 @@ __device__ __forceinline__ float atom_inter(const MapsDev& M, float k_out, int t
     int ix = min(max((int)floorf(ux), 0), M.nx - 2);
     int iy = min(max((int)floorf(uy), 0), M.ny - 2);
     int iz = min(max((int)floorf(uz), 0), M.nz - 2);
-    const float fx = ux - ix, fy = uy - iy, fz = uz - iz;
+    // The fractions are taken from the cell's own corner node, not from u:
+    // u carries the rounding of (x - o) / h at the scale of the whole box (a
+    // few 1e-6 of a cell), which near a capped map value (slopes up to
+    // 1e5 kcal/mol per 0.375 A) is worth 1e-2 kcal/mol.  x - node is exact
+    // (the node o + i h is representable and within a cell of x), and one
+    // residual step rounds (x - node) / h to within an ulp of f.
+    const float dx = xc - fmaf((float)ix, M.h, M.ox), dy = yc - fmaf((float)iy, M.h, M.oy),
+                dz = zc - fmaf((float)iz, M.h, M.oz);
+    float fx = dx * M.inv_h, fy = dy * M.inv_h, fz = dz * M.inv_h;
+    fx = fmaf(fmaf(-fx, M.h, dx), M.inv_h, fx);
+    fy = fmaf(fmaf(-fy, M.h, dy), M.inv_h, fy);
+    fz = fmaf(fmaf(-fz, M.h, dz), M.inv_h, fz);
     const int nxy = M.nx * M.ny;
     const float4* p = M.packed + 2 * ((long)t * nxy * M.nz + (iz * nxy + iy * M.nx + ix));
     const float aq = fabsf(q);

@@ -439,7 +439,8 @@ constexpr size_t kTcW1 = (size_t)H * KIN * 2;
 constexpr size_t kTcX = (size_t)TC_ROWS * KIN * 2;
 constexpr size_t kTcH1 = (size_t)TC_ROWS * H * 2;
 constexpr size_t kTcSmem = kTcW2 + kTcW1 + kTcX + kTcH1 + 3 * H * sizeof(float) + 32;
-constexpr long long kTcWaitNs = 1000000000ll;  // bounded wait on the MMA completion barrier (1 s)
+constexpr long long kTcWaitNs = 1000000000ll;   // default bound of a wait on an MMA completion barrier (1 s)
+constexpr long long kTcDrainNs = 1000000000ll;  // bound of the final wait for every issued MMA (1 s)
 
 __device__ __forceinline__ uint64_t tc_smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
@@ -468,9 +469,20 @@ __device__ __forceinline__ long long global_ns()
     return t;
 }
 
-// Wait for the given phase parity of an mbarrier, for at most kTcWaitNs.
-__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
+// Wait for the given phase parity of an mbarrier, for at most wait_ns
+// nanoseconds; wait_ns <= 0 tests the barrier once without waiting.
+__device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity, long long wait_ns)
 {
+    if (wait_ns <= 0) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+        return done != 0;
+    }
     const long long t0 = global_ns();
     for (;;) {
         uint32_t done;
@@ -481,7 +493,7 @@ __device__ __forceinline__ bool tc_wait(uint32_t mbar, uint32_t parity)
             : "r"(mbar), "r"(parity)
             : "memory");
         if (done) return true;
-        if (global_ns() - t0 > kTcWaitNs) return false;
+        if (global_ns() - t0 > wait_ns) return false;
     }
 }
 
@@ -499,7 +511,10 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
 
 constexpr int TC_THREADS = 512;  // 16 warps: warps w, w + 4, w + 8, w + 12 share TMEM lanes 32 (w % 4).., a column quarter each
 
-__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* status)
+// status: bit 0 set when a wait on an MMA completion barrier gave up after
+// wait_ns (the tile's rows are then written as NaN), bit 1 when the final
+// wait for every issued MMA gave up.
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* status, long long wait_ns)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* W2s = smem;
@@ -509,13 +524,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
     float* b1s = reinterpret_cast<float*>(H1s + kTcH1);
     float* b2s = b1s + H;
     float* w3s = b2s + H;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(w3s + H);  // [0]: layer-1 MMAs, [1]: layer-2 MMAs
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(w3s + H);  // [0]: layer-1 MMAs, [1]: layer-2 MMAs, [2]: drain
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
     __shared__ float part[3][TC_ROWS];  // the other column quarters' shares of each row's output
     const int tid = threadIdx.x, warp = tid >> 5;
     const int r = (warp & 3) * 32 + (tid & 31);  // this thread's row = its TMEM lane
     const int half = warp >> 2;                  // column quarter: columns [64 half, 64 half + 64)
-    const uint32_t s_base = smem_u32(smem), s_mbar1 = smem_u32(mbar), s_mbar2 = smem_u32(mbar + 1);
+    const uint32_t s_base = smem_u32(smem), s_mbar1 = smem_u32(mbar), s_mbar2 = smem_u32(mbar + 1),
+                   s_mbar3 = smem_u32(mbar + 2);
     if (warp == 0) {  // 512 TMEM columns: layer 1 in 0-255, layer 2 in 256-511
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot))
                      : "memory");
@@ -524,6 +540,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_mbar1) : "memory");
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_mbar2) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(s_mbar3) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (int i = tid; i < H * H / 8; i += TC_THREADS) {
@@ -544,7 +561,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
     // kind::f16 instruction descriptor: FP32 accumulate, BF16 A and B, both K-major, N = 256, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) |
                            ((uint32_t)(TC_ROWS >> 4) << 24);
-    // x_hat of one tile (BF16, canonical layout, K = 32); each column half writes two of the four chunks
+    // x_hat of one tile (BF16, canonical layout, K = 32); each column quarter writes one of the four 8-column chunks
     auto stage_x = [&](int tile) {
         const int row = tile * TC_ROWS + r;
 #pragma unroll
@@ -588,7 +605,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
     // overlap this tile's layer-2 MMAs and epilogue
     for (; tile < ntiles; tile += gridDim.x) {
         const int row = tile * TC_ROWS + r;
-        ok = tc_wait(s_mbar1, ph1) && ok;
+        ok = tc_wait(s_mbar1, ph1, wait_ns) && ok;
         ph1 ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         for (int c = half * 2; c < half * 2 + 2; ++c) {  // h1 = relu(x_hat W1^T + b1) -> BF16, row-major K = 256
@@ -627,7 +644,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (tid == 0 && next < ntiles) issue_layer1(tbase);
-        ok = tc_wait(s_mbar2, ph2) && ok;
+        ok = tc_wait(s_mbar2, ph2, wait_ns) && ok;
         ph2 ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         float acc = 0.f;
@@ -638,16 +655,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
             for (int e = 0; e < 32; ++e) acc += fmaxf(v[e] + b2s[c * 32 + e], 0.f) * w3s[c * 32 + e];
         }
         if (half > 0) part[half - 1][r] = acc;
-        // h1 and columns 256-511 are rewritten for the next tile only after every thread is done with them
+        // h1 and columns 256-511 are rewritten for the next tile only after every thread is done with them;
+        // a wait that gave up in any thread of the CTA marks the tile's rows (any row may have read
+        // an accumulator too early)
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
+        const bool all_ok = __syncthreads_and(ok) != 0;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         if (half == 0 && row < A.B)
-            A.y[row] = ok ? (acc + part[0][r] + part[1][r] + part[2][r] + A.theta[A.o.b3]) * A.nm.sigma_y + A.nm.mu_y
-                          : __int_as_float(0x7fc00000);
+            A.y[row] = all_ok ? (acc + part[0][r] + part[1][r] + part[2][r] + A.theta[A.o.b3]) * A.nm.sigma_y + A.nm.mu_y
+                              : __int_as_float(0x7fc00000);
     }
     if (!ok) atomicOr(status, 1);
+    // every MMA this CTA issued has completed before its tensor memory is released: one more commit
+    // tracks all of them, waited for under the normal bound whatever wait_ns was
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (tid == 0)
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(s_mbar3)
+                     : "memory");
+    if (!tc_wait(s_mbar3, 0u, kTcDrainNs) && tid == 0) atomicOr(status, 2);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
 }
@@ -684,6 +711,7 @@ struct adg_mlp {
     size_t eloss_n = 0;
     int engine = ADG_MLP_TCGEN05;  // forward pass engine
     int* status = nullptr;   // device: bit 0 set when a bounded wait of the tcgen05 forward expired
+    long long wait_ns = kTcWaitNs;  // bound of each wait of the tcgen05 forward on its MMAs
 };
 
 namespace {
@@ -925,7 +953,8 @@ int adg_mlp_forward(adg_ctx* ctx, const adg_mlp* M, const float* x, int B, float
         int nsm = 148;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M->device);
         const int ntiles = (B + TC_ROWS - 1) / TC_ROWS;
-        k_mlp_fwd_tc<<<(unsigned)std::min(ntiles, nsm), TC_THREADS, kTcSmem, ctx->stream>>>(a, M->status);
+        k_mlp_fwd_tc<<<(unsigned)std::min(ntiles, nsm), TC_THREADS, kTcSmem, ctx->stream>>>(a, M->status,
+                                                                                            M->wait_ns);
     } else {
         MCK(cudaFuncSetAttribute(k_mlp_act<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kActSmem));
         k_mlp_act<false><<<act_blocks(B, M->device), 256, kActSmem, ctx->stream>>>(a);
@@ -939,6 +968,13 @@ int adg_mlp_set_engine(adg_mlp* M, int engine)
 {
     if (!M || (engine != ADG_MLP_MMA_SYNC && engine != ADG_MLP_TCGEN05)) return ADG_EINVAL;
     M->engine = engine;
+    return ADG_OK;
+}
+
+int adg_mlp_set_wait_ns(adg_mlp* M, long long ns)
+{
+    if (!M || ns < 0) return ADG_EINVAL;
+    M->wait_ns = ns;
     return ADG_OK;
 }
 

@@ -51,6 +51,15 @@ cudaError_t scratch_address(int device, void** out)
     return cudaSuccess;
 }
 
+// Puts the caller's current device back when the call returns.
+struct DeviceRestore {
+    int prev = -1;
+    ~DeviceRestore()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
 }  // namespace
 
 extern "C" int adg_dock_noalloc(const adg_receptor* rec, const adg_ligand* lig, const adg_search_params* p,
@@ -64,6 +73,8 @@ extern "C" int adg_dock_noalloc(const adg_receptor* rec, const adg_ligand* lig, 
     if (p->nrun > ADG_NOALLOC_MAX_RUNS || (long)p->nrun * p->pop_size > ADG_NOALLOC_MAX_INDIVIDUALS)
         return ADG_ETOOBIG;
     cudaStream_t st = (cudaStream_t)stream;
+    DeviceRestore restore;
+    if (cudaGetDevice(&restore.prev) != cudaSuccess) return ADG_ECUDA;
     if (cudaSetDevice(rec->device) != cudaSuccess) return ADG_ECUDA;
     void* base = nullptr;
     if (scratch_address(rec->device, &base) != cudaSuccess) return ADG_ECUDA;

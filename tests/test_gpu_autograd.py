@@ -9,7 +9,7 @@ import pytest
 import oracle as O
 from paper_2007_03678_gb300 import synth as S
 
-from gpu_common import energy_tol, grad_ok, inside_box, near_face, problem
+from gpu_common import energy_tol, grad_ok, inside_box, near_face, problem, strict_at_gpu_coords
 
 pytestmark = pytest.mark.gpu
 
@@ -64,7 +64,7 @@ def test_autograd_matches_oracle_and_finite_differences(ctx, ff):
     R = adg.Receptor(ctx, grid, maps32)
     ligs = _ligands()
     assert len(ligs) * NPOSE == 65536
-    checked = fd_checked = 0
+    checked = fd_checked = strict_checked = 0
     for li, lig in enumerate(ligs):
         genes = S.random_genes(lig, NPOSE, grid, 40000 + li, spread=0.3)
         genes[::2, 3:7] *= 1.5  # non-unit quaternions: the q gradient carries the 1/|q| factor
@@ -84,6 +84,12 @@ def test_autograd_matches_oracle_and_finite_differences(ctx, ff):
         tol = energy_tol(ref_e, forces)
         bad = np.abs(e - ref_e) > tol
         assert not bad.any(), (li, [(int(p), e[p], ref_e[p], tol[p]) for p in np.nonzero(bad)[0][:4]])
+        # the scoring alone, at the CUDA path's own posed coordinates: every
+        # non-clashing pose at the plain 1e-3 + 1e-5|E|
+        clean_g, ok_g, ref_g = strict_at_gpu_coords(ctx, adg, ff, grid, maps64, Lg, L, g32, e)
+        bad = clean_g & ~ok_g
+        assert not bad.any(), (li, [(int(p), e[p], ref_g[p]) for p in np.nonzero(bad)[0][:4]])
+        strict_checked += int(clean_g.sum())
         smooth = inside_box(grid, xyz) & (ref_e < 1e3) & ~near_face(grid, xyz)
         ok = grad_ok(gg, ref_gg)[smooth]
         assert ok.all(), f"ligand {li}: {(~ok).any(axis=1).sum()} poses with a gradient component off"
@@ -104,6 +110,7 @@ def test_autograd_matches_oracle_and_finite_differences(ctx, ff):
             assert (np.abs(gg[p] - fd)[use] <= 1e-3 * scale).all(), (li, p, gg[p], fd)
             fd_checked += int(use.sum())
     assert checked > 0.1 * NLIG * NPOSE
+    assert strict_checked > 0.1 * NLIG * NPOSE
     assert fd_checked > 3000
 
 

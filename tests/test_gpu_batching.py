@@ -114,3 +114,44 @@ def test_run_halves_equal_one_group(ctx, ff):
     both = adg.dock(ctx, R, [L, other], p, best_trace=6)[0]
     for key in ("best_energy", "genes", "xyz", "evals", "generations", "best_trace"):
         assert np.array_equal(alone[key], both[key]), key
+
+
+def test_batched_dock_sampled_against_oracle(ctx, ff):
+    """One adg_dock call over 16 ligands that span the four atoms-per-lane
+    widths (up to 32, 64, 96 and 128 atoms): for every ligand and run, the
+    reported pose is the oracle's pose of the reported genotype, the reported
+    best energy is the oracle's energy of that genotype (genotype-level
+    tolerance), and the oracle's energy of the reported FP32 pose meets the
+    plain 1e-3 + 1e-5|E| wherever the pose does not clash; every run spends
+    its budget and its best-energy trace never rises."""
+    import oracle as O
+    from paper_2007_03678_gb300 import adg
+    from gpu_common import E_ABS, E_REL, energy_tol, inside_box
+    grid, rec, _, maps64, maps32 = problem("paper")
+    R = adg.Receptor(ctx, grid, maps32)
+    ligs = S.make_batch(10, seed=31) + [S.make_ligand(36, 5, 3131), S.make_ligand(60, 9, 3232),
+                                        S.make_ligand(78, 11, 3333), S.make_ligand(92, 13, 3434),
+                                        S.make_ligand(104, 14, 3535), S.make_ligand(116, 15, 3636, n_hd=12)]
+    widths = {(l.natoms + 31) // 32 for l in ligs}
+    assert widths == {1, 2, 3, 4}, widths
+    L = [adg.Ligand(ctx, ff, l) for l in ligs]
+    nev = 30_000
+    p = adg.search_params(nrun=4, pop_size=60, nev=nev, ls_method=adg.LS_ADADELTA, ls_max_iters=30, seed=19)
+    res = adg.dock(ctx, R, L, p, best_trace=8)
+    clean_checked = 0
+    for i, (lig, r) in enumerate(zip(ligs, res)):
+        assert (r["evals"] >= nev).all() and (r["evals"] < nev + 60 * 31).all(), i
+        assert np.all(np.diff(r["best_trace"], axis=1) <= 0), i
+        OL = O.Ligand(lig)
+        genes = r["genes"].astype(np.float64)
+        assert np.abs(r["xyz"] - O.pose(OL, genes)).max() < 1e-3, i
+        e_ref = O.score(ff, grid, maps64, OL, genes)[0]
+        forces = O.atom_gradients(ff, grid, maps64, OL, genes)
+        e = r["best_energy"].astype(np.float64)
+        assert (np.abs(e - e_ref) <= energy_tol(e_ref, forces)).all(), (i, e, e_ref)
+        xyz = r["xyz"].astype(np.float64)
+        e_xyz = O.score_xyz(ff, grid, maps64, OL, xyz)[0]
+        clean = inside_box(grid, xyz) & (e_xyz < 1e3)
+        assert (np.abs(e - e_xyz) <= E_ABS + E_REL * np.abs(e_xyz))[clean].all(), (i, e, e_xyz)
+        clean_checked += int(clean.sum())
+    assert clean_checked >= 0.75 * 4 * len(ligs)

@@ -190,3 +190,79 @@ def test_tcgen05_forward_matches_oracle_and_mma_sync(ctx, B):
     assert err.max() <= 3e-2, err.max()
     assert (err <= 1e-4).mean() >= 0.95, np.sort(err)[-10:]
     assert np.abs(y_tc - y_mma).max() <= 3e-2 * 3.0
+
+
+@pytest.mark.parametrize("B", [128 * (2 * 152 + 1) + 37, 65536, 1_000_000])
+def test_tcgen05_forward_persistent_tiles(ctx, B):
+    """The tcgen05 forward at sizes where every persistent CTA runs two or
+    more 128-row tiles (grid = min(tiles, SMs)), with a ragged last tile:
+    the second and later trips of the tile loop (mbarrier parities, the next
+    tile's x_hat staged during layer 2, tensor-memory columns reused) against
+    the oracle on a seeded sample of rows (all rows below 70,000) and against
+    the warp-level MMA forward on every row.  1,000,000 rows of 26 inputs is
+    the launch the benchmark times."""
+    import torch
+    from paper_2007_03678_gb300 import adg
+    nin = 26
+    rng = np.random.default_rng(70 + B % 1000)
+    x = rng.normal(0, 2, (B, nin)).astype(np.float32)
+    mu = rng.normal(0, 0.5, nin).astype(np.float32)
+    sig = rng.uniform(1, 3, nin).astype(np.float32)
+    net = adg.MLP(ctx, nin, seed=12)
+    th = net.get_params().astype(np.float64)
+    o = M.unpack(th, nin)
+    r2 = np.random.default_rng(13)
+    th = M.pack(o[0], r2.normal(0, 0.1, 256), o[2], r2.normal(0, 0.1, 256), o[4], 0.25).astype(np.float32)
+    net.set_params(th)
+    net.set_norm(mu, sig, -9.0, 3.0)
+    xd = torch.from_numpy(x).cuda()
+    net.set_engine(adg.MLP_TCGEN05)
+    y_tc = net.forward(xd).cpu().numpy().astype(np.float64)
+    net.check()
+    net.set_engine(adg.MLP_MMA_SYNC)
+    y_mma = net.forward(xd).cpu().numpy().astype(np.float64)
+    assert np.isfinite(y_tc).all()
+    assert np.abs(y_tc - y_mma).max() <= 3e-2 * 3.0
+    assert (np.abs(y_tc - y_mma) <= 1e-4 * 3.0).mean() >= 0.95
+    rows = np.arange(B) if B < 70_000 else np.sort(rng.choice(B, 20_000, replace=False))
+    rows = np.union1d(rows, np.arange(B - 37, B))  # the ragged last tile
+    yr, _ = M.forward(th.astype(np.float64), x[rows].astype(np.float64), nin, mu.astype(np.float64),
+                      sig.astype(np.float64), True)
+    err = np.abs((y_tc[rows] + 9.0) / 3.0 - yr)
+    assert err.max() <= 3e-2, err.max()
+    assert (err <= 1e-4).mean() >= 0.95, np.sort(err)[-10:]
+    net.close()
+
+
+def test_tcgen05_bounded_wait_reports_and_recovers(ctx):
+    """The failure path of the tcgen05 forward's bounded waits, made to run
+    out: with the bound at 0 a wait on the MMA completion barrier gives up at
+    its first unsuccessful test; adg_mlp_check then reports ADG_ETIMEOUT, the
+    rows of the tiles concerned are NaN and every other row is still the
+    oracle's.  The kernel drained its MMAs before freeing tensor memory, so
+    with the default bound restored the same network on the same context
+    computes every row again and the status is clear."""
+    import torch
+    from paper_2007_03678_gb300 import adg
+    for B in (100, 300):
+        x, t, mu, sig = _problem(80 + B, B)
+        net, th = _net(ctx, 14, mu, sig)
+        xd = torch.from_numpy(x).cuda()
+        net.set_engine(adg.MLP_TCGEN05)
+        yr, _ = M.forward(th, x.astype(np.float64), NIN, mu.astype(np.float64), sig.astype(np.float64), True)
+        net.set_wait_ns(0)
+        y0 = net.forward(xd).cpu().numpy().astype(np.float64)
+        with pytest.raises(adg.AdgError) as ei:
+            net.check()
+        assert ei.value.code == -6  # ADG_ETIMEOUT
+        nan = np.isnan(y0)
+        assert nan.any()
+        assert np.abs((y0[~nan] + 9.0) / 3.0 - yr[~nan]).max(initial=0.0) <= 3e-2
+        net.set_wait_ns(10 ** 9)
+        y1 = net.forward(xd).cpu().numpy().astype(np.float64)
+        net.check()
+        assert np.isfinite(y1).all()
+        assert np.abs((y1 + 9.0) / 3.0 - yr).max() <= 3e-2
+        with pytest.raises(adg.AdgError):
+            net.set_wait_ns(-1)
+        net.close()

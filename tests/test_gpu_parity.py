@@ -7,7 +7,7 @@ import oracle as O
 from paper_2007_03678_gb300 import synth as S
 
 from gpu_common import (E_ABS, E_REL, energy_ok, energy_tol, grad_ok, inside_box, near_face, problem,
-                        well_conditioned)
+                        strict_at_gpu_coords, well_conditioned)
 
 pytestmark = pytest.mark.gpu
 
@@ -139,6 +139,15 @@ def test_score_energy_and_gradients_random_poses(ctx, A, ff, name):
     assert (np.abs(e - ref_e) <= tol).all(), _parity_report(e, ref_e, np.ones(len(e), bool), tol)
     well = clean & well_conditioned(forces)
     assert energy_ok(e, ref_e)[well].all(), _parity_report(e, ref_e, well)
+    # the scoring alone: every non-clashing pose at the plain tolerance against
+    # the oracle's energy of the CUDA path's own posed coordinates
+    Lg, OL = A.Ligand(ctx, ff, lig), O.Ligand(lig)
+    clean_g, ok_g, ref_g = strict_at_gpu_coords(ctx, A, ff, grid, maps64, Lg, OL, genes, e)
+    assert clean_g.sum() > 50
+    assert ok_g[clean_g].all(), _parity_report(e, ref_g, clean_g)
+    only_widened = clean & ~energy_ok(e, ref_e)
+    print(f"{name}: {clean_g.sum()} non-clashing poses meet 1e-3 + 1e-5|E| at the GPU coordinates; "
+          f"{only_widened.sum()} of {clean.sum()} need the coordinate-rounding term at the genotype level")
     smooth = clean & ~near_face(grid, xyz)
     assert smooth.sum() > 0.9 * clean.sum() and smooth.sum() > 50
     ok = grad_ok(gg, ref_gg)[smooth]
@@ -200,6 +209,8 @@ def test_score_edge_cases(ctx, A, ff):
         assert energy_ok(e, ref_e)[well].all(), _parity_report(e, ref_e, well)
         tol = energy_tol(ref_e, forces)
         assert (np.abs(e - ref_e) <= tol).all(), _parity_report(e, ref_e, np.ones(len(e), bool), tol)
+        clean_g, ok_g, ref_g = strict_at_gpu_coords(ctx, A, ff, grid, maps64, Lg, L, genes, e)
+        assert ok_g[clean_g].all(), _parity_report(e, ref_g, clean_g)
         smooth = well & ~near_face(grid, xyz)
         assert grad_ok(gt.cpu().numpy(), ref_gt)[smooth].all()
 

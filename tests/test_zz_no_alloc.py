@@ -8,7 +8,7 @@ every other test has run; it passes alone in a fresh process too."""
 import numpy as np
 import pytest
 
-from gpu_common import E_ABS, E_REL, problem
+from gpu_common import problem
 
 pytestmark = pytest.mark.gpu
 
@@ -34,14 +34,13 @@ def test_noalloc_dock_matches_dock_on_two_calls(ctx, ff, ls_method):
     p = adg.search_params(nrun=12, pop_size=150, nev=20000, ls_method=ls_method, ls_max_iters=40, seed=77)
     ref = adg.dock(ctx, R, L, p)[0]
     ctx.sync()
+    # both paths run the same kernels on the same run-keyed random streams, so
+    # the results agree bit for bit; a slip in carving or clearing the shared
+    # array that moved a single individual would show here
     for call in range(2):
         got = adg.dock_noalloc(R, L, p)
-        e, e0 = got["best_energy"].astype(np.float64), ref["best_energy"].astype(np.float64)
-        assert (np.abs(e - e0) <= E_ABS + E_REL * np.abs(e0)).all(), (call, e, e0)
-        assert np.abs(got["genes"] - ref["genes"]).max() < 2e-3, call
-        assert np.abs(got["xyz"] - ref["xyz"]).max() < 2e-3, call
-        assert np.array_equal(got["evals"], ref["evals"]), call
-        assert np.array_equal(got["generations"], ref["generations"]), call
+        for key in ("best_energy", "genes", "xyz", "evals", "generations"):
+            assert np.array_equal(got[key], ref[key]), (call, key)
 
 
 def test_noalloc_rejects_oversized_requests(ctx, ff):
