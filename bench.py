@@ -266,7 +266,7 @@ def workload_config(nrun=None, nev=None) -> dict:
             "parallelism": "replicas"}
 
 
-TRIAGE_TRAIN, TRIAGE_STREAM = 1200, 2000
+TRIAGE_TRAIN, TRIAGE_STREAM = 4000, 20000
 # Figures of the generation kernel taken from ncu captures, valid only for
 # the kernel source they were taken on: the bench reports them only while
 # the SHA-256 (first 16 hex digits) of adg_kernels.cu + adg_internal.h
@@ -451,19 +451,15 @@ def run_differentiation(ctx, R, ff, reps=5):
             "per_ligand_calls": {"poses_per_s": 65536 / (ms_each / 1e3), "ms": ms_each}}
 
 
-def run_batching_full(nlig=4096, nrun=20, nev=1_000_000):
+def run_batching_full(ctx, R, ff, nlig=4096, nrun=20, nev=1_000_000):
     """The full batching configuration in one adg_dock call (the ligand
     groups' graphs on concurrent streams), after one short call that tunes
-    every shape bucket; prints one JSON line."""
+    every shape bucket.  Host-timed around the one call."""
     import torch
-    from paper_2007_03678_gb300 import adg, build, synth as S
-    build.build()
+    from paper_2007_03678_gb300 import adg, synth as S
+    t0 = time.perf_counter()
     bl = S.make_batch(nlig, seed=7, workers=0)
-    ff = S.forcefield()
-    grid, rec, _ = S.workload_inputs(S.PAPER)
-    ctx = adg.Context(0)
-    maps = adg.maps_build(ctx, ff, grid, rec)
-    R = adg.Receptor(ctx, grid, maps)
+    t_gen = time.perf_counter() - t0
     t0 = time.perf_counter()
     L = [adg.Ligand(ctx, ff, l) for l in bl]
     t_setup = time.perf_counter() - t0
@@ -476,28 +472,33 @@ def run_batching_full(nlig=4096, nrun=20, nev=1_000_000):
     res = adg.dock(ctx, R, L, p)
     dt = time.perf_counter() - t0
     ev = int(sum(r["evals"].sum() for r in res))
-    print(json.dumps({"workload": f"batching: {nlig} seeded ligands, {nrun} runs x 150 x {nev:,} evals, ADADELTA, "
-                                  "one adg_dock call", "seconds": dt, "ligands_per_s": nlig / dt,
-                      "evals_per_s": ev / dt, "evals": ev, "groups": ctx.stats()["dock_groups"],
-                      "ligand_setup_s": t_setup,
-                      "atoms": [min(l.natoms for l in bl), max(l.natoms for l in bl)],
-                      "torsions": [min(len(l.tors) for l in bl), max(len(l.tors) for l in bl)]}), flush=True)
+    out = {"workload": f"batching: {nlig} seeded ligands, {nrun} runs x 150 x {nev:,} evals, ADADELTA, "
+                       "one adg_dock call", "seconds": dt, "ligands_per_s": nlig / dt,
+           "evals_per_s": ev / dt, "evals": ev, "groups": ctx.stats()["dock_groups"],
+           "ligand_setup_s": t_setup, "ligand_generation_s": t_gen,
+           "atoms": [min(l.natoms for l in bl), max(l.natoms for l in bl)],
+           "torsions": [min(len(l.tors) for l in bl), max(len(l.tors) for l in bl)]}
     for lg in L:
         lg.close()
-    R.close()
-    ctx.close()
+    return out
 
 
 def run_triage(ctx, R, ff):
     """Learned triage against the plain path on a seeded stream: the network
     is trained on full dockings of a training set, then the stream is docked
     both ways (plain: full search of every ligand; triaged: early search of
-    every ligand, full search of the survivors).  Host-timed end to end."""
+    every ligand, full search of the survivors).  Host-timed end to end.
+    Recall of the plain path's top 1 % is reported with its 95 % Wilson
+    interval, beside the same survival fraction chosen by the early energy
+    alone (no network) and at other survival fractions."""
     import numpy as np
     from paper_2007_03678_gb300 import adg, synth as S, triage as T
     cfg = T.TriageConfig()
-    LT = [adg.Ligand(ctx, ff, l) for l in S.make_batch(TRIAGE_TRAIN, seed=101, workers=0)]
-    LS = [adg.Ligand(ctx, ff, l) for l in S.make_batch(TRIAGE_STREAM, seed=202, workers=0)]
+    t0 = time.perf_counter()
+    lt, ls = S.make_batch(TRIAGE_TRAIN, seed=101, workers=0), S.make_batch(TRIAGE_STREAM, seed=202, workers=0)
+    t_gen = time.perf_counter() - t0
+    LT = [adg.Ligand(ctx, ff, l) for l in lt]
+    LS = [adg.Ligand(ctx, ff, l) for l in ls]
     T.assign_stream_ids(LT, 1_000_000)
     T.assign_stream_ids(LS, 2_000_000)
     y_tr, x_tr, ev_tr, t_tr = T.dock_full(ctx, R, LT, cfg)
@@ -506,9 +507,17 @@ def run_triage(ctx, R, ff):
     tri.fit(x_tr, y_tr)
     t_fit = time.perf_counter() - t0
     T.dock_early(ctx, R, LS[:8], cfg)  # warm-up of the early geometry
-    y_st, _, ev_plain, t_plain = T.dock_full(ctx, R, LS, cfg)
+    y_st, x_st, ev_plain, t_plain = T.dock_full(ctx, R, LS, cfg)
     out = T.screen(ctx, R, LS, tri)
     keep = out["keep"]
+    hits, ntop = T.recall_counts(y_st, keep, cfg.top_frac)
+    keep_early = T.early_rule_survivors(x_st, cfg)
+    hits_e, _ = T.recall_counts(y_st, keep_early, cfg.top_frac)
+    pred = tri.predict(x_st)
+    curve = {}
+    for frac in (0.05, 0.10, 0.20):
+        kn, ke = T.keep_best(pred, frac), T.keep_best(x_st[:, adg.NDESC + cfg.early_gen - 1], frac)
+        curve[str(frac)] = {"network": T.recall(y_st, kn, cfg.top_frac), "early_energy": T.recall(y_st, ke, cfg.top_frac)}
     for l in LT + LS:
         l.close()
     return {"train_ligands": TRIAGE_TRAIN, "stream_ligands": TRIAGE_STREAM,
@@ -516,13 +525,19 @@ def run_triage(ctx, R, ff):
                        "local_search": "adadelta", "ls_max_iters": cfg.ls_max_iters},
             "network": f"{cfg.nin}-256-256-1 ReLU, BF16 weights / FP32 accumulate, ensemble of {tri.folds}",
             "ligands_per_s_plain": TRIAGE_STREAM / t_plain, "ligands_per_s_triaged": TRIAGE_STREAM / out["seconds"],
-            "speedup": t_plain / out["seconds"], "recall_top1pct": T.recall(y_st, keep, cfg.top_frac),
+            "speedup": t_plain / out["seconds"], "recall_top1pct": hits / ntop, "top1pct_ligands": ntop,
+            "recall_top1pct_ci95_wilson": list(T.wilson_interval(hits, ntop)),
+            "recall_top1pct_early_energy_rule": hits_e / ntop,
+            "recall_top1pct_early_energy_rule_ci95_wilson": list(T.wilson_interval(hits_e, ntop)),
+            "recall_by_survivor_fraction": curve,
             "survivors": float(keep.mean()), "evals_ratio": out["evals"] / ev_plain,
             "survivors_match_plain": bool(np.array_equal(out["energy"][keep], y_st[keep])),
-            "seconds": {"train_docking": t_tr, "fit": t_fit, "plain": t_plain, "triaged": out["seconds"],
-                        "early": out["seconds_early"], "full_survivors": out["seconds_full"]},
-            "sample": "seeded stand-in for the 10^6-ligand stream: 1,200 training and 2,000 stream ligands "
-                      "(heavy atoms 10-60, torsions 0-15)"}
+            "seconds": {"ligand_generation": t_gen, "train_docking": t_tr, "fit": t_fit, "plain": t_plain,
+                        "triaged": out["seconds"], "early": out["seconds_early"], "full_survivors": out["seconds_full"]},
+            "sample": f"seeded stand-in for the 10^6-ligand stream: {TRIAGE_TRAIN:,} training and {TRIAGE_STREAM:,} "
+                      f"stream ligands (heavy atoms 10-60, torsions 0-15); search {cfg.nrun} runs x {cfg.pop} x "
+                      f"{cfg.max_gen} generations of ADADELTA ({cfg.ls_max_iters} iterations), early search "
+                      f"= the first {cfg.early_gen} generations"}
 
 
 def main():
@@ -539,13 +554,10 @@ def main():
                     help="host-driven generation loop (kernel profilers cannot see kernels in conditional graphs)")
     ap.add_argument("--nrun", type=int, default=None, help="override the run count (small profiling cases)")
     ap.add_argument("--nev", type=int, default=None, help="override the evaluation budget (small profiling cases)")
-    ap.add_argument("--batching-full", action="store_true",
-                    help="instead of the bench line: the full batching configuration once (4,096 seeded ligands of "
-                         "10-60 heavy atoms and 0-15 torsions, 20 runs x 150 x 1,000,000 evals, ADADELTA; ~5 min)")
+    ap.add_argument("--no-batching-full", action="store_true",
+                    help="skip the full batching configuration (4,096 seeded ligands of 10-60 heavy atoms and 0-15 "
+                         "torsions, 20 runs x 150 x 1,000,000 evals, ADADELTA, one adg_dock call; ~5 min)")
     args = ap.parse_args()
-    if args.batching_full:
-        run_batching_full()
-        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -720,10 +732,12 @@ def main():
     if not args.no_triage:
         triage = run_triage(ctx, R, ff)
         mlp = run_mlp_inference(ctx)
-    plain = differentiation = None
+    plain = differentiation = batching_full = None
     if not args.no_batching:
         plain = run_plain_config(ctx, ff)
         differentiation = run_differentiation(ctx, R, ff)
+    if not args.no_batching_full:
+        batching_full = run_batching_full(ctx, R, ff)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -746,6 +760,7 @@ def main():
                 "config": workload_config(args.nrun, args.nev), "ligands_per_s": ligands_per_s,
                 "best_energy_median": float(np.median(results["best_energy"])),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk.summary(), "batching": batching,
+                "batching_full": batching_full,
                 "triage": triage, "mlp_inference": mlp, "plain": plain, "differentiation": differentiation,
                 "gpu_launches": st["kernel_launches"]}
         print(json.dumps(line), flush=True)

@@ -198,3 +198,33 @@ def recall(true_energy: np.ndarray, keep: np.ndarray, top_frac: float) -> float:
     k = max(1, int(round(top_frac * len(true_energy))))
     top = np.argsort(true_energy, kind="stable")[:k]
     return float(keep[top].mean())
+
+
+def recall_counts(true_energy: np.ndarray, keep: np.ndarray, top_frac: float) -> tuple:
+    """(survivors among the plain path's top `top_frac`, their number)."""
+    k = max(1, int(round(top_frac * len(true_energy))))
+    top = np.argsort(true_energy, kind="stable")[:k]
+    return int(keep[top].sum()), k
+
+
+def wilson_interval(hits: int, n: int, z: float = 1.959963984540054) -> tuple:
+    """Wilson score interval of a binomial proportion hits / n (95 % for the
+    default z): the proportions p whose normal-approximation test
+    |hits/n - p| <= z sqrt(p (1 - p) / n) does not reject, i.e. the roots of
+    a quadratic in p."""
+    if n <= 0:
+        return (0.0, 1.0)
+    ph = hits / n
+    den = 1.0 + z * z / n
+    mid = (ph + z * z / (2 * n)) / den
+    half = z * np.sqrt(ph * (1.0 - ph) / n + z * z / (4.0 * n * n)) / den
+    # at 0 or n hits one root is exactly 0 or 1 (kept exact, not rounded)
+    return (0.0 if hits == 0 else max(0.0, mid - half), 1.0 if hits == n else min(1.0, mid + half))
+
+
+def early_rule_survivors(feats: np.ndarray, cfg: TriageConfig) -> np.ndarray:
+    """The same survival fraction chosen without the network: the ligands
+    whose best early energy (over runs, after the early generations; the
+    feature column of the last early generation) is lowest."""
+    col = adg.NDESC + cfg.early_gen - 1
+    return keep_best(np.asarray(feats, np.float64)[:, col], cfg.keep_frac)

@@ -50,3 +50,41 @@ def test_config_defaults():
     assert cfg.nin == 16 + 2 * cfg.early_gen <= 32  # fits the network's input width
     p = cfg.params(cfg.early_gen)
     assert p.max_gen == cfg.early_gen and p.nrun == cfg.nrun and p.ls_method == cfg.ls_method
+
+
+def test_wilson_interval_and_recall_counts():
+    """The Wilson score interval: its end points are the proportions at which
+    the normal-approximation test is exactly at z (checked by substitution),
+    it contains the sample proportion, narrows as 1/sqrt(n), and for 20 of 20
+    hits has the closed form lower end n / (n + z^2)."""
+    z = 1.959963984540054
+    for hits, n in ((20, 20), (190, 200), (0, 50), (7, 9)):
+        lo, hi = T.wilson_interval(hits, n)
+        ph = hits / n
+        assert lo <= ph <= hi
+        for p in (lo, hi):
+            if 0.0 < p < 1.0:
+                assert abs(abs(ph - p) - z * np.sqrt(p * (1 - p) / n)) < 1e-12
+    assert np.isclose(T.wilson_interval(20, 20)[0], 20 / (20 + z * z))
+    w1 = np.diff(T.wilson_interval(90, 100))[0]
+    w2 = np.diff(T.wilson_interval(9000, 10000))[0]
+    assert 8 < w1 / w2 < 12
+    true_e = np.arange(1000, dtype=float)
+    keep = np.zeros(1000, bool)
+    keep[[0, 1, 2, 5, 30]] = True
+    assert T.recall_counts(true_e, keep, 0.01) == (4, 10)
+
+
+def test_early_rule_keeps_the_lowest_early_energies():
+    from paper_2007_03678_gb300 import build
+    build.build()
+    cfg = T.TriageConfig()
+    rng = np.random.default_rng(3)
+    n = 200
+    desc = rng.normal(size=(n, 16))
+    tr = -np.sort(rng.uniform(0, 10, size=(n, cfg.nrun, cfg.early_gen)), axis=2)
+    x = T.features(desc, tr, cfg.early_gen)
+    keep = T.early_rule_survivors(x, cfg)
+    best_early = tr[:, :, cfg.early_gen - 1].min(axis=1)
+    assert keep.sum() == int(np.ceil(cfg.keep_frac * n))
+    assert best_early[keep].max() <= best_early[~keep].min()
