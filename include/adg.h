@@ -385,22 +385,27 @@ int adg_mlp_set_params(adg_ctx* ctx, adg_mlp* mlp, const float* in);
 int adg_mlp_set_norm(adg_mlp* mlp, const float* mu, const float* sigma, float mu_y, float sigma_y);
 /* y[b] = prediction for x[b] (x: [B][nin], y: [B]). */
 int adg_mlp_forward(adg_ctx* ctx, const adg_mlp* mlp, const float* x, int B, float* y);
-/* Engine of adg_mlp_forward: ADG_MLP_TCGEN05 (default) -- persistent CTAs over 128-row tiles,
- * tcgen05.mma with FP32 accumulators in tensor memory; ADG_MLP_MMA_SYNC --
- * warp-level m16n8k16 MMAs, as the training kernels use.  Same numerics
- * (BF16 operands and stored h1, FP32 accumulation and h2). */
+/* Engine of adg_mlp_forward, adg_mlp_grad, adg_mlp_train_step and
+ * adg_mlp_fit: ADG_MLP_TCGEN05 (default) -- persistent CTAs over 128-row
+ * tiles, tcgen05.mma with FP32 accumulators in tensor memory (training: the
+ * forward with dh2, dh1 = dh2 W2 with W2^T staged, and the weight gradients
+ * with the batch as the K dimension); ADG_MLP_MMA_SYNC -- warp-level
+ * m16n8k16 MMAs over 32-row tiles.  Same numerics (BF16 operands and stored
+ * x_hat, h1, dh2, dh1; FP32 accumulation, h2 and biases); each engine's
+ * training is bit-reproducible (every sum has a fixed order). */
 enum { ADG_MLP_MMA_SYNC = 0, ADG_MLP_TCGEN05 = 1 };
 int adg_mlp_set_engine(adg_mlp* mlp, int engine);
-/* Synchronous: ADG_ETIMEOUT if a bounded wait of the tcgen05 forward pass
- * expired since the last check (the rows of the tiles concerned were written
- * as NaN), else ADG_OK. */
+/* Synchronous: ADG_ETIMEOUT if a bounded wait of a tcgen05 kernel expired
+ * since the last check (forward: the rows of the tiles concerned were written
+ * as NaN; training: those tiles added nothing to the gradient), else ADG_OK. */
 int adg_mlp_check(adg_ctx* ctx, adg_mlp* mlp);
-/* Bound, in nanoseconds, of each wait of the tcgen05 forward pass on its
- * tensor-core MMAs (default 1e9; 0 = test the barrier once and give up if the
- * MMAs are not done).  A wait that gives up sets the status adg_mlp_check
- * reports and the rows of that tile become NaN; the kernel still waits for
- * every MMA it issued, under its own 1 s bound, before it frees its tensor
- * memory, so the context stays usable.  The paper has no counterpart: this
+/* Bound, in nanoseconds, of each wait of the tcgen05 kernels (forward and
+ * training) on their tensor-core MMAs (default 1e9; 0 = test the barrier once
+ * and give up if the MMAs are not done).  A wait that gives up sets the
+ * status adg_mlp_check reports (forward: the rows of that tile become NaN;
+ * training: the tile adds nothing); every kernel still waits for each MMA it
+ * issued, under its own 1 s bound, before it frees its tensor memory, so the
+ * context stays usable.  The paper has no counterpart: this
  * is the failure-detection path of the device waits, exposed so that it can
  * be exercised.  ns < 0: ADG_EINVAL. */
 int adg_mlp_set_wait_ns(adg_mlp* mlp, long long ns);

@@ -1,8 +1,8 @@
 // adg_mlp.cu -- the triage network of the screening pipeline: a three-layer
 // perceptron nin -> 256 -> 256 -> 1 with ReLU, BF16 weights and FP32
-// accumulation on the tensor cores (warp-level mma m16n8k16, BF16 inputs,
-// FP32 accumulators), trained on the GPU by these kernels (forward, backward,
-// Adam).  The paper has no learned part; the network predicts a ligand's
+// accumulation on the tensor cores (two engines: tcgen05 MMAs with tensor
+// memory accumulators, and warp-level mma m16n8k16), trained on the GPU by
+// these kernels (forward, backward, Adam).  The paper has no learned part; the network predicts a ligand's
 // final best docking energy from its descriptors and the first generations
 // of its best-energy trace, so that ligands predicted hopeless can skip the
 // full search.
@@ -679,6 +679,486 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase) : "memory");
 }
 
+// ------------------------------------------------------------------ tcgen05 training
+// The training contractions on the 5th-generation tensor cores, in three
+// kernels over 128-row tiles, with the numerics of the warp-level engine
+// (x_hat, h1, dh2 and dh1 stored BF16 as operands, FP32 accumulation):
+//   k_mlp_train_fwd_tc   x_hat W1^T, h1 W2^T (tensor memory), then per row the
+//                        output, residual and dh2 = dy w3 [h2 > 0]; per-tile
+//                        column sums of dh2 (b2), dy h2 (w3), dy (b3), res^2
+//   k_mlp_train_bwd_tc   dh1 = (dh2 W2) [h1 > 0] with W2^T staged; per-tile
+//                        column sums of dh1 (b1)
+//   k_mlp_wgrad_tc       dW2 = dh2^T h1 and dW1 = dh1^T x_hat, the batch as the
+//                        K dimension in chunks of 64 rows (transposed into the
+//                        canonical K-major layout while staging); one CTA sums
+//                        the per-tile partials in tile order.
+// Every sum has a fixed order, so training stays bit-reproducible.  Waits on
+// the MMA barriers are bounded as in the forward kernel (status bit 0 when
+// one gives up; the tile's values are then zero), and every CTA waits for
+// all its MMAs before freeing tensor memory (bit 1 if that wait gives up).
+struct TrainArgs {
+    const float* theta;
+    const bf16* w1;      // [H][KIN]
+    const bf16* w2;      // [H][H]
+    const bf16* w3;      // [H]
+    Offs o;
+    int nin;
+    Norm nm;
+    const float* x;      // [*][nin]
+    const float* t;      // [*] raw targets
+    const int* idx;      // rows of x / t, or NULL
+    int B, Bpad;         // rows, rows padded to whole 128-row tiles
+    float inv_B;
+    bf16* xh;            // [Bpad][KIN]
+    bf16* h1;            // [Bpad][H]
+    bf16* dh2;           // [Bpad][H]
+    bf16* dh1;           // [Bpad][H]
+    float* part;         // [Bpad / 128][kPart]
+    float* grad;
+    float* loss;         // += sum of squared residuals * loss_scale
+    float loss_scale;
+};
+
+// Sum over the warp's 32 lanes of each of 32 per-lane values: afterwards lane
+// l holds the sum of v[l] (fixed order: a butterfly that halves the list each
+// round, the upper half going to the lanes with the round's bit set).
+__device__ __forceinline__ float warp_transpose_sum(float (&v)[32], int lane)
+{
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool up = (lane & s) != 0;
+#pragma unroll
+        for (int i = 0; i < s; ++i) {
+            const float send = up ? v[i] : v[i + s];
+            const float keep = up ? v[i + s] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
+}
+
+// Element (r, k) of an R x K BF16 operand in the canonical K-major layout
+// without swizzle (8-row x 16-byte core matrices), as a byte offset.
+__device__ __forceinline__ uint32_t kmajor_off(int r, int k, int K)
+{
+    return (uint32_t)((((r >> 3) * (K >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
+}
+
+__device__ __forceinline__ void tc_alloc(uint32_t* slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void mbar_init(uint32_t mbar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_sync()
+{
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// Every MMA the CTA issued is complete (a last commit by the issuing thread,
+// waited for under the normal bound) before the tensor memory is freed.
+__device__ __forceinline__ void tc_drain_dealloc(uint32_t mbar_drain, uint32_t tbase, uint32_t ncols, int* status,
+                                                 int warp, int tid)
+{
+    tc_sync();
+    if (tid == 0) tc_commit(mbar_drain);
+    if (!tc_wait(mbar_drain, 0u, kTcDrainNs) && tid == 0) atomicOr(status, 2);
+    tc_sync();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tbase), "r"(ncols) : "memory");
+}
+
+constexpr size_t kTfSmem = kTcW2 + kTcW1 + kTcX + kTcH1 + (3 * H + 2 * TC_ROWS) * sizeof(float) + 64;
+static_assert(kTcX == 8 * H * sizeof(float), "the column sums of a tile fill the x_hat operand buffer exactly");
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_train_fwd_tc(TrainArgs A, int* status, long long wait_ns)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* W2s = smem;
+    unsigned char* W1s = W2s + kTcW2;
+    unsigned char* Xs = W1s + kTcW1;
+    unsigned char* H1s = Xs + kTcX;
+    float* b1s = reinterpret_cast<float*>(H1s + kTcH1);
+    float* b2s = b1s + H;
+    float* w3s = b2s + H;
+    float* dys = w3s + H;           // [128] dy of each row
+    float* rqs = dys + TC_ROWS;     // [128] squared residual of each row
+    // per 32-row block the column sums of dh2 and of dy h2, [4][H] each, in the
+    // x_hat buffer (free from the end of layer 1 until the next tile is staged)
+    float* colb = reinterpret_cast<float*>(Xs);
+    float* colw = colb + 4 * H;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(rqs + TC_ROWS);  // layer 1, layer 2, drain
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 3);
+    __shared__ float part[3][TC_ROWS];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = (warp & 3) * 32 + lane, quarter = warp >> 2, rb = warp & 3;
+    const uint32_t s_base = smem_u32(smem), s_m1 = smem_u32(mbar), s_m2 = smem_u32(mbar + 1),
+                   s_m3 = smem_u32(mbar + 2);
+    if (warp == 0) tc_alloc(tslot, 512);
+    if (tid == 0) {
+        mbar_init(s_m1);
+        mbar_init(s_m2);
+        mbar_init(s_m3);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = tid; i < H * H / 8; i += TC_THREADS) {
+        const int n = i >> 5, k8 = i & 31;
+        *reinterpret_cast<uint4*>(W2s + (((n >> 3) * (H / 8) + k8) << 7) + ((n & 7) << 4)) =
+            *reinterpret_cast<const uint4*>(A.w2 + n * H + k8 * 8);
+    }
+    for (int i = tid; i < H * KIN / 8; i += TC_THREADS) {
+        const int n = i >> 2, k8 = i & 3;
+        *reinterpret_cast<uint4*>(W1s + (((n >> 3) * (KIN / 8) + k8) << 7) + ((n & 7) << 4)) =
+            *reinterpret_cast<const uint4*>(A.w1 + n * KIN + k8 * 8);
+    }
+    for (int j = tid; j < H; j += TC_THREADS) {
+        b1s[j] = A.theta[A.o.b1 + j];
+        b2s[j] = A.theta[A.o.b2 + j];
+        w3s[j] = __bfloat162float(A.w3[j]);
+    }
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) |
+                           ((uint32_t)(TC_ROWS >> 4) << 24);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    const uint32_t tbase = *tslot;
+    const uint32_t trow = tbase + ((uint32_t)(rb * 32) << 16);
+    const float b3 = A.theta[A.o.b3];
+    bool ok = true;
+    uint32_t ph1 = 0, ph2 = 0;
+    const int ntiles = A.Bpad / TC_ROWS;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int row = tile * TC_ROWS + r;
+        // x_hat (BF16): canonical operand in shared memory and row-major copy for the weight gradient
+        {
+            const int k8 = quarter;
+            uint32_t pk[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int k = k8 * 8 + 2 * q;
+                float v0 = 0.f, v1 = 0.f;
+                if (row < A.B) {
+                    const int src = A.idx ? A.idx[row] : row;
+                    if (k < A.nin) v0 = (A.x[(long)src * A.nin + k] - A.nm.mu[k]) / A.nm.sigma[k];
+                    if (k + 1 < A.nin) v1 = (A.x[(long)src * A.nin + k + 1] - A.nm.mu[k + 1]) / A.nm.sigma[k + 1];
+                }
+                pk[q] = pack2(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
+            }
+            const uint4 u = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            *reinterpret_cast<uint4*>(Xs + kmajor_off(r, k8 * 8, KIN)) = u;
+            *reinterpret_cast<uint4*>(A.xh + (long)row * KIN + k8 * 8) = u;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_sync();
+        if (tid == 0) {
+            for (int s = 0; s < KIN / 16; ++s)
+                tc_mma(tbase, tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1) + s * 256, 128, (KIN / 8) * 128),
+                       tc_smem_desc(s_base + (uint32_t)kTcW2 + s * 256, 128, (KIN / 8) * 128), idesc, s > 0);
+            tc_commit(s_m1);
+        }
+        ok = tc_wait(s_m1, ph1, wait_ns) && ok;
+        ph1 ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // h1 = relu(x_hat W1^T + b1) -> BF16: operand of layer 2 and row-major copy
+        for (int c = quarter * 2; c < quarter * 2 + 2; ++c) {
+            float v[32];
+            tc_ld32(trow + c * 32, v);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int j = c * 32 + q * 8 + 2 * e;
+                    pk[e] = pack2(__float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e] + b1s[j], 0.f)),
+                                  __float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e + 1] + b1s[j + 1], 0.f)));
+                }
+                const uint4 u = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+                *reinterpret_cast<uint4*>(H1s + kmajor_off(r, c * 32 + q * 8, H)) = u;
+                *reinterpret_cast<uint4*>(A.h1 + (long)row * H + c * 32 + q * 8) = u;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_sync();
+        if (tid == 0) {
+            for (int s = 0; s < H / 16; ++s)
+                tc_mma(tbase + H,
+                       tc_smem_desc(s_base + (uint32_t)(kTcW2 + kTcW1 + kTcX) + s * 256, 128, (H / 8) * 128),
+                       tc_smem_desc(s_base + s * 256, 128, (H / 8) * 128), idesc, s > 0);
+            tc_commit(s_m2);
+        }
+        ok = tc_wait(s_m2, ph2, wait_ns) && ok;
+        ph2 ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // output y = w3 . relu(h1 W2^T + b2) + b3 (column quarters summed through shared memory)
+        float acc = 0.f;
+        for (int c = quarter * 2; c < quarter * 2 + 2; ++c) {
+            float v[32];
+            tc_ld32(trow + H + c * 32, v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) acc += fmaxf(v[e] + b2s[c * 32 + e], 0.f) * w3s[c * 32 + e];
+        }
+        if (quarter > 0) part[quarter - 1][r] = acc;
+        // a wait that gave up anywhere in the CTA voids the tile (its rows add nothing)
+        const bool all_ok = __syncthreads_and(ok) != 0;
+        if (quarter == 0) {
+            float res = 0.f;
+            if (row < A.B && all_ok) {
+                const int src = A.idx ? A.idx[row] : row;
+                const float y = acc + part[0][r] + part[1][r] + part[2][r] + b3;
+                res = y - (A.t[src] - A.nm.mu_y) / A.nm.sigma_y;
+            }
+            dys[r] = 2.f * res * A.inv_B;
+            rqs[r] = res * res;
+        }
+        __syncthreads();
+        // dh2 = dy w3 [h2 > 0] (BF16, row-major), and per 32-row block the column
+        // sums of dh2 (b2 gradient) and of dy h2 (w3 gradient)
+        const float dy = dys[r];
+        for (int c = quarter * 2; c < quarter * 2 + 2; ++c) {
+            float v[32], gb[32], gw[32];
+            tc_ld32(trow + H + c * 32, v);
+#pragma unroll
+            for (int e = 0; e < 32; ++e) {
+                const int j = c * 32 + e;
+                const float h = fmaxf(v[e] + b2s[j], 0.f);
+                gb[e] = h > 0.f ? dy * w3s[j] : 0.f;
+                gw[e] = dy * h;
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e)
+                    pk[e] = pack2(__float2bfloat16_rn(gb[q * 8 + 2 * e]), __float2bfloat16_rn(gb[q * 8 + 2 * e + 1]));
+                *reinterpret_cast<uint4*>(A.dh2 + (long)row * H + c * 32 + q * 8) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+            colb[rb * H + c * 32 + lane] = warp_transpose_sum(gb, lane);
+            colw[rb * H + c * 32 + lane] = warp_transpose_sum(gw, lane);
+        }
+        __syncthreads();
+        // this tile's partial sums, row blocks in order
+        float* pt = A.part + (long)tile * kPart;
+        for (int j = tid; j < H; j += TC_THREADS) {
+            pt[H + j] = ((colb[j] + colb[H + j]) + colb[2 * H + j]) + colb[3 * H + j];
+            pt[2 * H + j] = ((colw[j] + colw[H + j]) + colw[2 * H + j]) + colw[3 * H + j];
+        }
+        if (tid == 0) {
+            float sd = 0.f, sq = 0.f;
+            for (int q = 0; q < TC_ROWS; ++q) {
+                sd += dys[q];
+                sq += rqs[q];
+            }
+            pt[3 * H] = sd;
+            pt[3 * H + 1] = sq;
+        }
+        // the next tile rewrites dys, rqs, colb, colw and the tensor memory only after every thread is done
+        tc_sync();
+    }
+    if (!ok) atomicOr(status, 1);
+    tc_drain_dealloc(s_m3, tbase, 512, status, warp, tid);
+}
+
+// dh1 = (dh2 W2) [h1 > 0] over 128-row tiles: W2^T staged once (operand B
+// with N = output column i, K = j), the tile's dh2 as operand A; per 32-row
+// block the column sums of dh1 (b1 gradient) into the tile's partials.
+constexpr size_t kTbSmem = kTcW2 + kTcH1 + 4 * H * sizeof(float) + 64;
+
+__global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_train_bwd_tc(TrainArgs A, int* status, long long wait_ns)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* W2t = smem;             // [i][j] canonical K-major (K = j)
+    unsigned char* D2s = W2t + kTcW2;      // [r][j] canonical K-major
+    float* colb = reinterpret_cast<float*>(D2s + kTcH1);  // [4][H]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(colb + 4 * H);  // MMA, drain
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int r = (warp & 3) * 32 + lane, quarter = warp >> 2, rb = warp & 3;
+    const uint32_t s_base = smem_u32(smem), s_m1 = smem_u32(mbar), s_m3 = smem_u32(mbar + 1);
+    if (warp == 0) tc_alloc(tslot, 256);
+    if (tid == 0) {
+        mbar_init(s_m1);
+        mbar_init(s_m3);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // W2^T: element (i, j) = W2[j][i]; each thread gathers 8 consecutive j of one i
+    for (int q = tid; q < H * H / 8; q += TC_THREADS) {
+        const int i = q % H, j8 = q / H;
+        uint32_t pk[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) pk[e] = pack2(A.w2[(j8 * 8 + 2 * e) * H + i], A.w2[(j8 * 8 + 2 * e + 1) * H + i]);
+        *reinterpret_cast<uint4*>(W2t + kmajor_off(i, j8 * 8, H)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    }
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(H >> 3) << 17) |
+                           ((uint32_t)(TC_ROWS >> 4) << 24);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_sync();
+    const uint32_t tbase = *tslot;
+    const uint32_t trow = tbase + ((uint32_t)(rb * 32) << 16);
+    bool ok = true;
+    uint32_t ph1 = 0;
+    const int ntiles = A.Bpad / TC_ROWS;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int row = tile * TC_ROWS + r;
+        for (int k8 = quarter * 8; k8 < quarter * 8 + 8; ++k8)  // this thread's row, a quarter of the 32 chunks
+            *reinterpret_cast<uint4*>(D2s + kmajor_off(r, k8 * 8, H)) =
+                *reinterpret_cast<const uint4*>(A.dh2 + (long)row * H + k8 * 8);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_sync();
+        if (tid == 0) {
+            for (int s = 0; s < H / 16; ++s)
+                tc_mma(tbase, tc_smem_desc(s_base + (uint32_t)kTcW2 + s * 256, 128, (H / 8) * 128),
+                       tc_smem_desc(s_base + s * 256, 128, (H / 8) * 128), idesc, s > 0);
+            tc_commit(s_m1);
+        }
+        ok = tc_wait(s_m1, ph1, wait_ns) && ok;
+        ph1 ^= 1u;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const bool all_ok = __syncthreads_and(ok) != 0;
+        for (int c = quarter * 2; c < quarter * 2 + 2; ++c) {
+            float v[32];
+            tc_ld32(trow + c * 32, v);
+            const uint4* hp = reinterpret_cast<const uint4*>(A.h1 + (long)row * H + c * 32);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const uint4 hu = hp[q];
+                const uint32_t hw[4] = {hu.x, hu.y, hu.z, hu.w};
+                uint32_t pk[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float h0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[e] & 0xffffu)));
+                    const float h1v = __bfloat162float(__ushort_as_bfloat16((unsigned short)(hw[e] >> 16)));
+                    float& a0 = v[q * 8 + 2 * e];
+                    float& a1 = v[q * 8 + 2 * e + 1];
+                    a0 = (all_ok && h0 > 0.f) ? a0 : 0.f;
+                    a1 = (all_ok && h1v > 0.f) ? a1 : 0.f;
+                    pk[e] = pack2(__float2bfloat16_rn(a0), __float2bfloat16_rn(a1));
+                }
+                *reinterpret_cast<uint4*>(A.dh1 + (long)row * H + c * 32 + q * 8) =
+                    make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            }
+            colb[rb * H + c * 32 + lane] = warp_transpose_sum(v, lane);
+        }
+        __syncthreads();
+        float* pt = A.part + (long)tile * kPart;
+        for (int j = tid; j < H; j += TC_THREADS)
+            pt[j] = ((colb[j] + colb[H + j]) + colb[2 * H + j]) + colb[3 * H + j];
+        tc_sync();
+    }
+    if (!ok) atomicOr(status, 1);
+    tc_drain_dealloc(s_m3, tbase, 256, status, warp, tid);
+}
+
+// Weight gradients on the tensor cores: CTA c < 2 computes rows [128 c, 128 c
+// + 128) of dW2 = dh2^T h1 (N = 256), CTA 2 + c the same rows of dW1 = dh1^T
+// x_hat (N = 32); the batch is the K dimension, staged in chunks of 64 rows
+// transposed into the canonical K-major layout.  CTA 4 sums the per-tile
+// partials in tile order.  128 threads: thread r reads tensor-memory lane r.
+constexpr int WG_CHUNK = 64;
+constexpr size_t kWgSmem = (size_t)TC_ROWS * WG_CHUNK * 2 + (size_t)H * WG_CHUNK * 2 + 64;
+
+__global__ void __launch_bounds__(128, 1) k_mlp_wgrad_tc(TrainArgs A, int* status, long long wait_ns)
+{
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (blockIdx.x == 4) {
+        const int ntiles = A.Bpad / TC_ROWS;
+        for (int c = tid; c < kPart; c += blockDim.x) {
+            float sum = 0.f;
+            for (int t = 0; t < ntiles; ++t) sum += A.part[(long)t * kPart + c];
+            if (c < H) A.grad[A.o.b1 + c] = sum;
+            else if (c < 2 * H) A.grad[A.o.b2 + c - H] = sum;
+            else if (c < 3 * H) A.grad[A.o.w3 + c - 2 * H] = sum;
+            else if (c == 3 * H) A.grad[A.o.b3] = sum;
+            else *A.loss += sum * A.loss_scale;
+        }
+        return;
+    }
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* As = smem;                                   // [128 j][64 rows]
+    unsigned char* Bs = As + (size_t)TC_ROWS * WG_CHUNK * 2;     // [N][64 rows]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + (size_t)H * WG_CHUNK * 2);  // MMA, drain
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
+    const bool w1part = blockIdx.x >= 2;
+    const int j0 = (blockIdx.x & 1) * TC_ROWS;
+    const int N = w1part ? KIN : H;
+    const bf16* Asrc = w1part ? A.dh1 : A.dh2;  // [rows][H]
+    const bf16* Bsrc = w1part ? A.xh : A.h1;    // [rows][N]
+    const uint32_t ncols = w1part ? 32u : 256u;
+    const uint32_t s_base = smem_u32(smem), s_m1 = smem_u32(mbar), s_m3 = smem_u32(mbar + 1);
+    if (warp == 0) tc_alloc(tslot, ncols);
+    if (tid == 0) {
+        mbar_init(s_m1);
+        mbar_init(s_m3);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+                           ((uint32_t)(TC_ROWS >> 4) << 24);
+    tc_sync();
+    const uint32_t tbase = *tslot;
+    bool ok = true;
+    uint32_t ph1 = 0;
+    for (int rc = 0; rc < A.Bpad; rc += WG_CHUNK) {
+        // A: element (m, k) = Asrc[rc + k][j0 + m]; B: element (n, k) = Bsrc[rc + k][n].
+        // Each thread gathers 8 consecutive k (rows) of one m or n.
+        for (int q = tid; q < TC_ROWS * WG_CHUNK / 8; q += 128) {
+            const int m = q % TC_ROWS, k8 = q / TC_ROWS;
+            uint32_t pk[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                pk[e] = pack2(Asrc[(long)(rc + k8 * 8 + 2 * e) * H + j0 + m],
+                              Asrc[(long)(rc + k8 * 8 + 2 * e + 1) * H + j0 + m]);
+            *reinterpret_cast<uint4*>(As + kmajor_off(m, k8 * 8, WG_CHUNK)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        for (int q = tid; q < N * WG_CHUNK / 8; q += 128) {
+            const int n = q % N, k8 = q / N;
+            uint32_t pk[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                pk[e] = pack2(Bsrc[(long)(rc + k8 * 8 + 2 * e) * N + n], Bsrc[(long)(rc + k8 * 8 + 2 * e + 1) * N + n]);
+            *reinterpret_cast<uint4*>(Bs + kmajor_off(n, k8 * 8, WG_CHUNK)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        tc_sync();
+        if (tid == 0) {
+            for (int s = 0; s < WG_CHUNK / 16; ++s)
+                tc_mma(tbase, tc_smem_desc(s_base + s * 256, 128, (WG_CHUNK / 8) * 128),
+                       tc_smem_desc(s_base + (uint32_t)(TC_ROWS * WG_CHUNK * 2) + s * 256, 128, (WG_CHUNK / 8) * 128),
+                       idesc, (rc > 0 || s > 0) ? 1 : 0);
+            tc_commit(s_m1);
+        }
+        ok = tc_wait(s_m1, ph1, wait_ns) && ok;  // the chunk's operands are rewritten only after its MMAs
+        ph1 ^= 1u;
+        tc_sync();
+    }
+    const bool all_ok = __syncthreads_and(ok) != 0;
+    // thread r holds row j0 + r of the gradient block in tensor-memory lane r
+    const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
+    const int j = j0 + tid;
+    for (int c = 0; c < N / 32; ++c) {
+        float v[32];
+        tc_ld32(trow + c * 32, v);
+#pragma unroll
+        for (int e = 0; e < 32; ++e) {
+            const int col = c * 32 + e;
+            const float g = all_ok ? v[e] : 0.f;
+            if (w1part) {
+                if (col < A.nin) A.grad[A.o.w1 + j * A.nin + col] = g;
+            } else {
+                A.grad[A.o.w2 + j * H + col] = g;
+            }
+        }
+    }
+    if (!ok) atomicOr(status, 1);
+    tc_drain_dealloc(s_m3, tbase, ncols, status, warp, tid);
+}
+
 uint64_t splitmix64(uint64_t& s)
 {
     uint64_t z = (s += 0x9E3779B97F4A7C15ull);
@@ -758,10 +1238,66 @@ unsigned act_blocks(int B, int device)
     return (unsigned)std::max(1, std::min(ntiles, nsm));
 }
 
+// The same gradient on the tcgen05 engine: forward with dh2, dh1, weight
+// gradients (three launches over 128-row tiles; see k_mlp_train_fwd_tc).
+int backprop_tc(adg_ctx* ctx, adg_mlp* M, cudaStream_t st, const float* x, const float* t, const int* idx, int B,
+                float* loss, float loss_scale)
+{
+    const int Bpad = (B + TC_ROWS - 1) / TC_ROWS * TC_ROWS;
+    const int ntiles = Bpad / TC_ROWS;
+    const size_t act_b = sizeof(bf16) * (size_t)Bpad * (KIN + 3 * H);
+    const size_t need = act_b + sizeof(float) * (size_t)ntiles * kPart;
+    if (need > M->act_bytes) {
+        MCK(cudaStreamSynchronize(st));
+        if (M->act) cudaFree(M->act);
+        M->act = nullptr;
+        M->act_bytes = 0;
+        MCK(cudaMalloc(&M->act, need));
+        M->act_bytes = need;
+    }
+    TrainArgs a{};
+    a.theta = M->theta;
+    a.w1 = M->w1;
+    a.w2 = M->w2;
+    a.w3 = M->w3;
+    a.o = M->o;
+    a.nin = M->nin;
+    a.nm = M->nm;
+    a.x = x;
+    a.t = t;
+    a.idx = idx;
+    a.B = B;
+    a.Bpad = Bpad;
+    a.inv_B = 1.f / (float)B;
+    a.xh = (bf16*)M->act;
+    a.h1 = a.xh + (size_t)Bpad * KIN;
+    a.dh2 = a.h1 + (size_t)Bpad * H;
+    a.dh1 = a.dh2 + (size_t)Bpad * H;
+    a.part = (float*)((char*)M->act + act_b);
+    a.grad = M->grad;
+    a.loss = loss;
+    a.loss_scale = loss_scale;
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M->device);
+    const unsigned grid = (unsigned)std::min(ntiles, nsm);
+    MCK(cudaFuncSetAttribute(k_mlp_train_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTfSmem));
+    MCK(cudaFuncSetAttribute(k_mlp_train_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTbSmem));
+    MCK(cudaFuncSetAttribute(k_mlp_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWgSmem));
+    k_mlp_train_fwd_tc<<<grid, TC_THREADS, kTfSmem, st>>>(a, M->status, M->wait_ns);
+    MCK(cudaGetLastError());
+    k_mlp_train_bwd_tc<<<grid, TC_THREADS, kTbSmem, st>>>(a, M->status, M->wait_ns);
+    MCK(cudaGetLastError());
+    k_mlp_wgrad_tc<<<5, 128, kWgSmem, st>>>(a, M->status, M->wait_ns);
+    MCK(cudaGetLastError());
+    ctx->stats.kernel_launches += 3;
+    return ADG_OK;
+}
+
 // Gradient of the batch loss into M->grad (and the loss, scaled, into *loss).
 int backprop(adg_ctx* ctx, adg_mlp* M, cudaStream_t st, const float* x, const float* t, const int* idx, int B,
              float* loss, float loss_scale)
 {
+    if (M->engine == ADG_MLP_TCGEN05) return backprop_tc(ctx, M, st, x, t, idx, B, loss, loss_scale);
     const int Bpad = (B + TR - 1) / TR * TR;
     const size_t act_b = sizeof(bf16) * (size_t)Bpad * (KIN + 3 * H);
     const size_t need = act_b + sizeof(float) * (size_t)(Bpad / TR) * kPart;

@@ -72,12 +72,19 @@ def test_forward_matches_oracle(ctx, B):
     assert (err <= 1e-4).mean() >= 0.95, np.sort(err)[-10:]
 
 
+@pytest.mark.parametrize("engine", ["tcgen05", "mma_sync"])
 @pytest.mark.parametrize("B", [7, 300, 1000])
-def test_gradient_matches_oracle(ctx, B):
+def test_gradient_matches_oracle(ctx, B, engine):
+    """The gradient of the batch loss against the FP64 oracle, on both engines:
+    tcgen05 (three launches: forward with dh2, dh1 = dh2 W2 with W2^T staged,
+    weight gradients with the batch as K) and warp-level MMAs."""
     import torch
+    from paper_2007_03678_gb300 import adg
     x, t, mu, sig = _problem(20 + B, B)
     net, th = _net(ctx, 4, mu, sig)
+    net.set_engine(adg.MLP_TCGEN05 if engine == "tcgen05" else adg.MLP_MMA_SYNC)
     g, loss = net.grad(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    net.check()
     g = g.cpu().numpy().astype(np.float64)
     lr, gr = M.loss_and_grad(th, x.astype(np.float64), t.astype(np.float64), NIN, mu.astype(np.float64),
                              sig.astype(np.float64), -9.0, 3.0, True)
@@ -266,3 +273,27 @@ def test_tcgen05_bounded_wait_reports_and_recovers(ctx):
         with pytest.raises(adg.AdgError):
             net.set_wait_ns(-1)
         net.close()
+
+
+def test_tcgen05_training_bounded_wait_reports(ctx):
+    """The training kernels' bounded waits made to run out: with the bound at
+    0 the gradient call reports ADG_ETIMEOUT through adg_mlp_check and the
+    network trains normally again once the bound is restored."""
+    import torch
+    from paper_2007_03678_gb300 import adg
+    x, t, mu, sig = _problem(90, 300)
+    net, th = _net(ctx, 15, mu, sig)
+    xd, td = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    net.set_wait_ns(0)
+    net.grad(xd, td)
+    with pytest.raises(adg.AdgError) as ei:
+        net.check()
+    assert ei.value.code == -6  # ADG_ETIMEOUT
+    net.set_wait_ns(10 ** 9)
+    g, loss = net.grad(xd, td)
+    net.check()
+    _, gr = M.loss_and_grad(th, x.astype(np.float64), t.astype(np.float64), NIN, mu.astype(np.float64),
+                            sig.astype(np.float64), -9.0, 3.0, True)
+    g = g.cpu().numpy().astype(np.float64)
+    assert np.abs(g - gr).max() <= 1e-2 * np.abs(gr).max()
+    net.close()
