@@ -280,7 +280,7 @@ TRIAGE_TRAIN, TRIAGE_STREAM = 4000, 20000
 #   l1_pipe_frac: the L1 / shared-memory data pipe's share of its peak
 #     (l1tex__data_pipe_lsu_wavefronts.avg.pct_of_peak_sustained_elapsed) in
 #     the full-section capture of one launch.
-GEN_CAPTURE = {"source_sha16": None, "traffic_bytes": None, "l1_pipe_frac": None}
+GEN_CAPTURE = {"source_sha16": "a7021c6ac90e02a9", "traffic_bytes": 38.52e6, "l1_pipe_frac": 0.692}
 
 
 def kernel_source_sha16() -> str:
@@ -334,6 +334,38 @@ def run_mlp_inference(ctx, rows=1_000_000, reps=10):
         ms = e0.elapsed_time(e1) / reps
         out[name] = {"ms": ms, "tflops": flops / ms / 1e9,
                      "frac_of_bf16_peak": (flops / ms / 1e9 / peak) if peak else None}
+    net.check()
+    net.close()
+    return out
+
+
+def run_mlp_training(ctx, rows=65536, reps=10):
+    """Triage-network gradient (forward, backward, weight gradients) on `rows`
+    random rows for both engines; device-timed, mean of `reps` calls."""
+    import numpy as np
+    import torch
+    from paper_2007_03678_gb300 import adg
+    nin = 26
+    net = adg.MLP(ctx, nin, seed=2)
+    net.set_norm(np.zeros(nin), np.ones(nin), 0.0, 1.0)
+    x = torch.randn(rows, nin, device=f"cuda:{ctx.device}")
+    t = torch.randn(rows, device=f"cuda:{ctx.device}")
+    # forward (two layers, K padded to 32), dh1 = dh2 W2, dW2 and dW1
+    flops = 2.0 * rows * (32 * 256 + 256 * 256) + 2.0 * rows * 256 * 256 + 2.0 * rows * (256 * 256 + 256 * 32)
+    out = {"rows": rows, "flops_per_call": flops}
+    for eng, name in ((adg.MLP_TCGEN05, "tcgen05"), (adg.MLP_MMA_SYNC, "mma_sync")):
+        net.set_engine(eng)
+        for _ in range(3):
+            net.grad(x, t)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            net.grad(x, t)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        out[name] = {"ms": ms, "tflops": flops / ms / 1e9}
     net.check()
     net.close()
     return out
@@ -554,10 +586,20 @@ def main():
                     help="host-driven generation loop (kernel profilers cannot see kernels in conditional graphs)")
     ap.add_argument("--nrun", type=int, default=None, help="override the run count (small profiling cases)")
     ap.add_argument("--nev", type=int, default=None, help="override the evaluation budget (small profiling cases)")
+    ap.add_argument("--mlp-only", action="store_true",
+                    help="instead of the bench line: the triage network's inference and training throughput only "
+                         "(profiling runs)")
     ap.add_argument("--no-batching-full", action="store_true",
                     help="skip the full batching configuration (4,096 seeded ligands of 10-60 heavy atoms and 0-15 "
                          "torsions, 20 runs x 150 x 1,000,000 evals, ADADELTA, one adg_dock call; ~5 min)")
     args = ap.parse_args()
+    if args.mlp_only:
+        from paper_2007_03678_gb300 import adg, build
+        build.build()
+        ctx = adg.Context(0)
+        print(json.dumps({"mlp_inference": run_mlp_inference(ctx), "mlp_training": run_mlp_training(ctx)}), flush=True)
+        ctx.close()
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -732,6 +774,7 @@ def main():
     if not args.no_triage:
         triage = run_triage(ctx, R, ff)
         mlp = run_mlp_inference(ctx)
+        mlp["training"] = run_mlp_training(ctx)
     plain = differentiation = batching_full = None
     if not args.no_batching:
         plain = run_plain_config(ctx, ff)

@@ -1056,18 +1056,43 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_train_bwd_tc(TrainArgs A,
     tc_drain_dealloc(s_m3, tbase, 256, status, warp, tid);
 }
 
-// Weight gradients on the tensor cores: CTA c < 2 computes rows [128 c, 128 c
-// + 128) of dW2 = dh2^T h1 (N = 256), CTA 2 + c the same rows of dW1 = dh1^T
-// x_hat (N = 32); the batch is the K dimension, staged in chunks of 64 rows
-// transposed into the canonical K-major layout.  CTA 4 sums the per-tile
-// partials in tile order.  128 threads: thread r reads tensor-memory lane r.
+// Weight gradients on the tensor cores: dW2 = dh2^T h1 (N = 256) and dW1 =
+// dh1^T x_hat (N = 32), each in two 128-row halves (j), with the batch as
+// the K dimension.  The batch's 64-row chunks are split over `nsplit` CTAs
+// per half (CTA mt * nsplit + sp: half mt & 1 of dW2 for mt < 2, of dW1
+// otherwise; split sp); each CTA accumulates its chunks in tensor memory and
+// writes its partial block (to the gradient itself when nsplit == 1, else to
+// scratch, summed in split order by k_mlp_wgrad_reduce).  Chunks are staged
+// by 8 x 8 blocks: eight 16-byte row loads, transposed in registers, stored
+// as eight 16-byte rows of the canonical K-major layout.  The last CTA sums
+// the per-tile partials (biases, w3, loss) in tile order.  128 threads:
+// thread r reads tensor-memory lane r.
 constexpr int WG_CHUNK = 64;
 constexpr size_t kWgSmem = (size_t)TC_ROWS * WG_CHUNK * 2 + (size_t)H * WG_CHUNK * 2 + 64;
+constexpr size_t kWgBlock = (size_t)H * H + (size_t)H * KIN;  // floats of one split's partial dW2 and dW1
 
-__global__ void __launch_bounds__(128, 1) k_mlp_wgrad_tc(TrainArgs A, int* status, long long wait_ns)
+// 8 x 8 BF16 block transpose: rows in[k] (8 elements each) -> out[e] = column e.
+__device__ __forceinline__ void transpose8x8(const uint4 (&in)[8], uint4 (&out)[8])
+{
+    uint32_t w[8][4];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        w[k][0] = in[k].x; w[k][1] = in[k].y; w[k][2] = in[k].z; w[k][3] = in[k].w;
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        const uint32_t sel = (e & 1) ? 0x7632u : 0x5410u;  // high or low halves of two words
+        const int c = e >> 1;
+        out[e] = make_uint4(__byte_perm(w[0][c], w[1][c], sel), __byte_perm(w[2][c], w[3][c], sel),
+                            __byte_perm(w[4][c], w[5][c], sel), __byte_perm(w[6][c], w[7][c], sel));
+    }
+}
+
+__global__ void __launch_bounds__(128, 1) k_mlp_wgrad_tc(TrainArgs A, float* scratch, int nsplit, int* status,
+                                                         long long wait_ns)
 {
     const int tid = threadIdx.x, warp = tid >> 5;
-    if (blockIdx.x == 4) {
+    if ((int)blockIdx.x == 4 * nsplit) {
         const int ntiles = A.Bpad / TC_ROWS;
         for (int c = tid; c < kPart; c += blockDim.x) {
             float sum = 0.f;
@@ -1085,12 +1110,15 @@ __global__ void __launch_bounds__(128, 1) k_mlp_wgrad_tc(TrainArgs A, int* statu
     unsigned char* Bs = As + (size_t)TC_ROWS * WG_CHUNK * 2;     // [N][64 rows]
     uint64_t* mbar = reinterpret_cast<uint64_t*>(Bs + (size_t)H * WG_CHUNK * 2);  // MMA, drain
     uint32_t* tslot = reinterpret_cast<uint32_t*>(mbar + 2);
-    const bool w1part = blockIdx.x >= 2;
-    const int j0 = (blockIdx.x & 1) * TC_ROWS;
+    const int mt = (int)blockIdx.x / nsplit, sp = (int)blockIdx.x % nsplit;
+    const bool w1part = mt >= 2;
+    const int j0 = (mt & 1) * TC_ROWS;
     const int N = w1part ? KIN : H;
     const bf16* Asrc = w1part ? A.dh1 : A.dh2;  // [rows][H]
     const bf16* Bsrc = w1part ? A.xh : A.h1;    // [rows][N]
     const uint32_t ncols = w1part ? 32u : 256u;
+    const int nchunks = A.Bpad / WG_CHUNK;
+    const int c0 = (int)((long)sp * nchunks / nsplit), c1 = (int)((long)(sp + 1) * nchunks / nsplit);
     const uint32_t s_base = smem_u32(smem), s_m1 = smem_u32(mbar), s_m3 = smem_u32(mbar + 1);
     if (warp == 0) tc_alloc(tslot, ncols);
     if (tid == 0) {
@@ -1104,25 +1132,29 @@ __global__ void __launch_bounds__(128, 1) k_mlp_wgrad_tc(TrainArgs A, int* statu
     const uint32_t tbase = *tslot;
     bool ok = true;
     uint32_t ph1 = 0;
-    for (int rc = 0; rc < A.Bpad; rc += WG_CHUNK) {
-        // A: element (m, k) = Asrc[rc + k][j0 + m]; B: element (n, k) = Bsrc[rc + k][n].
-        // Each thread gathers 8 consecutive k (rows) of one m or n.
-        for (int q = tid; q < TC_ROWS * WG_CHUNK / 8; q += 128) {
-            const int m = q % TC_ROWS, k8 = q / TC_ROWS;
-            uint32_t pk[4];
+    for (int ch = c0; ch < c1; ++ch) {
+        const long rc = (long)ch * WG_CHUNK;
+        // A: element (m, k) = Asrc[rc + k][j0 + m]: 16 x 8 blocks of 8 x 8, one per thread
+        {
+            const int m8 = tid & 15, k8 = tid >> 4;
+            uint4 in[8], out[8];
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                pk[e] = pack2(Asrc[(long)(rc + k8 * 8 + 2 * e) * H + j0 + m],
-                              Asrc[(long)(rc + k8 * 8 + 2 * e + 1) * H + j0 + m]);
-            *reinterpret_cast<uint4*>(As + kmajor_off(m, k8 * 8, WG_CHUNK)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            for (int k = 0; k < 8; ++k)
+                in[k] = *reinterpret_cast<const uint4*>(Asrc + (rc + k8 * 8 + k) * H + j0 + m8 * 8);
+            transpose8x8(in, out);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) *reinterpret_cast<uint4*>(As + kmajor_off(m8 * 8 + e, k8 * 8, WG_CHUNK)) = out[e];
         }
-        for (int q = tid; q < N * WG_CHUNK / 8; q += 128) {
-            const int n = q % N, k8 = q / N;
-            uint32_t pk[4];
+        // B: element (n, k) = Bsrc[rc + k][n]: (N / 8) x 8 blocks
+        for (int q = tid; q < (N / 8) * (WG_CHUNK / 8); q += 128) {
+            const int n8 = q % (N / 8), k8 = q / (N / 8);
+            uint4 in[8], out[8];
 #pragma unroll
-            for (int e = 0; e < 4; ++e)
-                pk[e] = pack2(Bsrc[(long)(rc + k8 * 8 + 2 * e) * N + n], Bsrc[(long)(rc + k8 * 8 + 2 * e + 1) * N + n]);
-            *reinterpret_cast<uint4*>(Bs + kmajor_off(n, k8 * 8, WG_CHUNK)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            for (int k = 0; k < 8; ++k)
+                in[k] = *reinterpret_cast<const uint4*>(Bsrc + (rc + k8 * 8 + k) * N + n8 * 8);
+            transpose8x8(in, out);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) *reinterpret_cast<uint4*>(Bs + kmajor_off(n8 * 8 + e, k8 * 8, WG_CHUNK)) = out[e];
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         tc_sync();
@@ -1130,7 +1162,7 @@ __global__ void __launch_bounds__(128, 1) k_mlp_wgrad_tc(TrainArgs A, int* statu
             for (int s = 0; s < WG_CHUNK / 16; ++s)
                 tc_mma(tbase, tc_smem_desc(s_base + s * 256, 128, (WG_CHUNK / 8) * 128),
                        tc_smem_desc(s_base + (uint32_t)(TC_ROWS * WG_CHUNK * 2) + s * 256, 128, (WG_CHUNK / 8) * 128),
-                       idesc, (rc > 0 || s > 0) ? 1 : 0);
+                       idesc, (ch > c0 || s > 0) ? 1 : 0);
             tc_commit(s_m1);
         }
         ok = tc_wait(s_m1, ph1, wait_ns) && ok;  // the chunk's operands are rewritten only after its MMAs
@@ -1138,17 +1170,22 @@ __global__ void __launch_bounds__(128, 1) k_mlp_wgrad_tc(TrainArgs A, int* statu
         tc_sync();
     }
     const bool all_ok = __syncthreads_and(ok) != 0;
-    // thread r holds row j0 + r of the gradient block in tensor-memory lane r
+    const bool any = c1 > c0;  // a split with no chunk contributes zeros
+    // thread r holds row j0 + r of the block in tensor-memory lane r
     const uint32_t trow = tbase + ((uint32_t)(warp * 32) << 16);
     const int j = j0 + tid;
+    float* dst = nsplit == 1 ? nullptr : scratch + (size_t)sp * kWgBlock;
     for (int c = 0; c < N / 32; ++c) {
         float v[32];
-        tc_ld32(trow + c * 32, v);
+        if (any) tc_ld32(trow + c * 32, v);
 #pragma unroll
         for (int e = 0; e < 32; ++e) {
             const int col = c * 32 + e;
-            const float g = all_ok ? v[e] : 0.f;
-            if (w1part) {
+            const float g = (all_ok && any) ? v[e] : 0.f;
+            if (dst) {
+                if (w1part) dst[(size_t)H * H + j * KIN + col] = g;
+                else dst[j * H + col] = g;
+            } else if (w1part) {
                 if (col < A.nin) A.grad[A.o.w1 + j * A.nin + col] = g;
             } else {
                 A.grad[A.o.w2 + j * H + col] = g;
@@ -1157,6 +1194,21 @@ __global__ void __launch_bounds__(128, 1) k_mlp_wgrad_tc(TrainArgs A, int* statu
     }
     if (!ok) atomicOr(status, 1);
     tc_drain_dealloc(s_m3, tbase, ncols, status, warp, tid);
+}
+
+// The split partials of dW2 and dW1 summed in split order into the gradient.
+__global__ void k_mlp_wgrad_reduce(const float* __restrict__ scratch, int nsplit, Offs o, int nin, float* grad)
+{
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= (int)kWgBlock) return;
+    float sum = 0.f;
+    for (int sp = 0; sp < nsplit; ++sp) sum += scratch[(size_t)sp * kWgBlock + p];
+    if (p < H * H) {
+        grad[o.w2 + p] = sum;
+    } else {
+        const int q = p - H * H, j = q / KIN, col = q % KIN;
+        if (col < nin) grad[o.w1 + j * nin + col] = sum;
+    }
 }
 
 uint64_t splitmix64(uint64_t& s)
@@ -1246,7 +1298,12 @@ int backprop_tc(adg_ctx* ctx, adg_mlp* M, cudaStream_t st, const float* x, const
     const int Bpad = (B + TC_ROWS - 1) / TC_ROWS * TC_ROWS;
     const int ntiles = Bpad / TC_ROWS;
     const size_t act_b = sizeof(bf16) * (size_t)Bpad * (KIN + 3 * H);
-    const size_t need = act_b + sizeof(float) * (size_t)ntiles * kPart;
+    // the weight gradient's K (batch) split: about one CTA per SM over the four row halves
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M->device);
+    const int nsplit = std::max(1, std::min(Bpad / WG_CHUNK, nsm / 4));
+    const size_t part_b = sizeof(float) * (size_t)ntiles * kPart;
+    const size_t need = act_b + part_b + (nsplit > 1 ? sizeof(float) * (size_t)nsplit * kWgBlock : 0);
     if (need > M->act_bytes) {
         MCK(cudaStreamSynchronize(st));
         if (M->act) cudaFree(M->act);
@@ -1255,6 +1312,7 @@ int backprop_tc(adg_ctx* ctx, adg_mlp* M, cudaStream_t st, const float* x, const
         MCK(cudaMalloc(&M->act, need));
         M->act_bytes = need;
     }
+    float* scratch = (float*)((char*)M->act + act_b + part_b);
     TrainArgs a{};
     a.theta = M->theta;
     a.w1 = M->w1;
@@ -1277,8 +1335,6 @@ int backprop_tc(adg_ctx* ctx, adg_mlp* M, cudaStream_t st, const float* x, const
     a.grad = M->grad;
     a.loss = loss;
     a.loss_scale = loss_scale;
-    int nsm = 148;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, M->device);
     const unsigned grid = (unsigned)std::min(ntiles, nsm);
     MCK(cudaFuncSetAttribute(k_mlp_train_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTfSmem));
     MCK(cudaFuncSetAttribute(k_mlp_train_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTbSmem));
@@ -1287,9 +1343,13 @@ int backprop_tc(adg_ctx* ctx, adg_mlp* M, cudaStream_t st, const float* x, const
     MCK(cudaGetLastError());
     k_mlp_train_bwd_tc<<<grid, TC_THREADS, kTbSmem, st>>>(a, M->status, M->wait_ns);
     MCK(cudaGetLastError());
-    k_mlp_wgrad_tc<<<5, 128, kWgSmem, st>>>(a, M->status, M->wait_ns);
+    k_mlp_wgrad_tc<<<4 * nsplit + 1, 128, kWgSmem, st>>>(a, scratch, nsplit, M->status, M->wait_ns);
     MCK(cudaGetLastError());
-    ctx->stats.kernel_launches += 3;
+    if (nsplit > 1) {
+        k_mlp_wgrad_reduce<<<(unsigned)((kWgBlock + 255) / 256), 256, 0, st>>>(scratch, nsplit, M->o, M->nin, M->grad);
+        MCK(cudaGetLastError());
+    }
+    ctx->stats.kernel_launches += nsplit > 1 ? 4 : 3;
     return ADG_OK;
 }
 
