@@ -151,6 +151,54 @@ def test_ga_decisions_bit_exact_first_5_generations(ctx, A, ls_method, iters):
     assert split <= limit_split * total, stats
 
 
+@pytest.mark.parametrize("ls_method,iters", [(0, 0), (2, 20), (1, 30)])
+def test_ga_decisions_replayed_on_the_gpu_population(ctx, A, ls_method, iters):
+    """Every GA decision of every generation, bit for bit: the oracle's
+    offspring builder (pinned) replayed on the CUDA path's own previous
+    population (its FP32 genes and energies, read exactly) must give the GPU's
+    tournament candidates and winners, elites, crossover points and mutation
+    masks, and the Philox local-search pick, with no near-tie exclusions --
+    for the first 8 generations of three runs, LS off, ADADELTA and
+    Solis-Wets (whose trajectories may differ from the oracle's own run; the
+    decisions are still those of the shared stream on the same population).
+    With LS off the children's genes are the oracle's children of the GPU
+    parents within FP32 rounding."""
+    grid, lig, maps64, maps32, ff = ga_problem()
+    pop, ngen, nrun = 150, 8, 3
+    op, ap = _params_pair(A, nrun=nrun, pop_size=pop, ls_method=ls_method, ls_max_iters=iters, max_gen=ngen,
+                          nev=10 ** 9, seed=GA_SEED + 1, lig_id=5)
+    R = A.Receptor(ctx, grid, maps32)
+    Lg = A.Ligand(ctx, ff, lig)
+    res, tr = A.dock(ctx, R, Lg, ap, trace_ngen=ngen)
+    T = lig.ntors
+    thr_ls = int(np.floor(float(ap.ls_rate) * 2 ** 24)) if ap.ls_rate < 1 else 2 ** 24
+    checked = 0
+    for run in range(nrun):
+        Pg = tr["init_genes"][run].astype(np.float64)
+        Pe = tr["init_energies"][run].astype(np.float64)
+        for g in range(ngen):
+            gd = tr["decisions"][run][g]
+            elite = int(np.argmin(Pe))  # ties to the lower index
+            assert gd[0, P1] == gd[0, P2] == elite
+            for i in range(1, pop):
+                child, d = O.make_offspring(op, T, Pg, Pe, run=run, ind=i, gen=g + 1)
+                want = (d["parent1"], d["parent2"], d["xlo"], d["xhi"], d["mut_mask"], d["a1"], d["b1"], d["a2"],
+                        d["b2"])
+                got = tuple(int(v) for v in gd[i, [P1, P2, XLO, XHI, MUT, A1, B1, A2, B2]])
+                assert got == want, (run, g + 1, i, got, want)
+                if ls_method == 0:
+                    assert np.abs(tr["genes"][run][g][i] - child).max() < 2e-6, (run, g + 1, i)
+                checked += 1
+            # the local-search pick: word 0 of the individual's LSPICK block
+            ctr = np.array([[5, (run << 16) | i, g + 1, 4 << 20] for i in range(pop)], np.uint32)
+            w = O.philox(ctr, op.seed & 0xFFFFFFFF, op.seed >> 32)[:, 0]
+            want_ls = ((w >> 8) < thr_ls) if ls_method != 0 else np.zeros(pop, bool)
+            assert np.array_equal(gd[:, LSA].astype(bool), want_ls)
+            Pg = tr["genes"][run][g].astype(np.float64)
+            Pe = tr["energies"][run][g].astype(np.float64)
+    assert checked == nrun * ngen * (pop - 1)
+
+
 def test_adadelta_eval_accounting(ctx, A, ff):
     grid, rec, lig, maps64, maps32 = problem("plain")
     pop, iters, nev = 150, 20, 20000
