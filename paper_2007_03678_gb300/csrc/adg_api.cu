@@ -1106,28 +1106,37 @@ int adg_score_multi(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* con
         if (members.empty()) continue;
         const Geo g = make_geo(apl, nslots, lig_bytes);
         const int nm = (int)members.size();
+        // poses per warp: up to 8, while the launch keeps at least two waves of blocks
+        long width_poses = 0;
+        for (int m = 0; m < nm; ++m) width_poses += npose[members[m]];
+        int nsm = 148;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+        const long waves2 = 2l * nsm * 2 * g.wpb;  // warps in two waves of two blocks per SM
+        const int ppw = (int)std::max(1l, std::min(8l, width_poses / std::max(1l, waves2)));
         std::vector<LigandRef> refs(nm);
-        std::vector<int> blk0(nm), rows(nm), np(nm), blk_lig;
+        std::vector<int> blk0(nm), rows(nm), np(nm), nblk(nm), blk_lig;
         for (int m = 0; m < nm; ++m) {
             const int i = members[m];
             refs[m] = ligs[i]->ref;
             blk0[m] = (int)blk_lig.size();
             rows[m] = (int)row0[i];
             np[m] = npose[i];
-            const int nb = (npose[i] + g.wpb - 1) / g.wpb;
+            const int nb = (npose[i] + g.wpb * ppw - 1) / (g.wpb * ppw);
+            nblk[m] = nb;
             for (int b = 0; b < nb; ++b) blk_lig.push_back(m);
         }
         // the launch's tables in one stream-ordered device buffer, freed after the launch
         const size_t o_ref = 0, o_bl = align_up(sizeof(LigandRef) * nm, 256),
                      o_b0 = align_up(o_bl + sizeof(int) * blk_lig.size(), 256),
                      o_r0 = align_up(o_b0 + sizeof(int) * nm, 256), o_np = align_up(o_r0 + sizeof(int) * nm, 256),
-                     bytes = align_up(o_np + sizeof(int) * nm, 256);
+                     o_nb = align_up(o_np + sizeof(int) * nm, 256), bytes = align_up(o_nb + sizeof(int) * nm, 256);
         std::vector<char> host(bytes, 0);
         memcpy(host.data() + o_ref, refs.data(), sizeof(LigandRef) * nm);
         memcpy(host.data() + o_bl, blk_lig.data(), sizeof(int) * blk_lig.size());
         memcpy(host.data() + o_b0, blk0.data(), sizeof(int) * nm);
         memcpy(host.data() + o_r0, rows.data(), sizeof(int) * nm);
         memcpy(host.data() + o_np, np.data(), sizeof(int) * nm);
+        memcpy(host.data() + o_nb, nblk.data(), sizeof(int) * nm);
         char* dev = nullptr;
         CK(ctx, cudaMallocAsync((void**)&dev, bytes, ctx->stream));
         cudaError_t e = cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
@@ -1138,6 +1147,7 @@ int adg_score_multi(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* con
             J.lig_blk0 = (const int*)(dev + o_b0);
             J.lig_row0 = (const int*)(dev + o_r0);
             J.lig_npose = (const int*)(dev + o_np);
+            J.lig_nblk = (const int*)(dev + o_nb);
             J.stride = ADG_MAX_GENES;
             e = launch_score_multi(ctx->stream, rec->maps, J, (int)blk_lig.size(), g, genes, energy,
                                    grad_kind == ADG_GRAD_NONE ? nullptr : grad, grad_kind);

@@ -193,6 +193,7 @@ struct ScoreMultiDev {
     const int* lig_blk0;    // [nlig] first block of each ligand
     const int* lig_row0;    // [nlig] first row of each ligand
     const int* lig_npose;   // [nlig]
+    const int* lig_nblk;    // [nlig] blocks of each ligand
     int stride;
 };
 cudaError_t launch_score_multi(cudaStream_t st, const MapsDev& m, const ScoreMultiDev& j, int nblocks, const Geo& g,

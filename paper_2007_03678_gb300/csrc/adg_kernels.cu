@@ -793,8 +793,10 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_scor
 }
 
 // Poses of several ligands in one launch: block b serves ligand J.blk_lig[b]
-// (the ligand's blocks are consecutive, from J.lig_blk0); its warps take the
-// ligand's poses in order, rows J.lig_row0 .. of the row-strided arrays.
+// (the ligand's blocks are consecutive, from J.lig_blk0; J.lig_nblk of them);
+// warp w of the ligand's blocks takes its poses w, w + (warps of the
+// ligand), ..., rows J.lig_row0 .. of the row-strided arrays, so the
+// ligand's tables staged once per block serve several poses per warp.
 template <int APL>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_score_multi(MapsDev M, ScoreMultiDev J, int na, int nslots,
                                                                         int lig_bytes, const float* __restrict__ genes,
@@ -804,12 +806,16 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_scor
     const int lane = threadIdx.x & 31;
     const int lig = J.blk_lig[blockIdx.x];
     const LigandRef SL = stage_ligand(J.ligs[lig], lig_bytes);
-    const int local = (blockIdx.x - J.lig_blk0[lig]) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (local >= J.lig_npose[lig]) return;
+    const int wpb = blockDim.x >> 5;
+    const int stride = J.lig_nblk[lig] * wpb;
     const WarpView ws = warp_view(na, nslots, lig_bytes);
-    const long row = (long)J.lig_row0[lig] + local;
-    score_pose<APL>(SL, M, ws, genes + row * J.stride, energy + row, grad ? grad + row * J.stride : nullptr,
-                    grad_kind, lane);
+    for (int local = (blockIdx.x - J.lig_blk0[lig]) * wpb + (threadIdx.x >> 5); local < J.lig_npose[lig];
+         local += stride) {
+        const long row = (long)J.lig_row0[lig] + local;
+        score_pose<APL>(SL, M, ws, genes + row * J.stride, energy + row, grad ? grad + row * J.stride : nullptr,
+                        grad_kind, lane);
+        __syncwarp();
+    }
 }
 
 cudaError_t launch_score(cudaStream_t st, const MapsDev& m, const LigandRef& l, const Geo& g, const float* genes,
