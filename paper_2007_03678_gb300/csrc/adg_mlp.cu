@@ -143,7 +143,7 @@ constexpr int kPart = 3 * H + 2;  // partial sums per tile
 template <bool TRAIN>
 __global__ void __launch_bounds__(256, 1) k_mlp_act(ActArgs A)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
+    extern __shared__ __align__(1024) unsigned char smem[];
     bf16* W2s = reinterpret_cast<bf16*>(smem);
     bf16* W1s = W2s + H * LW2;
     bf16* Xs = W1s + H * LW1;
