@@ -509,6 +509,17 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// relu(a + b[0]) and relu(c + b[1]) rounded to BF16 and packed (first value in
+// the low half): one two-wide add and one conversion that applies the ReLU
+// to the rounded values (the same result as rounding the ReLU's output).
+__device__ __forceinline__ uint32_t bias_relu_bf16x2(float a, float c, const float* b)
+{
+    const float2 h = __fadd2_rn(make_float2(a, c), *reinterpret_cast<const float2*>(b));
+    uint32_t r;
+    asm("cvt.rn.relu.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(h.y), "f"(h.x));
+    return r;
+}
+
 constexpr int TC_THREADS = 512;  // 16 warps: warps w, w + 4, w + 8, w + 12 share TMEM lanes 32 (w % 4).., a column quarter each
 
 // status: bit 0 set when a wait on an MMA completion barrier gave up after
@@ -617,8 +628,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int j = c * 32 + q * 8 + 2 * e;
-                    pk[e] = pack2(__float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e] + b1s[j], 0.f)),
-                                  __float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e + 1] + b1s[j + 1], 0.f)));
+                    pk[e] = bias_relu_bf16x2(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1], b1s + j);
                 }
                 *reinterpret_cast<uint4*>(H1s + (((r >> 3) * (H / 8) + c * 4 + q) << 7) + ((r & 7) << 4)) =
                     make_uint4(pk[0], pk[1], pk[2], pk[3]);
@@ -647,13 +657,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_fwd_tc(ActArgs A, int* st
         ok = tc_wait(s_mbar2, ph2, wait_ns) && ok;
         ph2 ^= 1u;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float acc = 0.f;
+        float2 acc2 = make_float2(0.f, 0.f);
         for (int c = half * 2; c < half * 2 + 2; ++c) {  // w3 . relu(h1 W2^T + b2) over this quarter's columns
             float v[32];
             tc_ld32(trow + H + c * 32, v);
 #pragma unroll
-            for (int e = 0; e < 32; ++e) acc += fmaxf(v[e] + b2s[c * 32 + e], 0.f) * w3s[c * 32 + e];
+            for (int e = 0; e < 32; e += 2) {  // two columns at a time (even and odd partial sums)
+                const float2 h = __fadd2_rn(make_float2(v[e], v[e + 1]),
+                                            *reinterpret_cast<const float2*>(b2s + c * 32 + e));
+                acc2 = __ffma2_rn(make_float2(fmaxf(h.x, 0.f), fmaxf(h.y, 0.f)),
+                                  *reinterpret_cast<const float2*>(w3s + c * 32 + e), acc2);
+            }
         }
+        const float acc = acc2.x + acc2.y;
         if (half > 0) part[half - 1][r] = acc;
         // h1 and columns 256-511 are rewritten for the next tile only after every thread is done with them;
         // a wait that gave up in any thread of the CTA marks the tile's rows (any row may have read
@@ -876,8 +892,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_mlp_train_fwd_tc(TrainArgs A,
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
                     const int j = c * 32 + q * 8 + 2 * e;
-                    pk[e] = pack2(__float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e] + b1s[j], 0.f)),
-                                  __float2bfloat16_rn(fmaxf(v[q * 8 + 2 * e + 1] + b1s[j + 1], 0.f)));
+                    pk[e] = bias_relu_bf16x2(v[q * 8 + 2 * e], v[q * 8 + 2 * e + 1], b1s + j);
                 }
                 const uint4 u = make_uint4(pk[0], pk[1], pk[2], pk[3]);
                 *reinterpret_cast<uint4*>(H1s + kmajor_off(r, c * 32 + q * 8, H)) = u;
