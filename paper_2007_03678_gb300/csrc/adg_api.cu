@@ -590,7 +590,8 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
     // choosing among the row's remaining pairs the partner that adds the fewest
     // shared-memory wavefronts to its quarter-warp's partner load in this step
     // (a partner another lane already reads is free); lanes with the fewest
-    // pairs left choose first.  A lane past its last row reads atom 0.
+    // pairs left choose first.  A lane past its last row reads atom 0 as the
+    // partner of its empty slots.
     std::vector<int> slots((size_t)nsteps * 32, -1);
     std::vector<int> slot_flags((size_t)nsteps * 32, 0);
     {
@@ -799,13 +800,20 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
     // --- pair records: per slot (c12, cm, cd, ij), stored for the kernel's
     // two-slot steps as pk[a] = (c12_a, c12_b, cm_a, cm_b) and
     // pk[b] = (cd_a, cd_b, ij_a, ij_b), slots a = 2t * 32 + lane and b = a + 32,
-    // so each coefficient pair arrives as one two-wide operand
+    // so each coefficient pair arrives as one two-wide operand.  Empty slots
+    // (the tail of a lane's list) have zero coefficients and the uncharged pad
+    // atom as their row atom, loaded at the lane's first empty slot.
     const int ns = nsteps * 32;
-    std::vector<uint4> rec(ns, make_uint4(0, 0, 0, 0));  // empty slots: all zero (add 0); moved as bits
+    const uint32_t pad_atom = (uint32_t)(32 * apl_for(N));
+    std::vector<uint4> rec(ns, make_uint4(0, 0, 0, 0));  // moved as bits
     for (int s = 0; s < ns; ++s) {
         const int p = slots[s];
-        if (p < 0) continue;
-        // the owner, if any, goes first: the kernel sums the force on ij & 127
+        if (p < 0) {
+            const bool first = s < 32 || slots[s - 32] >= 0;
+            rec[s].w = pad_atom | (first ? (uint32_t)kPairRowStart : 0u);
+            continue;
+        }
+        // the owner, if any, goes first: the kernel sums the force on ij & 255
         const int i = owner[p] == pairs[p].second ? pairs[p].second : pairs[p].first;
         const int j = pairs[p].first + pairs[p].second - i;  // internal
         const int ti = d->type[old_of[i]], tj = d->type[old_of[j]];
@@ -892,7 +900,7 @@ void model_schedule(const LigandPlan& pl, adg_schedule_stats* out)
             pw += wavefronts(w, true, &pi);
         }
         for (int sl = 0; sl < 2; ++sl) {
-            for (int l = 0; l < 32; ++l) w[l] = (ij[sl][l] & kPairRowStart) ? (int)(ij[sl][l] & 127) : -1;
+            for (int l = 0; l < 32; ++l) w[l] = (ij[sl][l] & kPairRowStart) ? (int)(ij[sl][l] & 255) : -1;
             pw += wavefronts(w, true, &pi);  // row atom at the row's first slot
             for (int l = 0; l < 32; ++l) w[l] = (int)((ij[sl][l] >> 16) & 127);
             pw += wavefronts(w, true, &pi);  // partner

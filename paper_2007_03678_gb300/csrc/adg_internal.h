@@ -19,11 +19,12 @@ constexpr int kMaxTors = ADG_MAX_TORS;
 constexpr int kGeneStride = 24;  // population rows are padded to 24 floats (>= 7 + 16)
 constexpr int kMaxWarpsPerBlock = 12;
 
-// Per-warp shared memory (floats): xyz[na], f[na] and pm[na] (float4 each),
-// the fragment transforms W[52] (float4, three rows per fragment), genes,
-// cand and best [32 each], then c[nslots] (the pair scalars (dE/dr)/r).
+// Per-warp shared memory (floats): xyz[na + 1] (posed atoms, then a pad atom
+// at the origin with zero charge), f[na] and pm[na] (float4 each), the
+// fragment transforms W[52] (float4, three rows per fragment), genes, cand
+// and best [32 each], then c[nslots] (the pair scalars (dE/dr)/r).
 // na = 32 * atoms-per-lane.
-__host__ __device__ inline size_t warp_smem_floats(int na, int nslots) { return (size_t)12 * na + 304 + nslots; }
+__host__ __device__ inline size_t warp_smem_floats(int na, int nslots) { return (size_t)12 * na + 308 + nslots; }
 
 // Launch geometry of one warp-per-individual kernel launch.  The block's
 // dynamic shared memory holds a copy of its ligand's blob (lig_bytes) and
@@ -68,9 +69,11 @@ struct LigandDev {
 // slots a = 2t * 32 + lane and b = a + 32 hold pk[a] = (c12_a, c12_b, cm_a,
 // cm_b) and pk[b] = (cd_a, cd_b, ij_a, ij_b), with
 // ij = i | j << 16 | kPairOwned | kPairRowEnd | kPairRowStart | kPairHB |
-// target << 24 (an empty slot is all zero: zero coefficients, no flag).  Atom
-// i is the same for a whole row, so a lane reads its coordinates only at the
-// row's first slot.
+// target << 24, i < 256.  Atom i is the same for a whole row, so a lane reads
+// its coordinates only at the row's first slot.  An empty slot has zero
+// coefficients and no row-end flag; its row atom is the pad atom na (read at
+// the lane's first empty slot, kPairRowStart), whose zero charge makes cq
+// vanish too, so an empty slot adds exactly 0 to the energy and has c_p = 0.
 // With m = 10 for H-bond pairs (kPairHB) and 6 otherwise, and cq = wq q_i q_j
 // from the charges the posed coordinates carry in .w:
 // E_pair = min(c12 r^-12 - cm r^-m, e_cap) + cq / (eps(r) r) + cd exp(-r^2/(2 s^2)).

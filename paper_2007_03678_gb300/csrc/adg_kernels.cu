@@ -248,7 +248,7 @@ cudaError_t launch_pack_maps(cudaStream_t st, const float* maps, const adg_grid_
 // ------------------------------------------------------------------ warp scoring
 // Per-warp views into the dynamic shared memory of the block.
 struct WarpView {
-    float4* xyz;   // posed coordinates [na] (internal atom order)
+    float4* xyz;   // posed coordinates [na] (internal atom order), then the pad atom
     float4* f;     // intramolecular force per atom, then prefix sums of the total force [na]
     float4* pm;    // prefix sums of the moments (x - t) x f [na]
     float4* W;     // fragment transforms, rows 3f..3f+2 = (R row, t) [52]
@@ -265,23 +265,31 @@ __device__ __forceinline__ WarpView warp_view(int na, int nslots, int lig_bytes)
                   (size_t)(threadIdx.x >> 5) * warp_smem_floats(na, nslots);
     WarpView v;
     v.xyz = reinterpret_cast<float4*>(base);
-    v.f = reinterpret_cast<float4*>(base + 4 * na);
-    v.pm = reinterpret_cast<float4*>(base + 8 * na);
-    v.W = reinterpret_cast<float4*>(base + 12 * na);
-    v.genes = base + 12 * na + 208;
+    v.f = reinterpret_cast<float4*>(base + 4 * na + 4);
+    v.pm = reinterpret_cast<float4*>(base + 8 * na + 4);
+    v.W = reinterpret_cast<float4*>(base + 12 * na + 4);
+    v.genes = base + 12 * na + 212;
     v.cand = v.genes + 32;
     v.best = v.cand + 32;
     v.c = v.best + 32;
+    // the pad atom: the row atom of empty pair slots (origin, zero charge);
+    // read only after the __syncwarp that ends every pose
+    if ((threadIdx.x & 31) == 0) v.xyz[na] = make_float4(0.f, 0.f, 0.f, 0.f);
     return v;
 }
 
 // Copy the block's ligand blob (header, pair slots, gather program) into the
 // front of the dynamic shared memory; every thread of the block calls this
 // before any warp leaves.  lig_bytes == 0 keeps the ligand in global memory.
+// With the form fixed at compile time (FORM = 1 staged, 0 global; -1 chosen
+// by lig_bytes) the returned pointers have one state space, so the compiler
+// addresses the staged ligand with 32-bit shared-memory loads instead of
+// generic ones.
+template <int FORM = -1>
 __device__ __forceinline__ LigandRef stage_ligand(const LigandRef& g, int lig_bytes)
 {
     extern __shared__ float4 dyn_smem4[];
-    if (lig_bytes == 0) return g;
+    if (FORM == 0 || (FORM < 0 && lig_bytes == 0)) return g;
     const int n16 = g.hdr->blob_bytes / 16;
     const int4* src = reinterpret_cast<const int4*>(g.hdr);
     int4* dst = reinterpret_cast<int4*>(dyn_smem4);
@@ -523,9 +531,9 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         // (c12, cm) of both slots, then (cd, ij) of both slots
         const float4 pa = P.pk[ia], pb = P.pk[ib];
         const int ija = __float_as_int(pb.z), ijb = __float_as_int(pb.w);
-        if (ija & kPairRowStart) xr = ws.xyz[ija & 127];
+        if (ija & kPairRowStart) xr = ws.xyz[ija & 255];
         const float4 xia = xr, xja = ws.xyz[(ija >> 16) & 127];
-        if (ijb & kPairRowStart) xr = ws.xyz[ijb & 127];
+        if (ijb & kPairRowStart) xr = ws.xyz[ijb & 255];
         const float4 xib = xr, xjb = ws.xyz[(ijb >> 16) & 127];
         // differences one slot at a time, so each lands in its half of a pair
         const float2 dx = v2(xia.x - xja.x, xib.x - xjb.x);
@@ -533,8 +541,8 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const float2 dz = v2(xia.z - xja.z, xib.z - xjb.z);
         const float2 r2 = fma2(dz, dz, fma2(dy, dy, mul2(dx, dx)));
         const float2 c12 = v2(pa.x, pa.y), cm = v2(pa.z, pa.w), cd = v2(pb.x, pb.y);
-        // cq = wq q_i q_j; an empty slot (ij == 0; a real pair has i != j) adds nothing
-        const float2 cq = v2((ija ? wq : 0.f) * xia.w * xja.w, (ijb ? wq : 0.f) * xib.w * xjb.w);
+        // cq = wq q_i q_j (0 on an empty slot: its row atom is the uncharged pad)
+        const float2 cq = v2(wq * xia.w * xja.w, wq * xib.w * xjb.w);
         const bool fla = r2.x < rmin2, flb = r2.y < rmin2;
         const float2 rr2 = v2(fla ? rmin2 : r2.x, flb ? rmin2 : r2.y);
         const float2 ri = v2(rsqrt_ftz(rr2.x), rsqrt_ftz(rr2.y));
@@ -1099,7 +1107,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
 // counts accumulate in evals[nruns + run] until k_dock_bookkeep folds them
 // in, so every warp of a generation sees the same total when it decides
 // whether its run is still active.
-template <int APL, int LS>
+template <int APL, int LS, bool STAGED>
 __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock_generation(MapsDev M, SearchDev S, DockDev Dk,
                                                                             int na, int nslots, int lig_bytes, int wpl,
                                                                             int gen_arg, const int* __restrict__ gen_dev)
@@ -1112,7 +1120,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_dock
     const long nruns = (long)Dk.nlig * S.nrun;
     const int lig = (int)(gw / wpl);
     const int local = (int)(gw % wpl);
-    const LigandRef LR = stage_ligand(Dk.ligs[lig], lig_bytes);
+    const LigandRef LR = stage_ligand<STAGED ? 1 : 0>(Dk.ligs[lig], lig_bytes);
     if (local >= S.nrun * S.pop) return;
     const int run = local / S.pop, ind = local % S.pop;
     const int run_g = lig * S.nrun + run;
@@ -1259,17 +1267,25 @@ cudaError_t launch_dock_init(cudaStream_t st, const MapsDev& m, const SearchDev&
     return cudaGetLastError();
 }
 
+template <int APL, int LS, bool STAGED>
+static cudaError_t gen_launch_form(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d,
+                                   const Geo& g, int gen, const int* gen_dev)
+{
+    const int wpl = warps_per_ligand(s, g);
+    const unsigned blocks = (unsigned)((long)d.nlig * wpl / g.wpb);
+    cudaError_t e = allow_smem(k_dock_generation<APL, LS, STAGED>, g.smem);
+    if (e != cudaSuccess) return e;
+    k_dock_generation<APL, LS, STAGED><<<blocks, g.wpb * 32, g.smem, st>>>(m, s, d, g.na, g.nslots, (int)g.lig_bytes,
+                                                                           wpl, gen, gen_dev);
+    return cudaGetLastError();
+}
+
 template <int APL, int LS>
 static cudaError_t gen_launch(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g,
                               int gen, const int* gen_dev)
 {
-    const int wpl = warps_per_ligand(s, g);
-    const unsigned blocks = (unsigned)((long)d.nlig * wpl / g.wpb);
-    cudaError_t e = allow_smem(k_dock_generation<APL, LS>, g.smem);
-    if (e != cudaSuccess) return e;
-    k_dock_generation<APL, LS><<<blocks, g.wpb * 32, g.smem, st>>>(m, s, d, g.na, g.nslots, (int)g.lig_bytes, wpl,
-                                                                   gen, gen_dev);
-    return cudaGetLastError();
+    return g.lig_bytes > 0 ? gen_launch_form<APL, LS, true>(st, m, s, d, g, gen, gen_dev)
+                           : gen_launch_form<APL, LS, false>(st, m, s, d, g, gen, gen_dev);
 }
 
 cudaError_t launch_dock_generation(cudaStream_t st, const MapsDev& m, const SearchDev& s, const DockDev& d, const Geo& g,
@@ -1287,19 +1303,25 @@ cudaError_t launch_dock_generation(cudaStream_t st, const MapsDev& m, const Sear
 }
 
 // ------------------------------------------------------------------ launch-geometry tuning
-template <int APL, int LS>
-static int blocks_per_sm(const Geo& g)
+template <int APL, int LS, bool STAGED>
+static int blocks_per_sm_form(const Geo& g)
 {
     int optin = 0, dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return 0;
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 0;
     if (g.smem > (size_t)optin) return 0;
-    if (allow_smem(k_dock_generation<APL, LS>, g.smem) != cudaSuccess) return 0;
+    if (allow_smem(k_dock_generation<APL, LS, STAGED>, g.smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dock_generation<APL, LS>, g.wpb * 32, g.smem) !=
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_dock_generation<APL, LS, STAGED>, g.wpb * 32, g.smem) !=
         cudaSuccess)
         return 0;
     return nb;
+}
+
+template <int APL, int LS>
+static int blocks_per_sm(const Geo& g)
+{
+    return g.lig_bytes > 0 ? blocks_per_sm_form<APL, LS, true>(g) : blocks_per_sm_form<APL, LS, false>(g);
 }
 
 int geo_blocks_per_sm(const Geo& g, int ls)
