@@ -926,9 +926,9 @@ void model_schedule(const LigandPlan& pl, adg_schedule_stats* out)
             for (int l = 0; l < 32; ++l) w[l] = (int)(e[l * 4 + q] & 127);
             gw += wavefronts(w, true, &gi);  // partner coordinates
         }
-        // flush at the atom's last group: its coordinates and force read, the force written
+        // flush at the atom's last group: its two sums written
         for (int l = 0; l < 32; ++l) w[l] = (e[l * 4 + 3] >> 31) ? (int)((e[l * 4] >> 7) & 127) : -1;
-        for (int r = 0; r < 3; ++r) gw += wavefronts(w, true, &gi);
+        gw += wavefronts(w, true, &gi);
     }
     out->pair_wavefronts = pw;
     out->pair_wavefronts_ideal = pi;

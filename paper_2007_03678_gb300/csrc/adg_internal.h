@@ -20,11 +20,11 @@ constexpr int kGeneStride = 24;  // population rows are padded to 24 floats (>= 
 constexpr int kMaxWarpsPerBlock = 12;
 
 // Per-warp shared memory (floats): xyz[na + 1] (posed atoms, then a pad atom
-// at the origin with zero charge), f[na] and pm[na] (float4 each), the
-// fragment transforms W[52] (float4, three rows per fragment), genes, cand
-// and best [32 each], then c[nslots] (the pair scalars (dE/dr)/r).
-// na = 32 * atoms-per-lane.
-__host__ __device__ inline size_t warp_smem_floats(int na, int nslots) { return (size_t)12 * na + 308 + nslots; }
+// at the origin with zero charge), f[na + 1] (then a sink slot) and pm[na]
+// (float4 each), the fragment transforms W[52] (float4, three rows per
+// fragment), genes, cand and best [32 each], then c[nslots] (the pair scalars
+// (dE/dr)/r).  na = 32 * atoms-per-lane.
+__host__ __device__ inline size_t warp_smem_floats(int na, int nslots) { return (size_t)12 * na + 312 + nslots; }
 
 // Launch geometry of one warp-per-individual kernel launch.  The block's
 // dynamic shared memory holds a copy of its ligand's blob (lig_bytes) and
@@ -81,17 +81,18 @@ struct LigandDev {
 // into rows, one row per owning atom, each row on one lane only, so the lane
 // sums c_p (x_i - x_j) in registers and stores it to f[target] at the row's
 // last slot (kPairRowEnd), target = i.  A pair no row could take runs as a
-// row of its own (kPairOwned clear) whose target is 32 * atoms-per-lane: a
-// sink slot past the ligand's atoms (f of an unused atom, or the first moment
-// slot, both rewritten before they are read), so the kernel sums every slot
+// row of its own (kPairOwned clear) whose target is 32 * atoms-per-lane: the
+// sink slot f[na] past the atoms, never read, so the kernel sums every slot
 // the same way.  Everything else -- the partner side of owned pairs, and
 // both sides of the unowned pairs -- goes through the force
 // gather: after the pair pass has stored c_p of every slot, lane l runs
 // gsteps groups of four entries gent[(k * 32 + l) * 4 + q] (one 16-byte load) = partner |
 // atom << 7 | slot << 14 (one atom per group; bit 31 on the last entry of
 // the atom's last group; lists padded with entries on an empty slot, c_p = 0,
-// whose partner is any posed atom, and all-zero groups at the end), sums c_p and c_p x_partner over the atom's entries, and at its last
-// group adds x_atom sum c_p - sum c_p x_partner to f[atom].  Every ligand has
+// whose partner is any posed atom, and all-zero groups at the end), sums c_p
+// and c_p x_partner over the atom's entries and at its last group stores both
+// sums (pm[atom], zero for atoms without entries); the force scan adds
+// x_atom sum c_p - sum c_p x_partner to the atom's force.  Every ligand has
 // at least one empty slot.
 constexpr int kPairOwned = 1 << 15;
 constexpr int kPairRowEnd = 1 << 14;

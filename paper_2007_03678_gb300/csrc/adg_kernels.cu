@@ -249,8 +249,8 @@ cudaError_t launch_pack_maps(cudaStream_t st, const float* maps, const adg_grid_
 // Per-warp views into the dynamic shared memory of the block.
 struct WarpView {
     float4* xyz;   // posed coordinates [na] (internal atom order), then the pad atom
-    float4* f;     // intramolecular force per atom, then prefix sums of the total force [na]
-    float4* pm;    // prefix sums of the moments (x - t) x f [na]
+    float4* f;     // row forces per atom, then prefix sums of the total force [na]; f[na]: sink
+    float4* pm;    // the force gather's (sum c_p, sum c_p x_partner) per atom, then prefix sums of the moments (x - t) x f [na]
     float4* W;     // fragment transforms, rows 3f..3f+2 = (R row, t) [52]
     float* genes;  // current genotype [32]
     float* cand;   // trial genotype [32]
@@ -266,9 +266,9 @@ __device__ __forceinline__ WarpView warp_view(int na, int nslots, int lig_bytes)
     WarpView v;
     v.xyz = reinterpret_cast<float4*>(base);
     v.f = reinterpret_cast<float4*>(base + 4 * na + 4);
-    v.pm = reinterpret_cast<float4*>(base + 8 * na + 4);
-    v.W = reinterpret_cast<float4*>(base + 12 * na + 4);
-    v.genes = base + 12 * na + 212;
+    v.pm = reinterpret_cast<float4*>(base + 8 * na + 8);
+    v.W = reinterpret_cast<float4*>(base + 12 * na + 8);
+    v.genes = base + 12 * na + 216;
     v.cand = v.genes + 32;
     v.best = v.cand + 32;
     v.c = v.best + 32;
@@ -351,7 +351,8 @@ __device__ __forceinline__ float warp_sum(float v)
 // composed down the fragment tree one level at a time (lane f builds
 // fragment f), then applied once to each atom.
 template <int APL>
-__device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, const WarpView& ws, int lane)
+__device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, const WarpView& ws, int lane,
+                                          float4 (&xo)[APL], int (&to)[APL])
 {
     const int N = L->natoms, NF = L->nfrag;
     float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;  // this lane's map: rotation rows | translation
@@ -392,27 +393,44 @@ __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const
         if (mylev == lev) {
             const int p = L->fpar[lane];
             const float4 p0 = ws.W[3 * p], p1 = ws.W[3 * p + 1], p2 = ws.W[3 * p + 2];
-#define ADG_ROW(P) make_float4(P.x * r0.x + P.y * r1.x + P.z * r2.x, P.x * r0.y + P.y * r1.y + P.z * r2.y, \
-                               P.x * r0.z + P.y * r1.z + P.z * r2.z, P.x * r0.w + P.y * r1.w + P.z * r2.w + P.w)
-            ws.W[3 * lane] = ADG_ROW(p0);
-            ws.W[3 * lane + 1] = ADG_ROW(p1);
-            ws.W[3 * lane + 2] = ADG_ROW(p2);
-#undef ADG_ROW
+            // row of W_parent times the local map, two columns per two-wide operation
+            const float2 r0a = v2(r0.x, r0.y), r0b = v2(r0.z, r0.w), r1a = v2(r1.x, r1.y), r1b = v2(r1.z, r1.w),
+                         r2a = v2(r2.x, r2.y), r2b = v2(r2.z, r2.w);
+            auto row = [&](const float4 P) {
+                const float2 a = __ffma2_rn(s2(P.z), r2a, __ffma2_rn(s2(P.y), r1a, __fmul2_rn(s2(P.x), r0a)));
+                const float2 b = __ffma2_rn(s2(P.z), r2b, __ffma2_rn(s2(P.y), r1b, __fmul2_rn(s2(P.x), r0b)));
+                return make_float4(a.x, a.y, b.x, b.y + P.w);
+            };
+            ws.W[3 * lane] = row(p0);
+            ws.W[3 * lane + 1] = row(p1);
+            ws.W[3 * lane + 2] = row(p2);
         }
         __syncwarp();
     }
 #pragma unroll
     for (int j = 0; j < APL; ++j) {
         const int a = lane + 32 * j;
+        xo[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+        to[j] = 0;
         if (a < N) {
             const float4 r = L->ref[a];
-            const int f = L->tf[a] >> 8;
+            const int tf = L->tf[a], f = tf >> 8;
             const float4 w0 = ws.W[3 * f], w1 = ws.W[3 * f + 1], w2 = ws.W[3 * f + 2];
-            ws.xyz[a] = make_float4(w0.x * r.x + w0.y * r.y + w0.z * r.z + w0.w, w1.x * r.x + w1.y * r.y + w1.z * r.z + w1.w,
-                                    w2.x * r.x + w2.y * r.y + w2.z * r.z + w2.w, r.w);  // .w: the charge
+            xo[j] = make_float4(w0.x * r.x + w0.y * r.y + w0.z * r.z + w0.w, w1.x * r.x + w1.y * r.y + w1.z * r.z + w1.w,
+                                w2.x * r.x + w2.y * r.y + w2.z * r.z + w2.w, r.w);  // .w: the charge
+            to[j] = tf & 255;
+            ws.xyz[a] = xo[j];
         }
     }
     __syncwarp();
+}
+
+template <int APL>
+__device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, const WarpView& ws, int lane)
+{
+    float4 xo[APL];
+    int to[APL];
+    warp_pose<APL>(L, g, ws, lane, xo, to);
 }
 
 // Both x-corners of a cell edge, one 32-byte record: (M_t, M_e, M_d, 0) at x and at x + 1.
@@ -499,7 +517,9 @@ template <int APL, bool GRAD>
 __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, const PairsDev& P, const MapsDev& M,
                                                const float* g, const WarpView& ws, int lane)
 {
-    warp_pose<APL>(L, g, ws, lane);
+    float4 xo[APL];  // this lane's posed atoms (charge in .w) and their types
+    int to[APL];
+    warp_pose<APL>(L, g, ws, lane, xo, to);
     const int N = L->natoms, T = L->ntors;
     const float k_out = L->k_out;
     float e = 0.f;
@@ -509,9 +529,12 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         fxr[j] = fyr[j] = fzr[j] = 0.f;
         const int a = lane + 32 * j;
         if (a < N) {
-            const float4 x = ws.xyz[a];
-            e += atom_inter<GRAD>(M, k_out, L->tf[a] & 255, L->ref[a].w, x.x, x.y, x.z, fxr[j], fyr[j], fzr[j]);
-            if (GRAD) ws.f[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 x = xo[j];
+            e += atom_inter<GRAD>(M, k_out, to[j], x.w, x.x, x.y, x.z, fxr[j], fyr[j], fzr[j]);
+            if (GRAD) {
+                ws.f[a] = make_float4(0.f, 0.f, 0.f, 0.f);
+                ws.pm[a] = make_float4(0.f, 0.f, 0.f, 0.f);  // atoms the gather does not reach
+            }
         }
     }
     if (GRAD) __syncwarp();  // rows below store into f of atoms other lanes cleared
@@ -606,9 +629,10 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     if (!GRAD) return out;
     __syncwarp();
     // force gather: f_atom += sum over its pairs that its row did not cover of
-    // c_p (x_atom - x_partner), formed as x_atom sum c_p - sum c_p x_partner
-    // at the atom's last group; every lane runs the same number of groups of
-    // four entries, so consecutive groups' loads overlap
+    // c_p (x_atom - x_partner), formed as x_atom sum c_p - sum c_p x_partner;
+    // the atom's last group stores (sum c_p, sum c_p x_partner) in pm[atom]
+    // and the scan below adds the force; every lane runs the same number of
+    // groups of four entries, so consecutive groups' loads overlap
     const int ngroups = L->gsteps;
     float sc = 0.f, bx = 0.f, by = 0.f, bz = 0.f;  // sum c_p and sum c_p x_partner of the current atom
 #pragma unroll 2
@@ -622,10 +646,8 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         bx = fmaf(c3, x3.x, fmaf(c2, x2.x, fmaf(c1, x1.x, fmaf(c0, x0.x, bx))));
         by = fmaf(c3, x3.y, fmaf(c2, x2.y, fmaf(c1, x1.y, fmaf(c0, x0.y, by))));
         bz = fmaf(c3, x3.z, fmaf(c2, x2.z, fmaf(c1, x1.z, fmaf(c0, x0.z, bz))));
-        if (e3 >> 31) {  // the atom's last group: add x_atom sum c_p - sum c_p x_partner to its row sum
-            const int atom = (e0 >> 7) & 127;
-            const float4 xa = ws.xyz[atom], fr = ws.f[atom];
-            ws.f[atom] = make_float4(fr.x + fmaf(xa.x, sc, -bx), fr.y + fmaf(xa.y, sc, -by), fr.z + fmaf(xa.z, sc, -bz), 0.f);
+        if (e3 >> 31) {  // the atom's last group
+            ws.pm[(e0 >> 7) & 127] = make_float4(sc, bx, by, bz);
             sc = bx = by = bz = 0.f;
         }
     }
@@ -642,11 +664,11 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
         const int a = lane + 32 * j;
         float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
         if (a < N) {
-            const float4 fi = ws.f[a];
-            v0 = fxr[j] + fi.x;
-            v1 = fyr[j] + fi.y;
-            v2 = fzr[j] + fi.z;
-            const float4 x = ws.xyz[a];
+            // total force: map gradient + row sum + x sum c_p - sum c_p x_partner
+            const float4 fi = ws.f[a], gi = ws.pm[a], x = ws.xyz[a];
+            v0 = fxr[j] + (fi.x + fmaf(x.x, gi.x, -gi.y));
+            v1 = fyr[j] + (fi.y + fmaf(x.y, gi.x, -gi.z));
+            v2 = fzr[j] + (fi.z + fmaf(x.z, gi.x, -gi.w));
             const float rx = x.x - tx, ry = x.y - ty, rz = x.z - tz;
             v3 = ry * v2 - rz * v1;
             v4 = rz * v0 - rx * v2;
