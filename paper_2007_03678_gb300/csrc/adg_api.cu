@@ -351,6 +351,158 @@ struct LigandPlan {
     int nf = 0, sum_moving = 0;
 };
 
+// Local search on the force-gather program.  An atom's entries may sit at any
+// position of the atom's groups (the sums do not depend on where), so two
+// entries of one atom are swapped whenever that lowers the modelled
+// wavefronts of the two positions' loads: the c_p words (one 4-byte load by
+// the warp) and the partner coordinates (16-byte loads, quarter-warps).
+// Padding entries (c_p = 0) may read any empty slot and any partner, and the
+// entries of a lane past its atoms (never stored) any slot and any partner:
+// each takes a word its load already reads where it can.  Deterministic (a
+// fixed xorshift stream), `budget` proposed swaps.
+constexpr long kGatherRefinePerEntry = 4;  // proposed swaps per gather entry
+
+struct GatherRefine {
+    std::vector<uint32_t>& gent;
+    const int ngroups, natoms;
+    const std::vector<int>& blk;        // [k * 32 + l]: the atom block of lane l's group k, -1 past its atoms
+    const std::vector<char>& empty;     // empty[slot]: c_p of the slot is exactly 0
+    std::vector<int> empties;           // the empty slots
+    enum { REAL = 0, PAD = 1, FREE = 2 };
+    std::vector<int> kind, cw, xw;      // per entry (k * 32 + l) * 4 + q
+
+    GatherRefine(std::vector<uint32_t>& g, int ng, int na, const std::vector<int>& b, const std::vector<char>& em)
+        : gent(g), ngroups(ng), natoms(na), blk(b), empty(em)
+    {
+        for (int s = 0; s < (int)em.size(); ++s)
+            if (em[s]) empties.push_back(s);
+        const size_t n = gent.size();
+        kind.assign(n, REAL);
+        cw.assign(n, 0);
+        xw.assign(n, 0);
+        for (size_t i = 0; i < n; ++i) {
+            const uint32_t e = gent[i];
+            cw[i] = (int)((e >> 14) & 0xffff);
+            xw[i] = (int)(e & 127);
+            if (blk[i / 4] < 0) kind[i] = FREE;
+            else if (empty[cw[i]]) kind[i] = PAD;
+        }
+    }
+    // modelled wavefronts of position q of group k; with `commit` the
+    // flexible entries keep the words chosen for them
+    int cost(int k, int q, bool commit)
+    {
+        int words[32], cnt[32] = {0}, n = 0, mx = 0, tot = 0;
+        auto has = [&](int w) {
+            for (int t = 0; t < n; ++t)
+                if (words[t] == w) return true;
+            return false;
+        };
+        auto add = [&](int w, int banks) {
+            if (has(w)) return;
+            words[n++] = w;
+            mx = std::max(mx, ++cnt[w % banks]);
+        };
+        const size_t base = (size_t)k * 128 + q;
+        for (int l = 0; l < 32; ++l)
+            if (kind[base + 4 * l] == REAL) add(cw[base + 4 * l], 32);
+        for (int l = 0; l < 32; ++l) {
+            const size_t i = base + 4 * l;
+            if (kind[i] == REAL) continue;
+            int w = -1;
+            for (int t = 0; t < n && w < 0; ++t)
+                if (kind[i] == FREE || empty[words[t]]) w = words[t];
+            if (w < 0) {
+                if (kind[i] == FREE) w = 0;
+                else {
+                    int best = 1 << 30;
+                    for (int s : empties)
+                        if (cnt[s % 32] < best) { best = cnt[s % 32]; w = s; }
+                }
+            }
+            add(w, 32);
+            if (commit) cw[i] = w;
+        }
+        tot += mx;
+        for (int qd = 0; qd < 4; ++qd) {
+            n = 0;
+            mx = 0;
+            for (int b = 0; b < 8; ++b) cnt[b] = 0;
+            for (int l = qd * 8; l < qd * 8 + 8; ++l)
+                if (kind[base + 4 * l] == REAL) add(xw[base + 4 * l], 8);
+            for (int l = qd * 8; l < qd * 8 + 8; ++l) {
+                const size_t i = base + 4 * l;
+                if (kind[i] == REAL) continue;
+                int w = n > 0 ? words[0] : 0;
+                if (n == 0 && kind[i] == PAD) w = xw[i] < natoms ? xw[i] : 0;
+                add(w, 8);
+                if (commit) xw[i] = w;
+            }
+            tot += mx;
+        }
+        return tot;
+    }
+    int total()
+    {
+        int t = 0;
+        for (int k = 0; k < ngroups; ++k)
+            for (int q = 0; q < 4; ++q) t += cost(k, q, false);
+        return t;
+    }
+    void run(long budget)
+    {
+        // each lane's blocks: first group and group count
+        std::vector<std::vector<std::pair<int, int>>> blocks(32);
+        for (int l = 0; l < 32; ++l)
+            for (int k = 0; k < ngroups; ++k) {
+                const int b = blk[(size_t)k * 32 + l];
+                if (b < 0) continue;
+                if (blocks[l].empty() || blocks[l].back().first + blocks[l].back().second != k ||
+                    blk[(size_t)(k - 1) * 32 + l] != b)
+                    blocks[l].push_back({k, 1});
+                else
+                    ++blocks[l].back().second;
+            }
+        uint32_t st = 0x9e3779b9u;
+        auto rnd = [&](uint32_t n) {
+            st ^= st << 13;
+            st ^= st >> 17;
+            st ^= st << 5;
+            return (uint32_t)(((uint64_t)st * n) >> 32);
+        };
+        for (long it = 0; it < budget; ++it) {
+            const int l = (int)rnd(32);
+            if (blocks[l].empty()) continue;
+            const auto& bk = blocks[l][rnd((uint32_t)blocks[l].size())];
+            const int npos = 4 * bk.second;
+            if (npos < 2) continue;
+            const int p1 = (int)rnd(npos), p2 = (int)rnd(npos);
+            const int k1 = bk.first + p1 / 4, q1 = p1 % 4, k2 = bk.first + p2 / 4, q2 = p2 % 4;
+            if (q1 == q2) continue;  // same column: the swap changes nothing
+            const size_t i1 = ((size_t)k1 * 32 + l) * 4 + q1, i2 = ((size_t)k2 * 32 + l) * 4 + q2;
+            const int before = cost(k1, q1, false) + cost(k2, q2, false);
+            std::swap(kind[i1], kind[i2]);
+            std::swap(cw[i1], cw[i2]);
+            std::swap(xw[i1], xw[i2]);
+            const int after = cost(k1, q1, false) + cost(k2, q2, false);
+            if (after > before) {
+                std::swap(kind[i1], kind[i2]);
+                std::swap(cw[i1], cw[i2]);
+                std::swap(xw[i1], xw[i2]);
+            }
+        }
+    }
+    void store()
+    {
+        for (int k = 0; k < ngroups; ++k)
+            for (int q = 0; q < 4; ++q) cost(k, q, true);
+        for (size_t i = 0; i < gent.size(); ++i) {
+            const uint32_t keep = gent[i] & (0x7fu << 7 | 0x80000000u);  // atom and last-group bit stay with the position
+            gent[i] = (kind[i] == FREE ? 0u : keep) | (uint32_t)xw[i] | ((uint32_t)cw[i] << 14);
+        }
+    }
+};
+
 int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& pl)
 {
     if (!ff || !d || !d->xyz || !d->type || !d->charge) return ADG_EINVAL;
@@ -744,6 +896,19 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
                 if (--left[l] == 0) ++ai[l];
             }
         }
+    }
+    if (ngroups > 0) {
+        std::vector<int> blk((size_t)ngroups * 32, -1);
+        for (int l = 0; l < 32; ++l) {
+            int k = 0;
+            for (int a2 : lane_atoms[l])
+                for (int g = 0; g < (int)(inc[a2].size() + 3) / 4; ++g) blk[(size_t)k++ * 32 + l] = a2;
+        }
+        std::vector<char> empty_slot(slots.size(), 0);
+        for (size_t sl = 0; sl < slots.size(); ++sl) empty_slot[sl] = slots[sl] < 0;
+        GatherRefine gr(gent, ngroups, N, blk, empty_slot);
+        gr.run(kGatherRefinePerEntry * (long)gent.size());
+        gr.store();
     }
     // --- device header
     LigandDev h;
