@@ -368,14 +368,19 @@ struct GatherRefine {
     const std::vector<int>& blk;        // [k * 32 + l]: the atom block of lane l's group k, -1 past its atoms
     const std::vector<char>& empty;     // empty[slot]: c_p of the slot is exactly 0
     std::vector<int> empties;           // the empty slots
+    int empty_of_bank[32];              // the lowest empty slot in each bank, -1 if none
     enum { REAL = 0, PAD = 1, FREE = 2 };
     std::vector<int> kind, cw, xw;      // per entry (k * 32 + l) * 4 + q
 
     GatherRefine(std::vector<uint32_t>& g, int ng, int na, const std::vector<int>& b, const std::vector<char>& em)
         : gent(g), ngroups(ng), natoms(na), blk(b), empty(em)
     {
+        for (int b = 0; b < 32; ++b) empty_of_bank[b] = -1;
         for (int s = 0; s < (int)em.size(); ++s)
-            if (em[s]) empties.push_back(s);
+            if (em[s]) {
+                empties.push_back(s);
+                if (empty_of_bank[s % 32] < 0) empty_of_bank[s % 32] = s;
+            }
         const size_t n = gent.size();
         kind.assign(n, REAL);
         cw.assign(n, 0);
@@ -389,53 +394,58 @@ struct GatherRefine {
         }
     }
     // modelled wavefronts of position q of group k; with `commit` the
-    // flexible entries keep the words chosen for them
+    // flexible entries keep the words chosen for them.  Words are kept per
+    // bank, so a membership test scans one bank; a flexible entry takes the
+    // first word added (padding: the first empty slot added).
     int cost(int k, int q, bool commit)
     {
-        int words[32], cnt[32] = {0}, n = 0, mx = 0, tot = 0;
-        auto has = [&](int w) {
-            for (int t = 0; t < n; ++t)
-                if (words[t] == w) return true;
-            return false;
-        };
-        auto add = [&](int w, int banks) {
-            if (has(w)) return;
-            words[n++] = w;
-            mx = std::max(mx, ++cnt[w % banks]);
+        int bw[32][32], cnt[32], mx = 0, tot = 0, first = -1, first_empty = -1;
+        auto add = [&](int w, int banks, bool slot) {
+            const int b = w % banks;
+            for (int t = 0; t < cnt[b]; ++t)
+                if (bw[b][t] == w) return;
+            bw[b][cnt[b]++] = w;
+            mx = std::max(mx, cnt[b]);
+            if (first < 0) first = w;
+            if (slot && first_empty < 0 && empty[w]) first_empty = w;
         };
         const size_t base = (size_t)k * 128 + q;
+        for (int b = 0; b < 32; ++b) cnt[b] = 0;
         for (int l = 0; l < 32; ++l)
-            if (kind[base + 4 * l] == REAL) add(cw[base + 4 * l], 32);
+            if (kind[base + 4 * l] == REAL) add(cw[base + 4 * l], 32, true);
         for (int l = 0; l < 32; ++l) {
             const size_t i = base + 4 * l;
             if (kind[i] == REAL) continue;
-            int w = -1;
-            for (int t = 0; t < n && w < 0; ++t)
-                if (kind[i] == FREE || empty[words[t]]) w = words[t];
+            int w = kind[i] == FREE ? first : first_empty;
             if (w < 0) {
                 if (kind[i] == FREE) w = 0;
-                else {
+                else {  // the lowest empty slot among the least filled banks that hold one
                     int best = 1 << 30;
-                    for (int s : empties)
-                        if (cnt[s % 32] < best) { best = cnt[s % 32]; w = s; }
+                    for (int b = 0; b < 32; ++b) {
+                        const int e = empty_of_bank[b];
+                        if (e >= 0 && (cnt[b] < best || (cnt[b] == best && e < w))) {
+                            best = cnt[b];
+                            w = e;
+                        }
+                    }
                 }
             }
-            add(w, 32);
+            add(w, 32, true);
             if (commit) cw[i] = w;
         }
         tot += mx;
         for (int qd = 0; qd < 4; ++qd) {
-            n = 0;
             mx = 0;
+            first = -1;
             for (int b = 0; b < 8; ++b) cnt[b] = 0;
             for (int l = qd * 8; l < qd * 8 + 8; ++l)
-                if (kind[base + 4 * l] == REAL) add(xw[base + 4 * l], 8);
+                if (kind[base + 4 * l] == REAL) add(xw[base + 4 * l], 8, false);
             for (int l = qd * 8; l < qd * 8 + 8; ++l) {
                 const size_t i = base + 4 * l;
                 if (kind[i] == REAL) continue;
-                int w = n > 0 ? words[0] : 0;
-                if (n == 0 && kind[i] == PAD) w = xw[i] < natoms ? xw[i] : 0;
-                add(w, 8);
+                int w = first >= 0 ? first : 0;
+                if (first < 0 && kind[i] == PAD) w = xw[i] < natoms ? xw[i] : 0;
+                add(w, 8, false);
                 if (commit) xw[i] = w;
             }
             tot += mx;
@@ -470,6 +480,9 @@ struct GatherRefine {
             st ^= st << 5;
             return (uint32_t)(((uint64_t)st * n) >> 32);
         };
+        std::vector<int> cc((size_t)ngroups * 4);  // each position's current cost
+        for (int k = 0; k < ngroups; ++k)
+            for (int q = 0; q < 4; ++q) cc[(size_t)k * 4 + q] = cost(k, q, false);
         for (long it = 0; it < budget; ++it) {
             const int l = (int)rnd(32);
             if (blocks[l].empty()) continue;
@@ -480,15 +493,18 @@ struct GatherRefine {
             const int k1 = bk.first + p1 / 4, q1 = p1 % 4, k2 = bk.first + p2 / 4, q2 = p2 % 4;
             if (q1 == q2) continue;  // same column: the swap changes nothing
             const size_t i1 = ((size_t)k1 * 32 + l) * 4 + q1, i2 = ((size_t)k2 * 32 + l) * 4 + q2;
-            const int before = cost(k1, q1, false) + cost(k2, q2, false);
+            const int before = cc[(size_t)k1 * 4 + q1] + cc[(size_t)k2 * 4 + q2];
             std::swap(kind[i1], kind[i2]);
             std::swap(cw[i1], cw[i2]);
             std::swap(xw[i1], xw[i2]);
-            const int after = cost(k1, q1, false) + cost(k2, q2, false);
-            if (after > before) {
+            const int c1 = cost(k1, q1, false), c2 = cost(k2, q2, false);
+            if (c1 + c2 > before) {
                 std::swap(kind[i1], kind[i2]);
                 std::swap(cw[i1], cw[i2]);
                 std::swap(xw[i1], xw[i2]);
+            } else {
+                cc[(size_t)k1 * 4 + q1] = c1;
+                cc[(size_t)k2 * 4 + q2] = c2;
             }
         }
     }
