@@ -561,6 +561,7 @@ def run_triage(ctx, R, ff):
             "recall_top1pct_ci95_wilson": list(T.wilson_interval(hits, ntop)),
             "recall_top1pct_early_energy_rule": hits_e / ntop,
             "recall_top1pct_early_energy_rule_ci95_wilson": list(T.wilson_interval(hits_e, ntop)),
+            "network_vs_early_rule_mcnemar": T.mcnemar_exact(y_st, keep, keep_early, cfg.top_frac),
             "recall_by_survivor_fraction": curve,
             "survivors": float(keep.mean()), "evals_ratio": out["evals"] / ev_plain,
             "survivors_match_plain": bool(np.array_equal(out["energy"][keep], y_st[keep])),

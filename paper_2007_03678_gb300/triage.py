@@ -222,6 +222,22 @@ def wilson_interval(hits: int, n: int, z: float = 1.959963984540054) -> tuple:
     return (0.0 if hits == 0 else max(0.0, mid - half), 1.0 if hits == n else min(1.0, mid + half))
 
 
+def mcnemar_exact(true_energy: np.ndarray, keep_a: np.ndarray, keep_b: np.ndarray, top_frac: float) -> dict:
+    """Paired comparison of two survival rules on the same top ligands:
+    b = top ligands only rule a keeps, c = only rule b keeps; under the null
+    hypothesis (equal recall) each discordant ligand falls either way with
+    probability 1/2, so the two-sided exact p-value is
+    min(1, 2 P(X <= min(b, c))), X ~ Binomial(b + c, 1/2)."""
+    from math import comb
+    k = max(1, int(round(top_frac * len(true_energy))))
+    top = np.argsort(true_energy, kind="stable")[:k]
+    a, bb = np.asarray(keep_a)[top], np.asarray(keep_b)[top]
+    b, c = int((a & ~bb).sum()), int((~a & bb).sum())
+    n = b + c
+    tail = sum(comb(n, i) for i in range(min(b, c) + 1)) / 2.0 ** n if n else 1.0
+    return {"only_a": b, "only_b": c, "p_two_sided": min(1.0, 2.0 * tail)}
+
+
 def early_rule_survivors(feats: np.ndarray, cfg: TriageConfig) -> np.ndarray:
     """The same survival fraction chosen without the network: the ligands
     whose best early energy (over runs, after the early generations; the

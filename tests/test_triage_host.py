@@ -88,3 +88,27 @@ def test_early_rule_keeps_the_lowest_early_energies():
     best_early = tr[:, :, cfg.early_gen - 1].min(axis=1)
     assert keep.sum() == int(np.ceil(cfg.keep_frac * n))
     assert best_early[keep].max() <= best_early[~keep].min()
+
+
+def test_mcnemar_exact_on_discordant_top_ligands():
+    """Only top ligands where the two rules disagree count; the p-value is the
+    two-sided exact binomial tail, checked against its closed forms: 0
+    discordant gives 1, 5 to 0 gives 2/32, and 3 to 3 gives 1 (capped)."""
+    true_e = np.arange(1000, dtype=float)  # ligands 0-9 are the top 1 %
+    a = np.zeros(1000, bool)
+    b = np.zeros(1000, bool)
+    a[:10] = b[:10] = True
+    r = T.mcnemar_exact(true_e, a, b, 0.01)
+    assert (r["only_a"], r["only_b"], r["p_two_sided"]) == (0, 0, 1.0)
+    b[:5] = False
+    b[500:600] = True  # outside the top: ignored
+    r = T.mcnemar_exact(true_e, a, b, 0.01)
+    assert (r["only_a"], r["only_b"]) == (5, 0) and abs(r["p_two_sided"] - 2 / 32) < 1e-15
+    a[:3] = False
+    b[:3] = True
+    a[3:6] = True
+    b[3:6] = False
+    r = T.mcnemar_exact(true_e, a, b, 0.01)
+    assert (r["only_a"], r["only_b"]) == (3, 3) and r["p_two_sided"] == 1.0
+    # symmetric in the two rules
+    assert T.mcnemar_exact(true_e, b, a, 0.01)["p_two_sided"] == r["p_two_sided"]
