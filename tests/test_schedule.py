@@ -32,10 +32,19 @@ def test_paper_scale_ligand(ff):
     st = adg.ligand_schedule(ff, lig)
     _check(st, 44, 748)
     assert st["nsteps"] == 24
-    # the conflict-aware schedule: within 5 % (pair loop) and 35 % (gather) of
-    # the conflict-free count for this ligand
+    # the conflict-aware schedule: within 5 % (pair loop) and 20 % (gather,
+    # after the swap search) of the conflict-free count for this ligand
     assert st["pair_wavefronts"] <= 1.05 * st["pair_wavefronts_ideal"]
-    assert st["gather_wavefronts"] <= 1.35 * st["gather_wavefronts_ideal"]
+    assert st["gather_wavefronts"] <= 1.20 * st["gather_wavefronts_ideal"]
+    # the greedy gather alone modelled 298 wavefronts for this ligand
+    assert st["gather_wavefronts"] <= 250
+
+
+def test_schedule_is_deterministic(ff):
+    """The gather search draws from a fixed xorshift stream and uses integer
+    arithmetic only: the same ligand gets the same schedule in every call."""
+    for lig in S.make_batch(8, seed=21):
+        assert adg.ligand_schedule(ff, lig) == adg.ligand_schedule(ff, lig)
 
 
 def test_batch_ligands(ff):
