@@ -348,26 +348,33 @@ __device__ __forceinline__ float warp_sum(float v)
 // Applying the torsions deepest first about their reference axes and then
 // x' = R(q/|q|)(x - c) + t is, per rigid fragment, one affine map
 // W_f = W_parent(f) * Rot_k(f): the rigid-body map for the root fragment,
-// composed down the fragment tree one level at a time (lane f builds
-// fragment f), then applied once to each atom.
+// composed down the fragment tree one level at a time (three lanes per
+// fragment, one per row, or one lane per fragment past 10 fragments), then
+// applied once to each atom.
 template <int APL>
 __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, const WarpView& ws, int lane,
                                           float4 (&xo)[APL], int (&to)[APL])
 {
     const int N = L->natoms, NF = L->nfrag;
-    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;  // this lane's map: rotation rows | translation
-    if (lane < NF) {
-        // lane 0: x' = R(q/|q|)(x - c) + t; lane f > 0: the rotation by theta
-        // about fragment f's torsion axis through o, x' = R(x - o) + o, with R
-        // from the unit quaternion (cos theta/2, sin theta/2 u).  One
+    // Up to 10 fragments: lane 3f + i builds row i of fragment f's map (the
+    // rows are independent, each needs the whole local map); otherwise lane f
+    // builds all three rows.  Either way each row is the same arithmetic.
+    const bool by_row = NF <= 10;
+    const int f = by_row ? lane / 3 : lane;
+    const int ri = by_row ? lane - 3 * f : 0;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0, r2 = r0;  // fragment f's local map: rotation rows | translation
+    if (f < NF) {
+        // fragment 0: x' = R(q/|q|)(x - c) + t; fragment f > 0: the rotation by
+        // theta about its torsion axis through o, x' = R(x - o) + o, with R from
+        // the unit quaternion (cos theta/2, sin theta/2 u).  One
         // quaternion-to-matrix path for both, so the lanes do not diverge.
-        const int k = lane > 0 ? L->ftor[lane] : 0;
+        const int k = f > 0 ? L->ftor[f] : 0;
         float s, c;
-        sincosf(lane > 0 ? 0.5f * g[7 + k] : 0.f, &s, &c);
+        sincosf(f > 0 ? 0.5f * g[7 + k] : 0.f, &s, &c);
         const float4 u = L->tax[k], o = L->tpt[k];
         float qw = c, qx = s * u.x, qy = s * u.y, qz = s * u.z;
         float px = o.x, py = o.y, pz = o.z, tx = o.x, ty = o.y, tz = o.z;
-        if (lane == 0) {
+        if (f == 0) {
             qw = g[3]; qx = g[4]; qy = g[5]; qz = g[6];
             const float qi = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
             qw *= qi; qx *= qi; qy *= qi; qz *= qi;
@@ -380,19 +387,22 @@ __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const
         r0 = make_float4(R00, R01, R02, tx - (R00 * px + R01 * py + R02 * pz));
         r1 = make_float4(R10, R11, R12, ty - (R10 * px + R11 * py + R12 * pz));
         r2 = make_float4(R20, R21, R22, tz - (R20 * px + R21 * py + R22 * pz));
-        if (lane == 0) {
-            ws.W[0] = r0;
-            ws.W[1] = r1;
-            ws.W[2] = r2;
+        if (f == 0) {
+            if (by_row) {
+                ws.W[ri] = ri == 0 ? r0 : (ri == 1 ? r1 : r2);
+            } else {
+                ws.W[0] = r0;
+                ws.W[1] = r1;
+                ws.W[2] = r2;
+            }
         }
     }
     __syncwarp();
     const int maxlev = L->maxlev;
-    const int mylev = (lane > 0 && lane < NF) ? L->flev[lane] : -1;
+    const int mylev = (f > 0 && f < NF) ? L->flev[f] : -1;
     for (int lev = 1; lev <= maxlev; ++lev) {
         if (mylev == lev) {
-            const int p = L->fpar[lane];
-            const float4 p0 = ws.W[3 * p], p1 = ws.W[3 * p + 1], p2 = ws.W[3 * p + 2];
+            const int p = L->fpar[f];
             // row of W_parent times the local map, two columns per two-wide operation
             const float2 r0a = v2(r0.x, r0.y), r0b = v2(r0.z, r0.w), r1a = v2(r1.x, r1.y), r1b = v2(r1.z, r1.w),
                          r2a = v2(r2.x, r2.y), r2b = v2(r2.z, r2.w);
@@ -401,9 +411,14 @@ __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const
                 const float2 b = __ffma2_rn(s2(P.z), r2b, __ffma2_rn(s2(P.y), r1b, __fmul2_rn(s2(P.x), r0b)));
                 return make_float4(a.x, a.y, b.x, b.y + P.w);
             };
-            ws.W[3 * lane] = row(p0);
-            ws.W[3 * lane + 1] = row(p1);
-            ws.W[3 * lane + 2] = row(p2);
+            if (by_row) {
+                ws.W[3 * f + ri] = row(ws.W[3 * p + ri]);
+            } else {
+                const float4 p0 = ws.W[3 * p], p1 = ws.W[3 * p + 1], p2 = ws.W[3 * p + 2];
+                ws.W[3 * f] = row(p0);
+                ws.W[3 * f + 1] = row(p1);
+                ws.W[3 * f + 2] = row(p2);
+            }
         }
         __syncwarp();
     }
