@@ -364,7 +364,8 @@ constexpr long kGatherRefinePerEntry = 4;  // proposed swaps per gather entry
 
 struct GatherRefine {
     std::vector<uint32_t>& gent;
-    const int ngroups, natoms;
+    const int ngroups;
+    const std::vector<char>& used;      // used[atom index]: a posed atom lives there
     const std::vector<int>& blk;        // [k * 32 + l]: the atom block of lane l's group k, -1 past its atoms
     const std::vector<char>& empty;     // empty[slot]: c_p of the slot is exactly 0
     std::vector<int> empties;           // the empty slots
@@ -372,8 +373,9 @@ struct GatherRefine {
     enum { REAL = 0, PAD = 1, FREE = 2 };
     std::vector<int> kind, cw, xw;      // per entry (k * 32 + l) * 4 + q
 
-    GatherRefine(std::vector<uint32_t>& g, int ng, int na, const std::vector<int>& b, const std::vector<char>& em)
-        : gent(g), ngroups(ng), natoms(na), blk(b), empty(em)
+    GatherRefine(std::vector<uint32_t>& g, int ng, const std::vector<char>& u, const std::vector<int>& b,
+                 const std::vector<char>& em)
+        : gent(g), ngroups(ng), used(u), blk(b), empty(em)
     {
         for (int b = 0; b < 32; ++b) empty_of_bank[b] = -1;
         for (int s = 0; s < (int)em.size(); ++s)
@@ -444,7 +446,7 @@ struct GatherRefine {
                 const size_t i = base + 4 * l;
                 if (kind[i] == REAL) continue;
                 int w = first >= 0 ? first : 0;
-                if (first < 0 && kind[i] == PAD) w = xw[i] < natoms ? xw[i] : 0;
+                if (first < 0 && kind[i] == PAD) w = used[xw[i]] ? xw[i] : 0;
                 add(w, 8, false);
                 if (commit) xw[i] = w;
             }
@@ -666,17 +668,28 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
         }
         for (int v : q) near[s][v] = 1;
     }
-    std::vector<std::pair<int, int>> pairs;  // internal indices
+    // --- atom indices: position a of the depth-first order gets index
+    // (a % apl) * 32 + a / apl, so each lane's atoms are consecutive positions
+    // (the force scan then needs one warp scan per evaluation, not apl); the
+    // pair and gather programs below work on indices
+    const int apl = apl_for(N), na = 32 * apl;
+    auto idx_of = [&](int a) { return (a % apl) * 32 + a / apl; };
+    std::vector<int> src_of(na, -1);  // the caller's index of the atom at each index, -1 if unused
+    for (int a = 0; a < N; ++a) src_of[idx_of(a)] = old_of[a];
+    std::vector<std::pair<int, int>> pairs;  // atom indices
     for (int i = 0; i < N; ++i)
         for (int j = i + 1; j < N; ++j)
-            if (frag[i] != frag[j] && !near[i][j]) pairs.emplace_back(std::min(nw[i], nw[j]), std::max(nw[i], nw[j]));
+            if (frag[i] != frag[j] && !near[i][j]) {
+                const int x = idx_of(nw[i]), y = idx_of(nw[j]);
+                pairs.emplace_back(std::min(x, y), std::max(x, y));
+            }
     const int P = (int)pairs.size();
     // --- lane schedule.  Rows: the not yet owned atom with the most
     // unscheduled pairs takes (up to a lane's share of) those pairs as its row,
     // first the pairs whose partner already owns a row (no row could take them
     // later).  A row runs on one lane, which keeps the owner's coordinates and
     // force in registers.  Pairs no row takes run as one-pair rows, unowned.
-    std::vector<std::vector<int>> inc_p(N);  // pairs by atom
+    std::vector<std::vector<int>> inc_p(na);  // pairs by atom
     for (int p = 0; p < P; ++p) {
         inc_p[pairs[p].first].push_back(p);
         inc_p[pairs[p].second].push_back(p);
@@ -688,7 +701,7 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
     std::vector<Row> rows;
     std::vector<int> owner(P, -1);
     {
-        std::vector<char> sched(P, 0), done(N, 0);
+        std::vector<char> sched(P, 0), done(na, 0);
         std::vector<int> load(32, 0);
         const int share = (P + 31) / 32;
         for (;;) {
@@ -696,7 +709,8 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
             const int room = share - load[lane];
             if (room <= 0) break;
             int best = -1, best_n = 0;
-            for (int a2 = 0; a2 < N; ++a2) {
+            for (int pos = 0; pos < N; ++pos) {
+                const int a2 = idx_of(pos);
                 if (done[a2]) continue;
                 int n2 = 0;
                 for (int p : inc_p[a2]) n2 += !sched[p];
@@ -823,7 +837,7 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
     for (int sl = 0; sl < (int)slots.size() && zero_slot < 0; ++sl)
         if (slots[sl] < 0) zero_slot = sl;
     if (zero_slot < 0) return ADG_EINVAL;  // unreachable: nsteps keeps one slot empty
-    std::vector<std::vector<std::pair<int, int>>> inc(N);
+    std::vector<std::vector<std::pair<int, int>>> inc(na);
     for (int sl = 0; sl < (int)slots.size(); ++sl) {
         const int p = slots[sl];
         if (p < 0) continue;
@@ -832,7 +846,7 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
         if (owner[p] != j) inc[j].emplace_back(i, sl);
     }
     std::vector<int> by_deg(N);
-    for (int i = 0; i < N; ++i) by_deg[i] = i;
+    for (int pos = 0; pos < N; ++pos) by_deg[pos] = idx_of(pos);
     std::stable_sort(by_deg.begin(), by_deg.end(), [&](int x, int y) { return inc[x].size() > inc[y].size(); });
     std::vector<std::vector<int>> lane_atoms(32);
     std::vector<int> gload(32, 0);
@@ -922,7 +936,9 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
         }
         std::vector<char> empty_slot(slots.size(), 0);
         for (size_t sl = 0; sl < slots.size(); ++sl) empty_slot[sl] = slots[sl] < 0;
-        GatherRefine gr(gent, ngroups, N, blk, empty_slot);
+        std::vector<char> used(na, 0);
+        for (int i = 0; i < na; ++i) used[i] = src_of[i] >= 0;
+        GatherRefine gr(gent, ngroups, used, blk, empty_slot);
         gr.run(kGatherRefinePerEntry * (long)gent.size());
         gr.store();
     }
@@ -951,11 +967,13 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
     h.inv_s2 = (float)(1.0 / ((double)ff->sigma * ff->sigma));
     h.k_out = ff->k_out;
     h.wq = (float)((double)ff->w_elec * ff->coulomb);
+    h.apl = apl;
+    h.last_idx = idx_of(N - 1);
     for (int n = 0; n < N; ++n) {
-        const int i = old_of[n];
-        h.ref[n] = make_float4(d->xyz[3 * i], d->xyz[3 * i + 1], d->xyz[3 * i + 2], d->charge[i]);
-        h.tf[n] = d->type[i] | (fnew[frag[i]] << 8);
-        h.old_of_new[n] = i;
+        const int i = old_of[n], x = idx_of(n);
+        h.ref[x] = make_float4(d->xyz[3 * i], d->xyz[3 * i + 1], d->xyz[3 * i + 2], d->charge[i]);
+        h.tf[x] = d->type[i] | (fnew[frag[i]] << 8);
+        h.old_of_new[x] = i;
     }
     h.nfrag = nf;
     h.maxlev = maxlev;
@@ -966,10 +984,10 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
         h.flev[fi] = flev[f];
     }
     for (int k = 0; k < T; ++k) {
-        h.ta[k] = nw[ta[k]];
-        h.tb[k] = nw[tb[k]];
-        h.slo[k] = slo[k];
-        h.shi[k] = shi[k];
+        h.ta[k] = idx_of(nw[ta[k]]);
+        h.tb[k] = idx_of(nw[tb[k]]);
+        h.hi_idx[k] = idx_of(shi[k] - 1);
+        h.lo_idx[k] = slo[k] > 0 ? idx_of(slo[k] - 1) : -1;
         const float* pa = d->xyz + 3 * ta[k];
         const float* pb = d->xyz + 3 * tb[k];
         double u[3] = {(double)pb[0] - pa[0], (double)pb[1] - pa[1], (double)pb[2] - pa[2]};
@@ -985,7 +1003,7 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
     // (the tail of a lane's list) have zero coefficients and the uncharged pad
     // atom as their row atom, loaded at the lane's first empty slot.
     const int ns = nsteps * 32;
-    const uint32_t pad_atom = (uint32_t)(32 * apl_for(N));
+    const uint32_t pad_atom = (uint32_t)na;
     std::vector<uint4> rec(ns, make_uint4(0, 0, 0, 0));  // moved as bits
     for (int s = 0; s < ns; ++s) {
         const int p = slots[s];
@@ -996,13 +1014,13 @@ int plan_ligand(const adg_forcefield* ff, const adg_ligand_desc* d, LigandPlan& 
         }
         // the owner, if any, goes first: the kernel sums the force on ij & 255
         const int i = owner[p] == pairs[p].second ? pairs[p].second : pairs[p].first;
-        const int j = pairs[p].first + pairs[p].second - i;  // internal
-        const int ti = d->type[old_of[i]], tj = d->type[old_of[j]];
-        const double qi = d->charge[old_of[i]], qj = d->charge[old_of[j]];
+        const int j = pairs[p].first + pairs[p].second - i;
+        const int ti = d->type[src_of[i]], tj = d->type[src_of[j]];
+        const double qi = d->charge[src_of[i]], qj = d->charge[src_of[j]];
         float c12, c6, c10;
         pair_coefs(*ff, ti, tj, &c12, &c6, &c10);
         const bool hb = c10 != 0.f;
-        const uint32_t tgt = (slot_flags[s] & kPairOwned) ? (uint32_t)i : (uint32_t)(32 * apl_for(N));
+        const uint32_t tgt = (slot_flags[s] & kPairOwned) ? (uint32_t)i : (uint32_t)na;
         const int ij = (int)((uint32_t)(i | (j << 16) | slot_flags[s] | (hb ? kPairHB : 0)) | (tgt << 24));
         const float cd = (float)((double)ff->w_desolv * (((double)ff->solpar[ti] + (double)ff->qasp * fabs(qi)) * ff->vol[tj] +
                                                          ((double)ff->solpar[tj] + (double)ff->qasp * fabs(qj)) * ff->vol[ti]));

@@ -54,11 +54,19 @@ struct LigandDev {
     // scoring constants (from the force field)
     float e_cap, rmin2, ms_A, ms_B, ms_k, ms_lb, inv_2s2, inv_s2, k_out;
     float wq;                            // w_elec * Coulomb constant: cq = wq q_i q_j
-    float4 ref[kMaxAtoms];               // reference x, y, z and charge q (internal order)
+    // Atom index: the atom at depth-first position a (fragment after
+    // fragment, each followed by its subtree) has index (a % apl) * 32 + a / apl,
+    // so lane l holds positions apl l .. apl l + apl - 1 at indices l, l + 32,
+    // ...; the indices of positions >= natoms are unused.  Every per-atom array
+    // here and in shared memory, and every atom in the pair and gather
+    // programs, uses the index.
+    int apl;                             // atoms per lane of this layout (1-4)
+    int last_idx;                        // index of position natoms - 1
+    float4 ref[kMaxAtoms];               // reference x, y, z and charge q
     int tf[kMaxAtoms];                   // map type | fragment << 8
-    int old_of_new[kMaxAtoms];           // caller's index of internal atom i
-    int ta[kMaxTors], tb[kMaxTors];      // bond atoms of torsion k (internal; a on the root side)
-    int slo[kMaxTors], shi[kMaxTors];    // atoms moved by torsion k
+    int old_of_new[kMaxAtoms];           // the caller's index of each atom
+    int ta[kMaxTors], tb[kMaxTors];      // torsion k's bond atoms (a on the root side)
+    int hi_idx[kMaxTors], lo_idx[kMaxTors];  // torsion k moves positions [lo, hi): indices of hi - 1 and lo - 1 (-1: lo = 0)
     float4 tpt[kMaxTors];                // reference position of atom a
     float4 tax[kMaxTors];                // reference unit axis a -> b
     int fpar[kMaxTors + 1], ftor[kMaxTors + 1], flev[kMaxTors + 1];

@@ -424,10 +424,10 @@ __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const
     }
 #pragma unroll
     for (int j = 0; j < APL; ++j) {
-        const int a = lane + 32 * j;
+        const int a = lane + 32 * j;  // the atom index of depth-first position apl lane + j
         xo[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         to[j] = 0;
-        if (a < N) {
+        if (j < L->apl && L->apl * lane + j < N) {
             const float4 r = L->ref[a];
             const int tf = L->tf[a], f = tf >> 8;
             const float4 w0 = ws.W[3 * f], w1 = ws.W[3 * f + 1], w2 = ws.W[3 * f + 2];
@@ -543,7 +543,7 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     for (int j = 0; j < APL; ++j) {
         fxr[j] = fyr[j] = fzr[j] = 0.f;
         const int a = lane + 32 * j;
-        if (a < N) {
+        if (APL * lane + j < N) {  // the atom of depth-first position APL lane + j
             const float4 x = xo[j];
             e += atom_inter<GRAD>(M, k_out, to[j], x.w, x.x, x.y, x.z, fxr[j], fyr[j], fzr[j]);
             if (GRAD) {
@@ -668,17 +668,21 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
     }
     __syncwarp();
     // Per atom: total force f and moment m = (x - t) x f.  Inclusive prefix
-    // sums over the internal atom order go to ws.f / ws.pm; the atoms moved by
-    // torsion k are the range [slo, shi), so
+    // sums over the depth-first atom order go to ws.f / ws.pm; the atoms moved
+    // by torsion k are the positions [lo, hi), so
     //   dE/dtheta_k = u . ((x - x_a) x f) summed there = u . M_k - (u x (x_a - t)) . F_k
     // with F_k, M_k differences of prefix sums and u the posed axis a -> b.
+    // Lane l holds positions APL l + j: a running sum over its own atoms,
+    // then one warp scan of the lane totals; position APL l + APL - 1 takes the
+    // warp scan's value, the others the previous lanes' total plus their
+    // running sum.
     const float tx = g[0], ty = g[1], tz = g[2];
-    float cf0 = 0.f, cf1 = 0.f, cf2 = 0.f, cm0 = 0.f, cm1 = 0.f, cm2 = 0.f;  // carry of earlier slots
+    float run[APL][6];
 #pragma unroll
     for (int j = 0; j < APL; ++j) {
         const int a = lane + 32 * j;
         float v0 = 0.f, v1 = 0.f, v2 = 0.f, v3 = 0.f, v4 = 0.f, v5 = 0.f;
-        if (a < N) {
+        if (APL * lane + j < N) {
             // total force: map gradient + row sum + x sum c_p - sum c_p x_partner
             const float4 fi = ws.f[a], gi = ws.pm[a], x = ws.xyz[a];
             v0 = fxr[j] + (fi.x + fmaf(x.x, gi.x, -gi.y));
@@ -689,38 +693,56 @@ __device__ __forceinline__ ScoreOut warp_score(const LigandDev* __restrict__ L, 
             v4 = rz * v0 - rx * v2;
             v5 = rx * v1 - ry * v0;
         }
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const float u0 = __shfl_up_sync(FULL_MASK, v0, o), u1 = __shfl_up_sync(FULL_MASK, v1, o),
-                        u2 = __shfl_up_sync(FULL_MASK, v2, o), u3 = __shfl_up_sync(FULL_MASK, v3, o),
-                        u4 = __shfl_up_sync(FULL_MASK, v4, o), u5 = __shfl_up_sync(FULL_MASK, v5, o);
-            if (lane >= o) {  // two-wide adds
-                const float2 a = __fadd2_rn(make_float2(v0, v1), make_float2(u0, u1));
-                const float2 b = __fadd2_rn(make_float2(v2, v3), make_float2(u2, u3));
-                const float2 d = __fadd2_rn(make_float2(v4, v5), make_float2(u4, u5));
-                v0 = a.x; v1 = a.y; v2 = b.x; v3 = b.y; v4 = d.x; v5 = d.y;
-            }
+        if (j > 0) {  // two-wide adds
+            const float2 a2 = __fadd2_rn(make_float2(run[j - 1][0], run[j - 1][1]), make_float2(v0, v1));
+            const float2 b2 = __fadd2_rn(make_float2(run[j - 1][2], run[j - 1][3]), make_float2(v2, v3));
+            const float2 d2 = __fadd2_rn(make_float2(run[j - 1][4], run[j - 1][5]), make_float2(v4, v5));
+            v0 = a2.x; v1 = a2.y; v2 = b2.x; v3 = b2.y; v4 = d2.x; v5 = d2.y;
         }
-        v0 += cf0; v1 += cf1; v2 += cf2; v3 += cm0; v4 += cm1; v5 += cm2;
-        ws.f[a] = make_float4(v0, v1, v2, 0.f);
-        ws.pm[a] = make_float4(v3, v4, v5, 0.f);
-        if (j + 1 < APL) {
-            cf0 = __shfl_sync(FULL_MASK, v0, 31); cf1 = __shfl_sync(FULL_MASK, v1, 31);
-            cf2 = __shfl_sync(FULL_MASK, v2, 31); cm0 = __shfl_sync(FULL_MASK, v3, 31);
-            cm1 = __shfl_sync(FULL_MASK, v4, 31); cm2 = __shfl_sync(FULL_MASK, v5, 31);
+        run[j][0] = v0; run[j][1] = v1; run[j][2] = v2; run[j][3] = v3; run[j][4] = v4; run[j][5] = v5;
+    }
+    float s0 = run[APL - 1][0], s1 = run[APL - 1][1], s2 = run[APL - 1][2], s3 = run[APL - 1][3],
+          s4 = run[APL - 1][4], s5 = run[APL - 1][5];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float u0 = __shfl_up_sync(FULL_MASK, s0, o), u1 = __shfl_up_sync(FULL_MASK, s1, o),
+                    u2 = __shfl_up_sync(FULL_MASK, s2, o), u3 = __shfl_up_sync(FULL_MASK, s3, o),
+                    u4 = __shfl_up_sync(FULL_MASK, s4, o), u5 = __shfl_up_sync(FULL_MASK, s5, o);
+        if (lane >= o) {  // two-wide adds
+            const float2 a2 = __fadd2_rn(make_float2(s0, s1), make_float2(u0, u1));
+            const float2 b2 = __fadd2_rn(make_float2(s2, s3), make_float2(u2, u3));
+            const float2 d2 = __fadd2_rn(make_float2(s4, s5), make_float2(u4, u5));
+            s0 = a2.x; s1 = a2.y; s2 = b2.x; s3 = b2.y; s4 = d2.x; s5 = d2.y;
+        }
+    }
+    ws.f[lane + 32 * (APL - 1)] = make_float4(s0, s1, s2, 0.f);
+    ws.pm[lane + 32 * (APL - 1)] = make_float4(s3, s4, s5, 0.f);
+    if (APL > 1) {
+        // the total of the lanes before this one
+        float e0 = __shfl_up_sync(FULL_MASK, s0, 1), e1 = __shfl_up_sync(FULL_MASK, s1, 1),
+              e2p = __shfl_up_sync(FULL_MASK, s2, 1), e3 = __shfl_up_sync(FULL_MASK, s3, 1),
+              e4 = __shfl_up_sync(FULL_MASK, s4, 1), e5 = __shfl_up_sync(FULL_MASK, s5, 1);
+        if (lane == 0) e0 = e1 = e2p = e3 = e4 = e5 = 0.f;
+#pragma unroll
+        for (int j = 0; j + 1 < APL; ++j) {
+            const float2 a2 = __fadd2_rn(make_float2(e0, e1), make_float2(run[j][0], run[j][1]));
+            const float2 b2 = __fadd2_rn(make_float2(e2p, e3), make_float2(run[j][2], run[j][3]));
+            const float2 d2 = __fadd2_rn(make_float2(e4, e5), make_float2(run[j][4], run[j][5]));
+            ws.f[lane + 32 * j] = make_float4(a2.x, a2.y, b2.x, 0.f);
+            ws.pm[lane + 32 * j] = make_float4(b2.y, d2.x, d2.y, 0.f);
         }
     }
     __syncwarp();
     float val = 0.f;
     if (lane < 6) {
-        const float4 F = ws.f[N - 1], Mt = ws.pm[N - 1];
+        const float4 F = ws.f[L->last_idx], Mt = ws.pm[L->last_idx];
         val = lane == 0 ? F.x : lane == 1 ? F.y : lane == 2 ? F.z : lane == 3 ? Mt.x : lane == 4 ? Mt.y : Mt.z;
     } else if (lane < 6 + T) {
         const int k = lane - 6;
-        const int lo = L->slo[k], hi = L->shi[k];
-        float4 F = ws.f[hi - 1], Mk = ws.pm[hi - 1];
-        if (lo > 0) {
-            const float4 F0 = ws.f[lo - 1], M0 = ws.pm[lo - 1];
+        const int lo = L->lo_idx[k], hi = L->hi_idx[k];
+        float4 F = ws.f[hi], Mk = ws.pm[hi];
+        if (lo >= 0) {
+            const float4 F0 = ws.f[lo], M0 = ws.pm[lo];
             F.x -= F0.x; F.y -= F0.y; F.z -= F0.z;
             Mk.x -= M0.x; Mk.y -= M0.y; Mk.z -= M0.z;
         }
@@ -915,7 +937,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_pose(LigandRef LR, i
     if (lane < G) ws.genes[lane] = genes[pose * G + lane];
     __syncwarp();
     warp_pose<4>(L, ws.genes, ws, lane);
-    for (int a = lane; a < N; a += 32) {
+    for (int j = 0; j < L->apl && L->apl * lane + j < N; ++j) {  // this lane's atoms
+        const int a = lane + 32 * j;
         const float4 x = ws.xyz[a];
         const long o = (pose * N + L->old_of_new[a]) * 3;
         xyz[o + 0] = x.x;
@@ -1543,7 +1566,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_finalize(MapsDe
         R.evals = (long long)Dk.evals[run_g];
     }
     if (lane < kGeneStride) R.genes[lane] = lane < G ? ws.genes[lane] : 0.f;
-    for (int a = lane; a < N; a += 32) {
+    for (int j = 0; j < L->apl && L->apl * lane + j < N; ++j) {  // this lane's atoms
+        const int a = lane + 32 * j;
         const float4 x = ws.xyz[a];
         const int o = 3 * L->old_of_new[a];
         R.xyz[o] = x.x;
@@ -1600,7 +1624,8 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_finalize_abi(Ma
     if (lane < ADG_MAX_GENES) R.genes[lane] = lane < G ? ws.genes[lane] : 0.f;
     for (int k = lane; k < 3 * ADG_MAX_ATOMS; k += 32) R.xyz[k] = 0.f;
     __syncwarp();
-    for (int a = lane; a < N; a += 32) {
+    for (int j = 0; j < L->apl && L->apl * lane + j < N; ++j) {  // this lane's atoms
+        const int a = lane + 32 * j;
         const float4 x = ws.xyz[a];
         const int o = 3 * L->old_of_new[a];
         R.xyz[o] = x.x;

@@ -186,13 +186,17 @@ def test_score_edge_cases(ctx, A, ff):
     e, _ = A.score(ctx, R, Lg, torch.zeros((0, 7 + lig.ntors), device="cuda"))
     assert e.numel() == 0
     cases = []
-    # rigid ligand (no torsion), one-atom ligand, a 128-atom 16-torsion ligand
+    # rigid ligand (no torsion), one-atom ligand, a 128-atom 16-torsion ligand,
+    # a 64-atom ligand (every atom index of two per lane used) and an 88-atom
+    # ligand (three atoms per lane, the last lanes partly empty)
     rigid = S.make_ligand(12, 0, 77)
     one = S.Ligand(np.zeros((1, 3)), np.array([S.T_OA], np.int32), np.array([-0.3]), np.zeros((0, 2), np.int32),
                    np.zeros((0, 2), np.int32), 0)
     big = S.make_ligand(116, 16, 78, n_hd=12)
-    assert big.natoms == 128
-    for lg in (rigid, one, big):
+    full2 = S.make_ligand(58, 7, 81)
+    three = S.make_ligand(80, 10, 79)
+    assert (big.natoms, full2.natoms, three.natoms) == (128, 64, 88)
+    for lg in (rigid, one, big, full2, three):
         genes = S.random_genes(lg, 700, grid, 24, spread=1.3).astype(np.float32)  # many poses leave the box
         Lg = A.Ligand(ctx, ff, lg)
         e, gt = A.score(ctx, R, Lg, _cuda(genes), A.GRAD_TANGENT)
