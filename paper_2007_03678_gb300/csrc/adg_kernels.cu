@@ -350,8 +350,9 @@ __device__ __forceinline__ float warp_sum(float v)
 // W_f = W_parent(f) * Rot_k(f): the rigid-body map for the root fragment,
 // composed down the fragment tree one level at a time (three lanes per
 // fragment, one per row, or one lane per fragment past 10 fragments), then
-// applied once to each atom.
-template <int APL>
+// applied once to each atom.  ANY: APL may exceed the ligand's own atoms per
+// lane (the layout width is then read from the ligand).
+template <int APL, bool ANY = false>
 __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, const WarpView& ws, int lane,
                                           float4 (&xo)[APL], int (&to)[APL])
 {
@@ -425,9 +426,10 @@ __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const
 #pragma unroll
     for (int j = 0; j < APL; ++j) {
         const int a = lane + 32 * j;  // the atom index of depth-first position apl lane + j
+        const int apl = ANY ? L->apl : APL;
         xo[j] = make_float4(0.f, 0.f, 0.f, 0.f);
         to[j] = 0;
-        if (j < L->apl && L->apl * lane + j < N) {
+        if (j < apl && apl * lane + j < N) {
             const float4 r = L->ref[a];
             const int tf = L->tf[a], f = tf >> 8;
             const float4 w0 = ws.W[3 * f], w1 = ws.W[3 * f + 1], w2 = ws.W[3 * f + 2];
@@ -440,12 +442,12 @@ __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const
     __syncwarp();
 }
 
-template <int APL>
+template <int APL, bool ANY>
 __device__ __forceinline__ void warp_pose(const LigandDev* __restrict__ L, const float* g, const WarpView& ws, int lane)
 {
     float4 xo[APL];
     int to[APL];
-    warp_pose<APL>(L, g, ws, lane, xo, to);
+    warp_pose<APL, ANY>(L, g, ws, lane, xo, to);
 }
 
 // Both x-corners of a cell edge, one 32-byte record: (M_t, M_e, M_d, 0) at x and at x + 1.
@@ -936,7 +938,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_pose(LigandRef LR, i
     const int G = 7 + L->ntors, N = L->natoms;
     if (lane < G) ws.genes[lane] = genes[pose * G + lane];
     __syncwarp();
-    warp_pose<4>(L, ws.genes, ws, lane);
+    warp_pose<4, true>(L, ws.genes, ws, lane);
     for (int j = 0; j < L->apl && L->apl * lane + j < N; ++j) {  // this lane's atoms
         const int a = lane + 32 * j;
         const float4 x = ws.xyz[a];
@@ -1558,7 +1560,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_finalize(MapsDe
     if (bi >= S.pop) bi = 0;  // only when every energy is NaN
     if (lane < G) ws.genes[lane] = Pg[(long)bi * kGeneStride + lane];
     __syncwarp();
-    warp_pose<4>(L, ws.genes, ws, lane);
+    warp_pose<4, true>(L, ws.genes, ws, lane);
     ResultDev& R = out[run_g];
     if (lane == 0) {
         R.best_energy = bv;
@@ -1614,7 +1616,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32) k_dock_finalize_abi(Ma
     if (bi >= S.pop) bi = 0;  // only when every energy is NaN
     if (lane < G) ws.genes[lane] = Pg[(long)bi * kGeneStride + lane];
     __syncwarp();
-    warp_pose<4>(L, ws.genes, ws, lane);
+    warp_pose<4, true>(L, ws.genes, ws, lane);
     adg_result& R = out[run_g];
     if (lane == 0) {
         R.best_energy = bv;
