@@ -619,6 +619,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
+        # the other workloads (batching, triage, the triage network, the plain
+        # configuration, differentiation) are single-GPU measurements reported
+        # from the one-GPU run; replicas time the paper-scale docking only
+        args.no_batching = args.no_triage = args.no_batching_full = True
     ff = S.forcefield()
     w = S.PAPER
     grid, rec, lig_desc = S.workload_inputs(w, lig_index=rank)
