@@ -258,12 +258,14 @@ int adg_score(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* lig, cons
  *   energy: device [total]
  *   grad:   device [total][ADG_MAX_GENES], NULL when grad_kind ==
  *           ADG_GRAD_NONE; a row gets 7+T (ADG_GRAD_GENES) or 6+T
- *           (ADG_GRAD_TANGENT) values in front, the rest is left as it was
- * Each pose gets the same values as adg_score gives it.  The launch tables
- * live in a stream-ordered device buffer (cudaMallocAsync) freed after the
- * launch.  ADG_EINVAL on a null argument, a negative count or a ligand of
- * another context, ADG_ETOOBIG beyond 2^30 rows; asynchronous on the
- * context's stream. */
+ *           (ADG_GRAD_TANGENT) values in front and zeros after them
+ * Each pose gets the same values as adg_score gives it.  The widths run on
+ * concurrent streams that fork from and join back into the context's stream.
+ * The launch tables (which block serves which ligand's rows) live in a device
+ * buffer the context keeps and re-uploads, in stream order, only when a call's
+ * tables differ from the previous call's.  ADG_EINVAL on a null argument, a
+ * negative count or a ligand of another context, ADG_ETOOBIG beyond 2^30 rows;
+ * asynchronous on the context's stream. */
 int adg_score_multi(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* const* ligs, int nlig, const int* npose,
                     const float* genes, float* energy, float* grad, int grad_kind);
 

@@ -468,8 +468,8 @@ def score_multi(ctx: Context, rec: Receptor, ligs, genes, npose, grad_kind: int 
         raise ValueError(f"genes must be float32 [{total}, {MAX_GENES}]")
     energy = torch.empty(total, dtype=torch.float32, device=genes.device)
     grad = None
-    if grad_kind != GRAD_NONE:
-        grad = torch.zeros((total, MAX_GENES), dtype=torch.float32, device=genes.device)
+    if grad_kind != GRAD_NONE:  # every column is written (zeros past the ligand's genes)
+        grad = torch.empty((total, MAX_GENES), dtype=torch.float32, device=genes.device)
     hs = (C.c_void_p * n)(*[l.handle.value for l in ligs])
     ctx._enter()
     _check(load().adg_score_multi(ctx.handle, rec.handle, hs, n, counts, _ptr(genes), _ptr(energy),

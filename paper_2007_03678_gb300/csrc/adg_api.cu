@@ -163,6 +163,7 @@ int adg_ctx_destroy(adg_ctx* ctx)
     }
     if (ctx->arena) cudaFree(ctx->arena);
     if (ctx->tune_buf) cudaFree(ctx->tune_buf);
+    if (ctx->multi_dev) cudaFree(ctx->multi_dev);
     if (ctx->host_active) cudaFreeHost(ctx->host_active);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1294,12 +1295,28 @@ int adg_score_multi(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* con
     if (total == 0) return ADG_OK;
     if (total > (1l << 30)) return ADG_ETOOBIG;
     CK(ctx, cudaSetDevice(ctx->device));
-    // one launch per atoms-per-lane width; rows keep the caller's ligand order
+    // one launch per atoms-per-lane width, the widths on concurrent streams;
+    // rows keep the caller's ligand order
     std::vector<long> row0(nlig);
     for (int i = 0, r = 0; i < nlig; ++i) {
         row0[i] = r;
         r += npose[i];
     }
+    int nsm = 148;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    struct Width {
+        Geo g;
+        int nblocks;
+        size_t o_ref, o_bl, o_b0, o_r0, o_np, o_nb;
+    };
+    std::vector<Width> widths;
+    std::vector<char> host;  // every width's tables, in one buffer
+    auto put = [&](const void* src, size_t n) {
+        const size_t o = align_up(host.size(), 256);
+        host.resize(o + n);
+        if (n) memcpy(host.data() + o, src, n);
+        return o;
+    };
     for (int apl = 1; apl <= 4; ++apl) {
         std::vector<int> members;
         int nslots = 32;
@@ -1311,14 +1328,13 @@ int adg_score_multi(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* con
                 lig_bytes = std::max(lig_bytes, ligs[i]->bytes);
             }
         if (members.empty()) continue;
-        const Geo g = make_geo(apl, nslots, lig_bytes);
+        Width w;
+        w.g = make_geo(apl, nslots, lig_bytes);
         const int nm = (int)members.size();
         // poses per warp: up to 8, while the launch keeps at least two waves of blocks
         long width_poses = 0;
         for (int m = 0; m < nm; ++m) width_poses += npose[members[m]];
-        int nsm = 148;
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-        const long waves2 = 2l * nsm * 2 * g.wpb;  // warps in two waves of two blocks per SM
+        const long waves2 = 2l * nsm * 2 * w.g.wpb;  // warps in two waves of two blocks per SM
         const int ppw = (int)std::max(1l, std::min(8l, width_poses / std::max(1l, waves2)));
         std::vector<LigandRef> refs(nm);
         std::vector<int> blk0(nm), rows(nm), np(nm), nblk(nm), blk_lig;
@@ -1328,43 +1344,76 @@ int adg_score_multi(adg_ctx* ctx, const adg_receptor* rec, const adg_ligand* con
             blk0[m] = (int)blk_lig.size();
             rows[m] = (int)row0[i];
             np[m] = npose[i];
-            const int nb = (npose[i] + g.wpb * ppw - 1) / (g.wpb * ppw);
+            const int nb = (npose[i] + w.g.wpb * ppw - 1) / (w.g.wpb * ppw);
             nblk[m] = nb;
             for (int b = 0; b < nb; ++b) blk_lig.push_back(m);
         }
-        // the launch's tables in one stream-ordered device buffer, freed after the launch
-        const size_t o_ref = 0, o_bl = align_up(sizeof(LigandRef) * nm, 256),
-                     o_b0 = align_up(o_bl + sizeof(int) * blk_lig.size(), 256),
-                     o_r0 = align_up(o_b0 + sizeof(int) * nm, 256), o_np = align_up(o_r0 + sizeof(int) * nm, 256),
-                     o_nb = align_up(o_np + sizeof(int) * nm, 256), bytes = align_up(o_nb + sizeof(int) * nm, 256);
-        std::vector<char> host(bytes, 0);
-        memcpy(host.data() + o_ref, refs.data(), sizeof(LigandRef) * nm);
-        memcpy(host.data() + o_bl, blk_lig.data(), sizeof(int) * blk_lig.size());
-        memcpy(host.data() + o_b0, blk0.data(), sizeof(int) * nm);
-        memcpy(host.data() + o_r0, rows.data(), sizeof(int) * nm);
-        memcpy(host.data() + o_np, np.data(), sizeof(int) * nm);
-        memcpy(host.data() + o_nb, nblk.data(), sizeof(int) * nm);
-        char* dev = nullptr;
-        CK(ctx, cudaMallocAsync((void**)&dev, bytes, ctx->stream));
-        cudaError_t e = cudaMemcpyAsync(dev, host.data(), bytes, cudaMemcpyHostToDevice, ctx->stream);
-        if (e == cudaSuccess) {
-            ScoreMultiDev J;
-            J.ligs = (const LigandRef*)(dev + o_ref);
-            J.blk_lig = (const int*)(dev + o_bl);
-            J.lig_blk0 = (const int*)(dev + o_b0);
-            J.lig_row0 = (const int*)(dev + o_r0);
-            J.lig_npose = (const int*)(dev + o_np);
-            J.lig_nblk = (const int*)(dev + o_nb);
-            J.stride = ADG_MAX_GENES;
-            e = launch_score_multi(ctx->stream, rec->maps, J, (int)blk_lig.size(), g, genes, energy,
-                                   grad_kind == ADG_GRAD_NONE ? nullptr : grad, grad_kind);
+        w.nblocks = (int)blk_lig.size();
+        w.o_ref = put(refs.data(), sizeof(LigandRef) * nm);
+        w.o_bl = put(blk_lig.data(), sizeof(int) * blk_lig.size());
+        w.o_b0 = put(blk0.data(), sizeof(int) * nm);
+        w.o_r0 = put(rows.data(), sizeof(int) * nm);
+        w.o_np = put(np.data(), sizeof(int) * nm);
+        w.o_nb = put(nblk.data(), sizeof(int) * nm);
+        widths.push_back(w);
+    }
+    cudaStream_t st = ctx->stream;
+    // the tables are uploaded only when they differ from the last call's: the
+    // buffer is rewritten in stream order, after every earlier launch that
+    // read it (earlier calls joined their streams back into this one)
+    if (host != ctx->multi_host) {
+        if (host.size() > ctx->multi_cap) {
+            if (ctx->multi_dev) CK(ctx, cudaFreeAsync(ctx->multi_dev, st));
+            ctx->multi_dev = nullptr;
+            ctx->multi_cap = 0;
+            CK(ctx, cudaMallocAsync(&ctx->multi_dev, host.size(), st));
+            ctx->multi_cap = host.size();
         }
-        const cudaError_t e2 = cudaFreeAsync(dev, ctx->stream);
-        if (e != cudaSuccess) return cuda_fail(ctx, e, "adg_score_multi");
-        if (e2 != cudaSuccess) return cuda_fail(ctx, e2, "cudaFreeAsync");
-        ctx->stats.h2d_bytes += (int64_t)bytes;
+        ctx->multi_host.clear();  // stale until the copy below is issued
+        CK(ctx, cudaMemcpyAsync(ctx->multi_dev, host.data(), host.size(), cudaMemcpyHostToDevice, st));
+        ctx->multi_host = host;
+        ctx->stats.h2d_bytes += (int64_t)host.size();
+    }
+    while (ctx->class_streams.size() + 1 < widths.size()) {
+        cudaStream_t s2;
+        CK(ctx, cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+        ctx->class_streams.push_back(s2);
+    }
+    cudaEvent_t fork = nullptr;
+    if (widths.size() > 1) {
+        CK(ctx, take_event(ctx, &fork));
+        CK(ctx, cudaEventRecord(fork, st));
+    }
+    const char* dev = (const char*)ctx->multi_dev;
+    cudaError_t e = cudaSuccess;
+    for (size_t k = 0; k < widths.size() && e == cudaSuccess; ++k) {
+        const Width& w = widths[k];
+        cudaStream_t sk = k == 0 ? st : ctx->class_streams[k - 1];
+        if (k > 0) e = cudaStreamWaitEvent(sk, fork, 0);
+        if (e != cudaSuccess) break;
+        ScoreMultiDev J;
+        J.ligs = (const LigandRef*)(dev + w.o_ref);
+        J.blk_lig = (const int*)(dev + w.o_bl);
+        J.lig_blk0 = (const int*)(dev + w.o_b0);
+        J.lig_row0 = (const int*)(dev + w.o_r0);
+        J.lig_npose = (const int*)(dev + w.o_np);
+        J.lig_nblk = (const int*)(dev + w.o_nb);
+        J.stride = ADG_MAX_GENES;
+        e = launch_score_multi(sk, rec->maps, J, w.nblocks, w.g, genes, energy,
+                               grad_kind == ADG_GRAD_NONE ? nullptr : grad, grad_kind);
         ctx->stats.kernel_launches += 1;
     }
+    // join: the context's stream waits for every width
+    for (size_t k = 1; k < widths.size(); ++k) {
+        cudaEvent_t done;
+        const cudaError_t e1 = take_event(ctx, &done);
+        if (e1 != cudaSuccess) return cuda_fail(ctx, e1, "adg_score_multi");
+        cudaEventRecord(done, ctx->class_streams[k - 1]);
+        cudaStreamWaitEvent(st, done, 0);
+        ctx->ev_free.push_back(done);
+    }
+    if (fork) ctx->ev_free.push_back(fork);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "adg_score_multi");
     return ADG_OK;
 }
 

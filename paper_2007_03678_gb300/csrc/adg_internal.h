@@ -271,4 +271,9 @@ struct adg_ctx {
     std::map<uint32_t, adg_tuned_shape> tuned;  // by shape bucket
     void* tune_buf = nullptr;                    // probe poses and energies
     size_t tune_bytes = 0;
+    // adg_score_multi's block -> ligand tables: the last upload, kept while
+    // the next call's tables are the same bytes
+    std::vector<char> multi_host;
+    void* multi_dev = nullptr;
+    size_t multi_cap = 0;
 };

@@ -810,7 +810,7 @@ static unsigned blocks_for(long nwarps, const Geo& g) { return (unsigned)((nwarp
 template <int APL>
 __device__ __forceinline__ void score_pose(const LigandRef& SL, const MapsDev& M, const WarpView& ws,
                                            const float* __restrict__ gin, float* __restrict__ energy,
-                                           float* __restrict__ grad, int grad_kind, int lane)
+                                           float* __restrict__ grad, int grad_kind, int lane, int grad_width = 0)
 {
     const LigandDev* L = SL.hdr;
     const int T = L->ntors, G = 7 + T, D = 6 + T;
@@ -824,7 +824,7 @@ __device__ __forceinline__ void score_pose(const LigandRef& SL, const MapsDev& M
     ScoreOut o = warp_score<APL, true>(L, SL.pairs, M, ws.genes, ws, lane);
     if (lane == 0) energy[0] = o.e;
     if (grad_kind == ADG_GRAD_TANGENT) {
-        if (lane < D) grad[lane] = o.gtan;
+        if (lane < max(D, grad_width)) grad[lane] = lane < D ? o.gtan : 0.f;  // a padded row's tail is 0
         return;
     }
     // gene gradient: t and theta from the tangent gradient, q by the chain rule
@@ -842,7 +842,7 @@ __device__ __forceinline__ void score_pose(const LigandRef& SL, const MapsDev& M
         else if (lane == 5) val = 2.f * (qw * ty + (tz * qx - tx * qz)) * iq;
         else val = 2.f * (qw * tz + (tx * qy - ty * qx)) * iq;
     } else if (lane < G) val = prev;
-    if (lane < G) grad[lane] = val;
+    if (lane < max(G, grad_width)) grad[lane] = lane < G ? val : 0.f;
 }
 
 template <int APL>
@@ -882,7 +882,7 @@ __global__ void __launch_bounds__(kMaxWarpsPerBlock * 32, ADG_MIN_BLOCKS) k_scor
          local += stride) {
         const long row = (long)J.lig_row0[lig] + local;
         score_pose<APL>(SL, M, ws, genes + row * J.stride, energy + row, grad ? grad + row * J.stride : nullptr,
-                        grad_kind, lane);
+                        grad_kind, lane, J.stride);
         __syncwarp();
     }
 }
