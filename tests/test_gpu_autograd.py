@@ -165,3 +165,39 @@ def test_batched_scoring_equals_per_ligand(ctx, ff):
         e1.sum().backward()
         assert torch.equal(e.detach(), e1.detach())
         assert torch.equal(x.grad, y.grad)
+
+
+def test_batched_scoring_across_changing_calls(ctx, ff):
+    """adg_score_multi keeps its launch tables between calls and uploads new
+    ones only when a call's ligands or counts differ: calls that alternate
+    between ligand sets (of one and of several widths) and counts each give
+    adg_score's values bit for bit, and every gradient row is written whole."""
+    import torch
+    from paper_2007_03678_gb300 import adg
+    grid, rec, _, maps64, maps32 = problem("paper")
+    R = adg.Receptor(ctx, grid, maps32)
+    pool = _ligands()[:6] + [S.make_ligand(80, 9, 5353), S.make_ligand(12, 2, 5454)]
+    L = [adg.Ligand(ctx, ff, l) for l in pool]
+    G = {i: torch.from_numpy(S.random_genes(l, 96, grid, 61000 + i, spread=0.3).astype(np.float32)).cuda()
+         for i, l in enumerate(pool)}
+    calls = [([0, 1, 6, 7], [40, 17, 33, 9]), ([2, 3], [64, 5]), ([0, 1, 6, 7], [40, 17, 33, 9]),
+             ([0, 1, 6, 7], [12, 50, 33, 9]), ([7, 6, 1, 0], [9, 33, 17, 40]), ([4], [96]), ([0, 1, 6, 7], [40, 17, 33, 9])]
+    for idx, counts in calls:
+        rows = torch.full((sum(counts), adg.MAX_GENES), 7.0, dtype=torch.float32, device="cuda")
+        r = 0
+        for i, k in zip(idx, counts):
+            g = G[i][:k]
+            rows[r:r + k] = 0.0
+            rows[r:r + k, :g.shape[1]] = g
+            r += k
+        e_all, g_all = adg.score_multi(ctx, R, [L[i] for i in idx], rows, counts, adg.GRAD_GENES)
+        ctx.sync()
+        r = 0
+        for i, k in zip(idx, counts):
+            g = G[i][:k].contiguous()
+            e1, g1 = adg.score(ctx, R, L[i], g, adg.GRAD_GENES)
+            ctx.sync()
+            assert torch.equal(e_all[r:r + k], e1), (idx, counts, i)
+            assert torch.equal(g_all[r:r + k, :g.shape[1]], g1), (idx, counts, i)
+            assert not g_all[r:r + k, g.shape[1]:].any()
+            r += k
