@@ -494,7 +494,7 @@ struct GatherRefine {
             if (npos < 2) continue;
             const int p1 = (int)rnd(npos), p2 = (int)rnd(npos);
             const int k1 = bk.first + p1 / 4, q1 = p1 % 4, k2 = bk.first + p2 / 4, q2 = p2 % 4;
-            if (q1 == q2) continue;  // same column: the swap changes nothing
+            if (k1 == k2 && q1 == q2) continue;  // the same position: nothing to swap
             const size_t i1 = ((size_t)k1 * 32 + l) * 4 + q1, i2 = ((size_t)k2 * 32 + l) * 4 + q2;
             const int before = cc[(size_t)k1 * 4 + q1] + cc[(size_t)k2 * 4 + q2];
             std::swap(kind[i1], kind[i2]);
