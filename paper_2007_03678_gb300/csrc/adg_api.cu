@@ -354,9 +354,9 @@ struct LigandPlan {
 
 // Local search on the force-gather program.  An atom's entries may sit at any
 // position of the atom's groups (the sums do not depend on where), so two
-// entries of one atom are swapped whenever that lowers the modelled
-// wavefronts of the two positions' loads: the c_p words (one 4-byte load by
-// the warp) and the partner coordinates (16-byte loads, quarter-warps).
+// entries of one atom are swapped unless that raises the modelled wavefronts
+// of the two positions' loads: the c_p words (one 4-byte load by the warp)
+// and the partner coordinates (16-byte loads, quarter-warps).
 // Padding entries (c_p = 0) may read any empty slot and any partner, and the
 // entries of a lane past its atoms (never stored) any slot and any partner:
 // each takes a word its load already reads where it can.  Deterministic (a
@@ -369,7 +369,6 @@ struct GatherRefine {
     const std::vector<char>& used;      // used[atom index]: a posed atom lives there
     const std::vector<int>& blk;        // [k * 32 + l]: the atom block of lane l's group k, -1 past its atoms
     const std::vector<char>& empty;     // empty[slot]: c_p of the slot is exactly 0
-    std::vector<int> empties;           // the empty slots
     int empty_of_bank[32];              // the lowest empty slot in each bank, -1 if none
     enum { REAL = 0, PAD = 1, FREE = 2 };
     std::vector<int> kind, cw, xw;      // per entry (k * 32 + l) * 4 + q
@@ -380,10 +379,7 @@ struct GatherRefine {
     {
         for (int b = 0; b < 32; ++b) empty_of_bank[b] = -1;
         for (int s = 0; s < (int)em.size(); ++s)
-            if (em[s]) {
-                empties.push_back(s);
-                if (empty_of_bank[s % 32] < 0) empty_of_bank[s % 32] = s;
-            }
+            if (em[s] && empty_of_bank[s % 32] < 0) empty_of_bank[s % 32] = s;
         const size_t n = gent.size();
         kind.assign(n, REAL);
         cw.assign(n, 0);
@@ -454,13 +450,6 @@ struct GatherRefine {
             tot += mx;
         }
         return tot;
-    }
-    int total()
-    {
-        int t = 0;
-        for (int k = 0; k < ngroups; ++k)
-            for (int q = 0; q < 4; ++q) t += cost(k, q, false);
-        return t;
     }
     void run(long budget)
     {
