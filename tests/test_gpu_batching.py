@@ -155,3 +155,40 @@ def test_batched_dock_sampled_against_oracle(ctx, ff):
         assert (np.abs(e - e_xyz) <= E_ABS + E_REL * np.abs(e_xyz))[clean].all(), (i, e, e_xyz)
         clean_checked += int(clean.sum())
     assert clean_checked >= 0.75 * 4 * len(ligs)
+
+
+def test_full_batching_configuration_sampled_against_oracle(ctx, ff):
+    """The full batching configuration's 4,096 ligands (the bench's seeded set,
+    heavy atoms 10-60, torsions 0-15) in one adg_dock call of 20 runs x 150,
+    here with one generation of ADADELTA per run instead of 1 M evaluations:
+    every run spends its budget, and for a sample of ligands of every
+    atoms-per-lane width each run's reported pose is the oracle's pose of the
+    reported genotype and its best energy the oracle's energy of that
+    genotype (genotype-level tolerance)."""
+    import oracle as O
+    from paper_2007_03678_gb300 import adg
+    from gpu_common import energy_tol
+    grid, rec, _, maps64, maps32 = problem("paper")
+    R = adg.Receptor(ctx, grid, maps32)
+    bl = S.make_batch(4096, seed=7, workers=0)
+    L = [adg.Ligand(ctx, ff, l) for l in bl]
+    nev = 40_000
+    p = adg.search_params(nrun=20, pop_size=150, nev=nev, ls_method=adg.LS_ADADELTA, seed=S.SEARCH_SEED)
+    res = adg.dock(ctx, R, L, p)
+    assert len(res) == 4096
+    for r in res:
+        assert (r["evals"] >= nev).all() and (r["generations"] == 1).all()
+    widths = np.array([(l.natoms + 31) // 32 for l in bl])
+    rng = np.random.default_rng(4096)
+    sample = np.concatenate([rng.choice(np.nonzero(widths == w)[0], min(8, int((widths == w).sum())), replace=False)
+                             for w in np.unique(widths)])
+    for i in sample:
+        lig, r = bl[i], res[i]
+        OL = O.Ligand(lig)
+        genes = r["genes"].astype(np.float64)
+        assert np.abs(r["xyz"] - O.pose(OL, genes)).max() < 1e-3, i
+        e_ref = O.score(ff, grid, maps64, OL, genes)[0]
+        forces = O.atom_gradients(ff, grid, maps64, OL, genes)
+        assert (np.abs(r["best_energy"] - e_ref) <= energy_tol(e_ref, forces)).all(), (i, r["best_energy"], e_ref)
+    for lg in L:
+        lg.close()
